@@ -1,0 +1,221 @@
+/*
+ * seed.h -- C ABI of the GB300 (sm_103a) implementation of the improved seed
+ * method of Abdel-Rehim, Morgan and Wilcox for Hermitian (or real symmetric)
+ * positive definite systems with several right-hand sides,
+ *
+ *     A x^j = b^j,  j = 1..nrhs                                  (Sec. 1)
+ *
+ * The method (Sec. 2.2 and Sec. 3): the first system is solved by the Lanczos
+ * form of CG with periodic reorthogonalization against the stored Lanczos
+ * basis V; while that basis grows, every other right-hand side receives the
+ * Galerkin projection over it ("single seeding"); the seeded systems are then
+ * finished with plain CG.
+ *
+ * Conventions for every entry point:
+ *  - All vector and matrix pointers are DEVICE pointers on the device that was
+ *    current when the context was created; the caller owns them.  The library
+ *    never frees, reallocates or retains them past the call, except the
+ *    operator arrays given to seed_create_* which must stay valid until
+ *    seed_destroy.
+ *  - Blocks of vectors are column-major: column j starts at ptr + j*ld
+ *    elements, ld >= n.  Complex data (SEED_C128) is interleaved (re, im)
+ *    doubles, the layout of C99 double complex / numpy complex128.
+ *  - Work is enqueued on the stream given at creation.  Calls that return
+ *    seed_info synchronise that stream once before returning; the others do
+ *    not synchronise.
+ *  - Errors are reported only through the returned status; nothing aborts,
+ *    throws or prints.  seed_last_error() gives a one-line reason.  Inputs are
+ *    validated on the host before any kernel is launched.
+ *  - A context is not thread-safe; different contexts are independent.
+ */
+#ifndef SEED_H_
+#define SEED_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEED_ABI_VERSION 1
+
+typedef struct seed_ctx seed_ctx;
+typedef struct CUstream_st *seed_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  SEED_OK = 0,
+  SEED_EINVAL = 1,   /* bad argument (size, ld, NULL pointer, malformed operator) */
+  SEED_ENOMEM = 2,   /* device allocation failed */
+  SEED_ECUDA = 3,    /* a CUDA runtime call failed (including no usable device) */
+  SEED_ENOTSPD = 4,  /* the LU of the Lanczos tridiagonal met delta_i <= 0 or NaN:
+                        A is not positive definite in floating point (Sec. 3,
+                        "LU factorization ... QR or LQ should be used for
+                        indefinite systems") */
+  SEED_ENOTCONV = 5, /* an iteration cap was reached before the tolerance */
+  SEED_ESTATE = 6,   /* call out of order (e.g. seed_project without a kept basis) */
+  SEED_ETIMEOUT = 7  /* reserved: a device-side wait ran out of its iteration limit */
+} seed_status;
+
+typedef enum {
+  SEED_F64 = 0,      /* real double */
+  SEED_C128 = 1      /* complex double, interleaved */
+} seed_dtype;
+
+/* Real symmetric positive definite matrix in CSR form (device arrays).
+ * row_ptr[n+1] (row_ptr[0] = 0, nondecreasing, row_ptr[n] = nnz),
+ * col_idx[nnz] in [0, n), vals[nnz].  Symmetry is the caller's promise. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const double *vals;
+} seed_csr;
+
+/* Wilson-Dirac operator on a 4-d lattice; the library solves with the normal
+ * operator A = D^H D (Sec. 4: "we multiply the system by the Hermitian
+ * transpose of the matrix", two applications of D per iteration).
+ *   (D psi)(n) = psi(n) - kappa sum_mu [ (1 - gamma_mu) U_mu(n) psi(n+mu)
+ *                                       + (1 + gamma_mu) U_mu(n-mu)^H psi(n-mu) ]
+ * Wilson parameter r = 1, gamma matrices in the DeGrand-Rossi (chiral) basis
+ * (gamma_5 = diag(1,1,-1,-1)); D^H = gamma_5 D gamma_5.  The paper names D but
+ * does not define it; this is the textbook form.
+ * Site index s = x + X*(y + Y*(z + Z*t)); spinor [site][spin 0..3][colour 0..2]
+ * complex (n = 12 * sites); links [mu 0..3][site][row][col] complex, U_mu(s).
+ * bc_t = 1 makes the t direction antiperiodic, 0 periodic (all others periodic).
+ * Each dims[k] >= 2. */
+typedef struct {
+  int32_t dims[4];
+  double kappa;
+  int32_t bc_t;
+  int32_t reserved;
+  const void *links;   /* device, complex double, 4*sites*9 elements */
+} seed_wilson;
+
+/* Parameters (Sec. 3 algorithm "Start": m, the frequency of
+ * reorthogonalization; tolerances for the seed and the remaining systems). */
+typedef struct {
+  int32_t m_max;          /* m: maximum Lanczos steps kept in V (>= 1) */
+  int32_t reorth_freq;    /* reorthogonalize at steps i with i % freq == 0 (i >= 2); 0 = never */
+  int32_t reorth_passes;  /* classical Gram-Schmidt passes per reorthogonalization (1 or 2) */
+  int32_t extra_iters;    /* Lanczos steps taken after the seed tolerance is first met (Sec. 3) */
+  int32_t keep_basis;     /* 1: keep V and T after seed_solve_first for seed_project */
+  int32_t x0_zero;        /* 1: X is overwritten with zeros and r_0 = b (no mvp) */
+  int32_t maxit_rest;     /* CG iteration cap per remaining system */
+  int32_t max_restarts;   /* CG restarts from the true residual if it exceeds 1.5 tol */
+  double tol_seed;        /* stop the seed when beta_i |zeta_i| / delta_i <= tol_seed ||b^1|| */
+  double tol_rest;        /* CG stops when ||r|| <= tol_rest ||b^j|| */
+  double breakdown_rel;   /* lucky breakdown when beta_i <= breakdown_rel * max row sum of |T| */
+} seed_params;
+
+/* Per right-hand side results. */
+typedef struct {
+  int32_t iters;          /* Lanczos steps (system 1) or CG iterations (systems 2..) */
+  int32_t mvps;           /* applications of A, including true-residual checks */
+  int32_t restarts;       /* CG restarts (systems 2..) */
+  int32_t converged;      /* 1 if the tolerance was met */
+  double est_relres;      /* recursive residual estimate / ||b^j|| */
+  double true_relres;     /* ||b^j - A x^j|| / ||b^j|| computed at the end */
+} seed_info;
+
+/* Counters over the life of a context. */
+typedef struct {
+  int64_t kernel_launches;   /* kernels of this library launched (including those inside CUDA graphs) */
+  int64_t graph_launches;
+  int64_t mvps;              /* operator applications */
+  int64_t reorth_events;
+  double ms_seed, ms_project, ms_rest;   /* device time of the last call of each kind */
+} seed_stats;
+
+int32_t seed_abi_version(void);
+
+/* Fill p with defaults: m_max 1000, reorth_freq 0, passes 2, extra 0,
+ * keep_basis 0, x0_zero 1, maxit_rest 100000, max_restarts 3, tol_seed 1e-12,
+ * tol_rest 1e-8, breakdown_rel 1e-14.  Returns SEED_EINVAL if p is NULL. */
+seed_status seed_params_default(seed_params *p);
+
+/* Create a context for a real CSR operator (dtype SEED_F64).  Allocates the
+ * Lanczos basis V (n x (m_max+1) doubles) and work space on the current
+ * device.  *out is NULL on failure. */
+seed_status seed_create_csr(seed_ctx **out, const seed_csr *A, const seed_params *p,
+                            seed_stream stream);
+
+/* Create a context for the Wilson normal operator (dtype SEED_C128).  Builds
+ * the site -> 8 neighbour table on the device. */
+seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_params *p,
+                               seed_stream stream);
+
+/* Sec. 3 "Lanczos Version of Single Seed CG with Periodic Reorthogonalization",
+ * steps 1-9, on the first column of B, seeding columns 2..nrhs (steps 4, 7).
+ *   B: n x nrhs (ldb), X: n x nrhs (ldx).  X in: initial guesses (ignored if
+ *   x0_zero); X out: x^1 solved, x^2..x^nrhs seeded.  B and X must not overlap.
+ *   info: NULL or nrhs entries; entry 0 receives the seed system's results
+ *   (its true residual costs one mvp), the others are zeroed.
+ * Returns SEED_OK (also for a lucky breakdown or when m_max is reached before
+ * the tolerance, then info[0].converged = 0), SEED_ENOTSPD, SEED_EINVAL, ...
+ * With keep_basis = 0 the basis is only valid until the next call. */
+seed_status seed_solve_first(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
+                             int32_t nrhs, seed_info *info);
+
+/* Galerkin projection of further right-hand sides over the kept basis of the
+ * last seed_solve_first (Sec. 2.1: seeding projects "over the Krylov
+ * subspace" of the first system):  x += V T^{-1} V^H (b - A x).
+ * Requires keep_basis = 1 (else SEED_ESTATE).  Costs ncols mvps unless
+ * x0_zero, in which case X is overwritten. */
+seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
+                         int32_t ncols);
+
+/* Plain CG (Sec. 1, Sec. 2.2: "The other right-hand sides, after being
+ * seeded, are solved with CG") on columns 2..nrhs of B from the seeded X, run
+ * in lockstep with per-column scalars.  Column 1 (the seed system) is left
+ * untouched.  Stops each column at ||r|| <= tol_rest ||b^j||, then checks the
+ * true residual and restarts from it if it exceeds 1.5 tol_rest.
+ * info: NULL or nrhs entries; entries 1..nrhs-1 are filled.
+ * Returns SEED_OK, or SEED_ENOTCONV if some column hit maxit_rest. */
+seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
+                            int32_t nrhs, seed_info *info);
+
+/* Y = op(X) for ncols columns: op 0 = A; for Wilson contexts op 1 = D and
+ * op 2 = D^H (used e.g. to form normal-equation right-hand sides b = D^H eta,
+ * Sec. 4).  X and Y must not overlap.  Not synchronising. */
+seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                       int32_t ncols);
+
+/* Build the site -> neighbour table for a lattice on the device:
+ * nbr[8*s + 2*mu] = s + mu-hat, nbr[8*s + 2*mu + 1] = s - mu-hat (periodic
+ * wrap), s = x + X*(y + Y*(z + Z*t)).  nbr: device, 8*sites int32.
+ * Synchronises the stream.  This is the table the Wilson kernels use. */
+seed_status seed_wilson_neighbors(const int32_t dims[4], int32_t *nbr, seed_stream stream);
+
+/* Tridiagonal T of the last seed solve (Sec. 3 steps 2, 5, 9):
+ * alpha[0..m-1] = alpha_1..alpha_m, beta[0..m] = beta_0..beta_m (beta_0 =
+ * ||r_0^1||), host arrays of capacity cap >= m+1; *m receives the number of
+ * Lanczos steps.  With alpha and beta both NULL only *m is returned.
+ * SEED_ESTATE before the first seed_solve_first. */
+seed_status seed_get_tridiag(const seed_ctx *ctx, double *alpha, double *beta, int32_t cap,
+                             int32_t *m);
+
+/* Copy the first ncols Lanczos vectors (column-major, ld = n, host memory). */
+seed_status seed_get_basis(const seed_ctx *ctx, void *V_host, int32_t ncols);
+
+seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out);
+
+/* Measurement helper (not part of the method): launch op(X) (op as in
+ * seed_apply) reps times back to back on the context's internal stream over
+ * ncols library-owned columns (filled with the byte 0x3F, i.e. normal
+ * doubles near 4.8e-4), with CUDA events on that stream
+ * around the launches; *ms_per_apply receives the mean device time of one
+ * application.  Synchronises.  reps in [1, 100000], ncols in [1, 64]. */
+seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t reps, double *ms_per_apply);
+
+/* One-line reason for the last failure on ctx (or of the last failed
+ * seed_create_* / context-free call on this thread when ctx is NULL). */
+const char *seed_last_error(const seed_ctx *ctx);
+
+/* Free V, the work space and the context.  NULL-safe.  Synchronises. */
+void seed_destroy(seed_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEED_H_ */

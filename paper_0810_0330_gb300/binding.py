@@ -1,0 +1,275 @@
+"""Thin Python binding of the C ABI in include/seed.h (ctypes).
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+libseed.so.  PyTorch supplies device memory and the current stream.  If the
+library has not been built, loading fails with an error; there is no other
+implementation to fall back on.
+
+Blocks of vectors are torch tensors viewed as column-major n x ncols: either
+a 1-d tensor of length n, or a 2-d tensor of shape (n, ncols) with stride
+(1, ld), e.g. ``Bt.t()`` for a contiguous (ncols, n) tensor ``Bt``.  CSR
+operators use float64, the Wilson operator complex128.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libseed.so")
+_lib = None
+_lock = threading.Lock()
+
+SEED_OK, SEED_EINVAL, SEED_ENOMEM, SEED_ECUDA, SEED_ENOTSPD, SEED_ENOTCONV, SEED_ESTATE, SEED_ETIMEOUT = range(8)
+STATUS_NAMES = ["SEED_OK", "SEED_EINVAL", "SEED_ENOMEM", "SEED_ECUDA", "SEED_ENOTSPD", "SEED_ENOTCONV",
+                "SEED_ESTATE", "SEED_ETIMEOUT"]
+
+# symbols declared in include/seed.h
+EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_create_wilson",
+           "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
+           "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
+           "seed_destroy"]
+
+
+class SeedError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s (%s)" % (where, name, msg))
+
+
+class seed_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("vals", C.c_void_p)]
+
+
+class seed_wilson(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 4), ("kappa", C.c_double), ("bc_t", C.c_int32), ("reserved", C.c_int32),
+                ("links", C.c_void_p)]
+
+
+class seed_params(C.Structure):
+    _fields_ = [("m_max", C.c_int32), ("reorth_freq", C.c_int32), ("reorth_passes", C.c_int32),
+                ("extra_iters", C.c_int32), ("keep_basis", C.c_int32), ("x0_zero", C.c_int32),
+                ("maxit_rest", C.c_int32), ("max_restarts", C.c_int32), ("tol_seed", C.c_double),
+                ("tol_rest", C.c_double), ("breakdown_rel", C.c_double)]
+
+
+class seed_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("mvps", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+                ("est_relres", C.c_double), ("true_relres", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class seed_stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("graph_launches", C.c_int64), ("mvps", C.c_int64),
+                ("reorth_events", C.c_int64), ("ms_seed", C.c_double), ("ms_project", C.c_double),
+                ("ms_rest", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib():
+    """Load libseed.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libseed.so is not built (run __graft_entry__.build() or "
+                                   "python -m paper_0810_0330_gb300.build)")
+            L = C.CDLL(LIB_PATH)
+            P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+            L.seed_abi_version.restype = I32
+            L.seed_params_default.argtypes = [C.POINTER(seed_params)]
+            L.seed_create_csr.argtypes = [C.POINTER(P), C.POINTER(seed_csr), C.POINTER(seed_params), P]
+            L.seed_create_wilson.argtypes = [C.POINTER(P), C.POINTER(seed_wilson), C.POINTER(seed_params), P]
+            L.seed_solve_first.argtypes = [P, P, I64, P, I64, I32, P]
+            L.seed_solve_rest.argtypes = [P, P, I64, P, I64, I32, P]
+            L.seed_project.argtypes = [P, P, I64, P, I64, I32]
+            L.seed_apply.argtypes = [P, I32, P, I64, P, I64, I32]
+            L.seed_wilson_neighbors.argtypes = [P, P, P]
+            L.seed_get_tridiag.argtypes = [P, P, P, I32, C.POINTER(I32)]
+            L.seed_get_basis.argtypes = [P, P, I32]
+            L.seed_get_stats.argtypes = [P, C.POINTER(seed_stats)]
+            L.seed_time_operator.argtypes = [P, I32, I32, I32, C.POINTER(C.c_double)]
+            L.seed_last_error.argtypes = [P]
+            L.seed_last_error.restype = C.c_char_p
+            L.seed_destroy.argtypes = [P]
+            L.seed_destroy.restype = None
+            for name in EXPORTS:
+                if name not in ("seed_last_error", "seed_destroy", "seed_abi_version"):
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str, ctx=None):
+    if status != SEED_OK:
+        msg = lib().seed_last_error(ctx)
+        raise SeedError(status, where, msg.decode() if msg else "")
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _block(t: torch.Tensor, n: int, name: str):
+    """(pointer, ld, ncols) of a column-major block."""
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dim() == 1:
+        if t.shape[0] != n or t.stride(0) != 1:
+            raise ValueError("%s: expected a contiguous vector of length %d" % (name, n))
+        return t.data_ptr(), n, 1
+    if t.dim() != 2 or t.shape[0] != n or (t.shape[1] > 1 and t.stride(0) != 1) or (t.shape[1] == 1 and t.stride(0) != 1):
+        raise ValueError("%s: expected shape (n, ncols) with stride (1, ld)" % name)
+    ld = t.stride(1) if t.shape[1] > 1 else n
+    return t.data_ptr(), ld, t.shape[1]
+
+
+class Context:
+    """An opaque seed_ctx* plus references that keep the operator arrays alive."""
+
+    def __init__(self, handle: int, n: int, dtype: torch.dtype, keep: tuple):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+        self.dtype = dtype
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            seed_destroy(self)
+        except Exception:
+            pass
+
+
+def seed_params_default(**overrides) -> seed_params:
+    p = seed_params()
+    _check(lib().seed_params_default(C.byref(p)), "seed_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def seed_create_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor, params: seed_params,
+                    stream=None) -> Context:
+    assert row_ptr.dtype == torch.int32 and col_idx.dtype == torch.int32 and vals.dtype == torch.float64
+    rp, ci, va = row_ptr.contiguous(), col_idx.contiguous(), vals.contiguous()
+    a = seed_csr(n=rp.shape[0] - 1, nnz=ci.shape[0], row_ptr=rp.data_ptr(), col_idx=ci.data_ptr(),
+                 vals=va.data_ptr())
+    h = C.c_void_p()
+    _check(lib().seed_create_csr(C.byref(h), C.byref(a), C.byref(params), _stream(stream)), "seed_create_csr")
+    return Context(h.value, a.n, torch.float64, (rp, ci, va))
+
+
+def seed_create_wilson(dims, kappa: float, links: torch.Tensor, params: seed_params, bc_t: int = 0,
+                       stream=None) -> Context:
+    assert links.dtype == torch.complex128
+    lk = links.contiguous()
+    a = seed_wilson(kappa=float(kappa), bc_t=int(bc_t), reserved=0, links=lk.data_ptr())
+    for k in range(4):
+        a.dims[k] = int(dims[k])
+    h = C.c_void_p()
+    _check(lib().seed_create_wilson(C.byref(h), C.byref(a), C.byref(params), _stream(stream)),
+           "seed_create_wilson")
+    vol = int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3])
+    return Context(h.value, 12 * vol, torch.complex128, (lk,))
+
+
+def _infos(nrhs):
+    return (seed_info * nrhs)()
+
+
+def seed_solve_first(ctx: Context, B: torch.Tensor, X: torch.Tensor):
+    pb, ldb, nb = _block(B, ctx.n, "B")
+    px, ldx, nx = _block(X, ctx.n, "X")
+    if nb != nx:
+        raise ValueError("B and X must have the same number of columns")
+    info = _infos(nb)
+    _check(lib().seed_solve_first(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_first", ctx.handle)
+    return [i.as_dict() for i in info]
+
+
+def seed_solve_rest(ctx: Context, B: torch.Tensor, X: torch.Tensor):
+    pb, ldb, nb = _block(B, ctx.n, "B")
+    px, ldx, nx = _block(X, ctx.n, "X")
+    if nb != nx:
+        raise ValueError("B and X must have the same number of columns")
+    info = _infos(nb)
+    _check(lib().seed_solve_rest(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_rest", ctx.handle)
+    return [i.as_dict() for i in info]
+
+
+def seed_project(ctx: Context, B: torch.Tensor, X: torch.Tensor):
+    pb, ldb, nb = _block(B, ctx.n, "B")
+    px, ldx, nx = _block(X, ctx.n, "X")
+    if nb != nx:
+        raise ValueError("B and X must have the same number of columns")
+    _check(lib().seed_project(ctx.handle, pb, ldb, px, ldx, nb), "seed_project", ctx.handle)
+
+
+def seed_apply(ctx: Context, op: int, X: torch.Tensor, Y: torch.Tensor):
+    px, ldx, nx = _block(X, ctx.n, "X")
+    py, ldy, ny = _block(Y, ctx.n, "Y")
+    if nx != ny:
+        raise ValueError("X and Y must have the same number of columns")
+    _check(lib().seed_apply(ctx.handle, int(op), px, ldx, py, ldy, nx), "seed_apply", ctx.handle)
+
+
+def seed_wilson_neighbors(dims, out: torch.Tensor, stream=None):
+    assert out.dtype == torch.int32 and out.is_cuda and out.is_contiguous()
+    d = (C.c_int32 * 4)(*[int(x) for x in dims])
+    _check(lib().seed_wilson_neighbors(d, out.data_ptr(), _stream(stream)), "seed_wilson_neighbors")
+
+
+def seed_get_tridiag(ctx: Context):
+    """(alpha_1..alpha_m, beta_0..beta_m) of the last seed solve, as numpy arrays."""
+    import numpy as np
+    m = C.c_int32()
+    _check(lib().seed_get_tridiag(ctx.handle, None, None, 0, C.byref(m)), "seed_get_tridiag", ctx.handle)
+    a = np.zeros(max(m.value, 1), dtype=np.float64)
+    b = np.zeros(m.value + 1, dtype=np.float64)
+    _check(lib().seed_get_tridiag(ctx.handle, a.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p),
+                                  m.value + 1, C.byref(m)), "seed_get_tridiag", ctx.handle)
+    return a[:m.value], b
+
+
+def seed_get_basis(ctx: Context, ncols: int):
+    import numpy as np
+    dt = np.float64 if ctx.dtype == torch.float64 else np.complex128
+    V = np.zeros((ncols, ctx.n), dtype=dt)
+    _check(lib().seed_get_basis(ctx.handle, V.ctypes.data_as(C.c_void_p), int(ncols)), "seed_get_basis",
+           ctx.handle)
+    return V.T
+
+
+def seed_get_stats(ctx: Context) -> dict:
+    s = seed_stats()
+    _check(lib().seed_get_stats(ctx.handle, C.byref(s)), "seed_get_stats", ctx.handle)
+    return s.as_dict()
+
+
+def seed_time_operator(ctx: Context, op: int, ncols: int, reps: int) -> float:
+    """Mean device time (ms) of one application of op over ncols columns."""
+    ms = C.c_double()
+    _check(lib().seed_time_operator(ctx.handle, int(op), int(ncols), int(reps), C.byref(ms)), "seed_time_operator",
+           ctx.handle)
+    return ms.value
+
+
+def seed_last_error(ctx: Context = None) -> str:
+    r = lib().seed_last_error(ctx.handle if ctx is not None else None)
+    return r.decode() if r else ""
+
+
+def seed_destroy(ctx: Context):
+    if ctx is not None and ctx.handle:
+        lib().seed_destroy(ctx.handle)
+        ctx.handle = C.c_void_p()

@@ -1,0 +1,120 @@
+// device_common.cuh -- scalar helpers and deterministic reductions shared by
+// the sm_103a kernels of this library.
+//
+// Every reduction here has a fixed shape for a fixed launch configuration, so
+// results are bitwise reproducible run to run: warp butterflies, then warps in
+// index order, then (grid level) block partials summed in index order by the
+// last block to finish.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SEED_DEV __device__ __forceinline__
+
+namespace seedk {
+
+// ---------------------------------------------------------------------------
+// scalar types: double (real problems) and double2 (complex, x = re, y = im)
+// ---------------------------------------------------------------------------
+SEED_DEV double2 c2(double re, double im) { return make_double2(re, im); }
+SEED_DEV double2 cadd(double2 a, double2 b) { return c2(a.x + b.x, a.y + b.y); }
+SEED_DEV double2 csub(double2 a, double2 b) { return c2(a.x - b.x, a.y - b.y); }
+SEED_DEV double2 cmul(double2 a, double2 b) { return c2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)); }
+// acc + a * b
+SEED_DEV double2 cfma(double2 a, double2 b, double2 acc) {
+  return c2(fma(-a.y, b.y, fma(a.x, b.x, acc.x)), fma(a.y, b.x, fma(a.x, b.y, acc.y)));
+}
+// acc + conj(a) * b
+SEED_DEV double2 cfmac(double2 a, double2 b, double2 acc) {
+  return c2(fma(a.y, b.y, fma(a.x, b.x, acc.x)), fma(-a.y, b.x, fma(a.x, b.y, acc.y)));
+}
+
+template <class T> struct Sc;
+template <> struct Sc<double> {
+  static SEED_DEV double zero() { return 0.0; }
+  static SEED_DEV double scale(double s, double x) { return s * x; }
+  static SEED_DEV double axpy(double a, double x, double y) { return fma(a, x, y); }          // y + a x
+  static SEED_DEV double caxpy(double2 a, double x, double y) { return fma(a.x, x, y); }      // y + a x (a real)
+  static SEED_DEV double redot(double a, double b, double acc) { return fma(a, b, acc); }   // acc + Re(conj(a) b)
+  static SEED_DEV double2 dotc(double a, double b, double2 acc) { return c2(fma(a, b, acc.x), acc.y); }
+  static SEED_DEV double nrm2(double a, double acc) { return fma(a, a, acc); }
+  static SEED_DEV double sub(double a, double b) { return a - b; }
+  static SEED_DEV double add(double a, double b) { return a + b; }
+};
+template <> struct Sc<double2> {
+  static SEED_DEV double2 zero() { return c2(0.0, 0.0); }
+  static SEED_DEV double2 scale(double s, double2 x) { return c2(s * x.x, s * x.y); }
+  static SEED_DEV double2 axpy(double a, double2 x, double2 y) { return c2(fma(a, x.x, y.x), fma(a, x.y, y.y)); }
+  static SEED_DEV double2 caxpy(double2 a, double2 x, double2 y) { return cfma(a, x, y); }
+  static SEED_DEV double redot(double2 a, double2 b, double acc) { return fma(a.y, b.y, fma(a.x, b.x, acc)); }
+  static SEED_DEV double2 dotc(double2 a, double2 b, double2 acc) { return cfmac(a, b, acc); }
+  static SEED_DEV double nrm2(double2 a, double acc) { return fma(a.y, a.y, fma(a.x, a.x, acc)); }
+  static SEED_DEV double2 sub(double2 a, double2 b) { return csub(a, b); }
+  static SEED_DEV double2 add(double2 a, double2 b) { return cadd(a, b); }
+};
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+SEED_DEV double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Sum of K values over the block; the result is returned to every thread.
+// smem must hold K * (NT/32) doubles.
+template <int K, int NT>
+SEED_DEV void block_sum(double (&v)[K], double *smem) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = warp_sum(v[k]);
+    if (lane == 0) smem[k * NW + warp] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += smem[k * NW + w];
+    v[k] = s;
+  }
+  __syncthreads();
+}
+
+// Signals that this block has written its partials; returns true (in every
+// thread of the block) for the last of `expected` blocks counted on `ticket`.
+// The last block resets the ticket for the next launch.
+SEED_DEV bool last_block_done(unsigned *ticket, unsigned expected) {
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == expected - 1u) ? 1u : 0u;
+    if (s_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0u;
+}
+
+// In the last block: sum partial[b*stride + k] over b = 0..nb-1 in a fixed
+// order; returned to every thread.  smem: NT/32 doubles.
+template <int NT>
+SEED_DEV double sum_partials(const double *partial, int nb, int stride, int k, double *smem) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += NT) s += __ldcg(partial + (int64_t)b * stride + k);
+  double v[1] = {s};
+  block_sum<1, NT>(v, smem);
+  return v[0];
+}
+
+// Flip the sign of x when the top bit of m is set (an integer op, no FP64 slot).
+SEED_DEV double xsign(double x, unsigned long long m) {
+  return __longlong_as_double(__double_as_longlong(x) ^ m);
+}
+
+}  // namespace seedk

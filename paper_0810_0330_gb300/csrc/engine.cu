@@ -1,0 +1,895 @@
+// engine.cu -- host side of the seed solver: the context, argument checks,
+// device memory, the schedule of kernels for each Lanczos / CG step, CUDA
+// graphs over runs of steps, status polling, and the C ABI (include/seed.h).
+//
+// Schedule.  The host knows the step index i of every Lanczos step it issues
+// (i advances by one per step while the device recurrence is active), so it
+// knows where Sec. 3 step 8 (reorthogonalization when i is a multiple of the
+// frequency) falls and issues those kernels only there.  Runs of steps are
+// captured once into a CUDA graph per pattern and replayed; all scalars stay
+// on the device.  After each run the host copies a small status block to
+// pinned memory; it checks the previous run's status while the next run
+// executes, so the GPU does not idle on the host.  A run issued after the
+// device stopped costs only the launches of kernels that return at once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "seed.h"
+#include "seed_internal.h"
+
+using namespace seedk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
+
+struct HostStatus {   // pinned, written by cudaMemcpyAsync from SeedState
+  int32_t i, active, stop_reason, converged_at;
+};
+
+}  // namespace
+
+struct seed_ctx {
+  int device = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t cs = nullptr;           // internal stream (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;
+  int kind = 0;                        // 0 = CSR, 1 = Wilson
+  seed_dtype dtype = SEED_F64;
+  int64_t n = 0;
+  size_t esz = 8;                      // element size
+  seed_params prm{};
+  CsrOp csr{};
+  WilsonOp wil{};
+  int32_t *nbr = nullptr;
+
+  // seed recurrence
+  void *V = nullptr;
+  int64_t ldv = 0;
+  void *vcur = nullptr, *u = nullptr, *f = nullptr, *w = nullptr;
+  SeedState *st = nullptr;
+  double *alpha_hist = nullptr, *beta_hist = nullptr, *delta_hist = nullptr;
+  double2 *eta = nullptr;
+  double *partials = nullptr;
+  unsigned *tickets = nullptr;
+  double2 *Hpart = nullptr, *H = nullptr;
+  int rows_per_item = 0, nrb = 0;
+  CallArgs *call = nullptr;            // device copy of the caller's X / ldx
+  double *colnorm = nullptr;           // scratch norms [kMaxRhs]
+
+  // multi-column work space (grown on demand): R0 / R, P, Q, Wilson temp
+  int cap_cols = 0;
+  void *R = nullptr, *P = nullptr, *Q = nullptr, *T = nullptr;
+
+  // lockstep CG
+  double *cg_d = nullptr;     // 5 * kMaxRhs doubles
+  int32_t *cg_i = nullptr;    // 7 * kMaxRhs ints
+  int32_t *h_flags = nullptr; // pinned [2][kMaxRhs]
+  HostStatus *h_status = nullptr;   // pinned [2]
+
+  std::map<std::string, GraphEntry> graphs;
+  std::string err;
+  seed_stats stats{};
+  int last_m = 0;
+  bool basis_valid = false;
+  bool seeded = false;
+  bool timing_project = false;
+};
+
+namespace {
+
+seed_status fail(seed_ctx *c, seed_status st, const std::string &msg) {
+  if (c) c->err = msg;
+  g_last_error = msg;
+  return st;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(ctx, SEED_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+bool is_device_ptr(const void *p, int device) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice) return a.device == device;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return false;
+}
+
+seed_status check_params(seed_ctx *ctx, const seed_params *p) {
+  if (!p) return fail(ctx, SEED_EINVAL, "params is NULL");
+  if (p->m_max < 1) return fail(ctx, SEED_EINVAL, "m_max must be >= 1");
+  if (p->m_max > 1000000) return fail(ctx, SEED_EINVAL, "m_max too large");
+  if (p->reorth_freq < 0) return fail(ctx, SEED_EINVAL, "reorth_freq must be >= 0");
+  if (p->reorth_passes < 1 || p->reorth_passes > 2) return fail(ctx, SEED_EINVAL, "reorth_passes must be 1 or 2");
+  if (p->extra_iters < 0) return fail(ctx, SEED_EINVAL, "extra_iters must be >= 0");
+  if (p->maxit_rest < 0 || p->max_restarts < 0) return fail(ctx, SEED_EINVAL, "maxit_rest / max_restarts < 0");
+  if (!(p->tol_seed >= 0.0) || !(p->tol_rest >= 0.0) || !(p->breakdown_rel >= 0.0))
+    return fail(ctx, SEED_EINVAL, "tolerances must be >= 0");
+  return SEED_OK;
+}
+
+template <class Tp>
+seed_status dalloc(seed_ctx *ctx, Tp **p, size_t bytes) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SEED_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  *p = reinterpret_cast<Tp *>(q);
+  return SEED_OK;
+}
+
+#define TRY(x)                        \
+  do {                                \
+    seed_status s_ = (x);             \
+    if (s_ != SEED_OK) return s_;     \
+  } while (0)
+
+seed_status alloc_common(seed_ctx *ctx) {
+  const int64_t n = ctx->n;
+  const size_t es = ctx->esz;
+  const int m = ctx->prm.m_max;
+  ctx->ldv = (n + 31) / 32 * 32;   // 256-byte aligned columns for complex, 256 B for real
+  TRY(dalloc(ctx, &ctx->V, (size_t)ctx->ldv * (m + 1) * es));
+  TRY(dalloc(ctx, &ctx->vcur, n * es));
+  TRY(dalloc(ctx, &ctx->u, n * es));
+  TRY(dalloc(ctx, &ctx->f, n * es));
+  TRY(dalloc(ctx, &ctx->w, n * es));
+  TRY(dalloc(ctx, &ctx->st, sizeof(SeedState)));
+  TRY(dalloc(ctx, &ctx->alpha_hist, sizeof(double) * (m + 2)));
+  TRY(dalloc(ctx, &ctx->beta_hist, sizeof(double) * (m + 2)));
+  TRY(dalloc(ctx, &ctx->delta_hist, sizeof(double) * (m + 2)));
+  TRY(dalloc(ctx, &ctx->eta, sizeof(double2) * kMaxRhs));
+  TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs)));
+  TRY(dalloc(ctx, &ctx->colnorm, sizeof(double) * kMaxRhs));
+  const int nb = vec_blocks(n);
+  TRY(dalloc(ctx, &ctx->partials, sizeof(double) * (size_t)nb * (2 * kMaxRhs + 4)));
+  TRY(dalloc(ctx, &ctx->tickets, sizeof(unsigned) * 256));
+  // reorthogonalization tiles: ~32 row blocks of >= 256 rows
+  int64_t rows = (n + 31) / 32;
+  rows = (rows + 255) / 256 * 256;
+  if (rows < 256) rows = 256;
+  ctx->rows_per_item = (int)rows;
+  ctx->nrb = (int)((n + rows - 1) / rows);
+  TRY(dalloc(ctx, &ctx->Hpart, sizeof(double2) * (size_t)ctx->nrb * (m + 1) * 2 + 64));
+  TRY(dalloc(ctx, &ctx->H, sizeof(double2) * (size_t)(m + 1) * 2));
+  TRY(dalloc(ctx, &ctx->cg_d, sizeof(double) * 5 * kMaxRhs));
+  TRY(dalloc(ctx, &ctx->cg_i, sizeof(int32_t) * 7 * kMaxRhs));
+  CU(cudaMemsetAsync(ctx->tickets, 0, sizeof(unsigned) * 256, ctx->cs));
+  CU(cudaMemsetAsync(ctx->w, 0, n * es, ctx->cs));
+  CU(cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * 2 * kMaxRhs));
+  CU(cudaMallocHost(&ctx->h_status, sizeof(HostStatus) * 2));
+  return SEED_OK;
+}
+
+seed_status ensure_cols(seed_ctx *ctx, int cols) {
+  if (cols <= ctx->cap_cols) return SEED_OK;
+  cudaStreamSynchronize(ctx->cs);
+  cudaFree(ctx->R); cudaFree(ctx->P); cudaFree(ctx->Q); cudaFree(ctx->T);
+  ctx->R = ctx->P = ctx->Q = ctx->T = nullptr;
+  ctx->cap_cols = 0;
+  // graphs captured with the old buffers are stale
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+  ctx->graphs.clear();
+  const size_t bytes = (size_t)ctx->ldv * cols * ctx->esz;
+  TRY(dalloc(ctx, &ctx->R, bytes));
+  TRY(dalloc(ctx, &ctx->P, bytes));
+  TRY(dalloc(ctx, &ctx->Q, bytes));
+  TRY(dalloc(ctx, &ctx->T, bytes));
+  ctx->cap_cols = cols;
+  return SEED_OK;
+}
+
+// Y = A X on ncols columns (mask: skip columns whose flag is 0).  Returns the kernel count.
+int apply_A(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, int ncols, const int32_t *mask) {
+  if (ctx->kind == 0) {
+    launch_csr_spmv(ctx->csr, (const double *)X, ldx, (double *)Y, ldy, ncols, mask, ctx->cs);
+    return 1;
+  }
+  launch_wilson_dslash(ctx->wil, +1, (const double2 *)X, ldx, (double2 *)ctx->T, ctx->ldv, ncols, mask, ctx->cs);
+  launch_wilson_dslash(ctx->wil, -1, (const double2 *)ctx->T, ctx->ldv, (double2 *)Y, ldy, ncols, mask, ctx->cs);
+  return 2;
+}
+
+template <class T>
+SeedBufs<T> seed_bufs(seed_ctx *ctx, int nrhs) {
+  SeedBufs<T> b;
+  b.n = ctx->n;
+  b.nrhs = nrhs;
+  b.nblocks = vec_blocks(ctx->n);
+  b.V = (T *)ctx->V;
+  b.ldv = ctx->ldv;
+  b.vcur = (T *)ctx->vcur;
+  b.u = (T *)ctx->u;
+  b.f = (T *)ctx->f;
+  b.w = (T *)ctx->w;
+  b.R0 = (const T *)ctx->R;
+  b.ldr = ctx->ldv;
+  b.call = ctx->call;
+  b.st = ctx->st;
+  b.alpha_hist = ctx->alpha_hist;
+  b.beta_hist = ctx->beta_hist;
+  b.delta_hist = ctx->delta_hist;
+  b.eta = ctx->eta;
+  b.partials = ctx->partials;
+  b.tickets = ctx->tickets;
+  return b;
+}
+
+template <class T>
+ReorthBufs<T> reorth_bufs(seed_ctx *ctx) {
+  ReorthBufs<T> r;
+  r.n = ctx->n;
+  r.rows_per_item = ctx->rows_per_item;
+  r.nrb = ctx->nrb;
+  r.nitems_grid = 152 * 4;
+  r.kcap = ctx->prm.m_max + 1;
+  r.V = (const T *)ctx->V;
+  r.ldv = ctx->ldv;
+  r.Hpart = ctx->Hpart;
+  r.H = ctx->H;
+  return r;
+}
+
+bool reorth_at(const seed_params &p, int i) { return p.reorth_freq > 0 && i >= 2 && i % p.reorth_freq == 0; }
+
+// Issue one Lanczos step (steps 5-9 of Sec. 3; step 2-4 when i == 1).
+template <class T>
+int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
+  SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
+  int k = apply_A(ctx, ctx->vcur, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr);
+  launch_seed_dots<T>(b, ctx->cs);
+  launch_seed_update<T>(b, !reorth, ctx->cs);
+  k += 2;
+  if (reorth) {
+    launch_reorth<T>(b, reorth_bufs<T>(ctx), ctx->prm.reorth_passes, ctx->cs);
+    k += reorth_kernel_count<T>(ctx->prm.reorth_passes);
+  }
+  launch_seed_normalize<T>(b, ctx->cs);
+  return k + 1;
+}
+
+// Capture (once) and launch a graph for the given pattern of steps.
+template <class T>
+seed_status launch_seed_run(seed_ctx *ctx, int nrhs, const std::vector<char> &pattern) {
+  std::string key = "S" + std::to_string(nrhs) + ":" + std::string(pattern.begin(), pattern.end());
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    GraphEntry g;
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(ctx->cs, cudaStreamCaptureModeThreadLocal));
+    for (char c : pattern) g.kernels += issue_seed_step<T>(ctx, nrhs, c == 'R');
+    CU(cudaStreamEndCapture(ctx->cs, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, SEED_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    it = ctx->graphs.emplace(key, g).first;
+  }
+  CU(cudaGraphLaunch(it->second.exec, ctx->cs));
+  ctx->stats.graph_launches++;
+  ctx->stats.kernel_launches += it->second.kernels;
+  return SEED_OK;
+}
+
+int run_length(const seed_params &p) {
+  if (p.reorth_freq <= 0) return 16;
+  if (p.reorth_freq == 1) return 8;
+  int best = 1;
+  for (int d = 1; d <= 32; ++d)
+    if (p.reorth_freq % d == 0) best = d;
+  return best >= 8 ? best : 16;
+}
+
+template <class T>
+seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
+                             seed_info *info) {
+  const int64_t n = ctx->n;
+  const seed_params &p = ctx->prm;
+  TRY(ensure_cols(ctx, std::max(nrhs, 1)));
+  ctx->basis_valid = false;
+  ctx->seeded = false;
+  CU(cudaEventRecord(ctx->t0, ctx->cs));
+
+  CallArgs ca{X, ldx};
+  CU(cudaMemcpyAsync(ctx->call, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  SeedState s0{};
+  s0.tol_rel = p.tol_seed;
+  s0.breakdown_rel = p.breakdown_rel;
+  s0.m_max = p.m_max;
+  s0.extra_iters = p.extra_iters;
+  s0.converged_at = -1;
+  s0.stop_at = -1;
+  CU(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->cs));
+  CU(cudaMemsetAsync(ctx->eta, 0, sizeof(double2) * kMaxRhs, ctx->cs));
+
+  // Step 1: x^j = x_0^j, r_0^j = b^j - A x_0^j (R holds r_0^2.. in columns 0..; r_0^1 in f via seed_start)
+  const T *r01 = (const T *)B;
+  int kern = 0;
+  if (p.x0_zero) {
+    launch_zero_cols<T>((T *)X, ldx, n, nrhs, ctx->cs);
+    if (nrhs > 1) launch_copy_cols<T>((const T *)B + ldb, ldb, (T *)ctx->R, ctx->ldv, n, nrhs - 1, ctx->cs);
+    kern += 1 + (nrhs > 1);
+  } else {
+    kern += apply_A(ctx, X, ldx, ctx->Q, ctx->ldv, nrhs, nullptr);
+    ctx->stats.mvps += nrhs;
+    launch_sub_from<T>((const T *)B, ldb, (const T *)ctx->Q, ctx->ldv, (T *)ctx->P, ctx->ldv, n, nrhs, ctx->cs);
+    if (nrhs > 1) launch_copy_cols<T>((const T *)ctx->P + ctx->ldv, ctx->ldv, (T *)ctx->R, ctx->ldv, n, nrhs - 1, ctx->cs);
+    r01 = (const T *)ctx->P;
+    kern += 1 + (nrhs > 1);
+  }
+  launch_colnorms<T>(n, (const T *)B, ldb, 1, &ctx->st->bnorm1, ctx->partials, ctx->tickets, ctx->cs);
+  SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
+  launch_seed_start<T>(b, r01, ctx->cs);
+  launch_seed_normalize<T>(b, ctx->cs);
+  kern += 3;
+  ctx->stats.kernel_launches += kern;
+
+  // Steps i = 1, 2, ... in runs of L steps aligned so that a run ends at a
+  // multiple of the reorthogonalization frequency whenever L divides it.
+  const int L = run_length(p);
+  int i_next = 1;            // first step of the next run
+  int slot = 0, pending = -1;
+  bool stopped = false;
+  while (!stopped) {
+    if (i_next <= p.m_max) {
+      int len = L - ((i_next - 1) % L);
+      if (i_next + len - 1 > p.m_max) len = p.m_max - i_next + 1;
+      std::vector<char> pattern(len);
+      for (int q = 0; q < len; ++q) pattern[q] = reorth_at(p, i_next + q) ? 'R' : '.';
+      TRY(launch_seed_run<T>(ctx, nrhs, pattern));
+      i_next += len;
+      CU(cudaMemcpyAsync(&ctx->h_status[slot], &ctx->st->i, sizeof(HostStatus), cudaMemcpyDeviceToHost, ctx->cs));
+      cudaEvent_t ev;
+      CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      CU(cudaEventRecord(ev, ctx->cs));
+      if (pending >= 0) {
+        // previous run's status
+        CU(cudaEventSynchronize(ctx->ev_out));
+        cudaEventDestroy(ctx->ev_out);
+        if (!ctx->h_status[pending].active) stopped = true;
+      }
+      ctx->ev_out = ev;
+      pending = slot;
+      slot ^= 1;
+    } else {
+      stopped = true;
+    }
+  }
+  CU(cudaStreamSynchronize(ctx->cs));
+  if (ctx->ev_out) {
+    cudaEventDestroy(ctx->ev_out);
+    ctx->ev_out = nullptr;
+  }
+  CU(cudaGetLastError());
+
+  SeedState st;
+  CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
+  const int steps = st.i >= 1 ? st.i : 0;
+  ctx->stats.mvps += (st.beta0 > 0.0) ? steps : 0;
+  ctx->last_m = (st.beta0 > 0.0) ? steps : 0;
+
+  // true residual of x^1 (one mvp)
+  kern = apply_A(ctx, X, ldx, ctx->Q, ctx->ldv, 1, nullptr);
+  launch_sub_from<T>((const T *)B, ldb, (const T *)ctx->Q, ctx->ldv, (T *)ctx->Q, ctx->ldv, n, 1, ctx->cs);
+  launch_colnorms<T>(n, (const T *)ctx->Q, ctx->ldv, 1, ctx->colnorm, ctx->partials, ctx->tickets, ctx->cs);
+  ctx->stats.kernel_launches += kern + 2;
+  ctx->stats.mvps += 1;
+  CU(cudaEventRecord(ctx->t1, ctx->cs));
+  double rn = 0.0;
+  CU(cudaMemcpyAsync(&rn, ctx->colnorm, sizeof(double), cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  CU(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->t0, ctx->t1);
+  ctx->stats.ms_seed = ms;
+
+  if (info) {
+    std::memset(info, 0, sizeof(seed_info) * nrhs);
+    info[0].iters = ctx->last_m;
+    info[0].mvps = ctx->last_m + 1 + (p.x0_zero ? 0 : 1);
+    info[0].converged = (st.stop_reason == STOP_BREAKDOWN || st.converged_at > 0 || st.beta0 == 0.0) ? 1 : 0;
+    info[0].est_relres = st.bnorm1 > 0.0 ? st.rho / st.bnorm1 : 0.0;
+    info[0].true_relres = st.bnorm1 > 0.0 ? rn / st.bnorm1 : 0.0;
+  }
+  ctx->seeded = true;
+  ctx->basis_valid = ctx->last_m > 0;
+  if (st.stop_reason == STOP_NOTSPD)
+    return fail(ctx, SEED_ENOTSPD, "delta_i <= 0 at Lanczos step " + std::to_string(st.i) +
+                                       ": operator not positive definite in floating point");
+  return SEED_OK;
+}
+
+template <class T>
+int issue_cg_iter(seed_ctx *ctx, const CgCols &c) {
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  int k = apply_A(ctx, ctx->P, ld, ctx->Q, ld, c.nc, c.active);
+  launch_cg_alpha<T>(n, (const T *)ctx->P, (const T *)ctx->Q, ld, c, ctx->partials, ctx->tickets, ctx->cs);
+  launch_cg_update<T>(n, ctx->call, (T *)ctx->R, (const T *)ctx->P, (const T *)ctx->Q, ld, c, ctx->partials,
+                      ctx->tickets, ctx->cs);
+  launch_cg_p<T>(n, (const T *)ctx->R, (T *)ctx->P, ld, c, ctx->cs);
+  return k + 3;
+}
+
+CgCols cg_cols(seed_ctx *ctx, int nc) {
+  CgCols c;
+  c.nc = nc;
+  double *d = ctx->cg_d;
+  int32_t *q = ctx->cg_i;
+  c.rho = d;
+  c.alpha = d + kMaxRhs;
+  c.beta = d + 2 * kMaxRhs;
+  c.bnorm = d + 3 * kMaxRhs;
+  c.relres = d + 4 * kMaxRhs;
+  c.active = q;
+  c.iters = q + kMaxRhs;
+  c.reached = q + 2 * kMaxRhs;
+  c.restarts = q + 3 * kMaxRhs;
+  c.converged = q + 4 * kMaxRhs;
+  c.needs_check = q + 5 * kMaxRhs;
+  c.mvps = q + 6 * kMaxRhs;
+  c.tol = ctx->prm.tol_rest;
+  c.tol_check = 1.5 * ctx->prm.tol_rest;
+  c.maxit = ctx->prm.maxit_rest;
+  c.max_restarts = ctx->prm.max_restarts;
+  return c;
+}
+
+template <class T>
+seed_status launch_cg_run(seed_ctx *ctx, const CgCols &c, int len) {
+  std::string key = "C" + std::to_string(c.nc) + ":" + std::to_string(len);
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    GraphEntry g;
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(ctx->cs, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < len; ++q) g.kernels += issue_cg_iter<T>(ctx, c);
+    CU(cudaStreamEndCapture(ctx->cs, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, SEED_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    it = ctx->graphs.emplace(key, g).first;
+  }
+  CU(cudaGraphLaunch(it->second.exec, ctx->cs));
+  ctx->stats.graph_launches++;
+  ctx->stats.kernel_launches += it->second.kernels;
+  return SEED_OK;
+}
+
+template <class T>
+seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
+                            seed_info *info) {
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  const int nc = nrhs - 1;
+  if (info) std::memset(info + 1, 0, sizeof(seed_info) * nc);
+  if (nc <= 0) return SEED_OK;
+  TRY(ensure_cols(ctx, nrhs));
+  CU(cudaEventRecord(ctx->t2, ctx->cs));
+  CallArgs ca{X, ldx};
+  CU(cudaMemcpyAsync(ctx->call, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  const CgCols c = cg_cols(ctx, nc);
+  const T *Bc = (const T *)B + ldb;
+  // K7: true residual of the seeded systems, then p = r
+  int kern = apply_A(ctx, (const T *)X + ldx, ldx, ctx->Q, ld, nc, nullptr);
+  launch_cg_init<T>(n, Bc, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, (T *)ctx->P, ld, c, ctx->partials, ctx->tickets,
+                    false, ctx->cs);
+  ctx->stats.kernel_launches += kern + 1;
+  ctx->stats.mvps += nc;
+
+  const int L = 16;
+  for (int round = 0;; ++round) {
+    // CG runs until no column is active (polled one run behind)
+    int slot = 0, pending = -1;
+    cudaEvent_t evs[2] = {nullptr, nullptr};
+    for (;;) {
+      TRY(launch_cg_run<T>(ctx, c, L));
+      CU(cudaMemcpyAsync(ctx->h_flags + slot * kMaxRhs, c.active, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost,
+                         ctx->cs));
+      if (!evs[slot]) CU(cudaEventCreateWithFlags(&evs[slot], cudaEventDisableTiming));
+      CU(cudaEventRecord(evs[slot], ctx->cs));
+      bool any = true;
+      if (pending >= 0) {
+        CU(cudaEventSynchronize(evs[pending]));
+        any = false;
+        for (int j = 0; j < nc; ++j) any |= ctx->h_flags[pending * kMaxRhs + j] != 0;
+      }
+      pending = slot;
+      slot ^= 1;
+      if (!any) break;
+    }
+    CU(cudaStreamSynchronize(ctx->cs));
+    for (auto &e : evs)
+      if (e) cudaEventDestroy(e);
+    // true residuals of the columns that stopped; restarts where needed
+    kern = apply_A(ctx, (const T *)X + ldx, ldx, ctx->Q, ld, nc, c.needs_check);
+    launch_cg_check<T>(n, Bc, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, ld, c, ctx->partials, ctx->tickets, ctx->cs);
+    launch_cg_init<T>(n, Bc, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, (T *)ctx->P, ld, c, ctx->partials,
+                      ctx->tickets, true, ctx->cs);
+    ctx->stats.kernel_launches += kern + 2;
+    CU(cudaMemcpyAsync(ctx->h_flags, c.active, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, ctx->cs));
+    CU(cudaStreamSynchronize(ctx->cs));
+    bool any = false;
+    for (int j = 0; j < nc; ++j) any |= ctx->h_flags[j] != 0;
+    if (!any || round > 64) break;
+  }
+  CU(cudaEventRecord(ctx->t3, ctx->cs));
+  CU(cudaGetLastError());
+
+  std::vector<int32_t> hi(7 * kMaxRhs);
+  std::vector<double> hd(5 * kMaxRhs);
+  CU(cudaMemcpyAsync(hi.data(), ctx->cg_i, sizeof(int32_t) * 7 * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaMemcpyAsync(hd.data(), ctx->cg_d, sizeof(double) * 5 * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->t2, ctx->t3);
+  ctx->stats.ms_rest = ms;
+  bool all = true;
+  int64_t mv = 0;
+  for (int j = 0; j < nc; ++j) {
+    const int conv = hi[4 * kMaxRhs + j];
+    all &= conv != 0;
+    mv += hi[6 * kMaxRhs + j];
+    if (info) {
+      seed_info &o = info[j + 1];
+      o.iters = hi[kMaxRhs + j];
+      o.mvps = hi[6 * kMaxRhs + j];
+      o.restarts = hi[3 * kMaxRhs + j];
+      o.converged = conv;
+      o.est_relres = hd[4 * kMaxRhs + j];
+      o.true_relres = hd[4 * kMaxRhs + j];
+    }
+  }
+  ctx->stats.mvps += mv - nc;   // the initial residual was counted above
+  if (!all) return fail(ctx, SEED_ENOTCONV, "CG did not reach tol_rest on every system within maxit_rest");
+  return SEED_OK;
+}
+
+seed_status check_block(seed_ctx *ctx, const void *A, int64_t lda, int cols, const char *name) {
+  if (cols < 1 || cols > kMaxRhs) return fail(ctx, SEED_EINVAL, std::string("number of columns must be 1..64 (") + name + ")");
+  if (lda < ctx->n) return fail(ctx, SEED_EINVAL, std::string("leading dimension < n (") + name + ")");
+  if (!is_device_ptr(A, ctx->device)) return fail(ctx, SEED_EINVAL, std::string(name) + " is not a device pointer on the context's device");
+  return SEED_OK;
+}
+
+bool overlap(const void *a, int64_t lda, const void *b, int64_t ldb, int cols, int64_t n, size_t es) {
+  const char *a0 = (const char *)a, *a1 = a0 + ((cols - 1) * lda + n) * es;
+  const char *b0 = (const char *)b, *b1 = b0 + ((cols - 1) * ldb + n) * es;
+  return a0 < b1 && b0 < a1;
+}
+
+struct StreamScope {   // order the internal stream after the caller's, and back
+  seed_ctx *ctx;
+  explicit StreamScope(seed_ctx *c) : ctx(c) {
+    cudaEventRecord(ctx->ev_in, ctx->user_stream);
+    cudaStreamWaitEvent(ctx->cs, ctx->ev_in, 0);
+  }
+  ~StreamScope() {
+    cudaEventRecord(ctx->ev_in, ctx->cs);
+    cudaStreamWaitEvent(ctx->user_stream, ctx->ev_in, 0);
+  }
+};
+
+seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream stream) {
+  TRY(check_params(ctx, p));
+  ctx->prm = *p;
+  CU(cudaGetDevice(&ctx->device));
+  ctx->user_stream = (cudaStream_t)stream;
+  CU(cudaStreamCreateWithFlags(&ctx->cs, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+  CU(cudaEventCreate(&ctx->t0));
+  CU(cudaEventCreate(&ctx->t1));
+  CU(cudaEventCreate(&ctx->t2));
+  CU(cudaEventCreate(&ctx->t3));
+  return SEED_OK;
+}
+
+void destroy(seed_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->cs) cudaStreamSynchronize(ctx->cs);
+  for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+  void *ptrs[] = {ctx->V, ctx->vcur, ctx->u, ctx->f, ctx->w, ctx->st, ctx->alpha_hist, ctx->beta_hist,
+                  ctx->delta_hist, ctx->eta, ctx->partials, ctx->tickets, ctx->Hpart, ctx->H, ctx->call,
+                  ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3};
+  for (auto e : evs)
+    if (e) cudaEventDestroy(e);
+  if (ctx->cs) cudaStreamDestroy(ctx->cs);
+  delete ctx;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int32_t seed_abi_version(void) { return SEED_ABI_VERSION; }
+
+seed_status seed_params_default(seed_params *p) {
+  if (!p) return fail(nullptr, SEED_EINVAL, "params is NULL");
+  p->m_max = 1000;
+  p->reorth_freq = 0;
+  p->reorth_passes = 2;
+  p->extra_iters = 0;
+  p->keep_basis = 0;
+  p->x0_zero = 1;
+  p->maxit_rest = 100000;
+  p->max_restarts = 3;
+  p->tol_seed = 1e-12;
+  p->tol_rest = 1e-8;
+  p->breakdown_rel = 1e-14;
+  return SEED_OK;
+}
+
+seed_status seed_create_csr(seed_ctx **out, const seed_csr *A, const seed_params *p, seed_stream stream) {
+  if (!out) return fail(nullptr, SEED_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A) return fail(nullptr, SEED_EINVAL, "operator is NULL");
+  if (A->n < 1 || A->n > ((int64_t)1 << 31) - 1) return fail(nullptr, SEED_EINVAL, "n must be in [1, 2^31)");
+  if (A->nnz < 0 || A->nnz > ((int64_t)1 << 31) - 1) return fail(nullptr, SEED_EINVAL, "nnz must be in [0, 2^31)");
+  seed_ctx *ctx = new seed_ctx();
+  seed_status s = create_common(ctx, p, stream);
+  if (s != SEED_OK) { destroy(ctx); return s; }
+  if (!is_device_ptr(A->row_ptr, ctx->device) || !is_device_ptr(A->col_idx, ctx->device) ||
+      !is_device_ptr(A->vals, ctx->device)) {
+    destroy(ctx);
+    return fail(nullptr, SEED_EINVAL, "CSR arrays must be device pointers on the current device");
+  }
+  // structural check on the host before any kernel reads the arrays
+  std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
+  if (cudaMemcpy(rp.data(), A->row_ptr, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      (A->nnz && cudaMemcpy(ci.data(), A->col_idx, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    cudaGetLastError();
+    destroy(ctx);
+    return fail(nullptr, SEED_ECUDA, "could not read the CSR arrays");
+  }
+  if (rp[0] != 0 || rp[A->n] != A->nnz) { destroy(ctx); return fail(nullptr, SEED_EINVAL, "row_ptr[0] != 0 or row_ptr[n] != nnz"); }
+  for (int64_t r = 0; r < A->n; ++r)
+    if (rp[r + 1] < rp[r]) { destroy(ctx); return fail(nullptr, SEED_EINVAL, "row_ptr is not nondecreasing"); }
+  for (int64_t k = 0; k < A->nnz; ++k)
+    if (ci[k] < 0 || ci[k] >= A->n) { destroy(ctx); return fail(nullptr, SEED_EINVAL, "col_idx out of range"); }
+  ctx->kind = 0;
+  ctx->dtype = SEED_F64;
+  ctx->n = A->n;
+  ctx->esz = sizeof(double);
+  ctx->csr = CsrOp{A->n, A->row_ptr, A->col_idx, A->vals};
+  s = alloc_common(ctx);
+  if (s == SEED_OK && cudaStreamSynchronize(ctx->cs) != cudaSuccess) s = fail(ctx, SEED_ECUDA, "set-up failed");
+  if (s != SEED_OK) { g_last_error = ctx->err; destroy(ctx); return s; }
+  *out = ctx;
+  return SEED_OK;
+}
+
+seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_params *p, seed_stream stream) {
+  if (!out) return fail(nullptr, SEED_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!A) return fail(nullptr, SEED_EINVAL, "operator is NULL");
+  int64_t vol = 1;
+  for (int k = 0; k < 4; ++k) {
+    if (A->dims[k] < 2 || A->dims[k] > 4096) return fail(nullptr, SEED_EINVAL, "lattice dims must be in [2, 4096]");
+    vol *= A->dims[k];
+  }
+  if (vol * 12 > ((int64_t)1 << 31) - 1) return fail(nullptr, SEED_EINVAL, "lattice too large (12*sites >= 2^31)");
+  if (A->bc_t != 0 && A->bc_t != 1) return fail(nullptr, SEED_EINVAL, "bc_t must be 0 or 1");
+  if (!std::isfinite(A->kappa)) return fail(nullptr, SEED_EINVAL, "kappa is not finite");
+  seed_ctx *ctx = new seed_ctx();
+  seed_status s = create_common(ctx, p, stream);
+  if (s != SEED_OK) { destroy(ctx); return s; }
+  if (!is_device_ptr(A->links, ctx->device)) {
+    destroy(ctx);
+    return fail(nullptr, SEED_EINVAL, "links must be a device pointer on the current device");
+  }
+  ctx->kind = 1;
+  ctx->dtype = SEED_C128;
+  ctx->n = 12 * vol;
+  ctx->esz = sizeof(double2);
+  s = alloc_common(ctx);
+  if (s == SEED_OK) s = dalloc(ctx, &ctx->nbr, sizeof(int32_t) * 8 * vol);
+  if (s == SEED_OK) {
+    launch_wilson_neighbors(A->dims, ctx->nbr, ctx->cs);
+    ctx->stats.kernel_launches += 1;
+    for (int k = 0; k < 4; ++k) ctx->wil.dims[k] = A->dims[k];
+    ctx->wil.sites = vol;
+    ctx->wil.kappa = A->kappa;
+    ctx->wil.bc_t = A->bc_t;
+    ctx->wil.links = (const double2 *)A->links;
+    ctx->wil.nbr = ctx->nbr;
+    if (cudaStreamSynchronize(ctx->cs) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      s = fail(ctx, SEED_ECUDA, "neighbour table build failed");
+  }
+  if (s != SEED_OK) { g_last_error = ctx->err; destroy(ctx); return s; }
+  *out = ctx;
+  return SEED_OK;
+}
+
+seed_status seed_solve_first(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t nrhs,
+                             seed_info *info) {
+  if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
+  TRY(check_block(ctx, B, ldb, nrhs, "B"));
+  TRY(check_block(ctx, X, ldx, nrhs, "X"));
+  if (overlap(B, ldb, X, ldx, nrhs, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
+  StreamScope scope(ctx);
+  if (ctx->kind == 0) return solve_first_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
+  return solve_first_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
+}
+
+seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t nrhs,
+                            seed_info *info) {
+  if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
+  TRY(check_block(ctx, B, ldb, nrhs, "B"));
+  TRY(check_block(ctx, X, ldx, nrhs, "X"));
+  if (overlap(B, ldb, X, ldx, nrhs, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
+  StreamScope scope(ctx);
+  if (ctx->kind == 0) return solve_rest_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
+  return solve_rest_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
+}
+
+seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t ncols) {
+  if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
+  if (!ctx->prm.keep_basis || !ctx->basis_valid)
+    return fail(ctx, SEED_ESTATE, "seed_project needs keep_basis = 1 and a finished seed_solve_first");
+  TRY(check_block(ctx, B, ldb, ncols, "B"));
+  TRY(check_block(ctx, X, ldx, ncols, "X"));
+  if (overlap(B, ldb, X, ldx, ncols, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
+  TRY(ensure_cols(ctx, ncols));
+  StreamScope scope(ctx);
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  int kern = 0;
+  if (ctx->kind == 0) {
+    if (ctx->prm.x0_zero) {
+      launch_zero_cols<double>((double *)X, ldx, n, ncols, ctx->cs);
+      launch_copy_cols<double>((const double *)B, ldb, (double *)ctx->R, ld, n, ncols, ctx->cs);
+      kern += 2;
+    } else {
+      kern += apply_A(ctx, X, ldx, ctx->Q, ld, ncols, nullptr);
+      launch_sub_from<double>((const double *)B, ldb, (const double *)ctx->Q, ld, (double *)ctx->R, ld, n, ncols, ctx->cs);
+      kern += 1;
+      ctx->stats.mvps += ncols;
+    }
+    launch_project<double>(n, (const double *)ctx->V, ctx->ldv, ctx->last_m, ctx->alpha_hist, ctx->beta_hist,
+                           (const double *)ctx->R, ld, (double *)X, ldx, ncols, ctx->H, ctx->Hpart, ctx->nrb,
+                           ctx->rows_per_item, ctx->cs);
+  } else {
+    if (ctx->prm.x0_zero) {
+      launch_zero_cols<double2>((double2 *)X, ldx, n, ncols, ctx->cs);
+      launch_copy_cols<double2>((const double2 *)B, ldb, (double2 *)ctx->R, ld, n, ncols, ctx->cs);
+      kern += 2;
+    } else {
+      kern += apply_A(ctx, X, ldx, ctx->Q, ld, ncols, nullptr);
+      launch_sub_from<double2>((const double2 *)B, ldb, (const double2 *)ctx->Q, ld, (double2 *)ctx->R, ld, n, ncols,
+                               ctx->cs);
+      kern += 1;
+      ctx->stats.mvps += ncols;
+    }
+    launch_project<double2>(n, (const double2 *)ctx->V, ctx->ldv, ctx->last_m, ctx->alpha_hist, ctx->beta_hist,
+                            (const double2 *)ctx->R, ld, (double2 *)X, ldx, ncols, ctx->H, ctx->Hpart, ctx->nrb,
+                            ctx->rows_per_item, ctx->cs);
+  }
+  ctx->stats.kernel_launches += kern + 4 * ((ncols + 1) / 2);
+  CU(cudaGetLastError());
+  return SEED_OK;
+}
+
+seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, void *Y, int64_t ldy, int32_t ncols) {
+  if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
+  if (op < 0 || op > 2 || (op > 0 && ctx->kind != 1)) return fail(ctx, SEED_EINVAL, "op must be 0 (A), or 1 (D) / 2 (D^H) for Wilson");
+  TRY(check_block(ctx, X, ldx, ncols, "X"));
+  TRY(check_block(ctx, Y, ldy, ncols, "Y"));
+  if (overlap(X, ldx, Y, ldy, ncols, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "X and Y overlap");
+  TRY(ensure_cols(ctx, ncols));
+  StreamScope scope(ctx);
+  if (op == 0) {
+    ctx->stats.kernel_launches += apply_A(ctx, X, ldx, Y, ldy, ncols, nullptr);
+    ctx->stats.mvps += ncols;
+  } else {
+    launch_wilson_dslash(ctx->wil, op == 1 ? +1 : -1, (const double2 *)X, ldx, (double2 *)Y, ldy, ncols, nullptr,
+                         ctx->cs);
+    ctx->stats.kernel_launches += 1;
+  }
+  CU(cudaGetLastError());
+  return SEED_OK;
+}
+
+seed_status seed_wilson_neighbors(const int32_t dims[4], int32_t *nbr, seed_stream stream) {
+  seed_ctx *ctx = nullptr;
+  if (!dims || !nbr) return fail(nullptr, SEED_EINVAL, "NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (dims[k] < 1 || dims[k] > 4096) return fail(nullptr, SEED_EINVAL, "lattice dims must be in [1, 4096]");
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (!is_device_ptr(nbr, dev)) return fail(nullptr, SEED_EINVAL, "nbr must be a device pointer");
+  launch_wilson_neighbors(dims, nbr, (cudaStream_t)stream);
+  CU(cudaStreamSynchronize((cudaStream_t)stream));
+  CU(cudaGetLastError());
+  return SEED_OK;
+}
+
+seed_status seed_get_tridiag(const seed_ctx *cctx, double *alpha, double *beta, int32_t cap, int32_t *m) {
+  seed_ctx *ctx = const_cast<seed_ctx *>(cctx);
+  if (!ctx || !m) return fail(ctx, SEED_EINVAL, "NULL argument");
+  if (!ctx->seeded) return fail(ctx, SEED_ESTATE, "no finished seed_solve_first");
+  *m = ctx->last_m;
+  if (!alpha && !beta) return SEED_OK;   // size query
+  if (cap < ctx->last_m + 1) return fail(ctx, SEED_EINVAL, "cap < m + 1");
+  if (alpha && ctx->last_m > 0)
+    CU(cudaMemcpy(alpha, ctx->alpha_hist + 1, sizeof(double) * ctx->last_m, cudaMemcpyDeviceToHost));
+  if (beta) CU(cudaMemcpy(beta, ctx->beta_hist, sizeof(double) * (ctx->last_m + 1), cudaMemcpyDeviceToHost));
+  return SEED_OK;
+}
+
+seed_status seed_get_basis(const seed_ctx *cctx, void *V_host, int32_t ncols) {
+  seed_ctx *ctx = const_cast<seed_ctx *>(cctx);
+  if (!ctx || !V_host) return fail(ctx, SEED_EINVAL, "NULL argument");
+  if (!ctx->seeded || ncols < 0 || ncols > ctx->last_m) return fail(ctx, SEED_EINVAL, "ncols out of range");
+  CU(cudaMemcpy2D(V_host, ctx->n * ctx->esz, ctx->V, ctx->ldv * ctx->esz, ctx->n * ctx->esz, ncols,
+                  cudaMemcpyDeviceToHost));
+  return SEED_OK;
+}
+
+seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t reps, double *ms_per_apply) {
+  if (!ctx || !ms_per_apply) return fail(ctx, SEED_EINVAL, "NULL argument");
+  if (op < 0 || op > 2 || (op > 0 && ctx->kind != 1)) return fail(ctx, SEED_EINVAL, "bad op");
+  if (ncols < 1 || ncols > kMaxRhs || reps < 1 || reps > 100000) return fail(ctx, SEED_EINVAL, "bad ncols / reps");
+  TRY(ensure_cols(ctx, ncols));
+  StreamScope scope(ctx);
+  CU(cudaMemsetAsync(ctx->P, 0x3F, (size_t)ctx->ldv * ncols * ctx->esz, ctx->cs));   // normal doubles ~4.8e-4
+  // one untimed launch, then the timed ones
+  for (int r = 0; r <= reps; ++r) {
+    if (r == 1) CU(cudaEventRecord(ctx->t0, ctx->cs));
+    if (op == 0) {
+      ctx->stats.kernel_launches += apply_A(ctx, ctx->P, ctx->ldv, ctx->Q, ctx->ldv, ncols, nullptr);
+    } else {
+      launch_wilson_dslash(ctx->wil, op == 1 ? +1 : -1, (const double2 *)ctx->P, ctx->ldv, (double2 *)ctx->Q,
+                           ctx->ldv, ncols, nullptr, ctx->cs);
+      ctx->stats.kernel_launches += 1;
+    }
+  }
+  CU(cudaEventRecord(ctx->t1, ctx->cs));
+  CU(cudaEventSynchronize(ctx->t1));
+  CU(cudaGetLastError());
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, ctx->t0, ctx->t1));
+  *ms_per_apply = (double)ms / reps;
+  return SEED_OK;
+}
+
+seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out) {
+  if (!ctx || !out) return fail(nullptr, SEED_EINVAL, "NULL argument");
+  *out = ctx->stats;
+  return SEED_OK;
+}
+
+const char *seed_last_error(const seed_ctx *ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_last_error.c_str();
+}
+
+void seed_destroy(seed_ctx *ctx) { destroy(ctx); }
+
+}  // extern "C"

@@ -1,0 +1,840 @@
+// krylov.cu -- the Sec. 3 seed recurrence, its periodic reorthogonalization,
+// the Galerkin projection over a kept basis, and lockstep CG for the seeded
+// systems, on sm_103a in FP64.
+//
+// All scalars of the recurrence (alpha_i, beta_i, delta_i, gamma_{i-1},
+// zeta_i, eta^j, the step index i and the stop flags) live in device memory
+// (SeedState); each kernel reads them at its start and the last block of a
+// reducing kernel writes the next values.  The host therefore never waits
+// inside an iteration and whole runs of steps can be replayed from one CUDA
+// graph.  Every kernel first checks `active` and returns at once when the
+// recurrence has stopped, so over-issued steps cost only their launch.
+//
+// Reductions are deterministic: block partials in a fixed layout, summed in
+// block order by the last block (see device_common.cuh).
+#include <math.h>
+
+#include "device_common.cuh"
+#include "seed_internal.h"
+
+namespace seedk {
+
+constexpr int NT = kVecThreads;
+constexpr int kSeedTicket = 0;     // tickets[0..15]: seed / reorth kernels
+constexpr int kColTicket = 16;     // tickets[16 + c]: per-column kernels
+
+#define GRID_STRIDE(e, n) \
+  for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < (n); e += (int64_t)gridDim.x * NT)
+
+int vec_blocks(int64_t n) {
+  int64_t b = (n + NT - 1) / NT;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3 step 9: beta_i = ||f||, residual estimate and the stopping test
+// (thread 0 of the last block).
+// ---------------------------------------------------------------------------
+template <class T>
+SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
+  SeedState *st = b.st;
+  const int i = st->i;
+  const double beta = sqrt(sumsq);
+  b.beta_hist[i] = beta;
+  const double row = fabs(st->alpha) + (i > 1 ? st->beta_prev : 0.0) + beta;
+  if (row > st->tnorm) st->tnorm = row;
+  const double rho = beta * fabs(st->zeta) / st->delta;
+  st->rho = rho;
+  st->beta = beta;
+  if (st->converged_at < 0 && rho <= st->tol_abs) {
+    st->converged_at = i;
+    st->stop_at = i + st->extra_iters;
+  }
+  int stop = STOP_RUNNING;
+  if (beta <= st->breakdown_rel * st->tnorm) stop = STOP_BREAKDOWN;
+  else if (st->stop_at >= 0 && i >= st->stop_at) stop = STOP_CONVERGED;
+  else if (i >= st->m_max) stop = STOP_MMAX;
+  if (stop != STOP_RUNNING) {
+    st->active = 0;
+    st->stop_reason = stop;
+  } else {
+    st->beta_prev = beta;
+    st->inv_beta = 1.0 / beta;
+    st->i = i + 1;
+  }
+}
+
+// Step 2 (start): f = r_0^1, beta_0 = ||r_0^1||; v_1 follows from the normalize kernel.
+template <class T>
+__global__ void __launch_bounds__(NT) k_seed_start(SeedBufs<T> b, const T *__restrict__ r01) {
+  __shared__ double sm[NT / 32];
+  double acc = 0.0;
+  GRID_STRIDE(e, b.n) {
+    const T r = r01[e];
+    b.f[e] = r;
+    acc = Sc<T>::nrm2(r, acc);
+  }
+  double v[1] = {acc};
+  block_sum<1, NT>(v, sm);
+  if (threadIdx.x == 0) b.partials[blockIdx.x] = v[0];
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  const double s = sum_partials<NT>(b.partials, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) {
+    SeedState *st = b.st;
+    const double b0 = sqrt(s);
+    st->beta0 = b0;
+    b.beta_hist[0] = b0;
+    st->i = 1;
+    st->tol_abs = st->tol_rel * st->bnorm1;
+    st->tnorm = 0.0;
+    st->beta_prev = 0.0;
+    st->converged_at = -1;
+    st->stop_at = -1;
+    st->rho = b0;
+    if (b0 > 0.0) {
+      st->active = 1;
+      st->stop_reason = STOP_RUNNING;
+      st->inv_beta = 1.0 / b0;
+    } else {
+      st->active = 0;
+      st->stop_reason = STOP_CONVERGED;
+      st->inv_beta = 0.0;
+    }
+  }
+}
+
+// v_i = f / beta_{i-1} into column i-1 of V and into vcur (the operator input).
+template <class T>
+__global__ void __launch_bounds__(NT) k_seed_normalize(SeedBufs<T> b) {
+  const SeedState *st = b.st;
+  if (!st->active) return;
+  const double inv = st->inv_beta;
+  T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
+  GRID_STRIDE(e, b.n) {
+    const T v = Sc<T>::scale(inv, b.f[e]);
+    vi[e] = v;
+    b.vcur[e] = v;
+  }
+}
+
+// Steps 5 and 7 (the dot products) and the scalar part of steps 3/4/6/7:
+//   grid.y = 0: f = A v_i - beta_{i-1} v_{i-1}, partial alpha_i = Re(v_i^H f)
+//   grid.y = j: partial g^j = v_i^H r_0^j
+// The last block forms alpha_i, gamma_{i-1}, delta_i, zeta_i and eta^j.
+template <class T>
+__global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
+  SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double sm[2 * NT / 32];
+  __shared__ double2 sums[kMaxRhs];
+  const int i = st->i;
+  const int y = blockIdx.y;
+  const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
+  double2 acc = c2(0.0, 0.0);
+  if (y == 0) {
+    if (i > 1) {
+      const double bp = st->beta_prev;
+      const T *vm = b.V + (int64_t)(i - 2) * b.ldv;
+      GRID_STRIDE(e, b.n) {
+        const T fe = Sc<T>::axpy(-bp, vm[e], b.u[e]);
+        b.f[e] = fe;
+        acc.x = Sc<T>::redot(vi[e], fe, acc.x);
+      }
+    } else {
+      GRID_STRIDE(e, b.n) {
+        const T fe = b.u[e];
+        b.f[e] = fe;
+        acc.x = Sc<T>::redot(vi[e], fe, acc.x);
+      }
+    }
+  } else {
+    const T *r = b.R0 + (int64_t)(y - 1) * b.ldr;
+    GRID_STRIDE(e, b.n) acc = Sc<T>::dotc(vi[e], r[e], acc);
+  }
+  double v[2] = {acc.x, acc.y};
+  block_sum<2, NT>(v, sm);
+  if (threadIdx.x == 0) {
+    b.partials[((int64_t)y * gridDim.x + blockIdx.x) * 2] = v[0];
+    b.partials[((int64_t)y * gridDim.x + blockIdx.x) * 2 + 1] = v[1];
+  }
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x * gridDim.y)) return;
+  for (int yy = 0; yy < (int)gridDim.y; ++yy) {
+    const double *p = b.partials + (int64_t)yy * gridDim.x * 2;
+    const double re = sum_partials<NT>(p, gridDim.x, 2, 0, sm);
+    const double im = sum_partials<NT>(p, gridDim.x, 2, 1, sm);
+    if (threadIdx.x == 0) sums[yy] = c2(re, im);
+  }
+  if (threadIdx.x == 0) {
+    const double a = sums[0].x;
+    double gam, del, zet;
+    if (i == 1) {           // step 3: delta_1 = alpha_1, zeta_1 = beta_0
+      gam = 0.0;
+      del = a;
+      zet = st->beta0;
+    } else {                // step 6
+      const double bp = st->beta_prev;
+      gam = bp / st->delta;
+      del = a - gam * bp;
+      zet = -gam * st->zeta;
+    }
+    for (int j = 1; j < b.nrhs; ++j) {   // steps 4 / 7
+      const double2 g = sums[j];
+      const double2 e = b.eta[j];
+      b.eta[j] = (i == 1) ? g : c2(g.x - gam * e.x, g.y - gam * e.y);
+    }
+    st->alpha = a;
+    st->gamma = gam;
+    st->delta = del;
+    st->zeta = zet;
+    b.alpha_hist[i] = a;
+    b.delta_hist[i] = del;
+    if (!(del > 0.0) || !isfinite(del)) {
+      st->active = 0;
+      st->stop_reason = STOP_NOTSPD;
+    }
+  }
+}
+
+// Steps 5 (f -= alpha_i v_i), 6 (w_i, x^1) and 7 (x^j), plus ||f||^2 when this
+// step has no reorthogonalization.
+template <class T, bool NORM>
+__global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
+  SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double2 s_eta[kMaxRhs];
+  __shared__ double sm[NT / 32];
+  for (int j = threadIdx.x; j < b.nrhs; j += NT) s_eta[j] = b.eta[j];
+  __syncthreads();
+  const int i = st->i;
+  const double a = st->alpha, zeta = st->zeta, inv_d = 1.0 / st->delta, bp = st->beta_prev;
+  const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
+  const int64_t ldx = b.call->ldx;
+  T *const X = reinterpret_cast<T *>(b.call->X);
+  double acc = 0.0;
+  GRID_STRIDE(e, b.n) {
+    const T ve = vi[e];
+    const T fe = Sc<T>::axpy(-a, ve, b.f[e]);
+    b.f[e] = fe;
+    const T we = (i > 1) ? Sc<T>::scale(inv_d, Sc<T>::axpy(-bp, b.w[e], ve)) : Sc<T>::scale(inv_d, ve);
+    b.w[e] = we;
+    T *x = X + e;
+    x[0] = Sc<T>::axpy(zeta, we, x[0]);
+    for (int j = 1; j < b.nrhs; ++j) x[j * ldx] = Sc<T>::caxpy(s_eta[j], we, x[j * ldx]);
+    if (NORM) acc = Sc<T>::nrm2(fe, acc);
+  }
+  if (!NORM) return;
+  double v[1] = {acc};
+  block_sum<1, NT>(v, sm);
+  if (threadIdx.x == 0) b.partials[blockIdx.x] = v[0];
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  const double s = sum_partials<NT>(b.partials, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) seed_finish(b, s);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3 step 8: reorthonormalize v_i against v_1..v_{i-1}, then
+// reorthogonalize f against v_1..v_i.  Classical Gram-Schmidt in blocked form:
+// H = V_{<i}^H [v_i f], [v_i f] -= V_{<i} H (repeated `passes` times), then
+// v_i /= ||v_i|| and f -= (v_i^H f) v_i (repeated `passes` times).
+// ---------------------------------------------------------------------------
+
+// lane l ends with the warp sum of v[l]; 31 adds per lane.
+SEED_DEV double warp_reduce_scatter32(double (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const double send = upper ? v[k] : v[k + w];
+      const double keep = upper ? v[k + w] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// One tile of H partials: rows [rb*R, (rb+1)*R) x columns [c0, c0+8) of V
+// against the two vectors F0, F1.  Hpart[(rb*kcap + c)*2 + v].
+template <class T>
+SEED_DEV void gram_tile(const T *__restrict__ V, int64_t ldv, int64_t n, int rows, int rb, int c0, int nc,
+                        const T *__restrict__ F0, const T *__restrict__ F1, double2 *Hpart, int kcap,
+                        double (*sred)[32]) {
+  double2 acc[8][2];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = c2(0.0, 0.0);
+  const int64_t r0 = (int64_t)rb * rows;
+  const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += NT) {
+    const T f0 = F0[row], f1 = F1[row];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c < nc) {
+        const T v = V[row + (int64_t)(c0 + c) * ldv];
+        acc[c][0] = Sc<T>::dotc(v, f0, acc[c][0]);
+        acc[c][1] = Sc<T>::dotc(v, f1, acc[c][1]);
+      }
+    }
+  }
+  double vals[32];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    vals[4 * c + 0] = acc[c][0].x;
+    vals[4 * c + 1] = acc[c][0].y;
+    vals[4 * c + 2] = acc[c][1].x;
+    vals[4 * c + 3] = acc[c][1].y;
+  }
+  const double mine = warp_reduce_scatter32(vals);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  sred[warp][lane] = mine;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const double s = ((sred[0][lane] + sred[1][lane]) + sred[2][lane]) + sred[3][lane];
+    const int c = lane >> 2, vv = (lane >> 1) & 1, ri = lane & 1;
+    if (c < nc) reinterpret_cast<double *>(Hpart)[(((int64_t)rb * kcap + c0 + c) * 2 + vv) * 2 + ri] = s;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_reorth_tiles(SeedBufs<T> b, ReorthBufs<T> r) {
+  const SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double sred[NT / 32][32];
+  const int i = st->i, k = i - 1;
+  const T *F0 = b.V + (int64_t)(i - 1) * b.ldv;
+  const int nck = (k + 7) / 8;
+  const int64_t items = (int64_t)r.nrb * nck;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int rb = (int)(it % r.nrb), cb = (int)(it / r.nrb);
+    const int c0 = cb * 8;
+    const int nc = (k - c0 < 8) ? k - c0 : 8;
+    gram_tile<T>(r.V, r.ldv, r.n, r.rows_per_item, rb, c0, nc, F0, b.f, r.Hpart, r.kcap, sred);
+  }
+}
+
+// H[c][v] = sum over row blocks (in order) of Hpart
+SEED_DEV void gram_reduce(const double2 *Hpart, double2 *H, int k, int nrb, int kcap) {
+  for (int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x; q < 2 * (int64_t)k; q += (int64_t)gridDim.x * NT) {
+    const int64_t c = q >> 1, v = q & 1;
+    double2 s = c2(0.0, 0.0);
+    for (int rb = 0; rb < nrb; ++rb) s = cadd(s, Hpart[((int64_t)rb * kcap + c) * 2 + v]);
+    H[c * 2 + v] = s;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_reorth_reduce(SeedBufs<T> b, ReorthBufs<T> r) {
+  const SeedState *st = b.st;
+  if (!st->active) return;
+  gram_reduce(r.Hpart, r.H, st->i - 1, r.nrb, r.kcap);
+}
+
+// F_v += sgn * V[:, 0:k] H[:, v] for the two vectors (one thread per row).
+template <class T>
+SEED_DEV void gram_update(const T *__restrict__ V, int64_t ldv, int64_t n, int k, const double2 *__restrict__ H,
+                          T *F0, T *F1, double sgn) {
+  __shared__ double2 sH[256][2];
+  const int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const bool valid = row < n;
+  T a0 = Sc<T>::zero(), a1 = Sc<T>::zero();
+  for (int c0 = 0; c0 < k; c0 += 256) {
+    const int cn = (k - c0 < 256) ? k - c0 : 256;
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * cn; q += NT) sH[q >> 1][q & 1] = H[(int64_t)(c0 + (q >> 1)) * 2 + (q & 1)];
+    __syncthreads();
+    if (valid) {
+      const T *vr = V + row + (int64_t)c0 * ldv;
+      for (int c = 0; c < cn; ++c) {
+        const T v = vr[(int64_t)c * ldv];
+        a0 = Sc<T>::caxpy(sH[c][0], v, a0);
+        a1 = Sc<T>::caxpy(sH[c][1], v, a1);
+      }
+    }
+  }
+  if (valid) {
+    F0[row] = Sc<T>::axpy(sgn, a0, F0[row]);
+    if (F1 != nullptr) F1[row] = Sc<T>::axpy(sgn, a1, F1[row]);
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_reorth_sub(SeedBufs<T> b, ReorthBufs<T> r) {
+  const SeedState *st = b.st;
+  if (!st->active) return;
+  const int i = st->i;
+  gram_update<T>(r.V, r.ldv, r.n, i - 1, r.H, b.V + (int64_t)(i - 1) * b.ldv, b.f, -1.0);
+}
+
+// scratch = 1 / ||v_i||
+template <class T>
+__global__ void __launch_bounds__(NT) k_reorth_norm_vi(SeedBufs<T> b) {
+  SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double sm[NT / 32];
+  const T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
+  double acc = 0.0;
+  GRID_STRIDE(e, b.n) acc = Sc<T>::nrm2(vi[e], acc);
+  double v[1] = {acc};
+  block_sum<1, NT>(v, sm);
+  if (threadIdx.x == 0) b.partials[blockIdx.x] = v[0];
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  const double s = sum_partials<NT>(b.partials, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) st->scratch = 1.0 / sqrt(s);
+}
+
+// v_i *= scratch; h = v_i^H f
+template <class T>
+__global__ void __launch_bounds__(NT) k_reorth_scale_dot(SeedBufs<T> b) {
+  SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double sm[2 * NT / 32];
+  T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
+  const double sc = st->scratch;
+  double2 acc = c2(0.0, 0.0);
+  GRID_STRIDE(e, b.n) {
+    const T v = Sc<T>::scale(sc, vi[e]);
+    vi[e] = v;
+    acc = Sc<T>::dotc(v, b.f[e], acc);
+  }
+  double v[2] = {acc.x, acc.y};
+  block_sum<2, NT>(v, sm);
+  if (threadIdx.x == 0) {
+    b.partials[blockIdx.x * 2] = v[0];
+    b.partials[blockIdx.x * 2 + 1] = v[1];
+  }
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  const double re = sum_partials<NT>(b.partials, gridDim.x, 2, 0, sm);
+  const double im = sum_partials<NT>(b.partials, gridDim.x, 2, 1, sm);
+  if (threadIdx.x == 0) st->h = c2(re, im);
+}
+
+// f -= h v_i; then either h = v_i^H f (DOT) or ||f||^2 -> step 9 (seed_finish)
+template <class T, bool DOT>
+__global__ void __launch_bounds__(NT) k_reorth_axpy(SeedBufs<T> b) {
+  SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double sm[2 * NT / 32];
+  const T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
+  const double2 h = st->h;
+  const double2 mh = c2(-h.x, -h.y);
+  double2 acc = c2(0.0, 0.0);
+  GRID_STRIDE(e, b.n) {
+    const T v = vi[e];
+    const T fe = Sc<T>::caxpy(mh, v, b.f[e]);
+    b.f[e] = fe;
+    if (DOT) acc = Sc<T>::dotc(v, fe, acc);
+    else acc.x = Sc<T>::nrm2(fe, acc.x);
+  }
+  double v[2] = {acc.x, acc.y};
+  block_sum<2, NT>(v, sm);
+  if (threadIdx.x == 0) {
+    b.partials[blockIdx.x * 2] = v[0];
+    b.partials[blockIdx.x * 2 + 1] = v[1];
+  }
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  const double re = sum_partials<NT>(b.partials, gridDim.x, 2, 0, sm);
+  const double im = sum_partials<NT>(b.partials, gridDim.x, 2, 1, sm);
+  if (threadIdx.x == 0) {
+    if (DOT) st->h = c2(re, im);
+    else seed_finish(b, re);
+  }
+}
+
+template <class T>
+void launch_seed_start(const SeedBufs<T> &b, const T *r01, cudaStream_t s) {
+  k_seed_start<T><<<b.nblocks, NT, 0, s>>>(b, r01);
+}
+template <class T>
+void launch_seed_normalize(const SeedBufs<T> &b, cudaStream_t s) {
+  k_seed_normalize<T><<<b.nblocks, NT, 0, s>>>(b);
+}
+template <class T>
+void launch_seed_dots(const SeedBufs<T> &b, cudaStream_t s) {
+  dim3 grid((unsigned)b.nblocks, (unsigned)b.nrhs);
+  k_seed_dots<T><<<grid, NT, 0, s>>>(b);
+}
+template <class T>
+void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s) {
+  if (with_norm) k_seed_update<T, true><<<b.nblocks, NT, 0, s>>>(b);
+  else k_seed_update<T, false><<<b.nblocks, NT, 0, s>>>(b);
+}
+template <class T>
+void launch_reorth(const SeedBufs<T> &b, const ReorthBufs<T> &r, int passes, cudaStream_t s) {
+  const int rows_blocks = (int)((r.n + NT - 1) / NT);
+  for (int p = 0; p < passes; ++p) {
+    k_reorth_tiles<T><<<r.nitems_grid, NT, 0, s>>>(b, r);
+    k_reorth_reduce<T><<<64, NT, 0, s>>>(b, r);
+    k_reorth_sub<T><<<rows_blocks, NT, 0, s>>>(b, r);
+  }
+  k_reorth_norm_vi<T><<<b.nblocks, NT, 0, s>>>(b);
+  k_reorth_scale_dot<T><<<b.nblocks, NT, 0, s>>>(b);
+  for (int p = 1; p < passes; ++p) k_reorth_axpy<T, true><<<b.nblocks, NT, 0, s>>>(b);
+  k_reorth_axpy<T, false><<<b.nblocks, NT, 0, s>>>(b);
+}
+template <class T>
+int reorth_kernel_count(int passes) {
+  return 3 * passes + 2 + passes;
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin projection over a kept basis: X += V T^{-1} V^H R
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(NT) k_gram_tiles(const T *V, int64_t ldv, int64_t n, int k, int rows, int nrb,
+                                                   const T *F0, const T *F1, double2 *Hpart, int kcap) {
+  __shared__ double sred[NT / 32][32];
+  const int nck = (k + 7) / 8;
+  const int64_t items = (int64_t)nrb * nck;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int rb = (int)(it % nrb), cb = (int)(it / nrb);
+    const int c0 = cb * 8;
+    const int nc = (k - c0 < 8) ? k - c0 : 8;
+    gram_tile<T>(V, ldv, n, rows, rb, c0, nc, F0, F1, Hpart, kcap, sred);
+  }
+}
+__global__ void k_gram_reduce(const double2 *Hpart, double2 *H, int k, int nrb, int kcap) {
+  gram_reduce(Hpart, H, k, nrb, kcap);
+}
+// Solve T y = g for both columns of G in place (Thomas algorithm; T from the
+// recorded alpha_1..alpha_m, beta_1..beta_{m-1}; index 1-based).  c' is kept
+// in cp[m] per column.
+__global__ void k_tridiag_solve(const double *alpha, const double *beta, int m, double2 *G, double *cp) {
+  const int v = threadIdx.x;
+  if (v >= 2) return;
+  double *c = cp + (int64_t)v * m;
+  double den = alpha[1];
+  c[0] = (m > 1) ? beta[1] / den : 0.0;
+  double2 d = G[v];
+  d = c2(d.x / den, d.y / den);
+  G[v] = d;
+  for (int k = 1; k < m; ++k) {
+    den = alpha[k + 1] - beta[k] * c[k - 1];
+    c[k] = (k + 1 < m) ? beta[k + 1] / den : 0.0;
+    const double2 g = G[(int64_t)k * 2 + v];
+    d = c2((g.x - beta[k] * d.x) / den, (g.y - beta[k] * d.y) / den);
+    G[(int64_t)k * 2 + v] = d;
+  }
+  for (int k = m - 2; k >= 0; --k) {
+    const double2 nx = G[(int64_t)(k + 1) * 2 + v];
+    const double2 cur = G[(int64_t)k * 2 + v];
+    G[(int64_t)k * 2 + v] = c2(cur.x - c[k] * nx.x, cur.y - c[k] * nx.y);
+  }
+}
+template <class T>
+__global__ void __launch_bounds__(NT) k_gram_add(const T *V, int64_t ldv, int64_t n, int k, const double2 *H, T *F0,
+                                                 T *F1) {
+  gram_update<T>(V, ldv, n, k, H, F0, F1, 1.0);
+}
+
+template <class T>
+void launch_project(int64_t n, const T *V, int64_t ldv, int m, const double *alpha, const double *beta, const T *R,
+                    int64_t ldr, T *X, int64_t ldx, int ncols, double2 *G, double2 *Gpart, int nrb,
+                    int rows_per_item, cudaStream_t s) {
+  const int rows_blocks = (int)((n + NT - 1) / NT);
+  for (int j = 0; j < ncols; j += 2) {
+    const bool two = j + 1 < ncols;
+    const T *F0 = R + (int64_t)j * ldr;
+    const T *F1 = two ? R + (int64_t)(j + 1) * ldr : F0;
+    k_gram_tiles<T><<<152 * 4, NT, 0, s>>>(V, ldv, n, m, rows_per_item, nrb, F0, F1, Gpart, m + 1);
+    k_gram_reduce<<<64, NT, 0, s>>>(Gpart, G, m, nrb, m + 1);
+    // the Thomas scratch reuses the (now reduced) partial buffer
+    k_tridiag_solve<<<1, 32, 0, s>>>(alpha, beta, m, G, reinterpret_cast<double *>(Gpart));
+    k_gram_add<T><<<rows_blocks, NT, 0, s>>>(V, ldv, n, m, G, X + (int64_t)j * ldx,
+                                             two ? X + (int64_t)(j + 1) * ldx : nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// column utilities
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(NT) k_copy_cols(const T *src, int64_t lds, T *dst, int64_t ldd, int64_t n) {
+  const int col = blockIdx.y;
+  src += (int64_t)col * lds;
+  dst += (int64_t)col * ldd;
+  GRID_STRIDE(e, n) dst[e] = src[e];
+}
+template <class T>
+__global__ void __launch_bounds__(NT) k_zero_cols(T *dst, int64_t ldd, int64_t n) {
+  dst += (int64_t)blockIdx.y * ldd;
+  GRID_STRIDE(e, n) dst[e] = Sc<T>::zero();
+}
+template <class T>
+__global__ void __launch_bounds__(NT) k_sub_from(const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, int64_t ldr,
+                                                 int64_t n) {
+  const int col = blockIdx.y;
+  B += (int64_t)col * ldb;
+  Q += (int64_t)col * ldq;
+  R += (int64_t)col * ldr;
+  GRID_STRIDE(e, n) R[e] = Sc<T>::sub(B[e], Q[e]);
+}
+template <class T>
+__global__ void __launch_bounds__(NT) k_colnorms(int64_t n, const T *X, int64_t ldx, double *out, double *partials,
+                                                 unsigned *tickets) {
+  __shared__ double sm[NT / 32];
+  const int col = blockIdx.y;
+  X += (int64_t)col * ldx;
+  double acc = 0.0;
+  GRID_STRIDE(e, n) acc = Sc<T>::nrm2(X[e], acc);
+  double v[1] = {acc};
+  block_sum<1, NT>(v, sm);
+  if (threadIdx.x == 0) partials[(int64_t)col * gridDim.x + blockIdx.x] = v[0];
+  if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
+  const double s = sum_partials<NT>(partials + (int64_t)col * gridDim.x, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) out[col] = sqrt(s);
+}
+
+template <class T>
+void launch_copy_cols(const T *src, int64_t lds, T *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)ncols);
+  k_copy_cols<T><<<g, NT, 0, s>>>(src, lds, dst, ldd, n);
+}
+template <class T>
+void launch_zero_cols(T *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)ncols);
+  k_zero_cols<T><<<g, NT, 0, s>>>(dst, ldd, n);
+}
+template <class T>
+void launch_sub_from(const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, int64_t ldr, int64_t n, int ncols,
+                     cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)ncols);
+  k_sub_from<T><<<g, NT, 0, s>>>(B, ldb, Q, ldq, R, ldr, n);
+}
+template <class T>
+void launch_colnorms(int64_t n, const T *X, int64_t ldx, int ncols, double *out, double *partials, unsigned *tickets,
+                     cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)ncols);
+  k_colnorms<T><<<g, NT, 0, s>>>(n, X, ldx, out, partials, tickets);
+}
+
+// ---------------------------------------------------------------------------
+// Lockstep CG (Hestenes-Stiefel) on nc columns; per-column scalars in CgCols.
+// ---------------------------------------------------------------------------
+
+// r = b - q (q = A x), p = r, rho = ||r||^2; a column already within tol is done.
+template <class T>
+__global__ void __launch_bounds__(NT) k_cg_init(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R,
+                                                T *P, int64_t ld, CgCols c, double *partials, unsigned *tickets) {
+  __shared__ double sm[2 * NT / 32];
+  const int col = blockIdx.y;
+  B += (int64_t)col * ldb;
+  Q += (int64_t)col * ldq;
+  R += (int64_t)col * ld;
+  P += (int64_t)col * ld;
+  double rr = 0.0, bb = 0.0;
+  GRID_STRIDE(e, n) {
+    const T bv = B[e];
+    const T r = Sc<T>::sub(bv, Q[e]);
+    R[e] = r;
+    P[e] = r;
+    rr = Sc<T>::nrm2(r, rr);
+    bb = Sc<T>::nrm2(bv, bb);
+  }
+  double v[2] = {rr, bb};
+  block_sum<2, NT>(v, sm);
+  double *part = partials + (int64_t)col * gridDim.x * 2;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x * 2] = v[0];
+    part[blockIdx.x * 2 + 1] = v[1];
+  }
+  if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
+  const double srr = sum_partials<NT>(part, gridDim.x, 2, 0, sm);
+  const double sbb = sum_partials<NT>(part, gridDim.x, 2, 1, sm);
+  if (threadIdx.x == 0) {
+    const double bn = sqrt(sbb), rn = sqrt(srr);
+    c.rho[col] = srr;
+    c.bnorm[col] = bn;
+    c.relres[col] = bn > 0.0 ? rn / bn : 0.0;
+    c.mvps[col] = 1;
+    c.iters[col] = 0;
+    c.restarts[col] = 0;
+    c.needs_check[col] = 0;
+    const int done = rn <= c.tol * bn;
+    c.active[col] = !done;
+    c.reached[col] = done;
+    c.converged[col] = done;
+  }
+}
+
+// alpha = rho / Re(p^H q)
+template <class T>
+__global__ void __launch_bounds__(NT) k_cg_alpha(int64_t n, const T *P, const T *Q, int64_t ld, CgCols c,
+                                                 double *partials, unsigned *tickets) {
+  __shared__ double sm[NT / 32];
+  const int col = blockIdx.y;
+  if (!c.active[col]) return;
+  P += (int64_t)col * ld;
+  Q += (int64_t)col * ld;
+  double acc = 0.0;
+  GRID_STRIDE(e, n) acc = Sc<T>::redot(P[e], Q[e], acc);
+  double v[1] = {acc};
+  block_sum<1, NT>(v, sm);
+  double *part = partials + (int64_t)col * gridDim.x;
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
+  const double pq = sum_partials<NT>(part, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) c.alpha[col] = c.rho[col] / pq;
+}
+
+// x += alpha p; r -= alpha q; test ||r|| <= tol ||b||; beta = rho'/rho
+template <class T>
+__global__ void __launch_bounds__(NT) k_cg_update(int64_t n, const CallArgs *call, T *R, const T *P, const T *Q,
+                                                  int64_t ld, CgCols c, double *partials, unsigned *tickets) {
+  __shared__ double sm[NT / 32];
+  const int col = blockIdx.y;
+  if (!c.active[col]) return;
+  // system col+2 of the call: column col+1 of X
+  T *X = reinterpret_cast<T *>(call->X) + (int64_t)(col + 1) * call->ldx;
+  R += (int64_t)col * ld;
+  P += (int64_t)col * ld;
+  Q += (int64_t)col * ld;
+  const double a = c.alpha[col];
+  double acc = 0.0;
+  GRID_STRIDE(e, n) {
+    X[e] = Sc<T>::axpy(a, P[e], X[e]);
+    const T r = Sc<T>::axpy(-a, Q[e], R[e]);
+    R[e] = r;
+    acc = Sc<T>::nrm2(r, acc);
+  }
+  double v[1] = {acc};
+  block_sum<1, NT>(v, sm);
+  double *part = partials + (int64_t)col * gridDim.x;
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
+  const double rr = sum_partials<NT>(part, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) {
+    const double rn = sqrt(rr), bn = c.bnorm[col];
+    c.iters[col] += 1;
+    c.mvps[col] += 1;
+    c.relres[col] = bn > 0.0 ? rn / bn : 0.0;
+    if (rn <= c.tol * bn) {
+      c.active[col] = 0;
+      c.reached[col] = 1;
+      c.needs_check[col] = 1;
+    } else if (c.iters[col] >= c.maxit) {
+      c.active[col] = 0;
+      c.needs_check[col] = 1;
+    } else {
+      c.beta[col] = rr / c.rho[col];
+      c.rho[col] = rr;
+    }
+  }
+}
+
+// p = r + beta p (also used with beta = 0 after a restart: p = r)
+template <class T>
+__global__ void __launch_bounds__(NT) k_cg_p(int64_t n, const T *R, T *P, int64_t ld, CgCols c, int copy_only) {
+  const int col = blockIdx.y;
+  if (!c.active[col]) return;
+  R += (int64_t)col * ld;
+  P += (int64_t)col * ld;
+  if (copy_only) {
+    GRID_STRIDE(e, n) P[e] = R[e];
+  } else {
+    const double be = c.beta[col];
+    GRID_STRIDE(e, n) P[e] = Sc<T>::axpy(be, P[e], R[e]);
+  }
+}
+
+// true residual r = b - A x for columns that stopped; converged if within
+// 1.5 tol, otherwise restart (p = r in the next kernel) while restarts remain.
+template <class T>
+__global__ void __launch_bounds__(NT) k_cg_check(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R,
+                                                 int64_t ld, CgCols c, double *partials, unsigned *tickets) {
+  __shared__ double sm[NT / 32];
+  const int col = blockIdx.y;
+  if (!c.needs_check[col]) return;
+  B += (int64_t)col * ldb;
+  Q += (int64_t)col * ldq;
+  R += (int64_t)col * ld;
+  double acc = 0.0;
+  GRID_STRIDE(e, n) {
+    const T r = Sc<T>::sub(B[e], Q[e]);
+    R[e] = r;
+    acc = Sc<T>::nrm2(r, acc);
+  }
+  double v[1] = {acc};
+  block_sum<1, NT>(v, sm);
+  double *part = partials + (int64_t)col * gridDim.x;
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
+  const double rr = sum_partials<NT>(part, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) {
+    const double rn = sqrt(rr), bn = c.bnorm[col];
+    c.relres[col] = bn > 0.0 ? rn / bn : 0.0;
+    c.mvps[col] += 1;
+    c.needs_check[col] = 0;
+    if (c.reached[col] && rn <= c.tol_check * bn) {
+      c.converged[col] = 1;
+    } else if (c.reached[col] && c.restarts[col] < c.max_restarts) {
+      c.restarts[col] += 1;
+      c.active[col] = 1;
+      c.reached[col] = 0;
+      c.rho[col] = rr;
+    }
+  }
+}
+
+template <class T>
+void launch_cg_init(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, T *P, int64_t ld,
+                    const CgCols &c, double *partials, unsigned *tickets, bool restart_only, cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  if (restart_only) k_cg_p<T><<<g, NT, 0, s>>>(n, R, P, ld, c, 1);
+  else k_cg_init<T><<<g, NT, 0, s>>>(n, B, ldb, Q, ldq, R, P, ld, c, partials, tickets);
+}
+template <class T>
+void launch_cg_alpha(int64_t n, const T *P, const T *Q, int64_t ld, const CgCols &c, double *partials,
+                     unsigned *tickets, cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  k_cg_alpha<T><<<g, NT, 0, s>>>(n, P, Q, ld, c, partials, tickets);
+}
+template <class T>
+void launch_cg_update(int64_t n, const CallArgs *call, T *R, const T *P, const T *Q, int64_t ld, const CgCols &c,
+                      double *partials, unsigned *tickets, cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  k_cg_update<T><<<g, NT, 0, s>>>(n, call, R, P, Q, ld, c, partials, tickets);
+}
+template <class T>
+void launch_cg_p(int64_t n, const T *R, T *P, int64_t ld, const CgCols &c, cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  k_cg_p<T><<<g, NT, 0, s>>>(n, R, P, ld, c, 0);
+}
+template <class T>
+void launch_cg_check(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, int64_t ld, const CgCols &c,
+                     double *partials, unsigned *tickets, cudaStream_t s) {
+  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  k_cg_check<T><<<g, NT, 0, s>>>(n, B, ldb, Q, ldq, R, ld, c, partials, tickets);
+}
+
+#define SEED_INSTANTIATE(T)                                                                                        \
+  template void launch_seed_start<T>(const SeedBufs<T> &, const T *, cudaStream_t);                              \
+  template void launch_seed_normalize<T>(const SeedBufs<T> &, cudaStream_t);                                     \
+  template void launch_seed_dots<T>(const SeedBufs<T> &, cudaStream_t);                                          \
+  template void launch_seed_update<T>(const SeedBufs<T> &, bool, cudaStream_t);                                  \
+  template void launch_reorth<T>(const SeedBufs<T> &, const ReorthBufs<T> &, int, cudaStream_t);                 \
+  template int reorth_kernel_count<T>(int);                                                                      \
+  template void launch_project<T>(int64_t, const T *, int64_t, int, const double *, const double *, const T *,   \
+                                  int64_t, T *, int64_t, int, double2 *, double2 *, int, int, cudaStream_t);     \
+  template void launch_copy_cols<T>(const T *, int64_t, T *, int64_t, int64_t, int, cudaStream_t);               \
+  template void launch_zero_cols<T>(T *, int64_t, int64_t, int, cudaStream_t);                                   \
+  template void launch_sub_from<T>(const T *, int64_t, const T *, int64_t, T *, int64_t, int64_t, int,           \
+                                   cudaStream_t);                                                                \
+  template void launch_colnorms<T>(int64_t, const T *, int64_t, int, double *, double *, unsigned *,             \
+                                   cudaStream_t);                                                                \
+  template void launch_cg_init<T>(int64_t, const T *, int64_t, const T *, int64_t, T *, T *, int64_t,            \
+                                  const CgCols &, double *, unsigned *, bool, cudaStream_t);                     \
+  template void launch_cg_alpha<T>(int64_t, const T *, const T *, int64_t, const CgCols &, double *, unsigned *, \
+                                   cudaStream_t);                                                                \
+  template void launch_cg_update<T>(int64_t, const CallArgs *, T *, const T *, const T *, int64_t, const CgCols &, \
+                                    double *, unsigned *, cudaStream_t);                                         \
+  template void launch_cg_p<T>(int64_t, const T *, T *, int64_t, const CgCols &, cudaStream_t);                  \
+  template void launch_cg_check<T>(int64_t, const T *, int64_t, const T *, int64_t, T *, int64_t,                \
+                                   const CgCols &, double *, unsigned *, cudaStream_t);
+
+SEED_INSTANTIATE(double)
+SEED_INSTANTIATE(double2)
+
+}  // namespace seedk

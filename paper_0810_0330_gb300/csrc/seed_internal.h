@@ -1,0 +1,156 @@
+// seed_internal.h -- declarations shared by the kernel translation units and
+// the engine (host).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace seedk {
+
+constexpr int kMaxRhs = 64;       // right-hand sides per call
+constexpr int kVecThreads = 128;  // threads per block of the vector kernels
+
+// Stop reasons of the seed recurrence (SeedState::stop_reason)
+enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4 };
+
+// Device-resident scalars of the Sec. 3 recurrence (paper notation).
+struct SeedState {
+  double alpha;       // alpha_i
+  double beta;        // beta_i of the last finished step
+  double beta_prev;   // beta_{i-1}
+  double delta;       // delta_i (delta_{i-1} until step 6 of step i runs)
+  double zeta;        // zeta_i
+  double gamma;       // gamma_{i-1}
+  double rho;         // beta_i |zeta_i| / delta_i
+  double tnorm;       // max row sum of |T|
+  double inv_beta;    // 1 / beta_i, used to form v_{i+1}
+  double beta0;       // ||r_0^1||
+  double bnorm1;      // ||b^1||
+  double tol_rel;     // tol_seed
+  double tol_abs;     // tol_seed * ||b^1||
+  double breakdown_rel;
+  double scratch;     // reorthogonalization: 1 / ||v_i||
+  double2 h;          // reorthogonalization: v_i^H f
+  int32_t i;          // current step (1-based)
+  int32_t active;     // 1 while the recurrence runs
+  int32_t stop_reason;
+  int32_t converged_at;
+  int32_t stop_at;
+  int32_t m_max;
+  int32_t extra_iters;
+  int32_t pad_;
+};
+
+// Caller buffers of the current call, read by the kernels from device memory so
+// that captured CUDA graphs stay valid across calls with other buffers.
+struct CallArgs {
+  void *X;             // x^1..x^nrhs, column-major
+  int64_t ldx;
+};
+
+// Buffers of one seed solve; T = double (real) or double2 (complex).
+template <class T>
+struct SeedBufs {
+  int64_t n;
+  int32_t nrhs;        // columns of X (1 = seed system only)
+  int32_t nblocks;     // blocks of the vector kernels (fixed for n)
+  T *V;                // n x (m_max+1), column c holds v_{c+1}
+  int64_t ldv;
+  T *vcur;             // copy of v_i, the operator's input
+  T *u;                // A v_i
+  T *f;                // the Lanczos residual vector
+  T *w;                // w_i
+  const T *R0;         // r_0^j for j = 2..nrhs, column j-2
+  int64_t ldr;
+  const CallArgs *call;  // X (x^j in column j-1) and ldx
+  SeedState *st;
+  double *alpha_hist;  // [m_max+1], alpha_i at index i
+  double *beta_hist;   // [m_max+1], beta_i at index i (beta_0 at 0)
+  double *delta_hist;  // [m_max+1]
+  double2 *eta;        // [kMaxRhs]
+  double *partials;    // >= nblocks * (2*nrhs + 2) doubles
+  unsigned *tickets;   // >= 4 counters, zero between launches
+};
+
+// Buffers of the blocked reorthogonalization (Sec. 3 step 8).
+template <class T>
+struct ReorthBufs {
+  int64_t n;
+  int32_t rows_per_item;   // rows of one partial product tile
+  int32_t nrb;             // row blocks = ceil(n / rows_per_item)
+  int32_t nitems_grid;     // persistent grid size of the tile kernel
+  int32_t kcap;            // column capacity of Hpart / H (m_max + 1)
+  const T *V;
+  int64_t ldv;
+  double2 *Hpart;          // [nrb][m_max+1][2]
+  double2 *H;              // [m_max+1][2]
+};
+
+// Per-column CG state (lockstep CG over nc columns).
+struct CgCols {
+  int32_t nc;
+  double *rho, *alpha, *beta, *bnorm, *relres;
+  int32_t *active, *iters, *reached, *restarts, *converged, *needs_check, *mvps;
+  double tol, tol_check;
+  int32_t maxit, max_restarts;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+
+// Wilson-Dirac (wilson.cu).  sign = +1 applies D, -1 applies D^H.
+struct WilsonOp {
+  int32_t dims[4];
+  int64_t sites;
+  double kappa;
+  int32_t bc_t;
+  const double2 *links;   // [4][sites][3][3]
+  const int32_t *nbr;     // [sites][8]
+};
+void launch_wilson_neighbors(const int32_t dims[4], int32_t *nbr, cudaStream_t s);
+void launch_wilson_dslash(const WilsonOp &op, int sign, const double2 *in, int64_t ldi, double2 *out,
+                          int64_t ldo, int ncols, const int32_t *col_active, cudaStream_t s);
+int wilson_kernels_per_apply();
+
+// CSR (csr.cu)
+struct CsrOp {
+  int64_t n;
+  const int32_t *row_ptr, *col_idx;
+  const double *vals;
+};
+void launch_csr_spmv(const CsrOp &op, const double *in, int64_t ldi, double *out, int64_t ldo, int ncols,
+                     const int32_t *col_active, cudaStream_t s);
+
+// Seed recurrence, reorthogonalization, CG (krylov.cu)
+int vec_blocks(int64_t n);
+template <class T> void launch_seed_start(const SeedBufs<T> &b, const T *r01, cudaStream_t s);
+template <class T> void launch_seed_normalize(const SeedBufs<T> &b, cudaStream_t s);
+template <class T> void launch_seed_dots(const SeedBufs<T> &b, cudaStream_t s);
+template <class T> void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s);
+template <class T> void launch_reorth(const SeedBufs<T> &b, const ReorthBufs<T> &r, int passes, cudaStream_t s);
+template <class T> int reorth_kernel_count(int passes);
+
+template <class T> void launch_sub_from(const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, int64_t ldr,
+                                        int64_t n, int ncols, cudaStream_t s);   // R = B - Q
+template <class T> void launch_cg_init(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, T *P,
+                                       int64_t ld, const CgCols &c, double *partials, unsigned *tickets,
+                                       bool restart_only, cudaStream_t s);
+template <class T> void launch_cg_alpha(int64_t n, const T *P, const T *Q, int64_t ld, const CgCols &c,
+                                        double *partials, unsigned *tickets, cudaStream_t s);
+template <class T> void launch_cg_update(int64_t n, const CallArgs *call, T *R, const T *P, const T *Q, int64_t ld,
+                                         const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s);
+template <class T> void launch_cg_p(int64_t n, const T *R, T *P, int64_t ld, const CgCols &c, cudaStream_t s);
+template <class T> void launch_cg_check(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R,
+                                        int64_t ld, const CgCols &c, double *partials, unsigned *tickets,
+                                        cudaStream_t s);
+template <class T> void launch_colnorms(int64_t n, const T *X, int64_t ldx, int ncols, double *out,
+                                        double *partials, unsigned *tickets, cudaStream_t s);
+template <class T> void launch_project(int64_t n, const T *V, int64_t ldv, int m, const double *alpha,
+                                       const double *beta, const T *R, int64_t ldr, T *X, int64_t ldx,
+                                       int ncols, double2 *G, double2 *Gpart, int nrb, int rows_per_item,
+                                       cudaStream_t s);
+template <class T> void launch_copy_cols(const T *src, int64_t lds, T *dst, int64_t ldd, int64_t n, int ncols,
+                                         cudaStream_t s);
+template <class T> void launch_zero_cols(T *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
+
+}  // namespace seedk

@@ -18,3 +18,12 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def seedlib():
+    """The CUDA library, built in-tree if needed (nvcc cross-compiles without a GPU)."""
+    from paper_0810_0330_gb300 import build as B
+    B.build()
+    from paper_0810_0330_gb300 import binding
+    return binding

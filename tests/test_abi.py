@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every entry point include/seed.h
+declares; argument errors come back as status codes (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "seed.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(seed_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("seed_create_csr", "seed_create_wilson", "seed_solve_first", "seed_project", "seed_solve_rest",
+              "seed_destroy", "seed_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(seedlib):
+    L = C.CDLL(seedlib.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+    assert sorted(seedlib.EXPORTS) == _declared()
+
+
+def test_abi_version_and_defaults(seedlib):
+    L = seedlib.lib()
+    assert L.seed_abi_version() == 1
+    p = seedlib.seed_params_default()
+    assert p.m_max == 1000 and p.reorth_passes == 2 and p.x0_zero == 1
+    assert p.tol_seed == 1e-12 and p.tol_rest == 1e-8
+
+
+def test_argument_errors_are_status_codes(seedlib):
+    L = seedlib.lib()
+    P = seedlib
+    assert L.seed_params_default(None) == P.SEED_EINVAL
+    h = C.c_void_p()
+    prm = P.seed_params_default()
+    # NULL operator / out pointer
+    assert L.seed_create_csr(None, None, C.byref(prm), None) == P.SEED_EINVAL
+    assert L.seed_create_csr(C.byref(h), None, C.byref(prm), None) == P.SEED_EINVAL
+    assert h.value is None
+    # bad sizes are rejected before any device call
+    a = P.seed_csr(n=0, nnz=0)
+    assert L.seed_create_csr(C.byref(h), C.byref(a), C.byref(prm), None) == P.SEED_EINVAL
+    w = P.seed_wilson(kappa=0.1, bc_t=0)
+    for k in range(4):
+        w.dims[k] = 1
+    assert L.seed_create_wilson(C.byref(h), C.byref(w), C.byref(prm), None) == P.SEED_EINVAL
+    w.dims[0] = w.dims[1] = w.dims[2] = w.dims[3] = 4
+    w.bc_t = 3
+    assert L.seed_create_wilson(C.byref(h), C.byref(w), C.byref(prm), None) == P.SEED_EINVAL
+    assert b"bc_t" in L.seed_last_error(None)
+    # bad parameters
+    bad = P.seed_params_default(reorth_passes=3)
+    w.bc_t = 0
+    assert L.seed_create_wilson(C.byref(h), C.byref(w), C.byref(bad), None) == P.SEED_EINVAL
+    # NULL context
+    assert L.seed_solve_first(None, None, 0, None, 0, 1, None) == P.SEED_EINVAL
+    assert L.seed_solve_rest(None, None, 0, None, 0, 1, None) == P.SEED_EINVAL
+    assert L.seed_project(None, None, 0, None, 0, 1) == P.SEED_EINVAL
+    L.seed_destroy(None)
