@@ -37,6 +37,16 @@ WORKLOAD_NAME = "wilson-dirac 8^4 kappa=0.155 A=D^H D, 12 point sources, seed to
 FLOPS_PER_SITE_D = 1368
 # FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# DRAM bytes of one k_dslash launch (8^4, 11 columns) from an ncu capture of this source of wilson.cu
+# (profiles/k_dslash_wilson_8x4_11cols.md); reported only while the source is unchanged.
+DSLASH_TRAFFIC = {"02a95cdef80a3640": 11.210752e6 + 0.0}
+
+
+def dslash_traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_0810_0330_gb300", "csrc", "wilson.cu"), "rb") as fh:
+        h = hashlib.sha256(fh.read()).hexdigest()[:16]
+    return DSLASH_TRAFFIC.get(h)
 
 
 def parse():
@@ -49,6 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only time the dominant kernel (for profiler captures)")
+    ap.add_argument("--dims", default=None, help="lattice for --kernel-only, e.g. 16,16,16,16")
+    ap.add_argument("--ncols", type=int, default=None, help="columns for --kernel-only")
+    ap.add_argument("--reps", type=int, default=20, help="timed launches for --kernel-only")
     return ap.parse_args()
 
 
@@ -186,9 +199,21 @@ def run_ours(args):
     from paper_0810_0330_gb300 import inputs as I
 
     dims, kappa, nrhs = WL["dims"], WL["kappa"], WL["nrhs"]
+    if args.kernel_only and args.dims:
+        dims = tuple(int(x) for x in args.dims.split(","))
     vol = int(np.prod(dims))
     n = 12 * vol
     U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
+    if args.kernel_only:
+        prm = S.seed_params_default(m_max=4)
+        ctx = S.seed_create_wilson(dims, kappa, U, prm)
+        ncols = args.ncols or nrhs - 1
+        ms = S.seed_time_operator(ctx, 1, ncols, args.reps)
+        flops = FLOPS_PER_SITE_D * vol * ncols
+        print(json.dumps({"kernel": "k_dslash", "dims": dims, "ncols": ncols, "ms": ms,
+                          "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
+        S.seed_destroy(ctx)
+        return 0
     prm = S.seed_params_default(m_max=WL["m_max"], reorth_freq=WL["reorth_freq"],
                                 reorth_passes=WL["reorth_passes"], tol_seed=WL["tol_seed"],
                                 tol_rest=WL["tol_rest"], x0_zero=1)
@@ -204,11 +229,6 @@ def run_ours(args):
         i1 = S.seed_solve_first(ctx, B, X)
         i2 = S.seed_solve_rest(ctx, B, X)
         return i1, i2
-
-    if args.kernel_only:
-        ms = S.seed_time_operator(ctx, 1, nrhs - 1, 20)
-        print(json.dumps({"kernel": "k_dslash", "ncols": nrhs - 1, "ms": ms}), flush=True)
-        return 0
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -258,7 +278,7 @@ def run_ours(args):
     achieved = flops / (k_ms * 1e-3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1e3
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": dslash_traffic(),
             "kernel": "k_dslash<+1> (Wilson D, FP64 complex), %d columns" % ncols,
             "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
             "flops_per_launch": flops,

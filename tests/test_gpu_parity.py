@@ -112,20 +112,42 @@ def run_gpu(seedlib, ctx, B, rest=True, ld=None):
     return info1, info2, Xs, host_cols(Xd)
 
 
-def compare_full(orc_res, info1, info2, Xs, X, label):
+def self_sensitivity(orc, op, B, ref, cols=(1,), tol_rest=1e-8, **seed_kw):
+    """How far the oracle's own seeded x^j and final CG solutions move when B
+    is perturbed elementwise by random one-ulp noise.  Between
+    reorthogonalizations the Lanczos basis loses orthogonality and the seeding
+    projection amplifies rounding (Sec. 3): on the 8^4 Wilson workload with a
+    reorthogonalization every 100 steps the oracle's seeded vectors move by
+    about 4e-2 and its final solutions by about 7e-9, against 1e-13 and 5e-10
+    every 10 steps.  Two correct implementations that round differently can
+    differ by that much, so the parity bound for systems 2.. is
+    max(1e-9, 10 x this sensitivity)."""
+    rng = np.random.default_rng(12345)
+    Bp = B * (1 + 2.2e-16 * rng.standard_normal(B.shape))
+    sp = orc.seed_first(op, Bp, **seed_kw)
+    seeded = np.linalg.norm(sp["X"][:, 1:] - ref["X_seeded"][:, 1:]) / np.linalg.norm(ref["X_seeded"][:, 1:])
+    final = 0.0
+    for j in cols:
+        x = orc.cg(op, Bp[:, j], sp["X"][:, j], tol=tol_rest)["x"]
+        final = max(final, relerr(x, ref["rest"][j - 1]["x"]))
+    return seeded, final
+
+
+def compare_full(orc_res, info1, info2, Xs, X, label, seeded_tol=REL_X, final_tol=REL_X):
     s = orc_res["seed"]
     assert info1[0]["iters"] == s["iters"], (label, info1[0]["iters"], s["iters"])
     assert relerr(X[:, 0], s["X"][:, 0]) < REL_X
-    assert relerr(Xs, orc_res["X_seeded"]) < REL_X, (label, relerr(Xs, orc_res["X_seeded"]))
+    assert relerr(Xs[:, 1:], orc_res["X_seeded"][:, 1:]) < seeded_tol, \
+        (label, relerr(Xs[:, 1:], orc_res["X_seeded"][:, 1:]), seeded_tol)
     for j, r in enumerate(orc_res["rest"], start=1):
         g = info2[j]
         assert g["converged"] == 1
         assert abs(g["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (label, j, g["iters"], r["iters"])
         if g["iters"] == r["iters"]:
-            assert relerr(X[:, j], r["x"]) < REL_X, (label, j, relerr(X[:, j], r["x"]))
+            assert relerr(X[:, j], r["x"]) < final_tol, (label, j, relerr(X[:, j], r["x"]), final_tol)
         else:
             # one iteration apart: both meet the tolerance; solutions agree to the CG accuracy
-            assert relerr(X[:, j], r["x"]) < 1e-6, (label, j)
+            assert relerr(X[:, j], r["x"]) < max(1e-6, final_tol), (label, j)
         assert g["true_relres"] <= 1.5e-8
 
 
@@ -160,9 +182,13 @@ def test_seed_wilson_small(seedlib, orc, freq, passes):
     ctx = wilson_ctx(seedlib, dims, kappa, U, bc_t=1, m_max=600, reorth_freq=freq, reorth_passes=passes,
                      tol_seed=1e-12, tol_rest=1e-8)
     info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
-    ref = orc.seed_solve_all(orc.Operator.wilson(dims, kappa, U, bc_t=1), B, m_max=600, reorth_freq=freq,
-                             reorth_passes=passes, tol_seed=1e-12, tol_rest=1e-8)
-    compare_full(ref, info1, info2, Xs, X, "wilson-small-%d" % freq)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    ref = orc.seed_solve_all(op, B, m_max=600, reorth_freq=freq, reorth_passes=passes, tol_seed=1e-12,
+                             tol_rest=1e-8)
+    s_seed, s_final = self_sensitivity(orc, op, B, ref, cols=(1, 3), m_max=600, reorth_freq=freq,
+                                       reorth_passes=passes, tol=1e-12)
+    compare_full(ref, info1, info2, Xs, X, "wilson-small-%d" % freq, seeded_tol=max(REL_X, 10 * s_seed),
+                 final_tol=max(REL_X, 10 * s_final))
 
 
 @pytest.mark.slow
@@ -178,9 +204,16 @@ def test_seed_wilson_8_4_full_workload(seedlib, orc):
     prm = dict(m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
     ctx = wilson_ctx(seedlib, dims, kappa, U, **prm)
     info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
-    ref = orc.seed_solve_all(orc.Operator.wilson(dims, kappa, U), B, m_max=3000, reorth_freq=100,
-                             reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
-    compare_full(ref, info1, info2, Xs, X, "wilson-8^4")
+    op = orc.Operator.wilson(dims, kappa, U)
+    ref = orc.seed_solve_all(op, B, m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
+    s_seed, s_final = self_sensitivity(orc, op, B, ref, cols=(1, 6), m_max=3000, reorth_freq=100,
+                                       reorth_passes=2, tol=1e-12)
+    compare_full(ref, info1, info2, Xs, X, "wilson-8^4", seeded_tol=max(REL_X, 10 * s_seed),
+                 final_tol=max(REL_X, 10 * s_final))
+    # the seed system and the tridiagonal are not affected by the projection's sensitivity
+    a, b = seedlib.seed_get_tridiag(ctx)
+    assert np.abs(a - ref["seed"]["alpha"]).max() < 1e-9 * np.abs(ref["seed"]["alpha"]).max()
+    assert np.abs(b - ref["seed"]["beta"]).max() < 1e-9 * np.abs(ref["seed"]["beta"]).max()
 
 
 # --------------------------------------------------------------------------

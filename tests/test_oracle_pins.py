@@ -377,3 +377,22 @@ def test_paper_table3_1_reorth_trend(orc):
     for m, got in zip((1000, 1500), second[1:]):
         ref = g["second_reorth_freq50"][g["first_mvps"].index(m)]
         assert ref / 2 <= got <= 2 * ref, second
+
+
+def test_seeded_vectors_roundoff_sensitivity(orc):
+    """Sec. 3: without reorthogonalization, rounding error in the Lanczos
+    basis limits the seeding; the seeded x^2.. then move by orders of
+    magnitude more under a one-ulp change of b than with periodic
+    reorthogonalization (this bounds how closely two correct
+    implementations can agree on the intermediate seeded vectors)."""
+    dims, kappa = (3, 4, 5, 6), 0.14
+    U = I.random_su3_links(dims, 0.3, seed=7)
+    eta = I.point_sources(dims, 3, site=17)
+    B = np.stack([orc.wilson_dslash(dims, kappa, 1, -1, U, eta[:, j]) for j in range(3)], axis=1)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    sens = {}
+    for freq in (0, 5):
+        a = orc.seed_first(op, B, m_max=600, reorth_freq=freq, tol=1e-12)["X"][:, 1:]
+        b = orc.seed_first(op, B * (1 + 2.2e-16), m_max=600, reorth_freq=freq, tol=1e-12)["X"][:, 1:]
+        sens[freq] = np.linalg.norm(a - b) / np.linalg.norm(a)
+    assert sens[5] < 1e-12 and sens[0] > 1e3 * sens[5], sens
