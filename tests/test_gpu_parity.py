@@ -1,10 +1,14 @@
 """GPU path (C ABI, sm_103a kernels) against the FP64 oracle, same seeded inputs.
 
-Tolerances (FP64, derived in the design notes): operator applies 1e-13
-relative per element; seed solves to 1e-12 agree in x^1 to 1e-9 relative and
-in alpha_i / beta_i to 1e-9; solutions of the remaining systems agree to 1e-9
-relative when the iteration counts match and the seeded-system iteration
-counts agree within 5 percent; index tables are bit-exact.
+Tolerances (FP64): operator applies 1e-13 relative per element; index tables
+bit-exact; the seed system's x^1 to 1e-9 relative and the same number of
+Lanczos steps; seeded-system CG iteration counts within 5 percent; true
+residuals within 1.5 x 1e-8.  The seeded vectors x^2.., the final solutions of
+systems 2.. and the late Lanczos coefficients are compared against
+max(1e-9, 10 x the oracle's own change under random one-ulp noise on B),
+measured in the test: loss of orthogonality between reorthogonalizations and
+exactly degenerate eigenvalues make those quantities depend on rounding in any
+implementation (the oracle included), see self_sensitivity below.
 """
 import numpy as np
 import pytest
@@ -130,7 +134,30 @@ def self_sensitivity(orc, op, B, ref, cols=(1,), tol_rest=1e-8, **seed_kw):
     for j in cols:
         x = orc.cg(op, Bp[:, j], sp["X"][:, j], tol=tol_rest)["x"]
         final = max(final, relerr(x, ref["rest"][j - 1]["x"]))
+    self_sensitivity.tridiag = tridiag_dev(sp["alpha"], sp["beta"], ref["seed"]["alpha"], ref["seed"]["beta"])
     return seeded, final
+
+
+def seeded_only_sensitivity(orc, op, B, X0=None, **seed_kw):
+    """The oracle's own one-ulp sensitivity of the seeded x^2.. alone.  Besides
+    loss of orthogonality, exactly degenerate eigenvalues (the square
+    Laplacian's lambda_kl = lambda_lk) make it large even with full
+    reorthogonalization: Lanczos finds the second direction of a degenerate
+    eigenspace from rounding, so which direction it finds -- and the
+    projection of the other right-hand sides onto it -- depends on rounding."""
+    rng = np.random.default_rng(12345)
+    Bp = B * (1 + 2.2e-16 * rng.standard_normal(B.shape))
+    a = orc.seed_first(op, B, X0=X0, **seed_kw)["X"][:, 1:]
+    b = orc.seed_first(op, Bp, X0=X0, **seed_kw)["X"][:, 1:]
+    return np.linalg.norm(a - b) / np.linalg.norm(a)
+
+
+def tridiag_dev(a, b, a_ref, b_ref):
+    """max relative deviation of alpha_1..alpha_m and beta_0..beta_m (common length)"""
+    m = min(len(a), len(a_ref))
+    da = np.abs(a[:m] - a_ref[:m]).max() / np.abs(a_ref).max()
+    db = np.abs(b[:m + 1] - b_ref[:m + 1]).max() / np.abs(b_ref).max()
+    return max(da, db)
 
 
 def compare_full(orc_res, info1, info2, Xs, X, label, seeded_tol=REL_X, final_tol=REL_X):
@@ -159,9 +186,11 @@ def test_seed_config_laplacian_64(seedlib, orc):
     prm = dict(m_max=4096, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8, keep_basis=1)
     ctx = csr_ctx(seedlib, rp, ci, v, **prm)
     info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
-    ref = orc.seed_solve_all(orc.Operator.csr(rp, ci, v), B, m_max=4096, reorth_freq=1, tol_seed=1e-12,
-                             tol_rest=1e-8)
-    compare_full(ref, info1, info2, Xs.real, X.real, "lap64")
+    op = orc.Operator.csr(rp, ci, v)
+    ref = orc.seed_solve_all(op, B, m_max=4096, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8)
+    s_seed, s_final = self_sensitivity(orc, op, B, ref, cols=(1, 2), m_max=4096, reorth_freq=1, tol=1e-12)
+    compare_full(ref, info1, info2, Xs.real, X.real, "lap64", seeded_tol=max(REL_X, 10 * s_seed),
+                 final_tol=max(REL_X, 10 * s_final))
     a, b = seedlib.seed_get_tridiag(ctx)
     assert np.abs(a - ref["seed"]["alpha"]).max() < 1e-9 * np.abs(ref["seed"]["alpha"]).max()
     assert np.abs(b - ref["seed"]["beta"]).max() < 1e-9 * np.abs(ref["seed"]["beta"]).max()
@@ -210,10 +239,13 @@ def test_seed_wilson_8_4_full_workload(seedlib, orc):
                                        reorth_passes=2, tol=1e-12)
     compare_full(ref, info1, info2, Xs, X, "wilson-8^4", seeded_tol=max(REL_X, 10 * s_seed),
                  final_tol=max(REL_X, 10 * s_final))
-    # the seed system and the tridiagonal are not affected by the projection's sensitivity
+    # the Lanczos coefficients of the late steps inherit the same sensitivity (the
+    # oracle's own alpha/beta move by about 7 percent at the last steps under
+    # one-ulp noise); the early ones agree to rounding
     a, b = seedlib.seed_get_tridiag(ctx)
-    assert np.abs(a - ref["seed"]["alpha"]).max() < 1e-9 * np.abs(ref["seed"]["alpha"]).max()
-    assert np.abs(b - ref["seed"]["beta"]).max() < 1e-9 * np.abs(ref["seed"]["beta"]).max()
+    assert len(a) == len(ref["seed"]["alpha"])
+    assert tridiag_dev(a, b, ref["seed"]["alpha"], ref["seed"]["beta"]) <= max(1e-9, 10 * self_sensitivity.tridiag)
+    assert tridiag_dev(a[:100], b[:101], ref["seed"]["alpha"][:100], ref["seed"]["beta"][:101]) < 1e-9
 
 
 # --------------------------------------------------------------------------
@@ -254,9 +286,13 @@ def test_zero_rhs_and_initial_guess(seedlib, orc):
     Bd, Xd = dev_cols(B), dev_cols(X0)
     info = seedlib.seed_solve_first(ctx2, Bd, Xd)
     torch.cuda.synchronize()
-    r = orc.seed_first(orc.Operator.csr(rp, ci, v), B, X0=X0, m_max=n, reorth_freq=2, tol=1e-12)
+    op = orc.Operator.csr(rp, ci, v)
+    r = orc.seed_first(op, B, X0=X0, m_max=n, reorth_freq=2, tol=1e-12)
     assert info[0]["iters"] == r["iters"]
-    assert relerr(host_cols(Xd).real, r["X"].real) < REL_X
+    Xg = host_cols(Xd).real
+    assert relerr(Xg[:, 0], r["X"][:, 0].real) < REL_X
+    sens = seeded_only_sensitivity(orc, op, B, X0=X0, m_max=n, reorth_freq=2, tol=1e-12)
+    assert relerr(Xg[:, 1:], r["X"][:, 1:].real) < max(REL_X, 10 * sens)
 
 
 def test_mmax_reached_and_not_spd(seedlib, orc):
@@ -266,8 +302,11 @@ def test_mmax_reached_and_not_spd(seedlib, orc):
     ctx = csr_ctx(seedlib, rp, ci, v, m_max=20, reorth_freq=0, tol_seed=1e-12)
     info1, _, _, X = run_gpu(seedlib, ctx, B, rest=False)
     assert info1[0]["iters"] == 20 and info1[0]["converged"] == 0
-    ref = orc.seed_first(orc.Operator.csr(rp, ci, v), B, m_max=20, reorth_freq=0, tol=1e-12)
-    assert relerr(X.real, ref["X"].real) < REL_X
+    op = orc.Operator.csr(rp, ci, v)
+    ref = orc.seed_first(op, B, m_max=20, reorth_freq=0, tol=1e-12)
+    assert relerr(X[:, 0].real, ref["X"][:, 0].real) < REL_X
+    sens = seeded_only_sensitivity(orc, op, B, m_max=20, reorth_freq=0, tol=1e-12)
+    assert relerr(X[:, 1:].real, ref["X"][:, 1:].real) < max(REL_X, 10 * sens)
     # an indefinite matrix makes delta_i <= 0: status, not a fault
     dn = d.copy()
     dn[:150] *= -1.0
@@ -288,9 +327,11 @@ def test_deterministic(seedlib):
 
 def test_project_matches_dense_formula(seedlib, orc):
     """seed_project: x = V T^{-1} V^H b over the kept basis equals the same
-    formula evaluated with the oracle's basis and tridiagonal."""
-    rp, ci, v = I.laplacian_2d_csr(20, 20)
-    n = 400
+    formula evaluated with the oracle's basis and tridiagonal.  A 20x19 grid
+    has distinct eigenvalues (smallest gap 1.5e-4), so the basis itself is
+    reproducible to rounding and the strict bound applies."""
+    rp, ci, v = I.laplacian_2d_csr(20, 19)
+    n = 380
     B = I.gaussian_rhs(n, 2, seed=6)
     Bn = I.gaussian_rhs(n, 3, seed=7)
     ctx = csr_ctx(seedlib, rp, ci, v, m_max=n, reorth_freq=1, tol_seed=1e-10, keep_basis=1)
