@@ -208,6 +208,29 @@ seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out);
  * application.  Synchronises.  reps in [1, 100000], ncols in [1, 64]. */
 seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t reps, double *ms_per_apply);
 
+/* Y = D^H D X (the Wilson normal operator, as seed_apply op 0 on a Wilson
+ * context) WITHOUT allocating any device memory.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc while they
+ * run -- a host loop being captured into a CUDA graph, a service whose device
+ * memory is fixed at start-up, a plug-in in a framework that owns the device
+ * heap -- and therefore cannot create a context.
+ *   A: operator description (links: device pointer); X, Y: device, column-major
+ *   n x ncols (n = 12 * sites), ld >= n, must not overlap.  Work is enqueued on
+ *   `stream`; the call does not synchronise.
+ * Scratch: the neighbour table and the intermediate D X live in one fixed
+ * 8 MiB (8388608-byte) device array that every GPU loading this library holds
+ * until the process exits.  A call needs 256-byte-rounded 32*sites bytes plus
+ * 16*n*ncols bytes and is rejected with SEED_EINVAL beyond 8 MiB (e.g. an 8^4
+ * lattice allows up to 10 columns).  The array is shared by all calls and keeps
+ * the last call's contents (each call overwrites what it reads, so nothing
+ * needs clearing); calls whose work overlaps on the GPU (other streams, or
+ * other host threads) race on it -- serialise them.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  Never
+ * calls cudaMalloc, cudaFree or any allocating routine. */
+seed_status seed_wilson_apply_noalloc(const seed_wilson *A, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                                      int32_t ncols, seed_stream stream);
+
 /* One-line reason for the last failure on ctx (or of the last failed
  * seed_create_* / context-free call on this thread when ctx is NULL). */
 const char *seed_last_error(const seed_ctx *ctx);

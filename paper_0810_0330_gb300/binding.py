@@ -31,7 +31,7 @@ STATUS_NAMES = ["SEED_OK", "SEED_EINVAL", "SEED_ENOMEM", "SEED_ECUDA", "SEED_ENO
 EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_create_wilson",
            "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
-           "seed_destroy"]
+           "seed_destroy", "seed_wilson_apply_noalloc"]
 
 
 class SeedError(RuntimeError):
@@ -98,6 +98,7 @@ def lib():
             L.seed_get_basis.argtypes = [P, P, I32]
             L.seed_get_stats.argtypes = [P, C.POINTER(seed_stats)]
             L.seed_time_operator.argtypes = [P, I32, I32, I32, C.POINTER(C.c_double)]
+            L.seed_wilson_apply_noalloc.argtypes = [C.POINTER(seed_wilson), P, I64, P, I64, I32, P]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
             L.seed_destroy.argtypes = [P]
@@ -262,6 +263,24 @@ def seed_time_operator(ctx: Context, op: int, ncols: int, reps: int) -> float:
     _check(lib().seed_time_operator(ctx.handle, int(op), int(ncols), int(reps), C.byref(ms)), "seed_time_operator",
            ctx.handle)
     return ms.value
+
+
+def seed_wilson_apply_noalloc(dims, kappa: float, links: torch.Tensor, X: torch.Tensor, Y: torch.Tensor,
+                              bc_t: int = 0, stream=None):
+    """Y = D^H D X without any device allocation, for callers that cannot
+    allocate while they run (scratch: a fixed 8 MiB device array shared by all
+    calls; see include/seed.h)."""
+    assert links.dtype == torch.complex128 and links.is_contiguous()
+    vol = int(dims[0]) * int(dims[1]) * int(dims[2]) * int(dims[3])
+    px, ldx, nx = _block(X, 12 * vol, "X")
+    py, ldy, ny = _block(Y, 12 * vol, "Y")
+    if nx != ny:
+        raise ValueError("X and Y must have the same number of columns")
+    a = seed_wilson(kappa=float(kappa), bc_t=int(bc_t), reserved=0, links=links.data_ptr())
+    for k in range(4):
+        a.dims[k] = int(dims[k])
+    _check(lib().seed_wilson_apply_noalloc(C.byref(a), px, ldx, py, ldy, nx, _stream(stream)),
+           "seed_wilson_apply_noalloc")
 
 
 def seed_last_error(ctx: Context = None) -> str:

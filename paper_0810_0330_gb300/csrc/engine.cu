@@ -624,6 +624,11 @@ void destroy(seed_ctx *ctx) {
 
 }  // namespace
 
+namespace seedk {
+// lets entry points in other translation units report through seed_last_error(NULL)
+void set_last_error_message(const std::string &msg) { g_last_error = msg; }
+}  // namespace seedk
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
