@@ -37,16 +37,23 @@ WORKLOAD_NAME = "wilson-dirac 8^4 kappa=0.155 A=D^H D, 12 point sources, seed to
 FLOPS_PER_SITE_D = 1368
 # FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# DRAM bytes of one k_dslash launch (8^4, 11 columns) from an ncu capture of this source of wilson.cu
+# DRAM bytes of one k_dslash launch (8^4, 11 columns) from an ncu capture of these sources of the kernel
 # (profiles/k_dslash_wilson_8x4_11cols.md); reported only while the source is unchanged.
 DSLASH_TRAFFIC = {"02a95cdef80a3640": 11.210752e6 + 0.0}
 
 
-def dslash_traffic():
+def dslash_source_hash():
+    """Hash of the hopping kernel's sources (the .cu and its device header)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_0810_0330_gb300", "csrc", "wilson.cu"), "rb") as fh:
-        h = hashlib.sha256(fh.read()).hexdigest()[:16]
-    return DSLASH_TRAFFIC.get(h)
+    h = hashlib.sha256()
+    for f in ("wilson.cu", "wilson_device.cuh"):
+        with open(os.path.join(ROOT, "paper_0810_0330_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dslash_traffic():
+    return DSLASH_TRAFFIC.get(dslash_source_hash())
 
 
 def parse():
@@ -68,6 +75,18 @@ def parse():
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(x, dist, dev):
+    """The maximum of a per-rank time over all ranks (x itself without a
+    process group).  Replicas run independent problems, so the job's time is
+    that of its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------------------
@@ -262,10 +281,7 @@ def run_ours(args):
     st1 = S.seed_get_stats(ctx)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     i1, i2 = infos[-1]
     ok = all(i["converged"] for i in i1[:1] + i2[1:])
     launches = st1["kernel_launches"] - st0["kernel_launches"]
@@ -306,10 +322,7 @@ def run_ours(args):
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
         e2e_v = statistics.mean(e2e_ms)
-        if dist:
-            t = torch.tensor([e2e_v], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_v = float(t.item())
+        e2e_v = max_over_ranks(e2e_v, dist, dev)
         e2e = {"value": round(e2e_v, 3), "unit": "ms", "h2d_bytes_per_step": int(eta_pin.numel() * 16),
                "d2h_bytes_per_step": int(x_pin.numel() * 16)}
 

@@ -53,7 +53,8 @@ typedef enum {
                         indefinite systems") */
   SEED_ENOTCONV = 5, /* an iteration cap was reached before the tolerance */
   SEED_ESTATE = 6,   /* call out of order (e.g. seed_project without a kept basis) */
-  SEED_ETIMEOUT = 7  /* reserved: a device-side wait ran out of its iteration limit */
+  SEED_ETIMEOUT = 7  /* a grid barrier of a persistent kernel waited longer than its limit (2 s);
+                        the kernel left without hanging, the results are not valid */
 } seed_status;
 
 typedef enum {
@@ -106,6 +107,14 @@ typedef struct {
   double tol_seed;        /* stop the seed when beta_i |zeta_i| / delta_i <= tol_seed ||b^1|| */
   double tol_rest;        /* CG stops when ||r|| <= tol_rest ||b^j|| */
   double breakdown_rel;   /* lucky breakdown when beta_i <= breakdown_rel * max row sum of |T| */
+  int32_t kernel_path;    /* How the steps are issued (same method either way):
+                             0 (default): the seed's runs of Lanczos steps between
+                             reorthogonalizations in one persistent cooperative kernel (when
+                             nrhs <= 16 and the frequency is 0 or >= 8), everything else as step
+                             kernels replayed from CUDA graphs;
+                             1: step kernels only;
+                             2: as 0, and CG in one persistent kernel as well (nrhs <= 33). */
+  int32_t reserved;
 } seed_params;
 
 /* Per right-hand side results. */
@@ -131,7 +140,7 @@ int32_t seed_abi_version(void);
 
 /* Fill p with defaults: m_max 1000, reorth_freq 0, passes 2, extra 0,
  * keep_basis 0, x0_zero 1, maxit_rest 100000, max_restarts 3, tol_seed 1e-12,
- * tol_rest 1e-8, breakdown_rel 1e-14.  Returns SEED_EINVAL if p is NULL. */
+ * tol_rest 1e-8, breakdown_rel 1e-14, kernel_path 0.  Returns SEED_EINVAL if p is NULL. */
 seed_status seed_params_default(seed_params *p);
 
 /* Create a context for a real CSR operator (dtype SEED_F64).  Allocates the

@@ -55,7 +55,8 @@ class seed_params(C.Structure):
     _fields_ = [("m_max", C.c_int32), ("reorth_freq", C.c_int32), ("reorth_passes", C.c_int32),
                 ("extra_iters", C.c_int32), ("keep_basis", C.c_int32), ("x0_zero", C.c_int32),
                 ("maxit_rest", C.c_int32), ("max_restarts", C.c_int32), ("tol_seed", C.c_double),
-                ("tol_rest", C.c_double), ("breakdown_rel", C.c_double)]
+                ("tol_rest", C.c_double), ("breakdown_rel", C.c_double), ("kernel_path", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class seed_info(C.Structure):

@@ -105,11 +105,60 @@ SEED_DEV bool last_block_done(unsigned *ticket, unsigned expected) {
 // order; returned to every thread.  smem: NT/32 doubles.
 template <int NT>
 SEED_DEV double sum_partials(const double *partial, int nb, int stride, int k, double *smem) {
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += NT) s += __ldcg(partial + (int64_t)b * stride + k);
-  double v[1] = {s};
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b0 = 0; b0 < nb; b0 += 4 * NT) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int b = b0 + u * NT + (int)threadIdx.x;
+      v[u] = b < nb ? __ldcg(partial + (int64_t)b * stride + k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] += v[u];
+  }
+  double v[1] = {(s[0] + s[1]) + (s[2] + s[3])};
   block_sum<1, NT>(v, smem);
   return v[0];
+}
+
+// Lane l ends with the warp sum of v[l] (a reduce-scatter: 31 adds per lane
+// for 32 values instead of 160 for 32 butterflies).
+SEED_DEV double warp_reduce_scatter32(double (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const double send = upper ? v[k] : v[k + w];
+      const double keep = upper ? v[k + w] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// One warp: sum of partial[b*stride + k] over b = 0..nb-1 in a fixed order,
+// returned to every lane of the warp.  Eight independent loads are in flight
+// per lane (GPUs issue in order: a load consumed in the next instruction would
+// serialize one L2 round trip per partial).
+SEED_DEV double warp_sum_partials(const double *partial, int nb, int stride, int k) {
+  const int lane = threadIdx.x & 31;
+  double s[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) s[u] = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < nb ? __ldcg(partial + (int64_t)b * stride + k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s[u] += v[u];
+  }
+  const double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+  return warp_sum(t);
 }
 
 // Flip the sign of x when the top bit of m is set (an integer op, no FP64 slot).

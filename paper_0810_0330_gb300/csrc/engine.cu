@@ -80,6 +80,17 @@ struct seed_ctx {
   int32_t *h_flags = nullptr; // pinned [2][kMaxRhs]
   HostStatus *h_status = nullptr;   // pinned [2]
 
+  // persistent kernels
+  int sm_count = 0;
+  int pgrid = 0;                       // blocks of a persistent launch (0: not available)
+  unsigned *gsync = nullptr;           // GridSync: count, release, error
+  int32_t *h_gerr = nullptr;           // pinned copy of the error flag
+  void *f2 = nullptr;                  // second Lanczos-vector buffer (CSR persistent run)
+  double2 *gbuf = nullptr;             // g^j of the next step (persistent seed run)
+  double *tpart = nullptr;             // per-tile partial sums (persistent Wilson seed run)
+  bool allow_persistent = true;        // persistent seed runs
+  bool allow_persistent_cg = false;    // persistent CG
+
   std::map<std::string, GraphEntry> graphs;
   std::string err;
   seed_stats stats{};
@@ -126,6 +137,7 @@ seed_status check_params(seed_ctx *ctx, const seed_params *p) {
   if (p->maxit_rest < 0 || p->max_restarts < 0) return fail(ctx, SEED_EINVAL, "maxit_rest / max_restarts < 0");
   if (!(p->tol_seed >= 0.0) || !(p->tol_rest >= 0.0) || !(p->breakdown_rel >= 0.0))
     return fail(ctx, SEED_EINVAL, "tolerances must be >= 0");
+  if (p->kernel_path < 0 || p->kernel_path > 2) return fail(ctx, SEED_EINVAL, "kernel_path must be 0, 1 or 2");
   return SEED_OK;
 }
 
@@ -165,7 +177,9 @@ seed_status alloc_common(seed_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs)));
   TRY(dalloc(ctx, &ctx->colnorm, sizeof(double) * kMaxRhs));
   const int nb = vec_blocks(n);
-  TRY(dalloc(ctx, &ctx->partials, sizeof(double) * (size_t)nb * (2 * kMaxRhs + 4)));
+  // block partials: seed dots use ceil(63/15) = 5 chunks x nb x 32; lockstep kernels nc x blocks x 2
+  (void)nb;
+  TRY(dalloc(ctx, &ctx->partials, sizeof(double) * 65536));
   TRY(dalloc(ctx, &ctx->tickets, sizeof(unsigned) * 256));
   // reorthogonalization tiles: ~32 row blocks of >= 256 rows
   int64_t rows = (n + 31) / 32;
@@ -181,7 +195,26 @@ seed_status alloc_common(seed_ctx *ctx) {
   CU(cudaMemsetAsync(ctx->w, 0, n * es, ctx->cs));
   CU(cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * 2 * kMaxRhs));
   CU(cudaMallocHost(&ctx->h_status, sizeof(HostStatus) * 2));
+  TRY(dalloc(ctx, &ctx->gsync, sizeof(unsigned) * kGridSyncWords));
+  TRY(dalloc(ctx, &ctx->f2, n * es));
+  TRY(dalloc(ctx, &ctx->gbuf, sizeof(double2) * kPersistMaxRhs));
+  TRY(dalloc(ctx, &ctx->tpart, sizeof(double) * (size_t)((n / 12 + 31) / 32 + 1)));
+  CU(cudaMallocHost(&ctx->h_gerr, sizeof(int32_t) * 2));
+  CU(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
+  int coop = 0;
+  CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+  ctx->pgrid = coop ? persistent_grid(ctx->kind, ctx->sm_count) : 0;
   return SEED_OK;
+}
+
+GridSync grid_sync_bufs(seed_ctx *ctx) {
+  GridSync g;
+  g.count = ctx->gsync;
+  g.release = ctx->gsync + 1;
+  g.error = reinterpret_cast<int *>(ctx->gsync + 2);
+  g.owners = ctx->gsync + 3;
+  g.sm_slots = ctx->gsync + 4;
+  return g;
 }
 
 seed_status ensure_cols(seed_ctx *ctx, int cols) {
@@ -302,6 +335,86 @@ int run_length(const seed_params &p) {
   return best >= 8 ? best : 16;
 }
 
+bool use_persistent_seed(seed_ctx *ctx, int nrhs) {
+  const int f = ctx->prm.reorth_freq;
+  return ctx->allow_persistent && ctx->pgrid > 0 && nrhs <= kPersistMaxRhs && (f == 0 || f >= 8);
+}
+
+// Runs of Lanczos steps from CUDA graphs, status polled one run behind.
+template <class T>
+seed_status seed_graph_runs(seed_ctx *ctx, int nrhs) {
+  const seed_params &p = ctx->prm;
+  // Steps i = 1, 2, ... in runs of L steps aligned so that a run ends at a
+  // multiple of the reorthogonalization frequency whenever L divides it.
+  const int L = run_length(p);
+  int i_next = 1;            // first step of the next run
+  int slot = 0, pending = -1;
+  bool stopped = false;
+  while (!stopped) {
+    if (i_next <= p.m_max) {
+      int len = L - ((i_next - 1) % L);
+      if (i_next + len - 1 > p.m_max) len = p.m_max - i_next + 1;
+      std::vector<char> pattern(len);
+      for (int q = 0; q < len; ++q) pattern[q] = reorth_at(p, i_next + q) ? 'R' : '.';
+      TRY(launch_seed_run<T>(ctx, nrhs, pattern));
+      i_next += len;
+      CU(cudaMemcpyAsync(&ctx->h_status[slot], &ctx->st->i, sizeof(HostStatus), cudaMemcpyDeviceToHost, ctx->cs));
+      cudaEvent_t ev;
+      CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      CU(cudaEventRecord(ev, ctx->cs));
+      if (pending >= 0) {
+        // previous run's status
+        CU(cudaEventSynchronize(ctx->ev_out));
+        cudaEventDestroy(ctx->ev_out);
+        if (!ctx->h_status[pending].active) stopped = true;
+      }
+      ctx->ev_out = ev;
+      pending = slot;
+      slot ^= 1;
+    } else {
+      stopped = true;
+    }
+  }
+  return SEED_OK;
+}
+
+// Segments of steps in one persistent launch each, up to the next step that
+// reorthogonalizes (Sec. 3 step 8), which runs from a one-step graph.
+template <class T>
+seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
+  const seed_params &p = ctx->prm;
+  const GridSync g = grid_sync_bufs(ctx);
+  for (;;) {
+    CU(cudaMemcpyAsync(&ctx->h_status[0], &ctx->st->i, sizeof(HostStatus), cudaMemcpyDeviceToHost, ctx->cs));
+    CU(cudaMemcpyAsync(ctx->h_gerr, g.error, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->cs));
+    CU(cudaStreamSynchronize(ctx->cs));
+    if (*ctx->h_gerr) return fail(ctx, SEED_ETIMEOUT, "a grid barrier of the persistent seed kernel timed out");
+    const HostStatus hs = ctx->h_status[0];
+    if (!hs.active) break;
+    const int i = hs.i;
+    if (reorth_at(p, i)) {
+      TRY(launch_seed_run<T>(ctx, nrhs, std::vector<char>{'R'}));
+      continue;
+    }
+    int i_stop = p.m_max + 1;
+    if (p.reorth_freq > 0) i_stop = std::min(i_stop, (i / p.reorth_freq + 1) * p.reorth_freq);
+    CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
+    SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
+    cudaError_t e;
+    if constexpr (sizeof(T) == sizeof(double2))
+      e = launch_seed_run_wilson(b, ctx->wil, (double2 *)ctx->T, ctx->gbuf, g, ctx->partials, ctx->tpart, i_stop,
+                                 ctx->pgrid, ctx->cs);
+    else
+      e = launch_seed_run_csr(b, ctx->csr, (double *)ctx->f2, ctx->gbuf, g, ctx->partials, i_stop, ctx->pgrid, ctx->cs);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, SEED_ECUDA, std::string("persistent seed launch: ") + cudaGetErrorString(e));
+    }
+    ctx->stats.kernel_launches += 1;
+  }
+  return SEED_OK;
+}
+
 template <class T>
 seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
                              seed_info *info) {
@@ -346,36 +459,10 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   kern += 3;
   ctx->stats.kernel_launches += kern;
 
-  // Steps i = 1, 2, ... in runs of L steps aligned so that a run ends at a
-  // multiple of the reorthogonalization frequency whenever L divides it.
-  const int L = run_length(p);
-  int i_next = 1;            // first step of the next run
-  int slot = 0, pending = -1;
-  bool stopped = false;
-  while (!stopped) {
-    if (i_next <= p.m_max) {
-      int len = L - ((i_next - 1) % L);
-      if (i_next + len - 1 > p.m_max) len = p.m_max - i_next + 1;
-      std::vector<char> pattern(len);
-      for (int q = 0; q < len; ++q) pattern[q] = reorth_at(p, i_next + q) ? 'R' : '.';
-      TRY(launch_seed_run<T>(ctx, nrhs, pattern));
-      i_next += len;
-      CU(cudaMemcpyAsync(&ctx->h_status[slot], &ctx->st->i, sizeof(HostStatus), cudaMemcpyDeviceToHost, ctx->cs));
-      cudaEvent_t ev;
-      CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      CU(cudaEventRecord(ev, ctx->cs));
-      if (pending >= 0) {
-        // previous run's status
-        CU(cudaEventSynchronize(ctx->ev_out));
-        cudaEventDestroy(ctx->ev_out);
-        if (!ctx->h_status[pending].active) stopped = true;
-      }
-      ctx->ev_out = ev;
-      pending = slot;
-      slot ^= 1;
-    } else {
-      stopped = true;
-    }
+  if (use_persistent_seed(ctx, nrhs)) {
+    TRY(seed_persistent_segments<T>(ctx, nrhs));
+  } else {
+    TRY(seed_graph_runs<T>(ctx, nrhs));
   }
   CU(cudaStreamSynchronize(ctx->cs));
   if (ctx->ev_out) {
@@ -497,30 +584,52 @@ seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
   ctx->stats.kernel_launches += kern + 1;
   ctx->stats.mvps += nc;
 
+  const bool persist = ctx->allow_persistent_cg && ctx->pgrid > 0 && nc <= kPersistMaxCols;
+  const GridSync g = grid_sync_bufs(ctx);
   const int L = 16;
   for (int round = 0;; ++round) {
-    // CG runs until no column is active (polled one run behind)
-    int slot = 0, pending = -1;
-    cudaEvent_t evs[2] = {nullptr, nullptr};
-    for (;;) {
-      TRY(launch_cg_run<T>(ctx, c, L));
-      CU(cudaMemcpyAsync(ctx->h_flags + slot * kMaxRhs, c.active, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost,
-                         ctx->cs));
-      if (!evs[slot]) CU(cudaEventCreateWithFlags(&evs[slot], cudaEventDisableTiming));
-      CU(cudaEventRecord(evs[slot], ctx->cs));
-      bool any = true;
-      if (pending >= 0) {
-        CU(cudaEventSynchronize(evs[pending]));
-        any = false;
-        for (int j = 0; j < nc; ++j) any |= ctx->h_flags[pending * kMaxRhs + j] != 0;
+    if (persist) {
+      // one persistent launch runs CG until no column is active
+      CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
+      cudaError_t e;
+      if constexpr (sizeof(T) == sizeof(double2))
+        e = launch_cg_run_wilson(ctx->wil, ctx->call, (double2 *)ctx->R, (double2 *)ctx->P, (double2 *)ctx->Q,
+                                 (double2 *)ctx->T, ld, c, g, ctx->partials, ctx->pgrid, ctx->cs);
+      else
+        e = launch_cg_run_csr(ctx->csr, ctx->call, (double *)ctx->R, (double *)ctx->P, (double *)ctx->Q, ld, c, g,
+                              ctx->partials, ctx->pgrid, ctx->cs);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SEED_ECUDA, std::string("persistent CG launch: ") + cudaGetErrorString(e));
       }
-      pending = slot;
-      slot ^= 1;
-      if (!any) break;
+      ctx->stats.kernel_launches += 1;
+      CU(cudaMemcpyAsync(ctx->h_gerr, g.error, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->cs));
+      CU(cudaStreamSynchronize(ctx->cs));
+      if (*ctx->h_gerr) return fail(ctx, SEED_ETIMEOUT, "a grid barrier of the persistent CG kernel timed out");
+    } else {
+      // CG runs until no column is active (polled one run behind)
+      int slot = 0, pending = -1;
+      cudaEvent_t evs[2] = {nullptr, nullptr};
+      for (;;) {
+        TRY(launch_cg_run<T>(ctx, c, L));
+        CU(cudaMemcpyAsync(ctx->h_flags + slot * kMaxRhs, c.active, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost,
+                           ctx->cs));
+        if (!evs[slot]) CU(cudaEventCreateWithFlags(&evs[slot], cudaEventDisableTiming));
+        CU(cudaEventRecord(evs[slot], ctx->cs));
+        bool any = true;
+        if (pending >= 0) {
+          CU(cudaEventSynchronize(evs[pending]));
+          any = false;
+          for (int j = 0; j < nc; ++j) any |= ctx->h_flags[pending * kMaxRhs + j] != 0;
+        }
+        pending = slot;
+        slot ^= 1;
+        if (!any) break;
+      }
+      CU(cudaStreamSynchronize(ctx->cs));
+      for (auto &e : evs)
+        if (e) cudaEventDestroy(e);
     }
-    CU(cudaStreamSynchronize(ctx->cs));
-    for (auto &e : evs)
-      if (e) cudaEventDestroy(e);
     // true residuals of the columns that stopped; restarts where needed
     kern = apply_A(ctx, (const T *)X + ldx, ldx, ctx->Q, ld, nc, c.needs_check);
     launch_cg_check<T>(n, Bc, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, ld, c, ctx->partials, ctx->tickets, ctx->cs);
@@ -593,6 +702,8 @@ struct StreamScope {   // order the internal stream after the caller's, and back
 seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream stream) {
   TRY(check_params(ctx, p));
   ctx->prm = *p;
+  ctx->allow_persistent = p->kernel_path != 1;
+  ctx->allow_persistent_cg = p->kernel_path == 2;
   CU(cudaGetDevice(&ctx->device));
   ctx->user_stream = (cudaStream_t)stream;
   CU(cudaStreamCreateWithFlags(&ctx->cs, cudaStreamNonBlocking));
@@ -610,11 +721,13 @@ void destroy(seed_ctx *ctx) {
   for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
   void *ptrs[] = {ctx->V, ctx->vcur, ctx->u, ctx->f, ctx->w, ctx->st, ctx->alpha_hist, ctx->beta_hist,
                   ctx->delta_hist, ctx->eta, ctx->partials, ctx->tickets, ctx->Hpart, ctx->H, ctx->call,
-                  ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr};
+                  ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
+                  ctx->gsync, ctx->f2, ctx->gbuf, ctx->tpart};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->h_gerr) cudaFreeHost(ctx->h_gerr);
   cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3};
   for (auto e : evs)
     if (e) cudaEventDestroy(e);
@@ -649,6 +762,8 @@ seed_status seed_params_default(seed_params *p) {
   p->tol_seed = 1e-12;
   p->tol_rest = 1e-8;
   p->breakdown_rel = 1e-14;
+  p->kernel_path = 0;
+  p->reserved = 0;
   return SEED_OK;
 }
 

@@ -14,8 +14,7 @@
 // block order by the last block (see device_common.cuh).
 #include <math.h>
 
-#include "device_common.cuh"
-#include "seed_internal.h"
+#include "seed_device.cuh"
 
 namespace seedk {
 
@@ -26,44 +25,24 @@ constexpr int kColTicket = 16;     // tickets[16 + c]: per-column kernels
 #define GRID_STRIDE(e, n) \
   for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < (n); e += (int64_t)gridDim.x * NT)
 
+// Single-vector kernels: at most one block per SM (152), a few elements per
+// thread; the FP64 work of these kernels is a few microseconds, so what
+// matters is few blocks, independent loads per thread and a short tail.
 int vec_blocks(int64_t n) {
   int64_t b = (n + NT - 1) / NT;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > 152) b = 152;
   if (b < 1) b = 1;
   return (int)b;
 }
 
-// ---------------------------------------------------------------------------
-// Sec. 3 step 9: beta_i = ||f||, residual estimate and the stopping test
-// (thread 0 of the last block).
-// ---------------------------------------------------------------------------
-template <class T>
-SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
-  SeedState *st = b.st;
-  const int i = st->i;
-  const double beta = sqrt(sumsq);
-  b.beta_hist[i] = beta;
-  const double row = fabs(st->alpha) + (i > 1 ? st->beta_prev : 0.0) + beta;
-  if (row > st->tnorm) st->tnorm = row;
-  const double rho = beta * fabs(st->zeta) / st->delta;
-  st->rho = rho;
-  st->beta = beta;
-  if (st->converged_at < 0 && rho <= st->tol_abs) {
-    st->converged_at = i;
-    st->stop_at = i + st->extra_iters;
-  }
-  int stop = STOP_RUNNING;
-  if (beta <= st->breakdown_rel * st->tnorm) stop = STOP_BREAKDOWN;
-  else if (st->stop_at >= 0 && i >= st->stop_at) stop = STOP_CONVERGED;
-  else if (i >= st->m_max) stop = STOP_MMAX;
-  if (stop != STOP_RUNNING) {
-    st->active = 0;
-    st->stop_reason = stop;
-  } else {
-    st->beta_prev = beta;
-    st->inv_beta = 1.0 / beta;
-    st->i = i + 1;
-  }
+// Kernels over nc lockstep columns: about 4 blocks per SM in total.
+int col_blocks(int64_t n, int nc) {
+  int64_t b = (n + NT * 4 - 1) / (NT * 4);
+  int64_t cap = 608 / (nc > 0 ? nc : 1);
+  if (cap < 1) cap = 1;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
 }
 
 // Step 2 (start): f = r_0^1, beta_0 = ||r_0^1||; v_1 follows from the normalize kernel.
@@ -119,82 +98,77 @@ __global__ void __launch_bounds__(NT) k_seed_normalize(SeedBufs<T> b) {
   }
 }
 
-// Steps 5 and 7 (the dot products) and the scalar part of steps 3/4/6/7:
-//   grid.y = 0: f = A v_i - beta_{i-1} v_{i-1}, partial alpha_i = Re(v_i^H f)
-//   grid.y = j: partial g^j = v_i^H r_0^j
-// The last block forms alpha_i, gamma_{i-1}, delta_i, zeta_i and eta^j.
+// Steps 5 and 7 (the dot products) and the scalar part of steps 3/4/6/7, in
+// one pass over the elements:  f = A v_i - beta_{i-1} v_{i-1};
+// alpha_i = Re(v_i^H f);  g^j = v_i^H r_0^j for j = 2..nrhs.
+// Values are packed 32 per chunk (alpha in slot 0 of chunk 0, then 15 complex
+// g^j per chunk), reduced per block with a warp reduce-scatter, and the last
+// block reduces all chunks warp-parallel and forms alpha_i, gamma_{i-1},
+// delta_i, zeta_i and eta^j.
+constexpr int kDotsPerChunk = 15;
+
 template <class T>
 __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
   SeedState *st = b.st;
   if (!st->active) return;
-  __shared__ double sm[2 * NT / 32];
+  __shared__ double sred[NT / 32][32];
   __shared__ double2 sums[kMaxRhs];
+  __shared__ double s_alpha;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = st->i;
-  const int y = blockIdx.y;
+  const int nr = b.nrhs;
+  const int nch = nr > 1 ? (nr - 1 + kDotsPerChunk - 1) / kDotsPerChunk : 1;
   const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
-  double2 acc = c2(0.0, 0.0);
-  if (y == 0) {
-    if (i > 1) {
-      const double bp = st->beta_prev;
-      const T *vm = b.V + (int64_t)(i - 2) * b.ldv;
-      GRID_STRIDE(e, b.n) {
-        const T fe = Sc<T>::axpy(-bp, vm[e], b.u[e]);
+  const T *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+  const double bp = (i > 1) ? st->beta_prev : 0.0;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int j0 = 1 + kDotsPerChunk * ch;
+    const int jn = nr - j0 < kDotsPerChunk ? nr - j0 : kDotsPerChunk;   // may be <= 0
+    double acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+    GRID_STRIDE(e, b.n) {
+      const T v = vi[e];
+      if (ch == 0) {
+        const T fe = (i > 1) ? Sc<T>::axpy(-bp, vm[e], b.u[e]) : b.u[e];
         b.f[e] = fe;
-        acc.x = Sc<T>::redot(vi[e], fe, acc.x);
+        acc[0] = Sc<T>::redot(v, fe, acc[0]);
       }
-    } else {
-      GRID_STRIDE(e, b.n) {
-        const T fe = b.u[e];
-        b.f[e] = fe;
-        acc.x = Sc<T>::redot(vi[e], fe, acc.x);
+#pragma unroll
+      for (int q = 0; q < kDotsPerChunk; ++q) {
+        if (q < jn) {
+          const double2 d = Sc<T>::dotc(v, b.R0[(int64_t)(j0 + q - 1) * b.ldr + e], c2(acc[1 + 2 * q], acc[2 + 2 * q]));
+          acc[1 + 2 * q] = d.x;
+          acc[2 + 2 * q] = d.y;
+        }
       }
     }
-  } else {
-    const T *r = b.R0 + (int64_t)(y - 1) * b.ldr;
-    GRID_STRIDE(e, b.n) acc = Sc<T>::dotc(vi[e], r[e], acc);
+    const double mine = warp_reduce_scatter32(acc);
+    sred[warp][lane] = mine;
+    __syncthreads();
+    if (threadIdx.x < 32)
+      b.partials[((int64_t)ch * gridDim.x + blockIdx.x) * 32 + lane] =
+          ((sred[0][lane] + sred[1][lane]) + sred[2][lane]) + sred[3][lane];
+    __syncthreads();
   }
-  double v[2] = {acc.x, acc.y};
-  block_sum<2, NT>(v, sm);
-  if (threadIdx.x == 0) {
-    b.partials[((int64_t)y * gridDim.x + blockIdx.x) * 2] = v[0];
-    b.partials[((int64_t)y * gridDim.x + blockIdx.x) * 2 + 1] = v[1];
-  }
-  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x * gridDim.y)) return;
-  for (int yy = 0; yy < (int)gridDim.y; ++yy) {
-    const double *p = b.partials + (int64_t)yy * gridDim.x * 2;
-    const double re = sum_partials<NT>(p, gridDim.x, 2, 0, sm);
-    const double im = sum_partials<NT>(p, gridDim.x, 2, 1, sm);
-    if (threadIdx.x == 0) sums[yy] = c2(re, im);
-  }
-  if (threadIdx.x == 0) {
-    const double a = sums[0].x;
-    double gam, del, zet;
-    if (i == 1) {           // step 3: delta_1 = alpha_1, zeta_1 = beta_0
-      gam = 0.0;
-      del = a;
-      zet = st->beta0;
-    } else {                // step 6
-      const double bp = st->beta_prev;
-      gam = bp / st->delta;
-      del = a - gam * bp;
-      zet = -gam * st->zeta;
-    }
-    for (int j = 1; j < b.nrhs; ++j) {   // steps 4 / 7
-      const double2 g = sums[j];
-      const double2 e = b.eta[j];
-      b.eta[j] = (i == 1) ? g : c2(g.x - gam * e.x, g.y - gam * e.y);
-    }
-    st->alpha = a;
-    st->gamma = gam;
-    st->delta = del;
-    st->zeta = zet;
-    b.alpha_hist[i] = a;
-    b.delta_hist[i] = del;
-    if (!(del > 0.0) || !isfinite(del)) {
-      st->active = 0;
-      st->stop_reason = STOP_NOTSPD;
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  for (int val = warp; val < 32 * nch; val += NT / 32) {
+    const int ch = val >> 5, q = val & 31;
+    const double sv = warp_sum_partials(b.partials + (int64_t)ch * gridDim.x * 32, gridDim.x, 32, q);
+    if (lane == 0) {
+      if (q == 0) {
+        if (ch == 0) s_alpha = sv;
+      } else if (q <= 2 * kDotsPerChunk) {
+        const int j = 1 + kDotsPerChunk * ch + (q - 1) / 2;
+        if (j < nr) {
+          if ((q - 1) % 2 == 0) sums[j].x = sv;
+          else sums[j].y = sv;
+        }
+      }
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) seed_step_scalars(b, i, s_alpha, sums);
 }
 
 // Steps 5 (f -= alpha_i v_i), 6 (w_i, x^1) and 7 (x^j), plus ||f||^2 when this
@@ -239,22 +213,6 @@ __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
 // H = V_{<i}^H [v_i f], [v_i f] -= V_{<i} H (repeated `passes` times), then
 // v_i /= ||v_i|| and f -= (v_i^H f) v_i (repeated `passes` times).
 // ---------------------------------------------------------------------------
-
-// lane l ends with the warp sum of v[l]; 31 adds per lane.
-SEED_DEV double warp_reduce_scatter32(double (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const bool upper = (lane & w) != 0;
-#pragma unroll
-    for (int k = 0; k < w; ++k) {
-      const double send = upper ? v[k] : v[k + w];
-      const double keep = upper ? v[k + w] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  return v[0];
-}
 
 // One tile of H partials: rows [rb*R, (rb+1)*R) x columns [c0, c0+8) of V
 // against the two vectors F0, F1.  Hpart[(rb*kcap + c)*2 + v].
@@ -453,8 +411,7 @@ void launch_seed_normalize(const SeedBufs<T> &b, cudaStream_t s) {
 }
 template <class T>
 void launch_seed_dots(const SeedBufs<T> &b, cudaStream_t s) {
-  dim3 grid((unsigned)b.nblocks, (unsigned)b.nrhs);
-  k_seed_dots<T><<<grid, NT, 0, s>>>(b);
+  k_seed_dots<T><<<b.nblocks, NT, 0, s>>>(b);
 }
 template <class T>
 void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s) {
@@ -606,7 +563,7 @@ void launch_sub_from(const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, int
 template <class T>
 void launch_colnorms(int64_t n, const T *X, int64_t ldx, int ncols, double *out, double *partials, unsigned *tickets,
                      cudaStream_t s) {
-  dim3 g((unsigned)vec_blocks(n), (unsigned)ncols);
+  dim3 g((unsigned)col_blocks(n, ncols), (unsigned)ncols);
   k_colnorms<T><<<g, NT, 0, s>>>(n, X, ldx, out, partials, tickets);
 }
 
@@ -781,31 +738,31 @@ __global__ void __launch_bounds__(NT) k_cg_check(int64_t n, const T *B, int64_t 
 template <class T>
 void launch_cg_init(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, T *P, int64_t ld,
                     const CgCols &c, double *partials, unsigned *tickets, bool restart_only, cudaStream_t s) {
-  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  dim3 g((unsigned)col_blocks(n, c.nc), (unsigned)c.nc);
   if (restart_only) k_cg_p<T><<<g, NT, 0, s>>>(n, R, P, ld, c, 1);
   else k_cg_init<T><<<g, NT, 0, s>>>(n, B, ldb, Q, ldq, R, P, ld, c, partials, tickets);
 }
 template <class T>
 void launch_cg_alpha(int64_t n, const T *P, const T *Q, int64_t ld, const CgCols &c, double *partials,
                      unsigned *tickets, cudaStream_t s) {
-  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  dim3 g((unsigned)col_blocks(n, c.nc), (unsigned)c.nc);
   k_cg_alpha<T><<<g, NT, 0, s>>>(n, P, Q, ld, c, partials, tickets);
 }
 template <class T>
 void launch_cg_update(int64_t n, const CallArgs *call, T *R, const T *P, const T *Q, int64_t ld, const CgCols &c,
                       double *partials, unsigned *tickets, cudaStream_t s) {
-  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  dim3 g((unsigned)col_blocks(n, c.nc), (unsigned)c.nc);
   k_cg_update<T><<<g, NT, 0, s>>>(n, call, R, P, Q, ld, c, partials, tickets);
 }
 template <class T>
 void launch_cg_p(int64_t n, const T *R, T *P, int64_t ld, const CgCols &c, cudaStream_t s) {
-  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  dim3 g((unsigned)col_blocks(n, c.nc), (unsigned)c.nc);
   k_cg_p<T><<<g, NT, 0, s>>>(n, R, P, ld, c, 0);
 }
 template <class T>
 void launch_cg_check(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, int64_t ld, const CgCols &c,
                      double *partials, unsigned *tickets, cudaStream_t s) {
-  dim3 g((unsigned)vec_blocks(n), (unsigned)c.nc);
+  dim3 g((unsigned)col_blocks(n, c.nc), (unsigned)c.nc);
   k_cg_check<T><<<g, NT, 0, s>>>(n, B, ldb, Q, ldq, R, ld, c, partials, tickets);
 }
 

@@ -1,0 +1,769 @@
+// persistent.cu -- persistent cooperative kernels for the seed solve (runs of
+// Sec. 3 Lanczos steps without reorthogonalization) and for the lockstep CG on
+// the seeded systems.  One launch runs many steps; grid-wide dependencies are
+// grid barriers instead of kernel boundaries.
+//
+// Why: on the benchmark's 8^4 lattice one Lanczos step is ~6 us of FP64 work
+// per SM in each operator half and a few microseconds of vector work; as a
+// chain of dependent kernels every step paid launch, ramp-up and tail five
+// times, and the small vector kernels ran latency-bound.
+//
+// Barriers: an arrival counter that only grows during a launch (the host zeroes
+// it before each launch); a block waits until it reaches epoch * gridDim.x.  A
+// "reducing" barrier lets the last block to arrive run the scalar step (it
+// reads every block's partial sums in a fixed order, so results are
+// deterministic) and then release the others.  Every wait is bounded: after
+// kBarrierTimeoutNs of waiting a block sets GridSync::error and all blocks
+// leave; the host turns that into SEED_ETIMEOUT.  The launch is cooperative,
+// so all blocks are resident and a barrier can only time out on a fault.
+//
+// Memory: data written by other blocks during the launch is read with ordinary
+// or L2 (__ldcg) loads after a barrier, never through the non-coherent
+// read-only path; every barrier is a release (fence, arrival) / acquire
+// (acquire load, fence) pair followed by a CTA barrier.
+//
+// Operator tiles (32 sites, 4 warps) go to at most one block per SM: the first
+// block that starts on an SM registers as a tile owner, so two tiles never
+// share an SM's FP64 pipe while another SM idles.
+#include "seed_device.cuh"
+#include "wilson_device.cuh"
+
+namespace seedk {
+
+constexpr int PT = kVecThreads;                          // 4 warps: the Wilson tile layout
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+SEED_DEV unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+SEED_DEV unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+template <class U> SEED_DEV U vload(const U *p) { return *(const volatile U *)p; }
+
+// thread 0: wait until *flag >= target; false on time-out or when another block failed
+SEED_DEV bool wait_geq(const unsigned *flag, unsigned target, int *error) {
+  unsigned long long t0 = 0;
+  for (unsigned spin = 0;; ++spin) {
+    if (ld_acquire(flag) >= target) return true;
+    if (vload(error)) return false;
+    if ((spin & 255u) == 255u) {
+      const unsigned long long t = gtimer();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > kBarrierTimeoutNs) {
+        atomicExch(error, 1);
+        return false;
+      }
+    }
+    __nanosleep(32);
+  }
+}
+
+SEED_DEV bool grid_sync(const GridSync &g, unsigned &epoch) {
+  __shared__ int s_ok;
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(g.count, 1u);
+    s_ok = wait_geq(g.count, epoch * gridDim.x, g.error) ? 1 : 0;
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <class F>
+SEED_DEV bool grid_reduce_sync(const GridSync &g, unsigned &epoch, F &&last_block_work) {
+  __shared__ int s_last, s_ok;
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(g.count, 1u);
+    s_last = (prev == epoch * gridDim.x - 1u) ? 1 : 0;
+    s_ok = 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    last_block_work();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(g.release, epoch);
+    }
+  } else if (threadIdx.x == 0) {
+    s_ok = wait_geq(g.release, epoch, g.error) ? 1 : 0;
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Tile ownership: (rank, owners) of this block; the first block on each SM owns
+// tiles.  If no block could register (SM ids >= 256), every block owns tiles.
+struct Owners {
+  int rank, count;
+};
+SEED_DEV bool register_owner(const GridSync &g, unsigned &epoch, Owners &o) {
+  __shared__ int s_rank;
+  if (threadIdx.x == 0) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    int r = -1;
+    if (sm < 256u && atomicAdd(g.sm_slots + sm, 1u) == 0u) r = (int)atomicAdd(g.owners, 1u);
+    s_rank = r;
+  }
+  if (!grid_sync(g, epoch)) return false;
+  const int n = (int)vload(g.owners);
+  if (n > 0) {
+    o.rank = s_rank;
+    o.count = n;
+  } else {
+    o.rank = blockIdx.x;
+    o.count = gridDim.x;
+  }
+  return true;
+}
+
+// Last block: s_vals[v] = sum over rows b < nrows of part[32 b + v] (v < 32),
+// one thread per row (16 independent 16-byte loads), then a block
+// reduce-scatter; fixed order, so deterministic.
+SEED_DEV void reduce_rows32(const double *part, int nrows, double *s_vals, double (*sred)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  for (int b = threadIdx.x; b < nrows; b += PT) {
+    const double2 *row = reinterpret_cast<const double2 *>(part + (int64_t)b * 32);
+    double2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __ldcg(row + k);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      acc[2 * k] += v[k].x;
+      acc[2 * k + 1] += v[k].y;
+    }
+  }
+  const double mine = warp_reduce_scatter32(acc);
+  sred[warp][lane] = mine;
+  __syncthreads();
+  if (threadIdx.x < 32) s_vals[lane] = ((sred[0][lane] + sred[1][lane]) + sred[2][lane]) + sred[3][lane];
+  __syncthreads();
+}
+
+// Block partial of 32 values: reduce-scatter and one row of bpart.
+SEED_DEV void write_row32(double (&acc)[32], double *bpart, double (*sred)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double mine = warp_reduce_scatter32(acc);
+  sred[warp][lane] = mine;
+  __syncthreads();
+  if (threadIdx.x < 32)
+    bpart[(int64_t)blockIdx.x * 32 + lane] = ((sred[0][lane] + sred[1][lane]) + sred[2][lane]) + sred[3][lane];
+}
+
+// Hopping sums of one 32-site tile into sacc[mu][component][site] (S = +1: D, -1: D^H).
+template <int S>
+SEED_DEV void wilson_tile(const WilsonOp &op, const double2 *in, int64_t s0, double (*sacc)[24][kWilsonSites + 1]) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const int64_t s = s0 + lane;
+  double2 acc[12];
+  if (s < op.sites) {
+    switch (mu) {
+      case 0: site_mu<0, S, false>(op, in, s, acc); break;
+      case 1: site_mu<1, S, false>(op, in, s, acc); break;
+      case 2: site_mu<2, S, false>(op, in, s, acc); break;
+      default: site_mu<3, S, false>(op, in, s, acc); break;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = c2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    sacc[mu][2 * k][lane] = acc[k].x;
+    sacc[mu][2 * k + 1][lane] = acc[k].y;
+  }
+  __syncthreads();
+}
+// complex component cc of tile-local site sl, summed over the 4 directions in order
+SEED_DEV double2 tile_sum(double (*sacc)[24][kWilsonSites + 1], int cc, int sl) {
+  return c2(((sacc[0][2 * cc][sl] + sacc[1][2 * cc][sl]) + sacc[2][2 * cc][sl]) + sacc[3][2 * cc][sl],
+            ((sacc[0][2 * cc + 1][sl] + sacc[1][2 * cc + 1][sl]) + sacc[2][2 * cc + 1][sl]) + sacc[3][2 * cc + 1][sl]);
+}
+
+// ---------------------------------------------------------------------------
+// Seed runs.  Per step i (paper notation):
+//   phase 1 (tiles): v_i = f / beta_{i-1} into V; t = D v_i        [Wilson only]
+//   phase 2 (tiles): u = A v_i; f = u - beta_{i-1} v_{i-1}; partial alpha_i
+//   reduce: alpha_i -> gamma_{i-1}, delta_i, zeta_i, eta^j (steps 3/4, 6/7),
+//           with g^j = v_i^H r_0^j formed in the previous step's update
+//   phase 3 (all blocks): f -= alpha_i v_i; w_i; x^1, x^j; partials ||f||^2
+//           and f^H r_0^j
+//   reduce: beta_i, stopping test (step 9); g^j of step i+1 =
+//           (f^H r_0^j) / beta_i, since v_{i+1} = f / beta_i.
+// A pre-phase at the start of a run forms g^j of its first step the same way.
+// ---------------------------------------------------------------------------
+
+// partial of f^H r_0^j (slots 1 + 2(j-1), 2 + 2(j-1)) for element e
+template <class T>
+SEED_DEV void add_fr0(const SeedBufs<T> &b, int64_t e, T fe, double (&acc)[32]) {
+  const int nr = b.nrhs;
+#pragma unroll
+  for (int q = 0; q < kPersistMaxRhs - 1; ++q) {
+    if (q < nr - 1) {
+      const double2 d = Sc<T>::dotc(fe, __ldg(b.R0 + (int64_t)q * b.ldr + e), c2(acc[1 + 2 * q], acc[2 + 2 * q]));
+      acc[1 + 2 * q] = d.x;
+      acc[2 + 2 * q] = d.y;
+    }
+  }
+}
+
+// g^j = scale * (reduced f^H r_0^j) into gbuf
+template <class T>
+SEED_DEV void store_g(const SeedBufs<T> &b, const double *s_vals, double scale, double2 *gbuf) {
+  for (int j = 1 + (int)threadIdx.x; j < b.nrhs; j += PT)
+    gbuf[j] = c2(scale * s_vals[1 + 2 * (j - 1)], scale * s_vals[2 + 2 * (j - 1)]);
+}
+
+// pre-phase: g^j of the first step from the current f
+template <class T>
+SEED_DEV bool seed_pre_dots(const SeedBufs<T> &b, const T *f, double2 *gbuf, const GridSync &g, unsigned &epoch,
+                            double *bpart, double (*sred)[32], double *s_vals) {
+  double acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT)
+    add_fr0<T>(b, e, f[e], acc);
+  write_row32(acc, bpart, sred);
+  return grid_reduce_sync(g, epoch, [&]() {
+    reduce_rows32(bpart, gridDim.x, s_vals, sred);
+    store_g<T>(b, s_vals, __ldcg(&b.st->inv_beta), gbuf);
+  });
+}
+
+// reduce alpha_i from parts[k * stride], k < nparts (written by the caller, in
+// an order that does not depend on which block ran which tile) and form the
+// step's scalars
+template <class T>
+SEED_DEV bool seed_alpha_barrier(const SeedBufs<T> &b, const double *parts, int nparts, int stride,
+                                 const double2 *gbuf, int i, const GridSync &g, unsigned &epoch, double *s_red,
+                                 double2 *s_sums) {
+  return grid_reduce_sync(g, epoch, [&]() {
+    for (int j = 1 + (int)threadIdx.x; j < b.nrhs; j += PT) s_sums[j] = __ldcg(gbuf + j);
+    if (threadIdx.x < 32) {
+      const double a = warp_sum_partials(parts, nparts, stride, 0);
+      __syncwarp();
+      if (threadIdx.x == 0) s_red[0] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) seed_step_scalars(b, i, s_red[0], s_sums);
+  });
+}
+
+// phase 3 and the step-9 barrier
+template <class T>
+SEED_DEV bool seed_update_phase(const SeedBufs<T> &b, T *f, const T *vi, int i, double2 *gbuf, const GridSync &g,
+                                unsigned &epoch, double *bpart, double (*sred)[32], double *s_vals, double2 *s_eta) {
+  SeedState *st = b.st;
+  const double a = vload(&st->alpha), zeta = vload(&st->zeta), inv_d = 1.0 / vload(&st->delta);
+  const double bp = (i > 1) ? vload(&st->beta_prev) : 0.0;
+  for (int j = threadIdx.x; j < b.nrhs; j += PT) s_eta[j] = __ldcg(b.eta + j);
+  __syncthreads();
+  T *const X = reinterpret_cast<T *>(b.call->X);
+  const int64_t ldx = b.call->ldx;
+  const int nr = b.nrhs;
+  double acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
+    T xv[kPersistMaxRhs];
+#pragma unroll
+    for (int j = 0; j < kPersistMaxRhs; ++j)
+      if (j < nr) xv[j] = __ldcg(X + j * ldx + e);
+    const T v = __ldcg(vi + e), f0 = __ldcg(f + e);
+    const T wp = (i > 1) ? __ldcg(b.w + e) : Sc<T>::zero();
+    const T fe = Sc<T>::axpy(-a, v, f0);
+    const T we = (i > 1) ? Sc<T>::scale(inv_d, Sc<T>::axpy(-bp, wp, v)) : Sc<T>::scale(inv_d, v);
+    f[e] = fe;
+    b.w[e] = we;
+    xv[0] = Sc<T>::axpy(zeta, we, xv[0]);
+#pragma unroll
+    for (int j = 1; j < kPersistMaxRhs; ++j)
+      if (j < nr) xv[j] = Sc<T>::caxpy(s_eta[j], we, xv[j]);
+#pragma unroll
+    for (int j = 0; j < kPersistMaxRhs; ++j)
+      if (j < nr) X[j * ldx + e] = xv[j];
+    acc[0] = Sc<T>::nrm2(fe, acc[0]);
+    add_fr0<T>(b, e, fe, acc);
+  }
+  write_row32(acc, bpart, sred);
+  return grid_reduce_sync(g, epoch, [&]() {
+    reduce_rows32(bpart, gridDim.x, s_vals, sred);
+    if (threadIdx.x == 0) seed_finish(b, s_vals[0]);
+    __syncthreads();
+    if (vload(&st->active)) store_g<T>(b, s_vals, vload(&st->inv_beta), gbuf);
+  });
+}
+
+// On leaving at a reorthogonalization step: v_i = f / beta_{i-1} into V and vcur.
+template <class T>
+SEED_DEV void seed_leave(const SeedBufs<T> &b, const T *f, int i_stop) {
+  SeedState *st = b.st;
+  if (!vload(&st->active) || vload(&st->i) != i_stop) return;
+  const double inv_b = vload(&st->inv_beta);
+  T *vi = b.V + (int64_t)(i_stop - 1) * b.ldv;
+  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
+    const T fe = __ldcg(f + e);
+    const T v = Sc<T>::scale(inv_b, fe);
+    vi[e] = v;
+    b.vcur[e] = v;
+    if (f != b.f) b.f[e] = fe;
+  }
+}
+
+__global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, WilsonOp op, double2 *tbuf,
+                                                         double2 *gbuf, GridSync g, double *bpart, double *tpart,
+                                                         int i_stop) {
+  __shared__ double sacc[4][24][kWilsonSites + 1];
+  __shared__ double sred[PT / 32][32];
+  __shared__ double s_vals[32];
+  __shared__ double s_red[PT / 32];
+  __shared__ double2 s_sums[kPersistMaxRhs];
+  __shared__ double2 s_eta[kPersistMaxRhs];
+  SeedState *st = b.st;
+  const int64_t sites = op.sites;
+  const int tiles = (int)((sites + kWilsonSites - 1) / kWilsonSites);
+  const double kappa = op.kappa;
+  unsigned epoch = 0;
+  Owners own;
+  if (!register_owner(g, epoch, own)) return;
+  if (vload(&st->active) && vload(&st->i) < i_stop)
+    if (!seed_pre_dots<double2>(b, b.f, gbuf, g, epoch, bpart, sred, s_vals)) return;
+  for (;;) {
+    const int i = vload(&st->i);
+    if (!vload(&st->active) || i >= i_stop) break;
+    const double inv_b = vload(&st->inv_beta);
+    double2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
+    if (own.rank >= 0) {
+      for (int tile = own.rank; tile < tiles; tile += own.count) {
+        const int64_t s0 = (int64_t)tile * kWilsonSites;
+        wilson_tile<+1>(op, b.f, s0, sacc);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
+          const int64_t ss = s0 + sl;
+          if (ss < sites) {
+            const double2 sum = tile_sum(sacc, cc, sl);
+            const int64_t e = 12 * ss + cc;
+            const double2 fe = b.f[e];
+            const double2 v = c2(inv_b * fe.x, inv_b * fe.y);
+            vi[e] = v;
+            tbuf[e] = c2(fma(-kappa, inv_b * sum.x, v.x), fma(-kappa, inv_b * sum.y, v.y));
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (!grid_sync(g, epoch)) return;
+
+    const double bp = (i > 1) ? vload(&st->beta_prev) : 0.0;
+    const double2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+    if (own.rank >= 0) {
+      for (int tile = own.rank; tile < tiles; tile += own.count) {
+        const int64_t s0 = (int64_t)tile * kWilsonSites;
+        wilson_tile<-1>(op, tbuf, s0, sacc);
+        double apart = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
+          const int64_t ss = s0 + sl;
+          if (ss < sites) {
+            const double2 sum = tile_sum(sacc, cc, sl);
+            const int64_t e = 12 * ss + cc;
+            const double2 tv = tbuf[e], v = vi[e];
+            const double2 m = (i > 1) ? vm[e] : c2(0.0, 0.0);
+            double2 u = c2(fma(-kappa, sum.x, tv.x), fma(-kappa, sum.y, tv.y));
+            if (i > 1) u = c2(fma(-bp, m.x, u.x), fma(-bp, m.y, u.y));
+            b.f[e] = u;
+            apart = fma(v.y, u.y, fma(v.x, u.x, apart));
+          }
+        }
+        double vv[1] = {apart};
+        block_sum<1, PT>(vv, s_red);
+        if (threadIdx.x == 0) tpart[tile] = vv[0];   // per tile: the sum order is fixed
+      }
+    }
+    if (!seed_alpha_barrier<double2>(b, tpart, tiles, 1, gbuf, i, g, epoch, s_red, s_sums)) return;
+    if (!vload(&st->active)) break;   // delta_i <= 0
+    if (!seed_update_phase<double2>(b, b.f, vi, i, gbuf, g, epoch, bpart, sred, s_vals, s_eta)) return;
+  }
+  seed_leave<double2>(b, b.f, i_stop);
+}
+
+// real CSR operator: the apply reads f_cur (two buffers alternate, since a row
+// reads other rows' entries while writing its own)
+__global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp op, double *f2, double2 *gbuf,
+                                                      GridSync g, double *bpart, int i_stop) {
+  __shared__ double sred[PT / 32][32];
+  __shared__ double s_vals[32];
+  __shared__ double s_red[PT / 32];
+  __shared__ double2 s_sums[kPersistMaxRhs];
+  __shared__ double2 s_eta[kPersistMaxRhs];
+  SeedState *st = b.st;
+  unsigned epoch = 0;
+  int par = 0;
+  if (vload(&st->active) && vload(&st->i) < i_stop)
+    if (!seed_pre_dots<double>(b, b.f, gbuf, g, epoch, bpart, sred, s_vals)) return;
+  for (;;) {
+    const int i = vload(&st->i);
+    if (!vload(&st->active) || i >= i_stop) break;
+    const double inv_b = vload(&st->inv_beta);
+    const double bp = (i > 1) ? vload(&st->beta_prev) : 0.0;
+    double *fc = par ? f2 : b.f, *fn = par ? b.f : f2;
+    double *vi = b.V + (int64_t)(i - 1) * b.ldv;
+    const double *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+    double apart = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * PT + threadIdx.x; r < b.n; r += (int64_t)gridDim.x * PT) {
+      const int32_t k0 = __ldg(op.row_ptr + r), k1 = __ldg(op.row_ptr + r + 1);
+      double sum = 0.0;
+      for (int32_t k = k0; k < k1; ++k) sum = fma(__ldg(op.vals + k), fc[__ldg(op.col_idx + k)], sum);
+      const double v = inv_b * fc[r];
+      vi[r] = v;
+      double u = inv_b * sum;
+      if (i > 1) u = fma(-bp, vm[r], u);
+      fn[r] = u;
+      apart = fma(v, u, apart);
+    }
+    {
+      double vv[1] = {apart};
+      block_sum<1, PT>(vv, s_red);
+      if (threadIdx.x == 0) bpart[(int64_t)blockIdx.x * 32] = vv[0];   // rows follow blockIdx: fixed order
+    }
+    if (!seed_alpha_barrier<double>(b, bpart, gridDim.x, 32, gbuf, i, g, epoch, s_red, s_sums)) return;
+    if (!vload(&st->active)) break;
+    if (!seed_update_phase<double>(b, fn, vi, i, gbuf, g, epoch, bpart, sred, s_vals, s_eta)) return;
+    par ^= 1;
+  }
+  seed_leave<double>(b, par ? f2 : b.f, i_stop);
+}
+
+// ---------------------------------------------------------------------------
+// lockstep CG (Hestenes-Stiefel) on nc columns, per-column scalars in CgCols:
+//   phase 1: t = D p;  phase 2: q = D^H t, p^H q;  alpha = rho / Re(p^H q)
+//   phase 3: x += alpha p, r -= alpha q, ||r||^2;  convergence, beta
+//   phase 4: p = r + beta p
+// ---------------------------------------------------------------------------
+// elements per thread of a vector work item: all loads of an item are in
+// flight together (8 real or 4 complex per thread and vector)
+template <class T> __host__ __device__ constexpr int elems_per_thread() { return sizeof(T) == sizeof(double) ? 8 : 4; }
+
+// (runs in the last block of a reducing barrier, on any SM: L2 loads, all
+// issued before use)
+SEED_DEV void cg_update_fin(const CgCols &c, int j, double rr) {
+  const int act = __ldcg(c.active + j), it = __ldcg(c.iters + j), mv = __ldcg(c.mvps + j);
+  const double bn = __ldcg(c.bnorm + j), rho = __ldcg(c.rho + j);
+  if (!act) return;
+  const double rn = sqrt(rr);
+  c.iters[j] = it + 1;
+  c.mvps[j] = mv + 1;
+  c.relres[j] = bn > 0.0 ? rn / bn : 0.0;
+  if (rn <= c.tol * bn) {
+    c.active[j] = 0;
+    c.reached[j] = 1;
+    c.needs_check[j] = 1;
+  } else if (it + 1 >= c.maxit) {
+    c.active[j] = 0;
+    c.needs_check[j] = 1;
+  } else {
+    c.beta[j] = rr / rho;
+    c.rho[j] = rr;
+  }
+}
+
+SEED_DEV void cg_alpha_fin(const CgCols &c, int j, double pq) {
+  const int act = __ldcg(c.active + j);
+  const double rho = __ldcg(c.rho + j);
+  if (act) c.alpha[j] = rho / pq;
+}
+
+// per-column block partials (s_colacc) -> one row of bpart -> reducing barrier;
+// the last block reduces all rows and applies fin(j, sum) per column
+template <class F>
+SEED_DEV bool col_reduce_barrier(const GridSync &g, unsigned &epoch, double *bpart, const double *s_colacc, int nc,
+                                 double (*sred)[32], double *s_vals, F &&fin) {
+  if (threadIdx.x < 32) bpart[(int64_t)blockIdx.x * 32 + threadIdx.x] = threadIdx.x < nc ? s_colacc[threadIdx.x] : 0.0;
+  return grid_reduce_sync(g, epoch, [&]() {
+    reduce_rows32(bpart, gridDim.x, s_vals, sred);
+    if ((int)threadIdx.x < nc) fin(threadIdx.x, s_vals[threadIdx.x]);
+  });
+}
+
+// phases 3 and 4 for both operators
+template <class T>
+SEED_DEV bool cg_vector_phases(const CallArgs *call, T *R, T *P, const T *Q, int64_t ld, int64_t n, const CgCols &c,
+                               const GridSync &g, unsigned &epoch, double *bpart, int *s_act, double *s_a,
+                               double *s_colacc, double *s_red, double (*sred)[32], double *s_vals) {
+  constexpr int kElem = elems_per_thread<T>(), kChunk = PT * kElem;
+  const int nc = c.nc;
+  const int nchunks = (int)((n + kChunk - 1) / kChunk);
+  T *const X = reinterpret_cast<T *>(call->X) + call->ldx;   // systems 2.. are columns 1.. of X
+  const int64_t ldx = call->ldx;
+  for (int j = threadIdx.x; j < nc; j += PT) {
+    s_a[j] = __ldcg(c.alpha + j);
+    s_colacc[j] = 0.0;
+  }
+  __syncthreads();
+  for (int item = blockIdx.x; item < nchunks * nc; item += gridDim.x) {
+    const int j = item / nchunks, ch = item - j * nchunks;
+    if (!s_act[j]) continue;
+    const double a = s_a[j];
+    T *x = X + j * ldx;
+    T *r = R + j * ld;
+    const T *p = P + j * ld, *q = Q + j * ld;
+    T pv[kElem], qv[kElem], xv[kElem], rv[kElem];
+#pragma unroll
+    for (int k = 0; k < kElem; ++k) {
+      const int64_t e = (int64_t)ch * kChunk + k * PT + threadIdx.x;
+      if (e < n) {
+        pv[k] = p[e];
+        qv[k] = q[e];
+        xv[k] = x[e];
+        rv[k] = r[e];
+      }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kElem; ++k) {
+      const int64_t e = (int64_t)ch * kChunk + k * PT + threadIdx.x;
+      if (e < n) {
+        x[e] = Sc<T>::axpy(a, pv[k], xv[k]);
+        const T rn = Sc<T>::axpy(-a, qv[k], rv[k]);
+        r[e] = rn;
+        acc = Sc<T>::nrm2(rn, acc);
+      }
+    }
+    double vv[1] = {acc};
+    block_sum<1, PT>(vv, s_red);
+    if (threadIdx.x == 0) s_colacc[j] += vv[0];
+  }
+  __syncthreads();
+  if (!col_reduce_barrier(g, epoch, bpart, s_colacc, nc, sred, s_vals, [&](int j, double s) { cg_update_fin(c, j, s); }))
+    return false;
+  // phase 4 on the columns still active
+  for (int j = threadIdx.x; j < nc; j += PT) {
+    s_act[j] = __ldcg(c.active + j);
+    s_a[j] = __ldcg(c.beta + j);
+  }
+  __syncthreads();
+  for (int item = blockIdx.x; item < nchunks * nc; item += gridDim.x) {
+    const int j = item / nchunks, ch = item - j * nchunks;
+    if (!s_act[j]) continue;
+    const double be = s_a[j];
+    const T *r = R + j * ld;
+    T *p = P + j * ld;
+    T pv[kElem], rv[kElem];
+#pragma unroll
+    for (int k = 0; k < kElem; ++k) {
+      const int64_t e = (int64_t)ch * kChunk + k * PT + threadIdx.x;
+      if (e < n) {
+        pv[k] = p[e];
+        rv[k] = r[e];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kElem; ++k) {
+      const int64_t e = (int64_t)ch * kChunk + k * PT + threadIdx.x;
+      if (e < n) p[e] = Sc<T>::axpy(be, pv[k], rv[k]);
+    }
+  }
+  return grid_sync(g, epoch);
+}
+
+SEED_DEV bool cg_load_active(const CgCols &c, int *s_act) {
+  for (int j = threadIdx.x; j < c.nc; j += PT) s_act[j] = __ldcg(c.active + j);
+  __syncthreads();
+  int any = 0;
+  for (int j = 0; j < c.nc; ++j) any |= s_act[j];
+  return any != 0;
+}
+
+__global__ void __launch_bounds__(PT) k_cg_run_wilson(WilsonOp op, const CallArgs *call, double2 *R, double2 *P,
+                                                       double2 *Q, double2 *tbuf, int64_t ld, CgCols c, GridSync g,
+                                                       double *bpart) {
+  __shared__ double sacc[4][24][kWilsonSites + 1];
+  __shared__ double sred[PT / 32][32];
+  __shared__ double s_vals[32];
+  __shared__ int s_act[kPersistMaxCols];
+  __shared__ double s_a[kPersistMaxCols];
+  __shared__ double s_colacc[kPersistMaxCols];
+  __shared__ double s_red[PT / 32];
+  const int64_t sites = op.sites, n = 12 * op.sites;
+  const int tiles = (int)((sites + kWilsonSites - 1) / kWilsonSites);
+  const int nc = c.nc;
+  const double kappa = op.kappa;
+  unsigned epoch = 0;
+  while (cg_load_active(c, s_act)) {
+    for (int item = blockIdx.x; item < tiles * nc; item += gridDim.x) {
+      const int j = item / tiles, tile = item - j * tiles;
+      if (!s_act[j]) continue;
+      const int64_t s0 = (int64_t)tile * kWilsonSites;
+      const double2 *p = P + j * ld;
+      double2 *t = tbuf + j * ld;
+      wilson_tile<+1>(op, p, s0, sacc);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
+        const int64_t ss = s0 + sl;
+        if (ss < sites) {
+          const double2 sum = tile_sum(sacc, cc, sl);
+          const int64_t e = 12 * ss + cc;
+          const double2 pv = p[e];
+          t[e] = c2(fma(-kappa, sum.x, pv.x), fma(-kappa, sum.y, pv.y));
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(g, epoch)) return;
+    for (int j = threadIdx.x; j < nc; j += PT) s_colacc[j] = 0.0;
+    __syncthreads();
+    for (int item = blockIdx.x; item < tiles * nc; item += gridDim.x) {
+      const int j = item / tiles, tile = item - j * tiles;
+      if (!s_act[j]) continue;
+      const int64_t s0 = (int64_t)tile * kWilsonSites;
+      const double2 *t = tbuf + j * ld, *p = P + j * ld;
+      double2 *q = Q + j * ld;
+      wilson_tile<-1>(op, t, s0, sacc);
+      double pq = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
+        const int64_t ss = s0 + sl;
+        if (ss < sites) {
+          const double2 sum = tile_sum(sacc, cc, sl);
+          const int64_t e = 12 * ss + cc;
+          const double2 tv = t[e], pv = p[e];
+          const double2 qv = c2(fma(-kappa, sum.x, tv.x), fma(-kappa, sum.y, tv.y));
+          q[e] = qv;
+          pq = fma(pv.y, qv.y, fma(pv.x, qv.x, pq));
+        }
+      }
+      double vv[1] = {pq};
+      block_sum<1, PT>(vv, s_red);
+      if (threadIdx.x == 0) s_colacc[j] += vv[0];
+    }
+    __syncthreads();
+    if (!col_reduce_barrier(g, epoch, bpart, s_colacc, nc, sred, s_vals,
+                            [&](int j, double s) { cg_alpha_fin(c, j, s); }))
+      return;
+    if (!cg_vector_phases<double2>(call, R, P, Q, ld, n, c, g, epoch, bpart, s_act, s_a, s_colacc, s_red, sred,
+                                   s_vals))
+      return;
+  }
+}
+
+__global__ void __launch_bounds__(PT) k_cg_run_csr(CsrOp op, const CallArgs *call, double *R, double *P, double *Q,
+                                                    int64_t ld, CgCols c, GridSync g, double *bpart) {
+  __shared__ double sred[PT / 32][32];
+  __shared__ double s_vals[32];
+  __shared__ int s_act[kPersistMaxCols];
+  __shared__ double s_a[kPersistMaxCols];
+  __shared__ double s_colacc[kPersistMaxCols];
+  __shared__ double s_red[PT / 32];
+  constexpr int kElem = elems_per_thread<double>(), kChunk = PT * kElem;
+  const int64_t n = op.n;
+  const int nc = c.nc;
+  const int nchunks = (int)((n + kChunk - 1) / kChunk);
+  unsigned epoch = 0;
+  while (cg_load_active(c, s_act)) {
+    for (int j = threadIdx.x; j < nc; j += PT) s_colacc[j] = 0.0;
+    __syncthreads();
+    for (int item = blockIdx.x; item < nchunks * nc; item += gridDim.x) {
+      const int j = item / nchunks, ch = item - j * nchunks;
+      if (!s_act[j]) continue;
+      const double *p = P + j * ld;
+      double *q = Q + j * ld;
+      double pq = 0.0;
+#pragma unroll
+      for (int k = 0; k < kElem; ++k) {
+        const int64_t r = (int64_t)ch * kChunk + k * PT + threadIdx.x;
+        if (r < n) {
+          const int32_t k0 = __ldg(op.row_ptr + r), k1 = __ldg(op.row_ptr + r + 1);
+          double s = 0.0;
+          for (int32_t kk = k0; kk < k1; ++kk) s = fma(__ldg(op.vals + kk), p[__ldg(op.col_idx + kk)], s);
+          q[r] = s;
+          pq = fma(p[r], s, pq);
+        }
+      }
+      double vv[1] = {pq};
+      block_sum<1, PT>(vv, s_red);
+      if (threadIdx.x == 0) s_colacc[j] += vv[0];
+    }
+    __syncthreads();
+    if (!col_reduce_barrier(g, epoch, bpart, s_colacc, nc, sred, s_vals,
+                            [&](int j, double s) { cg_alpha_fin(c, j, s); }))
+      return;
+    if (!cg_vector_phases<double>(call, R, P, Q, ld, n, c, g, epoch, bpart, s_act, s_a, s_colacc, s_red, sred,
+                                  s_vals))
+      return;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int persistent_grid(int kind, int sm_count) {
+  int per_sm = 0, per_sm2 = 0;
+  cudaError_t e;
+  if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed_run_csr, PT, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed_run_wilson, PT, 0);
+  if (e == cudaSuccess) {
+    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_run_csr, PT, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_run_wilson, PT, 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int b = per_sm < per_sm2 ? per_sm : per_sm2;
+  if (b > 2) b = 2;
+  return b * sm_count;
+}
+
+cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, double2 *gbuf,
+                                   GridSync g, double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s) {
+  SeedBufs<double2> bb = b;
+  WilsonOp o = op;
+  void *args[] = {&bb, &o, &tbuf, &gbuf, &g, &bpart, &tpart, &i_stop};
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson, dim3(grid), dim3(PT), args, 0, s);
+}
+cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, double2 *gbuf, GridSync g,
+                                double *bpart, int i_stop, int grid, cudaStream_t s) {
+  SeedBufs<double> bb = b;
+  CsrOp o = op;
+  void *args[] = {&bb, &o, &f2, &gbuf, &g, &bpart, &i_stop};
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_csr, dim3(grid), dim3(PT), args, 0, s);
+}
+cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,
+                                 double2 *tbuf, int64_t ld, const CgCols &c, GridSync g, double *bpart, int grid,
+                                 cudaStream_t s) {
+  WilsonOp o = op;
+  CgCols cc = c;
+  void *args[] = {&o, &call, &R, &P, &Q, &tbuf, &ld, &cc, &g, &bpart};
+  return cudaLaunchCooperativeKernel((const void *)k_cg_run_wilson, dim3(grid), dim3(PT), args, 0, s);
+}
+cudaError_t launch_cg_run_csr(const CsrOp &op, const CallArgs *call, double *R, double *P, double *Q, int64_t ld,
+                              const CgCols &c, GridSync g, double *bpart, int grid, cudaStream_t s) {
+  CsrOp o = op;
+  CgCols cc = c;
+  void *args[] = {&o, &call, &R, &P, &Q, &ld, &cc, &g, &bpart};
+  return cudaLaunchCooperativeKernel((const void *)k_cg_run_csr, dim3(grid), dim3(PT), args, 0, s);
+}
+
+}  // namespace seedk

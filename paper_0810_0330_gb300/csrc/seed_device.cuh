@@ -1,0 +1,92 @@
+// seed_device.cuh -- the scalar part of the Sec. 3 recurrence, shared by the
+// step-by-step kernels (krylov.cu) and the persistent kernels (persistent.cu).
+// Both run in thread 0 of the one block that holds the reduced sums.  In the
+// persistent kernels that block changes from step to step (it is whichever
+// block reaches the barrier last, on any SM), so state is read with L2 loads
+// (never from a stale L1 line written by another SM); all loads are issued
+// before their values are used, so their L2 round trips overlap.
+#pragma once
+#include <math.h>
+
+#include "device_common.cuh"
+#include "seed_internal.h"
+
+namespace seedk {
+
+// Steps 3/6 (delta_i, gamma_{i-1}, zeta_i) and 4/7 (eta^j) from alpha_i and
+// g^j = v_i^H r_0^j (sums[j], j = 1..nrhs-1); beta_{i-1} is st->beta_prev.
+template <class T>
+SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const double2 *sums) {
+  SeedState *st = b.st;
+  const double bp = __ldcg(&st->beta_prev), dprev = __ldcg(&st->delta), zprev = __ldcg(&st->zeta),
+               beta0 = __ldcg(&st->beta0);
+  const int nr = b.nrhs;
+  double2 e[kMaxRhs];
+#pragma unroll 16
+  for (int j = 1; j < nr; ++j) e[j] = __ldcg(b.eta + j);
+  double gam, del, zet;
+  if (i == 1) {           // step 3: delta_1 = alpha_1, zeta_1 = beta_0
+    gam = 0.0;
+    del = a;
+    zet = beta0;
+  } else {                // step 6
+    gam = bp / dprev;
+    del = a - gam * bp;
+    zet = -gam * zprev;
+  }
+#pragma unroll 16
+  for (int j = 1; j < nr; ++j) {   // steps 4 / 7
+    const double2 g = sums[j];
+    b.eta[j] = (i == 1) ? g : c2(g.x - gam * e[j].x, g.y - gam * e[j].y);
+  }
+  st->alpha = a;
+  st->gamma = gam;
+  st->delta = del;
+  st->zeta = zet;
+  b.alpha_hist[i] = a;
+  b.delta_hist[i] = del;
+  if (!(del > 0.0) || !isfinite(del)) {
+    st->active = 0;
+    st->stop_reason = STOP_NOTSPD;
+  }
+}
+
+// Sec. 3 step 9: beta_i = ||f||, residual estimate and the stopping test.
+template <class T>
+SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
+  SeedState *st = b.st;
+  const int i = __ldcg(&st->i);
+  const double alpha = __ldcg(&st->alpha), bp = __ldcg(&st->beta_prev), tnorm = __ldcg(&st->tnorm),
+               zeta = __ldcg(&st->zeta), delta = __ldcg(&st->delta), tol_abs = __ldcg(&st->tol_abs),
+               brel = __ldcg(&st->breakdown_rel);
+  int converged_at = __ldcg(&st->converged_at), stop_at = __ldcg(&st->stop_at);
+  const int extra = __ldcg(&st->extra_iters), m_max = __ldcg(&st->m_max);
+  const double beta = sqrt(sumsq);
+  b.beta_hist[i] = beta;
+  const double row = fabs(alpha) + (i > 1 ? bp : 0.0) + beta;
+  const double tn = row > tnorm ? row : tnorm;
+  const double rho = beta * fabs(zeta) / delta;
+  if (converged_at < 0 && rho <= tol_abs) {
+    converged_at = i;
+    stop_at = i + extra;
+  }
+  int stop = STOP_RUNNING;
+  if (beta <= brel * tn) stop = STOP_BREAKDOWN;
+  else if (stop_at >= 0 && i >= stop_at) stop = STOP_CONVERGED;
+  else if (i >= m_max) stop = STOP_MMAX;
+  st->tnorm = tn;
+  st->rho = rho;
+  st->beta = beta;
+  st->converged_at = converged_at;
+  st->stop_at = stop_at;
+  if (stop != STOP_RUNNING) {
+    st->active = 0;
+    st->stop_reason = stop;
+  } else {
+    st->beta_prev = beta;
+    st->inv_beta = 1.0 / beta;
+    st->i = i + 1;
+  }
+}
+
+}  // namespace seedk

@@ -10,7 +10,7 @@ constexpr int kMaxRhs = 64;       // right-hand sides per call
 constexpr int kVecThreads = 128;  // threads per block of the vector kernels
 
 // Stop reasons of the seed recurrence (SeedState::stop_reason)
-enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4 };
+enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4, STOP_TIMEOUT = 5 };
 
 // Device-resident scalars of the Sec. 3 recurrence (paper notation).
 struct SeedState {
@@ -94,6 +94,16 @@ struct CgCols {
   int32_t maxit, max_restarts;
 };
 
+// Grid barrier of the persistent kernels (all zeroed before every launch).
+constexpr int kGridSyncWords = 4 + 256;
+struct GridSync {
+  unsigned *count;       // arrivals, monotonic within a launch
+  unsigned *release;     // last epoch released by a reducing barrier
+  int *error;            // 1 after a barrier wait ran past its time limit
+  unsigned *owners;      // number of blocks that own operator tiles
+  unsigned *sm_slots;    // [256] blocks seen per SM id
+};
+
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -152,5 +162,26 @@ template <class T> void launch_project(int64_t n, const T *V, int64_t ldv, int m
 template <class T> void launch_copy_cols(const T *src, int64_t lds, T *dst, int64_t ldd, int64_t n, int ncols,
                                          cudaStream_t s);
 template <class T> void launch_zero_cols(T *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
+
+// Persistent cooperative kernels (persistent.cu).  Seed: runs Lanczos steps
+// i < i_stop (none of which reorthogonalizes) while the recurrence is active;
+// on leaving with i == i_stop it forms v_i in V and vcur for the step-by-step
+// path.  CG: runs lockstep iterations until no column is active.  Both return
+// cudaErrorCooperativeLaunchTooLarge and friends from the launch, and report a
+// barrier time-out through GridSync::error.  nrhs <= kPersistMaxRhs, nc <= 32.
+constexpr int kPersistMaxRhs = 16;
+constexpr int kPersistMaxCols = 32;
+int persistent_grid(int kind, int sm_count);
+// gbuf: [kPersistMaxRhs] device scratch for g^j of the next step.
+// tpart: one double per 32-site tile
+cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, double2 *gbuf,
+                                   GridSync g, double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
+cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, double2 *gbuf, GridSync g,
+                                double *bpart, int i_stop, int grid, cudaStream_t s);
+cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,
+                                 double2 *tbuf, int64_t ld, const CgCols &c, GridSync g, double *bpart, int grid,
+                                 cudaStream_t s);
+cudaError_t launch_cg_run_csr(const CsrOp &op, const CallArgs *call, double *R, double *P, double *Q, int64_t ld,
+                              const CgCols &c, GridSync g, double *bpart, int grid, cudaStream_t s);
 
 }  // namespace seedk

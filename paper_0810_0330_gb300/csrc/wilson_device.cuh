@@ -1,0 +1,134 @@
+// wilson_device.cuh -- device code of the Wilson-Dirac hop (spin projection,
+// SU(3) multiply, reconstruction), shared by the stand-alone operator kernels
+// (wilson.cu) and the persistent solver kernels (persistent.cu).
+//
+// In the chiral basis g_mu = [[0, B_mu], [B_mu^H, 0]] with 2x2 blocks whose
+// rows each hold one entry from {1, i, -1, -i}.  Hence (1 - s g_mu) psi has
+// upper half h = psi_up - s B_mu psi_dn and lower half -s B_mu^H h: a hop
+// multiplies only the two-spinor h by the link, 84 FP64 operations per hop.
+// Phases and boundary signs are register swaps and sign-bit XORs.
+//
+// NC selects how spinors are loaded: true = the read-only path (__ldg), for
+// kernels in which the input does not change; false = ordinary loads, for
+// persistent kernels that rewrite the input between grid barriers.  Ordinary
+// loads may hit L1 (the 8 hops of a site reuse each neighbour's spinor); they
+// see other blocks' writes because every grid barrier is a release (fence +
+// arrival) / acquire (acquire load + fence) pair followed by a CTA barrier.
+#pragma once
+#include "device_common.cuh"
+#include "seed_internal.h"
+
+namespace seedk {
+
+template <bool NC> SEED_DEV double2 ldv(const double2 *p) {
+  if constexpr (NC) return __ldg(p);
+  else return *p;
+}
+
+// ---------------------------------------------------------------------------
+// phases: code 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+// ---------------------------------------------------------------------------
+template <int C> SEED_DEV double2 ph_add(double2 z, double2 w) {   // z + phase(C) w
+  if constexpr (C == 0) return c2(z.x + w.x, z.y + w.y);
+  else if constexpr (C == 1) return c2(z.x - w.y, z.y + w.x);
+  else if constexpr (C == 2) return c2(z.x - w.x, z.y - w.y);
+  else return c2(z.x + w.y, z.y - w.x);
+}
+constexpr unsigned long long kSign = 0x8000000000000000ull;
+template <int C> SEED_DEV double2 ph_mul(double2 w) {              // phase(C) w, no FP64 op
+  if constexpr (C == 0) return w;
+  else if constexpr (C == 1) return c2(xsign(w.y, kSign), w.x);
+  else if constexpr (C == 2) return c2(xsign(w.x, kSign), xsign(w.y, kSign));
+  else return c2(w.y, xsign(w.x, kSign));
+}
+__host__ __device__ constexpr int ph_neg(int c) { return (c + 2) & 3; }
+__host__ __device__ constexpr int ph_conj(int c) { return (4 - c) & 3; }
+
+// B_mu row k has its one nonzero in column J(mu,k) with phase P(mu,k):
+//   B_x = [[0, i], [i, 0]], B_y = [[0, -1], [1, 0]], B_z = [[i, 0], [0, -i]], B_t = 1
+__host__ __device__ constexpr int bJ(int mu, int k) { return (mu <= 1) ? 1 - k : k; }
+__host__ __device__ constexpr int bP(int mu, int k) {
+  return mu == 0 ? 1 : mu == 1 ? (k == 0 ? 2 : 0) : mu == 2 ? (k == 0 ? 1 : 3) : 0;
+}
+
+// One hop of (1 - S g_MU) M psi(nb) into acc[spin*3 + colour];  M = U (FWD) or
+// U^H.  FIRST: acc is overwritten instead of accumulated.  neg: boundary sign.
+template <int MU, int S, bool FWD, bool FIRST, bool NC = true>
+SEED_DEV void hop(const double2 *__restrict__ psi, const double2 *__restrict__ U, unsigned long long neg,
+                  double2 (&acc)[12]) {
+  // h_k = psi_k - S * P(k) psi_{2+J(k)}
+  constexpr int c0 = S > 0 ? ph_neg(bP(MU, 0)) : bP(MU, 0);
+  constexpr int c1 = S > 0 ? ph_neg(bP(MU, 1)) : bP(MU, 1);
+  double2 h0[3], h1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2 p0 = ldv<NC>(psi + a), p1 = ldv<NC>(psi + 3 + a);
+    const double2 q0 = ldv<NC>(psi + 3 * (2 + bJ(MU, 0)) + a), q1 = ldv<NC>(psi + 3 * (2 + bJ(MU, 1)) + a);
+    h0[a] = ph_add<c0>(p0, q0);
+    h1[a] = ph_add<c1>(p1, q1);
+    h0[a].x = xsign(h0[a].x, neg); h0[a].y = xsign(h0[a].y, neg);
+    h1[a].x = xsign(h1[a].x, neg); h1[a].y = xsign(h1[a].y, neg);
+  }
+  double2 u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = __ldg(U + k);
+  // chi_k = M h_k
+  double2 x0[3], x1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if constexpr (FWD) {
+      x0[a] = cmul(u[3 * a], h0[0]);
+      x1[a] = cmul(u[3 * a], h1[0]);
+      x0[a] = cfma(u[3 * a + 1], h0[1], x0[a]);
+      x1[a] = cfma(u[3 * a + 1], h1[1], x1[a]);
+      x0[a] = cfma(u[3 * a + 2], h0[2], x0[a]);
+      x1[a] = cfma(u[3 * a + 2], h1[2], x1[a]);
+    } else {
+      double2 uc = c2(u[a].x, xsign(u[a].y, kSign));
+      x0[a] = cmul(uc, h0[0]);
+      x1[a] = cmul(uc, h1[0]);
+      x0[a] = cfmac(u[3 + a], h0[1], x0[a]);
+      x1[a] = cfmac(u[3 + a], h1[1], x1[a]);
+      x0[a] = cfmac(u[6 + a], h0[2], x0[a]);
+      x1[a] = cfmac(u[6 + a], h1[2], x1[a]);
+    }
+  }
+  // upper spins get chi; lower spin 2+J(k) gets -S conj(P(k)) chi_k
+  constexpr int l0 = S > 0 ? ph_neg(ph_conj(bP(MU, 0))) : ph_conj(bP(MU, 0));
+  constexpr int l1 = S > 0 ? ph_neg(ph_conj(bP(MU, 1))) : ph_conj(bP(MU, 1));
+  constexpr int s0 = 2 + bJ(MU, 0), s1 = 2 + bJ(MU, 1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if constexpr (FIRST) {
+      acc[a] = x0[a];
+      acc[3 + a] = x1[a];
+      acc[3 * s0 + a] = ph_mul<l0>(x0[a]);
+      acc[3 * s1 + a] = ph_mul<l1>(x1[a]);
+    } else {
+      acc[a] = cadd(acc[a], x0[a]);
+      acc[3 + a] = cadd(acc[3 + a], x1[a]);
+      acc[3 * s0 + a] = ph_add<l0>(acc[3 * s0 + a], x0[a]);
+      acc[3 * s1 + a] = ph_add<l1>(acc[3 * s1 + a], x1[a]);
+    }
+  }
+}
+
+template <int MU, int S, bool NC = true>
+SEED_DEV void site_mu(const WilsonOp &op, const double2 *__restrict__ in, int64_t s, double2 (&acc)[12]) {
+  const int32_t nf = __ldg(op.nbr + 8 * s + 2 * MU);
+  const int32_t nb = __ldg(op.nbr + 8 * s + 2 * MU + 1);
+  unsigned long long negf = 0ull, negb = 0ull;
+  if (MU == 3 && op.bc_t) {
+    const int64_t slab = (int64_t)op.dims[0] * op.dims[1] * op.dims[2];
+    const int64_t t = s / slab;
+    if (t == op.dims[3] - 1) negf = kSign;
+    if (t == 0) negb = kSign;
+  }
+  // forward: (1 - S g) U_mu(s) psi(s + mu); backward: (1 + S g) U_mu(s - mu)^H psi(s - mu)
+  hop<MU, S, true, true, NC>(in + 12 * (int64_t)nf, op.links + ((int64_t)MU * op.sites + s) * 9, negf, acc);
+  hop<MU, -S, false, false, NC>(in + 12 * (int64_t)nb, op.links + ((int64_t)MU * op.sites + nb) * 9, negb, acc);
+}
+
+constexpr int kWilsonSites = 32;   // sites per block; 4 warps (one per mu)
+
+}  // namespace seedk

@@ -25,26 +25,15 @@ def laplacian_2d_csr(n1: int, n2: int):
     diagonal, -1 per neighbour).  Row r = i + n1*j (i fastest); columns are
     ascending within each row.  Returns (row_ptr i32, col_idx i32, vals f64)."""
     n = n1 * n2
-    row_ptr = np.zeros(n + 1, dtype=np.int32)
-    cols, vals = [], []
-    for j in range(n2):
-        for i in range(n1):
-            r = i + n1 * j
-            entries = []
-            if j > 0:
-                entries.append((r - n1, -1.0))
-            if i > 0:
-                entries.append((r - 1, -1.0))
-            entries.append((r, 4.0))
-            if i < n1 - 1:
-                entries.append((r + 1, -1.0))
-            if j < n2 - 1:
-                entries.append((r + n1, -1.0))
-            for c, v in entries:
-                cols.append(c)
-                vals.append(v)
-            row_ptr[r + 1] = len(cols)
-    return row_ptr, np.asarray(cols, dtype=np.int32), np.asarray(vals, dtype=np.float64)
+    r = np.arange(n, dtype=np.int64)
+    i, j = r % n1, r // n1
+    # candidate entries of each row in ascending column order: r-n1, r-1, r, r+1, r+n1
+    cand = np.stack([r - n1, r - 1, r, r + 1, r + n1], axis=1)
+    ok = np.stack([j > 0, i > 0, np.ones(n, dtype=bool), i < n1 - 1, j < n2 - 1], axis=1)
+    v = np.broadcast_to(np.array([-1.0, -1.0, 4.0, -1.0, -1.0]), (n, 5))
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(ok.sum(axis=1), out=row_ptr[1:])
+    return row_ptr.astype(np.int32), cand[ok].astype(np.int32), np.ascontiguousarray(v[ok], dtype=np.float64)
 
 
 def laplacian_3d_csr(n1: int, n2: int, n3: int, shift: float = 0.0):

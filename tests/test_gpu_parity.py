@@ -178,12 +178,14 @@ def compare_full(orc_res, info1, info2, Xs, X, label, seeded_tol=REL_X, final_to
         assert g["true_relres"] <= 1.5e-8
 
 
-def test_seed_config_laplacian_64(seedlib, orc):
+@pytest.mark.parametrize("kernel_path", [0, 1, 2])
+def test_seed_config_laplacian_64(seedlib, orc, kernel_path):
     """64x64 Laplacian, 4 Gaussian RHS (seed 0), seed to 1e-12 with full
-    reorthogonalization, then CG to 1e-8."""
+    reorthogonalization, then CG to 1e-8 (persistent CG kernel on path 0,
+    step kernels on path 1)."""
     rp, ci, v = I.laplacian_2d_csr(64, 64)
     B = I.gaussian_rhs(4096, 4, seed=0)
-    prm = dict(m_max=4096, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8, keep_basis=1)
+    prm = dict(m_max=4096, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8, keep_basis=1, kernel_path=kernel_path)
     ctx = csr_ctx(seedlib, rp, ci, v, **prm)
     info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
     op = orc.Operator.csr(rp, ci, v)
@@ -200,16 +202,18 @@ def test_seed_config_laplacian_64(seedlib, orc):
     assert info1[0]["true_relres"] < 1e-11
 
 
-@pytest.mark.parametrize("freq,passes", [(1, 2), (5, 1), (0, 2), (7, 2)])
-def test_seed_wilson_small(seedlib, orc, freq, passes):
+@pytest.mark.parametrize("kernel_path", [0, 1, 2])
+@pytest.mark.parametrize("freq,passes", [(1, 2), (5, 1), (0, 2), (7, 2), (10, 2)])
+def test_seed_wilson_small(seedlib, orc, freq, passes, kernel_path):
     """3x4x5x6 lattice (n = 4320, sites not a multiple of the block), kappa
-    0.14, antiperiodic t, 5 point-source-derived RHS b = D^H eta."""
+    0.14, antiperiodic t, 5 point-source-derived RHS b = D^H eta.  Frequencies
+    0 and 10 run the seed in persistent segments on path 0."""
     dims, kappa = (3, 4, 5, 6), 0.14
     U = I.random_su3_links(dims, 0.3, seed=7)
     eta = I.point_sources(dims, 5, site=17)
     B = np.stack([orc.wilson_dslash(dims, kappa, 1, -1, U, eta[:, j]) for j in range(5)], axis=1)
     ctx = wilson_ctx(seedlib, dims, kappa, U, bc_t=1, m_max=600, reorth_freq=freq, reorth_passes=passes,
-                     tol_seed=1e-12, tol_rest=1e-8)
+                     tol_seed=1e-12, tol_rest=1e-8, kernel_path=kernel_path)
     info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
     op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
     ref = orc.seed_solve_all(op, B, m_max=600, reorth_freq=freq, reorth_passes=passes, tol_seed=1e-12,
@@ -220,23 +224,39 @@ def test_seed_wilson_small(seedlib, orc, freq, passes):
                  final_tol=max(REL_X, 10 * s_final))
 
 
+_WORKLOAD_REF = {}
+
+
+def _workload_reference(orc):
+    """Oracle solution of the benchmark workload and its one-ulp sensitivity (computed once)."""
+    if not _WORKLOAD_REF:
+        dims, kappa = (8, 8, 8, 8), 0.155
+        U = I.random_su3_links(dims, 0.3, seed=0)
+        eta = I.point_sources(dims, 12)
+        B = np.stack([orc.wilson_dslash(dims, kappa, 0, -1, U, eta[:, j]) for j in range(12)], axis=1)
+        op = orc.Operator.wilson(dims, kappa, U)
+        ref = orc.seed_solve_all(op, B, m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12,
+                                 tol_rest=1e-8)
+        sens = self_sensitivity(orc, op, B, ref, cols=(1, 6), m_max=3000, reorth_freq=100, reorth_passes=2,
+                                tol=1e-12)
+        _WORKLOAD_REF.update(dims=dims, kappa=kappa, U=U, B=B, ref=ref, sens=sens, tridiag=self_sensitivity.tridiag)
+    return _WORKLOAD_REF
+
+
 @pytest.mark.slow
-def test_seed_wilson_8_4_full_workload(seedlib, orc):
+@pytest.mark.parametrize("kernel_path", [0, 1, 2])
+def test_seed_wilson_8_4_full_workload(seedlib, orc, kernel_path):
     """The benchmark workload: 8^4 lattice, kappa 0.155, links exp(0.3 i H)
     from seed 0, 12 unit point sources, b = D^H eta, seed to 1e-12 with
     reorthogonalization every 100 steps (two CGS passes), then CG to 1e-8.
-    All 12 solutions against the oracle."""
-    dims, kappa = (8, 8, 8, 8), 0.155
-    U = I.random_su3_links(dims, 0.3, seed=0)
-    eta = I.point_sources(dims, 12)
-    B = np.stack([orc.wilson_dslash(dims, kappa, 0, -1, U, eta[:, j]) for j in range(12)], axis=1)
-    prm = dict(m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
+    All 12 solutions against the oracle, on both kernel paths."""
+    w = _workload_reference(orc)
+    dims, kappa, U, B, ref = w["dims"], w["kappa"], w["U"], w["B"], w["ref"]
+    prm = dict(m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8, kernel_path=kernel_path)
     ctx = wilson_ctx(seedlib, dims, kappa, U, **prm)
     info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
-    op = orc.Operator.wilson(dims, kappa, U)
-    ref = orc.seed_solve_all(op, B, m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
-    s_seed, s_final = self_sensitivity(orc, op, B, ref, cols=(1, 6), m_max=3000, reorth_freq=100,
-                                       reorth_passes=2, tol=1e-12)
+    s_seed, s_final = w["sens"]
+    self_sensitivity.tridiag = w["tridiag"]
     compare_full(ref, info1, info2, Xs, X, "wilson-8^4", seeded_tol=max(REL_X, 10 * s_seed),
                  final_tol=max(REL_X, 10 * s_final))
     # the Lanczos coefficients of the late steps inherit the same sensitivity (the
