@@ -37,6 +37,11 @@ WORKLOAD_NAME = "wilson-dirac 8^4 kappa=0.155 A=D^H D, 12 point sources, seed to
 FLOPS_PER_SITE_D = 1368
 # FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+try:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _fh:
+        MEASURED_PEAKS = json.load(_fh)
+except (OSError, ValueError):
+    MEASURED_PEAKS = {}
 # DRAM bytes of one k_dslash launch (8^4, 11 columns) from an ncu capture of these sources of the kernel
 # (profiles/k_dslash_wilson_8x4_11cols.md); reported only while the source is unchanged.
 DSLASH_TRAFFIC = {"02a95cdef80a3640": 11.210752e6 + 0.0}
@@ -69,6 +74,11 @@ def parse():
     ap.add_argument("--dims", default=None, help="lattice for --kernel-only, e.g. 16,16,16,16")
     ap.add_argument("--ncols", type=int, default=None, help="columns for --kernel-only")
     ap.add_argument("--reps", type=int, default=20, help="timed launches for --kernel-only")
+    ap.add_argument("--csr-side", type=int, default=None,
+                    help="--kernel-only on the 2-d Laplacian CSR of this side instead of the Wilson operator")
+    ap.add_argument("--sweep", action="store_true",
+                    help="operator-apply bandwidth sweep (CSR Laplacian and Wilson D at growing sizes)")
+    ap.add_argument("--sweep-max", type=int, default=3, help="sweep points per operator (1..4)")
     return ap.parse_args()
 
 
@@ -200,6 +210,72 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# operator-apply sweep: sizes below and above the 129 MB L2
+# ---------------------------------------------------------------------------
+L2_BYTES = 129e6
+
+
+def csr_bytes(n, nnz):
+    """Algorithmic bytes of one CSR apply: values and column indices once, the
+    row pointers, x once, y written once."""
+    return 12 * nnz + 4 * (n + 1) + 16 * n
+
+
+def wilson_bytes(sites, ncols):
+    """Algorithmic bytes of one D apply: links (4 x 144 B per site, each read
+    once and used by both hops), input and output spinors (192 B each) per column."""
+    return sites * (576 + 384 * ncols)
+
+
+def run_sweep(args):
+    import torch
+    from paper_0810_0330_gb300 import binding as S
+    from paper_0810_0330_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    hbm = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
+    pts = []
+    for side in (64, 512, 2048, 4096)[:args.sweep_max + 1]:
+        rp, ci, v = I.laplacian_2d_csr(side, side)
+        n, nnz = side * side, ci.shape[0]
+        ctx = S.seed_create_csr(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                                torch.from_numpy(v).to(dev), S.seed_params_default(m_max=4))
+        reps = max(20, min(2000, int(2e9 / csr_bytes(n, nnz))))
+        ms = S.seed_time_operator(ctx, 0, 1, reps)
+        b = csr_bytes(n, nnz)
+        pts.append({"op": "csr_spmv", "kernel": "k_csr_spmv", "n": n, "nnz": nnz, "ncols": 1, "ms": ms,
+                    "bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac_hbm": b / (ms * 1e-3) / 1e9 / hbm,
+                    "l2_resident": b < L2_BYTES, "reps": reps})
+        S.seed_destroy(ctx)
+        del rp, ci, v
+    for L in (8, 16, 24)[:args.sweep_max]:
+        dims = (L, L, L, L)
+        sites = L ** 4
+        U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
+        ctx = S.seed_create_wilson(dims, WL["kappa"], U, S.seed_params_default(m_max=4))
+        for ncols in (1, 11):
+            b = wilson_bytes(sites, ncols)
+            reps = max(10, min(500, int(4e9 / b)))
+            ms = S.seed_time_operator(ctx, 1, ncols, reps)
+            fl = FLOPS_PER_SITE_D * sites * ncols
+            pts.append({"op": "wilson_D", "kernel": "k_dslash<+1>", "dims": dims, "n": 12 * sites, "ncols": ncols,
+                        "ms": ms, "bytes": b, "gbs": b / (ms * 1e-3) / 1e9, "frac_hbm": b / (ms * 1e-3) / 1e9 / hbm,
+                        "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64": fl / (ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                        "l2_resident": b < L2_BYTES, "reps": reps})
+        S.seed_destroy(ctx)
+        del U
+        torch.cuda.empty_cache()
+    for p in pts:
+        for k in ("ms", "gbs", "frac_hbm", "tflops", "frac_fp64"):
+            if k in p:
+                p[k] = round(p[k], 5)
+    print(json.dumps({"sweep": pts, "hbm_peak_gbs": hbm, "fp64_peak_tflops": FP64_PEAK_GFLOPS / 1e3,
+                      "timing": "mean of back-to-back launches on the same buffers (CUDA events, library stream)"}),
+          flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -217,6 +293,16 @@ def run_ours(args):
     from paper_0810_0330_gb300 import binding as S
     from paper_0810_0330_gb300 import inputs as I
 
+    if args.kernel_only and args.csr_side:
+        rp, ci, v = I.laplacian_2d_csr(args.csr_side, args.csr_side)
+        ctx = S.seed_create_csr(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                                torch.from_numpy(v).to(dev), S.seed_params_default(m_max=4))
+        ms = S.seed_time_operator(ctx, 0, 1, args.reps)
+        b = csr_bytes(args.csr_side ** 2, ci.shape[0])
+        print(json.dumps({"kernel": "k_csr_spmv", "n": args.csr_side ** 2, "nnz": int(ci.shape[0]), "ms": ms,
+                          "bytes": b, "gbs": b / (ms * 1e-3) / 1e9}), flush=True)
+        S.seed_destroy(ctx)
+        return 0
     dims, kappa, nrhs = WL["dims"], WL["kappa"], WL["nrhs"]
     if args.kernel_only and args.dims:
         dims = tuple(int(x) for x in args.dims.split(","))
@@ -354,6 +440,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.sweep:
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -29,8 +29,31 @@ SEED_DEV double2 cfmac(double2 a, double2 b, double2 acc) {
   return c2(fma(a.y, b.y, fma(a.x, b.x, acc.x)), fma(-a.y, b.x, fma(a.x, b.y, acc.y)));
 }
 
+// single precision complex (mixed-precision path: FP32 vectors, FP64 scalars)
+SEED_DEV float2 c2(float re, float im) { return make_float2(re, im); }
+SEED_DEV float2 cadd(float2 a, float2 b) { return c2(a.x + b.x, a.y + b.y); }
+SEED_DEV float2 csub(float2 a, float2 b) { return c2(a.x - b.x, a.y - b.y); }
+SEED_DEV float2 cmul(float2 a, float2 b) { return c2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
+SEED_DEV float2 cfma(float2 a, float2 b, float2 acc) {
+  return c2(fmaf(-a.y, b.y, fmaf(a.x, b.x, acc.x)), fmaf(a.y, b.x, fmaf(a.x, b.y, acc.y)));
+}
+SEED_DEV float2 cfmac(float2 a, float2 b, float2 acc) {
+  return c2(fmaf(a.y, b.y, fmaf(a.x, b.x, acc.x)), fmaf(-a.y, b.x, fmaf(a.x, b.y, acc.y)));
+}
+
+// Vector element traits.  Scalars of the recurrences are always FP64 (double,
+// double2); A / A2 are the per-thread accumulator types of dot products (FP64
+// for FP64 vectors; FP32 for FP32 vectors, whose per-thread sums cover a few
+// dozen elements and are widened to FP64 before the block and grid sums).
+// caxpy2 takes a coefficient already converted to A2 (staged once per block).
 template <class T> struct Sc;
 template <> struct Sc<double> {
+  using A = double;
+  using A2 = double2;
+  static SEED_DEV double2 zero2() { return c2(0.0, 0.0); }
+  static SEED_DEV double2 pair(double re, double im) { return c2(re, im); }
+  static SEED_DEV double2 from2(double2 a) { return a; }
+  static SEED_DEV double caxpy2(double2 a, double x, double y) { return fma(a.x, x, y); }
   static SEED_DEV double zero() { return 0.0; }
   static SEED_DEV double scale(double s, double x) { return s * x; }
   static SEED_DEV double axpy(double a, double x, double y) { return fma(a, x, y); }          // y + a x
@@ -42,6 +65,12 @@ template <> struct Sc<double> {
   static SEED_DEV double add(double a, double b) { return a + b; }
 };
 template <> struct Sc<double2> {
+  using A = double;
+  using A2 = double2;
+  static SEED_DEV double2 zero2() { return c2(0.0, 0.0); }
+  static SEED_DEV double2 pair(double re, double im) { return c2(re, im); }
+  static SEED_DEV double2 from2(double2 a) { return a; }
+  static SEED_DEV double2 caxpy2(double2 a, double2 x, double2 y) { return cfma(a, x, y); }
   static SEED_DEV double2 zero() { return c2(0.0, 0.0); }
   static SEED_DEV double2 scale(double s, double2 x) { return c2(s * x.x, s * x.y); }
   static SEED_DEV double2 axpy(double a, double2 x, double2 y) { return c2(fma(a, x.x, y.x), fma(a, x.y, y.y)); }
@@ -51,6 +80,26 @@ template <> struct Sc<double2> {
   static SEED_DEV double nrm2(double2 a, double acc) { return fma(a.y, a.y, fma(a.x, a.x, acc)); }
   static SEED_DEV double2 sub(double2 a, double2 b) { return csub(a, b); }
   static SEED_DEV double2 add(double2 a, double2 b) { return cadd(a, b); }
+};
+template <> struct Sc<float2> {
+  using A = float;
+  using A2 = float2;
+  static SEED_DEV float2 zero2() { return c2(0.f, 0.f); }
+  static SEED_DEV float2 pair(float re, float im) { return c2(re, im); }
+  static SEED_DEV float2 from2(double2 a) { return c2((float)a.x, (float)a.y); }
+  static SEED_DEV float2 caxpy2(float2 a, float2 x, float2 y) { return cfma(a, x, y); }
+  static SEED_DEV float2 zero() { return c2(0.f, 0.f); }
+  static SEED_DEV float2 scale(double s, float2 x) { const float f = (float)s; return c2(f * x.x, f * x.y); }
+  static SEED_DEV float2 axpy(double a, float2 x, float2 y) {
+    const float f = (float)a;
+    return c2(fmaf(f, x.x, y.x), fmaf(f, x.y, y.y));
+  }
+  static SEED_DEV float2 caxpy(double2 a, float2 x, float2 y) { return cfma(from2(a), x, y); }
+  static SEED_DEV float redot(float2 a, float2 b, float acc) { return fmaf(a.y, b.y, fmaf(a.x, b.x, acc)); }
+  static SEED_DEV float2 dotc(float2 a, float2 b, float2 acc) { return cfmac(a, b, acc); }
+  static SEED_DEV float nrm2(float2 a, float acc) { return fmaf(a.y, a.y, fmaf(a.x, a.x, acc)); }
+  static SEED_DEV float2 sub(float2 a, float2 b) { return csub(a, b); }
+  static SEED_DEV float2 add(float2 a, float2 b) { return cadd(a, b); }
 };
 
 // ---------------------------------------------------------------------------
@@ -165,5 +214,19 @@ SEED_DEV double warp_sum_partials(const double *partial, int nb, int stride, int
 SEED_DEV double xsign(double x, unsigned long long m) {
   return __longlong_as_double(__double_as_longlong(x) ^ m);
 }
+SEED_DEV float xsign(float x, unsigned m) { return __int_as_float(__float_as_int(x) ^ (int)m); }
+
+// Sign-bit masks of the complex element types (phases by XOR, no FP op).
+template <class C> struct CxBits;
+template <> struct CxBits<double2> {
+  using R = double;
+  using U = unsigned long long;
+  static constexpr U sign = 0x8000000000000000ull;
+};
+template <> struct CxBits<float2> {
+  using R = float;
+  using U = unsigned;
+  static constexpr U sign = 0x80000000u;
+};
 
 }  // namespace seedk

@@ -49,13 +49,13 @@ int col_blocks(int64_t n, int nc) {
 template <class T>
 __global__ void __launch_bounds__(NT) k_seed_start(SeedBufs<T> b, const T *__restrict__ r01) {
   __shared__ double sm[NT / 32];
-  double acc = 0.0;
+  typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, b.n) {
     const T r = r01[e];
     b.f[e] = r;
     acc = Sc<T>::nrm2(r, acc);
   }
-  double v[1] = {acc};
+  double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
   if (threadIdx.x == 0) b.partials[blockIdx.x] = v[0];
   if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
   for (int ch = 0; ch < nch; ++ch) {
     const int j0 = 1 + kDotsPerChunk * ch;
     const int jn = nr - j0 < kDotsPerChunk ? nr - j0 : kDotsPerChunk;   // may be <= 0
-    double acc[32];
+    typename Sc<T>::A acc[32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 32; ++q) acc[q] = 0;
     GRID_STRIDE(e, b.n) {
       const T v = vi[e];
       if (ch == 0) {
@@ -137,13 +137,16 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
 #pragma unroll
       for (int q = 0; q < kDotsPerChunk; ++q) {
         if (q < jn) {
-          const double2 d = Sc<T>::dotc(v, b.R0[(int64_t)(j0 + q - 1) * b.ldr + e], c2(acc[1 + 2 * q], acc[2 + 2 * q]));
+          const auto d = Sc<T>::dotc(v, b.R0[(int64_t)(j0 + q - 1) * b.ldr + e], Sc<T>::pair(acc[1 + 2 * q], acc[2 + 2 * q]));
           acc[1 + 2 * q] = d.x;
           acc[2 + 2 * q] = d.y;
         }
       }
     }
-    const double mine = warp_reduce_scatter32(acc);
+    double accd[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) accd[q] = (double)acc[q];
+    const double mine = warp_reduce_scatter32(accd);
     sred[warp][lane] = mine;
     __syncthreads();
     if (threadIdx.x < 32)
@@ -177,16 +180,16 @@ template <class T, bool NORM>
 __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
   SeedState *st = b.st;
   if (!st->active) return;
-  __shared__ double2 s_eta[kMaxRhs];
+  __shared__ typename Sc<T>::A2 s_eta[kMaxRhs];
   __shared__ double sm[NT / 32];
-  for (int j = threadIdx.x; j < b.nrhs; j += NT) s_eta[j] = b.eta[j];
+  for (int j = threadIdx.x; j < b.nrhs; j += NT) s_eta[j] = Sc<T>::from2(b.eta[j]);
   __syncthreads();
   const int i = st->i;
   const double a = st->alpha, zeta = st->zeta, inv_d = 1.0 / st->delta, bp = st->beta_prev;
   const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
   const int64_t ldx = b.call->ldx;
   T *const X = reinterpret_cast<T *>(b.call->X);
-  double acc = 0.0;
+  typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, b.n) {
     const T ve = vi[e];
     const T fe = Sc<T>::axpy(-a, ve, b.f[e]);
@@ -195,11 +198,11 @@ __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
     b.w[e] = we;
     T *x = X + e;
     x[0] = Sc<T>::axpy(zeta, we, x[0]);
-    for (int j = 1; j < b.nrhs; ++j) x[j * ldx] = Sc<T>::caxpy(s_eta[j], we, x[j * ldx]);
+    for (int j = 1; j < b.nrhs; ++j) x[j * ldx] = Sc<T>::caxpy2(s_eta[j], we, x[j * ldx]);
     if (NORM) acc = Sc<T>::nrm2(fe, acc);
   }
   if (!NORM) return;
-  double v[1] = {acc};
+  double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
   if (threadIdx.x == 0) b.partials[blockIdx.x] = v[0];
   if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
@@ -220,9 +223,9 @@ template <class T>
 SEED_DEV void gram_tile(const T *__restrict__ V, int64_t ldv, int64_t n, int rows, int rb, int c0, int nc,
                         const T *__restrict__ F0, const T *__restrict__ F1, double2 *Hpart, int kcap,
                         double (*sred)[32]) {
-  double2 acc[8][2];
+  typename Sc<T>::A2 acc[8][2];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = c2(0.0, 0.0);
+  for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = Sc<T>::zero2();
   const int64_t r0 = (int64_t)rb * rows;
   const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += NT) {
@@ -294,21 +297,22 @@ __global__ void __launch_bounds__(NT) k_reorth_reduce(SeedBufs<T> b, ReorthBufs<
 template <class T>
 SEED_DEV void gram_update(const T *__restrict__ V, int64_t ldv, int64_t n, int k, const double2 *__restrict__ H,
                           T *F0, T *F1, double sgn) {
-  __shared__ double2 sH[256][2];
+  __shared__ typename Sc<T>::A2 sH[256][2];
   const int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x;
   const bool valid = row < n;
   T a0 = Sc<T>::zero(), a1 = Sc<T>::zero();
   for (int c0 = 0; c0 < k; c0 += 256) {
     const int cn = (k - c0 < 256) ? k - c0 : 256;
     __syncthreads();
-    for (int q = threadIdx.x; q < 2 * cn; q += NT) sH[q >> 1][q & 1] = H[(int64_t)(c0 + (q >> 1)) * 2 + (q & 1)];
+    for (int q = threadIdx.x; q < 2 * cn; q += NT)
+      sH[q >> 1][q & 1] = Sc<T>::from2(H[(int64_t)(c0 + (q >> 1)) * 2 + (q & 1)]);
     __syncthreads();
     if (valid) {
       const T *vr = V + row + (int64_t)c0 * ldv;
       for (int c = 0; c < cn; ++c) {
         const T v = vr[(int64_t)c * ldv];
-        a0 = Sc<T>::caxpy(sH[c][0], v, a0);
-        a1 = Sc<T>::caxpy(sH[c][1], v, a1);
+        a0 = Sc<T>::caxpy2(sH[c][0], v, a0);
+        a1 = Sc<T>::caxpy2(sH[c][1], v, a1);
       }
     }
   }
@@ -333,9 +337,9 @@ __global__ void __launch_bounds__(NT) k_reorth_norm_vi(SeedBufs<T> b) {
   if (!st->active) return;
   __shared__ double sm[NT / 32];
   const T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
-  double acc = 0.0;
+  typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, b.n) acc = Sc<T>::nrm2(vi[e], acc);
-  double v[1] = {acc};
+  double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
   if (threadIdx.x == 0) b.partials[blockIdx.x] = v[0];
   if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
@@ -351,13 +355,13 @@ __global__ void __launch_bounds__(NT) k_reorth_scale_dot(SeedBufs<T> b) {
   __shared__ double sm[2 * NT / 32];
   T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
   const double sc = st->scratch;
-  double2 acc = c2(0.0, 0.0);
+  typename Sc<T>::A2 acc = Sc<T>::zero2();
   GRID_STRIDE(e, b.n) {
     const T v = Sc<T>::scale(sc, vi[e]);
     vi[e] = v;
     acc = Sc<T>::dotc(v, b.f[e], acc);
   }
-  double v[2] = {acc.x, acc.y};
+  double v[2] = {(double)acc.x, (double)acc.y};
   block_sum<2, NT>(v, sm);
   if (threadIdx.x == 0) {
     b.partials[blockIdx.x * 2] = v[0];
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(NT) k_reorth_axpy(SeedBufs<T> b) {
   const T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
   const double2 h = st->h;
   const double2 mh = c2(-h.x, -h.y);
-  double2 acc = c2(0.0, 0.0);
+  typename Sc<T>::A2 acc = Sc<T>::zero2();
   GRID_STRIDE(e, b.n) {
     const T v = vi[e];
     const T fe = Sc<T>::caxpy(mh, v, b.f[e]);
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(NT) k_reorth_axpy(SeedBufs<T> b) {
     if (DOT) acc = Sc<T>::dotc(v, fe, acc);
     else acc.x = Sc<T>::nrm2(fe, acc.x);
   }
-  double v[2] = {acc.x, acc.y};
+  double v[2] = {(double)acc.x, (double)acc.y};
   block_sum<2, NT>(v, sm);
   if (threadIdx.x == 0) {
     b.partials[blockIdx.x * 2] = v[0];
@@ -534,9 +538,9 @@ __global__ void __launch_bounds__(NT) k_colnorms(int64_t n, const T *X, int64_t 
   __shared__ double sm[NT / 32];
   const int col = blockIdx.y;
   X += (int64_t)col * ldx;
-  double acc = 0.0;
+  typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, n) acc = Sc<T>::nrm2(X[e], acc);
-  double v[1] = {acc};
+  double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
   if (threadIdx.x == 0) partials[(int64_t)col * gridDim.x + blockIdx.x] = v[0];
   if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
@@ -581,7 +585,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(int64_t n, const T *B, int64_t l
   Q += (int64_t)col * ldq;
   R += (int64_t)col * ld;
   P += (int64_t)col * ld;
-  double rr = 0.0, bb = 0.0;
+  typename Sc<T>::A rr = 0, bb = 0;
   GRID_STRIDE(e, n) {
     const T bv = B[e];
     const T r = Sc<T>::sub(bv, Q[e]);
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(int64_t n, const T *B, int64_t l
     rr = Sc<T>::nrm2(r, rr);
     bb = Sc<T>::nrm2(bv, bb);
   }
-  double v[2] = {rr, bb};
+  double v[2] = {(double)rr, (double)bb};
   block_sum<2, NT>(v, sm);
   double *part = partials + (int64_t)col * gridDim.x * 2;
   if (threadIdx.x == 0) {
@@ -625,9 +629,9 @@ __global__ void __launch_bounds__(NT) k_cg_alpha(int64_t n, const T *P, const T 
   if (!c.active[col]) return;
   P += (int64_t)col * ld;
   Q += (int64_t)col * ld;
-  double acc = 0.0;
+  typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, n) acc = Sc<T>::redot(P[e], Q[e], acc);
-  double v[1] = {acc};
+  double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
   double *part = partials + (int64_t)col * gridDim.x;
   if (threadIdx.x == 0) part[blockIdx.x] = v[0];
@@ -649,14 +653,14 @@ __global__ void __launch_bounds__(NT) k_cg_update(int64_t n, const CallArgs *cal
   P += (int64_t)col * ld;
   Q += (int64_t)col * ld;
   const double a = c.alpha[col];
-  double acc = 0.0;
+  typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, n) {
     X[e] = Sc<T>::axpy(a, P[e], X[e]);
     const T r = Sc<T>::axpy(-a, Q[e], R[e]);
     R[e] = r;
     acc = Sc<T>::nrm2(r, acc);
   }
-  double v[1] = {acc};
+  double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
   double *part = partials + (int64_t)col * gridDim.x;
   if (threadIdx.x == 0) part[blockIdx.x] = v[0];
@@ -707,13 +711,13 @@ __global__ void __launch_bounds__(NT) k_cg_check(int64_t n, const T *B, int64_t 
   B += (int64_t)col * ldb;
   Q += (int64_t)col * ldq;
   R += (int64_t)col * ld;
-  double acc = 0.0;
+  typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, n) {
     const T r = Sc<T>::sub(B[e], Q[e]);
     R[e] = r;
     acc = Sc<T>::nrm2(r, acc);
   }
-  double v[1] = {acc};
+  double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
   double *part = partials + (int64_t)col * gridDim.x;
   if (threadIdx.x == 0) part[blockIdx.x] = v[0];
@@ -793,5 +797,6 @@ void launch_cg_check(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq
 
 SEED_INSTANTIATE(double)
 SEED_INSTANTIATE(double2)
+SEED_INSTANTIATE(float2)
 
 }  // namespace seedk

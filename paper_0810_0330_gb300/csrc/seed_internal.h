@@ -109,18 +109,24 @@ struct GridSync {
 // ---------------------------------------------------------------------------
 
 // Wilson-Dirac (wilson.cu).  sign = +1 applies D, -1 applies D^H.
-struct WilsonOp {
+// C = double2 (FP64 links) or float2 (FP32 copy of the links, mixed precision)
+template <class C>
+struct WilsonOpT {
   int32_t dims[4];
   int64_t sites;
   double kappa;
   int32_t bc_t;
-  const double2 *links;   // [4][sites][3][3]
+  const C *links;         // [4][sites][3][3]
   const int32_t *nbr;     // [sites][8]
 };
+using WilsonOp = WilsonOpT<double2>;
+using WilsonOp32 = WilsonOpT<float2>;
 void launch_wilson_neighbors(const int32_t dims[4], int32_t *nbr, cudaStream_t s);
 void launch_wilson_dslash(const WilsonOp &op, int sign, const double2 *in, int64_t ldi, double2 *out,
                           int64_t ldo, int ncols, const int32_t *col_active, cudaStream_t s);
 int wilson_kernels_per_apply();
+void launch_wilson_dslash32(const WilsonOp32 &op, int sign, const float2 *in, int64_t ldi, float2 *out, int64_t ldo,
+                            int ncols, const int32_t *col_active, cudaStream_t s);
 
 // CSR (csr.cu)
 struct CsrOp {

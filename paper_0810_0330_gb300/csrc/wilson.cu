@@ -53,19 +53,20 @@ void launch_wilson_neighbors(const int32_t dims[4], int32_t *nbr, cudaStream_t s
 }
 
 
-template <int S>
-__global__ void __launch_bounds__(128) k_dslash(WilsonOp op, const double2 *__restrict__ in, int64_t ldi,
-                                                double2 *__restrict__ out, int64_t ldo,
+template <int S, class C>
+__global__ void __launch_bounds__(128) k_dslash(WilsonOpT<C> op, const C *__restrict__ in, int64_t ldi,
+                                                C *__restrict__ out, int64_t ldo,
                                                 const int32_t *__restrict__ col_active) {
+  using R = typename CxBits<C>::R;
   const int col = blockIdx.y;
   if (col_active != nullptr && col_active[col] == 0) return;
   in += (int64_t)col * ldi;
   out += (int64_t)col * ldo;
-  __shared__ double sacc[4][24][kWilsonSites + 1];
+  __shared__ R sacc[4][24][kWilsonSites + 1];
   const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
   const int64_t s0 = (int64_t)blockIdx.x * kWilsonSites;
   const int64_t s = s0 + lane;
-  double2 acc[12];
+  C acc[12];
   if (s < op.sites) {
     switch (mu) {
       case 0: site_mu<0, S>(op, in, s, acc); break;
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(128) k_dslash(WilsonOp op, const double2 *__re
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = c2(0.0, 0.0);
+    for (int k = 0; k < 12; ++k) acc[k] = C{0, 0};
   }
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
@@ -83,19 +84,30 @@ __global__ void __launch_bounds__(128) k_dslash(WilsonOp op, const double2 *__re
     sacc[mu][2 * k + 1][lane] = acc[k].y;
   }
   __syncthreads();
-  const double *ind = reinterpret_cast<const double *>(in);
-  double *outd = reinterpret_cast<double *>(out);
+  const R *ind = reinterpret_cast<const R *>(in);
+  R *outd = reinterpret_cast<R *>(out);
+  const R mk = (R)(-op.kappa);
   for (int o = threadIdx.x; o < kWilsonSites * 24; o += 128) {
     const int sl = o / 24, c = o - 24 * (o / 24);
     const int64_t ss = s0 + sl;
     if (ss >= op.sites) continue;
-    const double sum = ((sacc[0][c][sl] + sacc[1][c][sl]) + sacc[2][c][sl]) + sacc[3][c][sl];
-    outd[24 * ss + c] = fma(-op.kappa, sum, __ldg(ind + 24 * ss + c));
+    const R sum = ((sacc[0][c][sl] + sacc[1][c][sl]) + sacc[2][c][sl]) + sacc[3][c][sl];
+    outd[24 * ss + c] = fma(mk, sum, __ldg(ind + 24 * ss + c));
   }
 }
 
 void launch_wilson_dslash(const WilsonOp &op, int sign, const double2 *in, int64_t ldi, double2 *out, int64_t ldo,
                           int ncols, const int32_t *col_active, cudaStream_t s) {
+  dim3 grid((unsigned)((op.sites + kWilsonSites - 1) / kWilsonSites), (unsigned)ncols);
+  if (sign > 0) k_dslash<+1><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);
+  else k_dslash<-1><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);
+}
+
+// FP32 operator of the mixed-precision path: the same kernel on float2 data
+// (links converted once at context creation).  Bound by memory traffic, not
+// by the FP32 pipe (1368 flop per 480 B per site and column).
+void launch_wilson_dslash32(const WilsonOp32 &op, int sign, const float2 *in, int64_t ldi, float2 *out, int64_t ldo,
+                            int ncols, const int32_t *col_active, cudaStream_t s) {
   dim3 grid((unsigned)((op.sites + kWilsonSites - 1) / kWilsonSites), (unsigned)ncols);
   if (sign > 0) k_dslash<+1><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);
   else k_dslash<-1><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);

@@ -5,8 +5,9 @@
 // In the chiral basis g_mu = [[0, B_mu], [B_mu^H, 0]] with 2x2 blocks whose
 // rows each hold one entry from {1, i, -1, -i}.  Hence (1 - s g_mu) psi has
 // upper half h = psi_up - s B_mu psi_dn and lower half -s B_mu^H h: a hop
-// multiplies only the two-spinor h by the link, 84 FP64 operations per hop.
-// Phases and boundary signs are register swaps and sign-bit XORs.
+// multiplies only the two-spinor h by the link, 84 floating-point operations
+// per hop.  Phases and boundary signs are register swaps and sign-bit XORs.
+// C = double2 (the FP64 operator) or float2 (its FP32 copy, mixed precision).
 //
 // NC selects how spinors are loaded: true = the read-only path (__ldg), for
 // kernels in which the input does not change; false = ordinary loads, for
@@ -20,26 +21,26 @@
 
 namespace seedk {
 
-template <bool NC> SEED_DEV double2 ldv(const double2 *p) {
+template <bool NC, class C> SEED_DEV C ldv(const C *p) {
   if constexpr (NC) return __ldg(p);
   else return *p;
 }
 
 // ---------------------------------------------------------------------------
-// phases: code 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+// phases: code 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i  (C = double2 or float2)
 // ---------------------------------------------------------------------------
-template <int C> SEED_DEV double2 ph_add(double2 z, double2 w) {   // z + phase(C) w
-  if constexpr (C == 0) return c2(z.x + w.x, z.y + w.y);
-  else if constexpr (C == 1) return c2(z.x - w.y, z.y + w.x);
-  else if constexpr (C == 2) return c2(z.x - w.x, z.y - w.y);
-  else return c2(z.x + w.y, z.y - w.x);
+template <int P, class C> SEED_DEV C ph_add(C z, C w) {   // z + phase(P) w
+  if constexpr (P == 0) return C{z.x + w.x, z.y + w.y};
+  else if constexpr (P == 1) return C{z.x - w.y, z.y + w.x};
+  else if constexpr (P == 2) return C{z.x - w.x, z.y - w.y};
+  else return C{z.x + w.y, z.y - w.x};
 }
-constexpr unsigned long long kSign = 0x8000000000000000ull;
-template <int C> SEED_DEV double2 ph_mul(double2 w) {              // phase(C) w, no FP64 op
-  if constexpr (C == 0) return w;
-  else if constexpr (C == 1) return c2(xsign(w.y, kSign), w.x);
-  else if constexpr (C == 2) return c2(xsign(w.x, kSign), xsign(w.y, kSign));
-  else return c2(w.y, xsign(w.x, kSign));
+template <int P, class C> SEED_DEV C ph_mul(C w) {         // phase(P) w, no FP op
+  constexpr auto m = CxBits<C>::sign;
+  if constexpr (P == 0) return w;
+  else if constexpr (P == 1) return C{xsign(w.y, m), w.x};
+  else if constexpr (P == 2) return C{xsign(w.x, m), xsign(w.y, m)};
+  else return C{w.y, xsign(w.x, m)};
 }
 __host__ __device__ constexpr int ph_neg(int c) { return (c + 2) & 3; }
 __host__ __device__ constexpr int ph_conj(int c) { return (4 - c) & 3; }
@@ -52,28 +53,28 @@ __host__ __device__ constexpr int bP(int mu, int k) {
 }
 
 // One hop of (1 - S g_MU) M psi(nb) into acc[spin*3 + colour];  M = U (FWD) or
-// U^H.  FIRST: acc is overwritten instead of accumulated.  neg: boundary sign.
-template <int MU, int S, bool FWD, bool FIRST, bool NC = true>
-SEED_DEV void hop(const double2 *__restrict__ psi, const double2 *__restrict__ U, unsigned long long neg,
-                  double2 (&acc)[12]) {
+// U^H.  FIRST: acc is overwritten instead of accumulated.  neg: boundary sign
+// mask (0 or the sign bit).
+template <int MU, int S, bool FWD, bool FIRST, bool NC = true, class C>
+SEED_DEV void hop(const C *__restrict__ psi, const C *__restrict__ U, typename CxBits<C>::U neg, C (&acc)[12]) {
   // h_k = psi_k - S * P(k) psi_{2+J(k)}
   constexpr int c0 = S > 0 ? ph_neg(bP(MU, 0)) : bP(MU, 0);
   constexpr int c1 = S > 0 ? ph_neg(bP(MU, 1)) : bP(MU, 1);
-  double2 h0[3], h1[3];
+  C h0[3], h1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double2 p0 = ldv<NC>(psi + a), p1 = ldv<NC>(psi + 3 + a);
-    const double2 q0 = ldv<NC>(psi + 3 * (2 + bJ(MU, 0)) + a), q1 = ldv<NC>(psi + 3 * (2 + bJ(MU, 1)) + a);
+    const C p0 = ldv<NC>(psi + a), p1 = ldv<NC>(psi + 3 + a);
+    const C q0 = ldv<NC>(psi + 3 * (2 + bJ(MU, 0)) + a), q1 = ldv<NC>(psi + 3 * (2 + bJ(MU, 1)) + a);
     h0[a] = ph_add<c0>(p0, q0);
     h1[a] = ph_add<c1>(p1, q1);
     h0[a].x = xsign(h0[a].x, neg); h0[a].y = xsign(h0[a].y, neg);
     h1[a].x = xsign(h1[a].x, neg); h1[a].y = xsign(h1[a].y, neg);
   }
-  double2 u[9];
+  C u[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) u[k] = __ldg(U + k);
   // chi_k = M h_k
-  double2 x0[3], x1[3];
+  C x0[3], x1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if constexpr (FWD) {
@@ -84,7 +85,7 @@ SEED_DEV void hop(const double2 *__restrict__ psi, const double2 *__restrict__ U
       x0[a] = cfma(u[3 * a + 2], h0[2], x0[a]);
       x1[a] = cfma(u[3 * a + 2], h1[2], x1[a]);
     } else {
-      double2 uc = c2(u[a].x, xsign(u[a].y, kSign));
+      C uc = C{u[a].x, xsign(u[a].y, CxBits<C>::sign)};
       x0[a] = cmul(uc, h0[0]);
       x1[a] = cmul(uc, h1[0]);
       x0[a] = cfmac(u[3 + a], h0[1], x0[a]);
@@ -113,16 +114,16 @@ SEED_DEV void hop(const double2 *__restrict__ psi, const double2 *__restrict__ U
   }
 }
 
-template <int MU, int S, bool NC = true>
-SEED_DEV void site_mu(const WilsonOp &op, const double2 *__restrict__ in, int64_t s, double2 (&acc)[12]) {
+template <int MU, int S, bool NC = true, class C>
+SEED_DEV void site_mu(const WilsonOpT<C> &op, const C *__restrict__ in, int64_t s, C (&acc)[12]) {
   const int32_t nf = __ldg(op.nbr + 8 * s + 2 * MU);
   const int32_t nb = __ldg(op.nbr + 8 * s + 2 * MU + 1);
-  unsigned long long negf = 0ull, negb = 0ull;
+  typename CxBits<C>::U negf = 0, negb = 0;
   if (MU == 3 && op.bc_t) {
     const int64_t slab = (int64_t)op.dims[0] * op.dims[1] * op.dims[2];
     const int64_t t = s / slab;
-    if (t == op.dims[3] - 1) negf = kSign;
-    if (t == 0) negb = kSign;
+    if (t == op.dims[3] - 1) negf = CxBits<C>::sign;
+    if (t == 0) negb = CxBits<C>::sign;
   }
   // forward: (1 - S g) U_mu(s) psi(s + mu); backward: (1 + S g) U_mu(s - mu)^H psi(s - mu)
   hop<MU, S, true, true, NC>(in + 12 * (int64_t)nf, op.links + ((int64_t)MU * op.sites + s) * 9, negf, acc);
