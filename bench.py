@@ -74,6 +74,12 @@ def parse():
     ap.add_argument("--dims", default=None, help="lattice for --kernel-only, e.g. 16,16,16,16")
     ap.add_argument("--ncols", type=int, default=None, help="columns for --kernel-only")
     ap.add_argument("--reps", type=int, default=20, help="timed launches for --kernel-only")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="mixed: FP32 operator and Krylov vectors, FP64 scalars and reliable updates")
+    ap.add_argument("--lattice", default=None,
+                    help="lattice of the solve workload, e.g. 16,16,16,32 (default 8,8,8,8)")
+    ap.add_argument("--sources", choices=["point", "z4"], default="point",
+                    help="right-hand sides: 12 unit point sources at site 0, or 12 Z4 noise vectors (seed 0)")
     ap.add_argument("--csr-side", type=int, default=None,
                     help="--kernel-only on the 2-d Laplacian CSR of this side instead of the Wilson operator")
     ap.add_argument("--sweep", action="store_true",
@@ -221,10 +227,21 @@ def csr_bytes(n, nnz):
     return 12 * nnz + 4 * (n + 1) + 16 * n
 
 
-def wilson_bytes(sites, ncols):
+def wilson_bytes(sites, ncols, fp32=False):
     """Algorithmic bytes of one D apply: links (4 x 144 B per site, each read
-    once and used by both hops), input and output spinors (192 B each) per column."""
-    return sites * (576 + 384 * ncols)
+    once and used by both hops), input and output spinors (192 B each) per
+    column; half of that with FP32 data."""
+    b = sites * (576 + 384 * ncols)
+    return b // 2 if fp32 else b
+
+
+def workload_name(dims, sources, mixed):
+    if tuple(dims) == WL["dims"] and sources == "point" and not mixed:
+        return WORKLOAD_NAME
+    src = "12 point sources" if sources == "point" else "12 Z4 noise sources (seed 0)"
+    prec = ", mixed precision (FP32 iterations, FP64 reliable updates)" if mixed else ""
+    return ("wilson-dirac %s kappa=0.155 A=D^H D, %s, seed tol 1e-12 reorth/100, CG tol 1e-8%s"
+            % ("x".join(map(str, dims)), src, prec))
 
 
 def run_sweep(args):
@@ -306,6 +323,10 @@ def run_ours(args):
     dims, kappa, nrhs = WL["dims"], WL["kappa"], WL["nrhs"]
     if args.kernel_only and args.dims:
         dims = tuple(int(x) for x in args.dims.split(","))
+    if args.lattice:
+        dims = tuple(int(x) for x in args.lattice.split(","))
+    mixed = args.precision == "mixed"
+    default_wl = dims == WL["dims"] and args.sources == "point" and not mixed
     vol = int(np.prod(dims))
     n = 12 * vol
     U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
@@ -321,9 +342,9 @@ def run_ours(args):
         return 0
     prm = S.seed_params_default(m_max=WL["m_max"], reorth_freq=WL["reorth_freq"],
                                 reorth_passes=WL["reorth_passes"], tol_seed=WL["tol_seed"],
-                                tol_rest=WL["tol_rest"], x0_zero=1)
+                                tol_rest=WL["tol_rest"], x0_zero=1, precision=1 if mixed else 0)
     ctx = S.seed_create_wilson(dims, kappa, U, prm)
-    eta_h = I.point_sources(dims, nrhs)
+    eta_h = I.point_sources(dims, nrhs) if args.sources == "point" else I.z4_noise(n, nrhs, seed=0)
     ETA = torch.from_numpy(np.ascontiguousarray(eta_h.T)).to(dev).t()     # (n, nrhs) column-major
     B = torch.empty((nrhs, n), dtype=torch.complex128, device=dev).t()
     X = torch.empty((nrhs, n), dtype=torch.complex128, device=dev).t()
@@ -374,18 +395,31 @@ def run_ours(args):
 
     # dominant kernel: the Wilson hopping kernel over the 11 lockstep CG columns
     ncols = nrhs - 1
-    k_ms = S.seed_time_operator(ctx, 1, ncols, 200)
-    k_ms1 = S.seed_time_operator(ctx, 1, 1, 200)
-    flops = FLOPS_PER_SITE_D * vol * ncols
-    achieved = flops / (k_ms * 1e-3) / 1e12
-    peak = FP64_PEAK_GFLOPS / 1e3
-    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": dslash_traffic(),
-            "kernel": "k_dslash<+1> (Wilson D, FP64 complex), %d columns" % ncols,
-            "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
-            "flops_per_launch": flops,
-            "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from unit counts and "
-                         "max clock; a probe measured 1.20 TFLOP/s)"}
+    if not mixed:
+        k_ms = S.seed_time_operator(ctx, 1, ncols, 200)
+        k_ms1 = S.seed_time_operator(ctx, 1, 1, 200)
+        flops = FLOPS_PER_SITE_D * vol * ncols
+        achieved = flops / (k_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": dslash_traffic() if dims == WL["dims"] else None,
+                "kernel": "k_dslash<+1> (Wilson D, FP64 complex), %d columns" % ncols,
+                "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
+                "flops_per_launch": flops,
+                "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from unit counts and "
+                             "max clock; a probe measured 1.20 TFLOP/s)"}
+    else:
+        k_ms = S.seed_time_operator(ctx, 4, ncols, 200)
+        k_ms1 = S.seed_time_operator(ctx, 4, 1, 200)
+        b = wilson_bytes(vol, ncols, fp32=True)
+        achieved = b / (k_ms * 1e-3) / 1e9
+        peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_dslash<+1, float2> (Wilson D, FP32 complex), %d columns" % ncols,
+                "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
+                "bytes_per_launch": b, "l2_resident": b < L2_BYTES,
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
     # end to end through the public API, host buffers (pinned), copies inside the timed region
     e2e = None
@@ -413,15 +447,17 @@ def run_ours(args):
                "d2h_bytes_per_step": int(x_pin.numel() * 16)}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and default_wl:
         total_s, detail = oracle_sample()
         cpu = cpu_baseline_obj(total_s, detail)
 
     if rank == 0:
         out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": WORKLOAD_NAME, "lattice": "8x8x8x8", "n": n, "nrhs": nrhs,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+               "data": "synthetic",
+               "config": {"workload": workload_name(dims, args.sources, mixed), "lattice": "x".join(map(str, dims)),
+                          "n": n, "nrhs": nrhs, "precision": args.precision,
                           "kappa": kappa, "tol_seed": WL["tol_seed"], "reorth_freq": WL["reorth_freq"],
                           "reorth_passes": WL["reorth_passes"], "tol_rest": WL["tol_rest"],
                           "parallelism": "replicas" if world > 1 else "single-gpu",

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define SEED_ABI_VERSION 1
+#define SEED_ABI_VERSION 2
 
 typedef struct seed_ctx seed_ctx;
 typedef struct CUstream_st *seed_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -114,14 +114,31 @@ typedef struct {
                              kernels replayed from CUDA graphs;
                              1: step kernels only;
                              2: as 0, and CG in one persistent kernel as well (nrhs <= 33). */
+  int32_t precision;      /* 0 (default): FP64 throughout.
+                             1: mixed.  Operator applies and Krylov vectors (V included) in FP32
+                             (the context keeps an FP32 copy of the operator); every scalar of the
+                             recurrences and every reduction in FP64.  The FP32 seed Lanczos seeds
+                             all systems (Sec. 3 steps 1-9, same stopping rule), the corrections
+                             are added to X in FP64, then each system is finished by CG with FP32
+                             iterations and FP64 reliable updates (x += the FP32 correction,
+                             r = b - A x recomputed with the FP64 operator) until the FP64 true
+                             residual meets its tolerance: tol_seed for system 1 (inside
+                             seed_solve_first), tol_rest for the others.  The paper runs FP64 only;
+                             this is the GPU extension.  seed_project and seed_get_basis use the
+                             FP64 path only (SEED_ESTATE after a mixed seed solve). */
   int32_t reserved;
+  double reliable_delta;  /* mixed only: a reliable update is made when the FP32 recursive residual
+                             has fallen below reliable_delta times its value at the last update
+                             (checked every 16 iterations), and whenever it meets the tolerance;
+                             0 selects 0.1.  Range [0, 1). */
 } seed_params;
 
 /* Per right-hand side results. */
 typedef struct {
-  int32_t iters;          /* Lanczos steps (system 1) or CG iterations (systems 2..) */
-  int32_t mvps;           /* applications of A, including true-residual checks */
-  int32_t restarts;       /* CG restarts (systems 2..) */
+  int32_t iters;          /* Lanczos steps (system 1) or CG iterations (systems 2..); mixed
+                             precision: system 1 adds its refinement CG iterations */
+  int32_t mvps;           /* applications of A, including true-residual checks (FP32 and FP64) */
+  int32_t restarts;       /* CG restarts (systems 2..); mixed precision: FP64 reliable updates */
   int32_t converged;      /* 1 if the tolerance was met */
   double est_relres;      /* recursive residual estimate / ||b^j|| */
   double true_relres;     /* ||b^j - A x^j|| / ||b^j|| computed at the end */
@@ -140,7 +157,8 @@ int32_t seed_abi_version(void);
 
 /* Fill p with defaults: m_max 1000, reorth_freq 0, passes 2, extra 0,
  * keep_basis 0, x0_zero 1, maxit_rest 100000, max_restarts 3, tol_seed 1e-12,
- * tol_rest 1e-8, breakdown_rel 1e-14, kernel_path 0.  Returns SEED_EINVAL if p is NULL. */
+ * tol_rest 1e-8, breakdown_rel 1e-14, kernel_path 0, precision 0,
+ * reliable_delta 0.  Returns SEED_EINVAL if p is NULL. */
 seed_status seed_params_default(seed_params *p);
 
 /* Create a context for a real CSR operator (dtype SEED_F64).  Allocates the
@@ -186,7 +204,10 @@ seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
 
 /* Y = op(X) for ncols columns: op 0 = A; for Wilson contexts op 1 = D and
  * op 2 = D^H (used e.g. to form normal-equation right-hand sides b = D^H eta,
- * Sec. 4).  X and Y must not overlap.  Not synchronising. */
+ * Sec. 4).  On a mixed-precision context ops 3 = A, 4 = D, 5 = D^H apply the
+ * FP32 copy of the operator to FP32 data (float, or interleaved complex float
+ * for Wilson), the arithmetic of the mixed solver's iterations.  X and Y must
+ * not overlap.  Not synchronising. */
 seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, void *Y, int64_t ldy,
                        int32_t ncols);
 
@@ -204,13 +225,16 @@ seed_status seed_wilson_neighbors(const int32_t dims[4], int32_t *nbr, seed_stre
 seed_status seed_get_tridiag(const seed_ctx *ctx, double *alpha, double *beta, int32_t cap,
                              int32_t *m);
 
-/* Copy the first ncols Lanczos vectors (column-major, ld = n, host memory). */
+/* Copy the first ncols Lanczos vectors (column-major, ld = n, host memory).
+ * SEED_ESTATE on a mixed-precision context (its basis is FP32). */
 seed_status seed_get_basis(const seed_ctx *ctx, void *V_host, int32_t ncols);
 
 seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out);
 
 /* Measurement helper (not part of the method): launch op(X) (op as in
- * seed_apply) reps times back to back on the context's internal stream over
+ * seed_apply; on a mixed-precision context also 3 = A, 4 = D, 5 = D^H with the
+ * FP32 copy of the operator on FP32 columns filled with the byte 0x3F, floats
+ * near 0.75) reps times back to back on the context's internal stream over
  * ncols library-owned columns (filled with the byte 0x3F, i.e. normal
  * doubles near 4.8e-4), with CUDA events on that stream
  * around the launches; *ms_per_apply receives the mean device time of one

@@ -56,7 +56,7 @@ class seed_params(C.Structure):
                 ("extra_iters", C.c_int32), ("keep_basis", C.c_int32), ("x0_zero", C.c_int32),
                 ("maxit_rest", C.c_int32), ("max_restarts", C.c_int32), ("tol_seed", C.c_double),
                 ("tol_rest", C.c_double), ("breakdown_rel", C.c_double), ("kernel_path", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("precision", C.c_int32), ("reserved", C.c_int32), ("reliable_delta", C.c_double)]
 
 
 class seed_info(C.Structure):

@@ -81,6 +81,23 @@ template <> struct Sc<double2> {
   static SEED_DEV double2 sub(double2 a, double2 b) { return csub(a, b); }
   static SEED_DEV double2 add(double2 a, double2 b) { return cadd(a, b); }
 };
+template <> struct Sc<float> {
+  using A = float;
+  using A2 = float2;
+  static SEED_DEV float2 zero2() { return c2(0.f, 0.f); }
+  static SEED_DEV float2 pair(float re, float im) { return c2(re, im); }
+  static SEED_DEV float2 from2(double2 a) { return c2((float)a.x, (float)a.y); }
+  static SEED_DEV float caxpy2(float2 a, float x, float y) { return fmaf(a.x, x, y); }
+  static SEED_DEV float zero() { return 0.f; }
+  static SEED_DEV float scale(double s, float x) { return (float)s * x; }
+  static SEED_DEV float axpy(double a, float x, float y) { return fmaf((float)a, x, y); }
+  static SEED_DEV float caxpy(double2 a, float x, float y) { return fmaf((float)a.x, x, y); }
+  static SEED_DEV float redot(float a, float b, float acc) { return fmaf(a, b, acc); }
+  static SEED_DEV float2 dotc(float a, float b, float2 acc) { return c2(fmaf(a, b, acc.x), acc.y); }
+  static SEED_DEV float nrm2(float a, float acc) { return fmaf(a, a, acc); }
+  static SEED_DEV float sub(float a, float b) { return a - b; }
+  static SEED_DEV float add(float a, float b) { return a + b; }
+};
 template <> struct Sc<float2> {
   using A = float;
   using A2 = float2;

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "seed.h"
@@ -91,6 +92,16 @@ struct seed_ctx {
   bool allow_persistent = true;        // persistent seed runs
   bool allow_persistent_cg = false;    // persistent CG
 
+  // mixed precision: V, vcur, u, f, w hold FP32 vectors (vsz bytes per element)
+  int precision = 0;
+  size_t vsz = 8;
+  WilsonOp32 wil32{};
+  CsrOp32 csr32{};
+  void *op32 = nullptr;                // FP32 copy of the links / matrix values
+  void *R32 = nullptr, *P32 = nullptr, *Q32 = nullptr, *T32 = nullptr;
+  void *E32 = nullptr;                 // FP32 corrections, cap_cols + 1 columns (column 0 spare)
+  CallArgs *call32 = nullptr;          // [0]: seed run (X = E), [1]: mixed CG
+
   std::map<std::string, GraphEntry> graphs;
   std::string err;
   seed_stats stats{};
@@ -138,6 +149,9 @@ seed_status check_params(seed_ctx *ctx, const seed_params *p) {
   if (!(p->tol_seed >= 0.0) || !(p->tol_rest >= 0.0) || !(p->breakdown_rel >= 0.0))
     return fail(ctx, SEED_EINVAL, "tolerances must be >= 0");
   if (p->kernel_path < 0 || p->kernel_path > 2) return fail(ctx, SEED_EINVAL, "kernel_path must be 0, 1 or 2");
+  if (p->precision < 0 || p->precision > 1) return fail(ctx, SEED_EINVAL, "precision must be 0 or 1");
+  if (!(p->reliable_delta >= 0.0 && p->reliable_delta < 1.0))
+    return fail(ctx, SEED_EINVAL, "reliable_delta must be in [0, 1)");
   return SEED_OK;
 }
 
@@ -161,7 +175,7 @@ seed_status dalloc(seed_ctx *ctx, Tp **p, size_t bytes) {
 
 seed_status alloc_common(seed_ctx *ctx) {
   const int64_t n = ctx->n;
-  const size_t es = ctx->esz;
+  const size_t es = ctx->vsz;   // Krylov vectors: FP64, or FP32 in mixed precision
   const int m = ctx->prm.m_max;
   ctx->ldv = (n + 31) / 32 * 32;   // 256-byte aligned columns for complex, 256 B for real
   TRY(dalloc(ctx, &ctx->V, (size_t)ctx->ldv * (m + 1) * es));
@@ -189,8 +203,9 @@ seed_status alloc_common(seed_ctx *ctx) {
   ctx->nrb = (int)((n + rows - 1) / rows);
   TRY(dalloc(ctx, &ctx->Hpart, sizeof(double2) * (size_t)ctx->nrb * (m + 1) * 2 + 64));
   TRY(dalloc(ctx, &ctx->H, sizeof(double2) * (size_t)(m + 1) * 2));
-  TRY(dalloc(ctx, &ctx->cg_d, sizeof(double) * 5 * kMaxRhs));
-  TRY(dalloc(ctx, &ctx->cg_i, sizeof(int32_t) * 7 * kMaxRhs));
+  TRY(dalloc(ctx, &ctx->cg_d, sizeof(double) * kCgDoubles * kMaxRhs));
+  TRY(dalloc(ctx, &ctx->cg_i, sizeof(int32_t) * kCgInts * kMaxRhs));
+  if (ctx->precision == 1) TRY(dalloc(ctx, &ctx->call32, sizeof(CallArgs) * 2));
   CU(cudaMemsetAsync(ctx->tickets, 0, sizeof(unsigned) * 256, ctx->cs));
   CU(cudaMemsetAsync(ctx->w, 0, n * es, ctx->cs));
   CU(cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * 2 * kMaxRhs));
@@ -222,6 +237,8 @@ seed_status ensure_cols(seed_ctx *ctx, int cols) {
   cudaStreamSynchronize(ctx->cs);
   cudaFree(ctx->R); cudaFree(ctx->P); cudaFree(ctx->Q); cudaFree(ctx->T);
   ctx->R = ctx->P = ctx->Q = ctx->T = nullptr;
+  cudaFree(ctx->R32); cudaFree(ctx->P32); cudaFree(ctx->Q32); cudaFree(ctx->T32); cudaFree(ctx->E32);
+  ctx->R32 = ctx->P32 = ctx->Q32 = ctx->T32 = ctx->E32 = nullptr;
   ctx->cap_cols = 0;
   // graphs captured with the old buffers are stale
   for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -231,6 +248,14 @@ seed_status ensure_cols(seed_ctx *ctx, int cols) {
   TRY(dalloc(ctx, &ctx->P, bytes));
   TRY(dalloc(ctx, &ctx->Q, bytes));
   TRY(dalloc(ctx, &ctx->T, bytes));
+  if (ctx->precision == 1) {
+    const size_t b32 = (size_t)ctx->ldv * cols * ctx->vsz;
+    TRY(dalloc(ctx, &ctx->R32, b32));
+    TRY(dalloc(ctx, &ctx->P32, b32));
+    TRY(dalloc(ctx, &ctx->Q32, b32));
+    TRY(dalloc(ctx, &ctx->T32, b32));
+    TRY(dalloc(ctx, &ctx->E32, b32 + (size_t)ctx->ldv * ctx->vsz));
+  }
   ctx->cap_cols = cols;
   return SEED_OK;
 }
@@ -245,6 +270,22 @@ int apply_A(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, int
   launch_wilson_dslash(ctx->wil, -1, (const double2 *)ctx->T, ctx->ldv, (double2 *)Y, ldy, ncols, mask, ctx->cs);
   return 2;
 }
+
+// Y = A X with the FP32 copy of the operator (mixed precision).  Returns the kernel count.
+int apply_A32(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, int ncols, const int32_t *mask) {
+  if (ctx->kind == 0) {
+    launch_csr_spmv32(ctx->csr32, (const float *)X, ldx, (float *)Y, ldy, ncols, mask, ctx->cs);
+    return 1;
+  }
+  launch_wilson_dslash32(ctx->wil32, +1, (const float2 *)X, ldx, (float2 *)ctx->T32, ctx->ldv, ncols, mask, ctx->cs);
+  launch_wilson_dslash32(ctx->wil32, -1, (const float2 *)ctx->T32, ctx->ldv, (float2 *)Y, ldy, ncols, mask, ctx->cs);
+  return 2;
+}
+
+template <class T> constexpr bool kLow = std::is_same_v<T, float> || std::is_same_v<T, float2>;
+
+// E: column 0 of the corrections (system 1); its spare column sits before it
+template <class T> T *E_cols(seed_ctx *ctx) { return (T *)ctx->E32 + ctx->ldv; }
 
 template <class T>
 SeedBufs<T> seed_bufs(seed_ctx *ctx, int nrhs) {
@@ -261,6 +302,10 @@ SeedBufs<T> seed_bufs(seed_ctx *ctx, int nrhs) {
   b.R0 = (const T *)ctx->R;
   b.ldr = ctx->ldv;
   b.call = ctx->call;
+  if constexpr (kLow<T>) {
+    b.R0 = (const T *)ctx->R32 + ctx->ldv;   // r_0^2.. (FP32), column 0 holds r_0^1
+    b.call = ctx->call32;                    // x^j := FP32 corrections e^j
+  }
   b.st = ctx->st;
   b.alpha_hist = ctx->alpha_hist;
   b.beta_hist = ctx->beta_hist;
@@ -292,7 +337,8 @@ bool reorth_at(const seed_params &p, int i) { return p.reorth_freq > 0 && i >= 2
 template <class T>
 int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
   SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
-  int k = apply_A(ctx, ctx->vcur, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr);
+  int k = kLow<T> ? apply_A32(ctx, ctx->vcur, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr)
+                  : apply_A(ctx, ctx->vcur, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr);
   launch_seed_dots<T>(b, ctx->cs);
   launch_seed_update<T>(b, !reorth, ctx->cs);
   k += 2;
@@ -307,7 +353,7 @@ int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
 // Capture (once) and launch a graph for the given pattern of steps.
 template <class T>
 seed_status launch_seed_run(seed_ctx *ctx, int nrhs, const std::vector<char> &pattern) {
-  std::string key = "S" + std::to_string(nrhs) + ":" + std::string(pattern.begin(), pattern.end());
+  std::string key = (kLow<T> ? "s" : "S") + std::to_string(nrhs) + ":" + std::string(pattern.begin(), pattern.end());
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     GraphEntry g;
@@ -529,6 +575,7 @@ CgCols cg_cols(seed_ctx *ctx, int nc) {
   c.beta = d + 2 * kMaxRhs;
   c.bnorm = d + 3 * kMaxRhs;
   c.relres = d + 4 * kMaxRhs;
+  c.rupd = d + 5 * kMaxRhs;
   c.active = q;
   c.iters = q + kMaxRhs;
   c.reached = q + 2 * kMaxRhs;
@@ -536,10 +583,12 @@ CgCols cg_cols(seed_ctx *ctx, int nc) {
   c.converged = q + 4 * kMaxRhs;
   c.needs_check = q + 5 * kMaxRhs;
   c.mvps = q + 6 * kMaxRhs;
+  c.upd = q + 7 * kMaxRhs;
   c.tol = ctx->prm.tol_rest;
   c.tol_check = 1.5 * ctx->prm.tol_rest;
   c.maxit = ctx->prm.maxit_rest;
   c.max_restarts = ctx->prm.max_restarts;
+  c.delta = ctx->prm.reliable_delta > 0.0 ? ctx->prm.reliable_delta : 0.1;
   return c;
 }
 
@@ -674,6 +723,243 @@ seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
   return SEED_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision: FP32 iterations, FP64 scalars and reliable updates
+// ---------------------------------------------------------------------------
+
+// Capture (once, under `key`) and launch a graph of the work issue() enqueues.
+template <class F>
+seed_status run_graph(seed_ctx *ctx, const std::string &key, F issue) {
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    GraphEntry g;
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(ctx->cs, cudaStreamCaptureModeThreadLocal));
+    g.kernels = issue();
+    CU(cudaStreamEndCapture(ctx->cs, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, SEED_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    it = ctx->graphs.emplace(key, g).first;
+  }
+  CU(cudaGraphLaunch(it->second.exec, ctx->cs));
+  ctx->stats.graph_launches++;
+  ctx->stats.kernel_launches += it->second.kernels;
+  return SEED_OK;
+}
+
+// One lockstep CG iteration in FP32 (the operator's FP32 copy, FP32 vectors,
+// FP64 alpha / beta / norms); x is the FP32 correction E (call32[1]).
+template <class T32>
+int issue_mixed_iter(seed_ctx *ctx, const CgCols &c) {
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  int k = apply_A32(ctx, ctx->P32, ld, ctx->Q32, ld, c.nc, c.active);
+  launch_cg_alpha<T32>(n, (const T32 *)ctx->P32, (const T32 *)ctx->Q32, ld, c, ctx->partials, ctx->tickets, ctx->cs);
+  launch_cg_update<T32>(n, ctx->call32 + 1, (T32 *)ctx->R32, (const T32 *)ctx->P32, (const T32 *)ctx->Q32, ld, c,
+                        ctx->partials, ctx->tickets, ctx->cs);
+  launch_cg_p<T32>(n, (const T32 *)ctx->R32, (T32 *)ctx->P32, ld, c, ctx->cs);
+  return k + 3;
+}
+
+// CG on columns c0..c0+nc-1 of B and X (FP64) to ||b - A x|| <= tol ||b||
+// measured with the FP64 operator: runs of 16 FP32 iterations, each run
+// followed by the reliable update of the columns that need one.
+template <class T64, class T32>
+seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t ldx, int c0, int nc, double tol,
+                     CgCols *cols_out) {
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  CgCols c = cg_cols(ctx, nc);
+  c.tol = tol;
+  c.tol_check = tol;
+  T32 *E = E_cols<T32>(ctx) + (int64_t)c0 * ld;
+  const CallArgs ca{(void *)(E - ld), ld};   // k_cg_update writes column col+1 of call->X
+  CU(cudaMemcpyAsync(ctx->call32 + 1, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
+  launch_mixed_init<T64, T32>(n, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, E, ld, c,
+                              ctx->partials, ctx->tickets, ctx->cs);
+  ctx->stats.kernel_launches += kern + 1;
+  ctx->stats.mvps += nc;
+  const int L = 16;
+  // the graph bakes in CgCols (tolerance included): system 1 (c0 = 0) and the others have their own
+  const std::string key = "M" + std::to_string(nc) + ":" + std::to_string(L) + ":" + std::to_string(c0);
+  int slot = 0, pending = -1;
+  cudaEvent_t evs[2] = {nullptr, nullptr};
+  for (;;) {
+    TRY(run_graph(ctx, key, [&] {
+      int k = 0;
+      for (int q = 0; q < L; ++q) k += issue_mixed_iter<T32>(ctx, c);
+      return k;
+    }));
+    // reliable updates (direct launches: B and X are this call's buffers)
+    launch_mixed_flag(c, ctx->cs);
+    launch_fold<T64, T32>(Xc, ldx, E, ld, n, nc, c.upd, ctx->cs);
+    kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, c.upd);
+    launch_mixed_residual<T64, T32>(n, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, ld, c,
+                                    ctx->partials, ctx->tickets, ctx->cs);
+    ctx->stats.kernel_launches += kern + 3;
+    CU(cudaMemcpyAsync(ctx->h_flags + slot * kMaxRhs, c.active, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost,
+                       ctx->cs));
+    if (!evs[slot]) CU(cudaEventCreateWithFlags(&evs[slot], cudaEventDisableTiming));
+    CU(cudaEventRecord(evs[slot], ctx->cs));
+    bool any = true;
+    if (pending >= 0) {
+      CU(cudaEventSynchronize(evs[pending]));
+      any = false;
+      for (int j = 0; j < nc; ++j) any |= ctx->h_flags[pending * kMaxRhs + j] != 0;
+    }
+    pending = slot;
+    slot ^= 1;
+    if (!any) break;
+  }
+  CU(cudaStreamSynchronize(ctx->cs));
+  for (auto &e : evs)
+    if (e) cudaEventDestroy(e);
+  CU(cudaGetLastError());
+  if (cols_out) *cols_out = c;
+  return SEED_OK;
+}
+
+struct CgHost {
+  std::vector<int32_t> i;
+  std::vector<double> d;
+  int32_t iters(int j) const { return i[kMaxRhs + j]; }
+  int32_t restarts(int j) const { return i[3 * kMaxRhs + j]; }
+  int32_t converged(int j) const { return i[4 * kMaxRhs + j]; }
+  int32_t mvps(int j) const { return i[6 * kMaxRhs + j]; }
+  double relres(int j) const { return d[4 * kMaxRhs + j]; }
+};
+
+seed_status read_cg(seed_ctx *ctx, CgHost *h) {
+  h->i.resize(kCgInts * kMaxRhs);
+  h->d.resize(kCgDoubles * kMaxRhs);
+  CU(cudaMemcpyAsync(h->i.data(), ctx->cg_i, sizeof(int32_t) * kCgInts * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaMemcpyAsync(h->d.data(), ctx->cg_d, sizeof(double) * kCgDoubles * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  return SEED_OK;
+}
+
+// Sec. 3 steps 1-9 with FP32 vectors and operator (FP64 scalars), then system
+// 1 finished to tol_seed by mixed CG.
+template <class T64, class T32>
+seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
+                              seed_info *info) {
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  const seed_params &p = ctx->prm;
+  TRY(ensure_cols(ctx, std::max(nrhs, 1)));
+  ctx->basis_valid = false;
+  ctx->seeded = false;
+  CU(cudaEventRecord(ctx->t0, ctx->cs));
+  T32 *E = E_cols<T32>(ctx);
+  const CallArgs ca{(void *)E, ld};
+  CU(cudaMemcpyAsync(ctx->call32, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  SeedState s0{};
+  s0.tol_rel = p.tol_seed;
+  s0.breakdown_rel = p.breakdown_rel;
+  s0.m_max = p.m_max;
+  s0.extra_iters = p.extra_iters;
+  s0.converged_at = -1;
+  s0.stop_at = -1;
+  CU(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->cs));
+  CU(cudaMemsetAsync(ctx->eta, 0, sizeof(double2) * kMaxRhs, ctx->cs));
+
+  // Step 1 in FP64: r_0^j = b^j - A x_0^j, rounded to FP32 (column 0 starts the Lanczos run)
+  int kern = 0;
+  if (p.x0_zero) {
+    launch_zero_cols<T64>((T64 *)X, ldx, n, nrhs, ctx->cs);
+    launch_to_low<T64, T32>((const T64 *)B, ldb, (T32 *)ctx->R32, ld, n, nrhs, ctx->cs);
+    kern += 2;
+  } else {
+    kern += apply_A(ctx, X, ldx, ctx->Q, ld, nrhs, nullptr);
+    ctx->stats.mvps += nrhs;
+    launch_sub_from<T64>((const T64 *)B, ldb, (const T64 *)ctx->Q, ld, (T64 *)ctx->P, ld, n, nrhs, ctx->cs);
+    launch_to_low<T64, T32>((const T64 *)ctx->P, ld, (T32 *)ctx->R32, ld, n, nrhs, ctx->cs);
+    kern += 2;
+  }
+  launch_zero_cols<T32>(E, ld, n, nrhs, ctx->cs);
+  launch_colnorms<T64>(n, (const T64 *)B, ldb, 1, &ctx->st->bnorm1, ctx->partials, ctx->tickets, ctx->cs);
+  SeedBufs<T32> b = seed_bufs<T32>(ctx, nrhs);
+  launch_seed_start<T32>(b, (const T32 *)ctx->R32, ctx->cs);
+  launch_seed_normalize<T32>(b, ctx->cs);
+  kern += 4;
+  ctx->stats.kernel_launches += kern;
+  TRY(seed_graph_runs<T32>(ctx, nrhs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  if (ctx->ev_out) {
+    cudaEventDestroy(ctx->ev_out);
+    ctx->ev_out = nullptr;
+  }
+  CU(cudaGetLastError());
+  SeedState st;
+  CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
+  const int steps = (st.beta0 > 0.0 && st.i >= 1) ? st.i : 0;
+  ctx->stats.mvps += steps;
+  ctx->last_m = steps;
+  if (st.stop_reason == STOP_NOTSPD) {
+    CU(cudaEventRecord(ctx->t1, ctx->cs));
+    return fail(ctx, SEED_ENOTSPD, "delta_i <= 0 at Lanczos step " + std::to_string(st.i) +
+                                       ": operator not positive definite in floating point");
+  }
+  // x^j += e^j (the FP32 Lanczos corrections), then system 1 to tol_seed
+  launch_fold<T64, T32>((T64 *)X, ldx, E, ld, n, nrhs, nullptr, ctx->cs);
+  ctx->stats.kernel_launches += 1;
+  TRY((mixed_cg<T64, T32>(ctx, (const T64 *)B, ldb, (T64 *)X, ldx, 0, 1, p.tol_seed, nullptr)));
+  CU(cudaEventRecord(ctx->t1, ctx->cs));
+  CgHost h;
+  TRY(read_cg(ctx, &h));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->t0, ctx->t1);
+  ctx->stats.ms_seed = ms;
+  ctx->stats.mvps += h.mvps(0) - 1;   // the first true residual was counted by mixed_cg
+  if (info) {
+    std::memset(info, 0, sizeof(seed_info) * nrhs);
+    info[0].iters = steps + h.iters(0);
+    info[0].mvps = steps + h.mvps(0) + (p.x0_zero ? 0 : 1);
+    info[0].restarts = h.restarts(0);
+    info[0].converged = h.converged(0);
+    info[0].est_relres = st.bnorm1 > 0.0 ? st.rho / st.bnorm1 : 0.0;
+    info[0].true_relres = h.relres(0);
+  }
+  ctx->seeded = true;
+  ctx->basis_valid = false;   // V holds FP32 vectors: no FP64 projection from it
+  if (!h.converged(0)) return fail(ctx, SEED_ENOTCONV, "system 1 did not reach tol_seed within maxit_rest");
+  return SEED_OK;
+}
+
+template <class T64, class T32>
+seed_status solve_rest_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
+                             seed_info *info) {
+  const int nc = nrhs - 1;
+  if (info) std::memset(info + 1, 0, sizeof(seed_info) * (nc > 0 ? nc : 0));
+  if (nc <= 0) return SEED_OK;
+  TRY(ensure_cols(ctx, nrhs));
+  CU(cudaEventRecord(ctx->t2, ctx->cs));
+  TRY((mixed_cg<T64, T32>(ctx, (const T64 *)B + ldb, ldb, (T64 *)X + ldx, ldx, 1, nc, ctx->prm.tol_rest, nullptr)));
+  CU(cudaEventRecord(ctx->t3, ctx->cs));
+  CgHost h;
+  TRY(read_cg(ctx, &h));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->t2, ctx->t3);
+  ctx->stats.ms_rest = ms;
+  bool all = true;
+  int64_t mv = 0;
+  for (int j = 0; j < nc; ++j) {
+    all &= h.converged(j) != 0;
+    mv += h.mvps(j);
+    if (info) {
+      seed_info &o = info[j + 1];
+      o.iters = h.iters(j);
+      o.mvps = h.mvps(j);
+      o.restarts = h.restarts(j);
+      o.converged = h.converged(j);
+      o.est_relres = h.relres(j);
+      o.true_relres = h.relres(j);
+    }
+  }
+  ctx->stats.mvps += mv - nc;
+  if (!all) return fail(ctx, SEED_ENOTCONV, "CG did not reach tol_rest on every system within maxit_rest");
+  return SEED_OK;
+}
+
 seed_status check_block(seed_ctx *ctx, const void *A, int64_t lda, int cols, const char *name) {
   if (cols < 1 || cols > kMaxRhs) return fail(ctx, SEED_EINVAL, std::string("number of columns must be 1..64 (") + name + ")");
   if (lda < ctx->n) return fail(ctx, SEED_EINVAL, std::string("leading dimension < n (") + name + ")");
@@ -703,7 +989,9 @@ seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream strea
   TRY(check_params(ctx, p));
   ctx->prm = *p;
   ctx->allow_persistent = p->kernel_path != 1;
-  ctx->allow_persistent_cg = p->kernel_path == 2;
+  ctx->allow_persistent_cg = p->kernel_path == 2 && p->precision == 0;
+  ctx->precision = p->precision;
+  if (p->precision == 1) ctx->allow_persistent = false;   // the persistent kernels are FP64 only
   CU(cudaGetDevice(&ctx->device));
   ctx->user_stream = (cudaStream_t)stream;
   CU(cudaStreamCreateWithFlags(&ctx->cs, cudaStreamNonBlocking));
@@ -722,7 +1010,8 @@ void destroy(seed_ctx *ctx) {
   void *ptrs[] = {ctx->V, ctx->vcur, ctx->u, ctx->f, ctx->w, ctx->st, ctx->alpha_hist, ctx->beta_hist,
                   ctx->delta_hist, ctx->eta, ctx->partials, ctx->tickets, ctx->Hpart, ctx->H, ctx->call,
                   ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
-                  ctx->gsync, ctx->f2, ctx->gbuf, ctx->tpart};
+                  ctx->gsync, ctx->f2, ctx->gbuf, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
+                  ctx->T32, ctx->E32, ctx->call32};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
@@ -763,7 +1052,9 @@ seed_status seed_params_default(seed_params *p) {
   p->tol_rest = 1e-8;
   p->breakdown_rel = 1e-14;
   p->kernel_path = 0;
+  p->precision = 0;
   p->reserved = 0;
+  p->reliable_delta = 0.0;
   return SEED_OK;
 }
 
@@ -798,8 +1089,17 @@ seed_status seed_create_csr(seed_ctx **out, const seed_csr *A, const seed_params
   ctx->dtype = SEED_F64;
   ctx->n = A->n;
   ctx->esz = sizeof(double);
+  ctx->vsz = ctx->precision == 1 ? sizeof(float) : sizeof(double);
   ctx->csr = CsrOp{A->n, A->row_ptr, A->col_idx, A->vals};
   s = alloc_common(ctx);
+  if (s == SEED_OK && ctx->precision == 1) {
+    s = dalloc(ctx, &ctx->op32, sizeof(float) * (size_t)(A->nnz > 0 ? A->nnz : 1));
+    if (s == SEED_OK) {
+      if (A->nnz > 0) launch_to_low<double, float>(A->vals, A->nnz, (float *)ctx->op32, A->nnz, A->nnz, 1, ctx->cs);
+      ctx->stats.kernel_launches += A->nnz > 0;
+      ctx->csr32 = CsrOp32{A->n, A->row_ptr, A->col_idx, (const float *)ctx->op32};
+    }
+  }
   if (s == SEED_OK && cudaStreamSynchronize(ctx->cs) != cudaSuccess) s = fail(ctx, SEED_ECUDA, "set-up failed");
   if (s != SEED_OK) { g_last_error = ctx->err; destroy(ctx); return s; }
   *out = ctx;
@@ -829,8 +1129,17 @@ seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_
   ctx->dtype = SEED_C128;
   ctx->n = 12 * vol;
   ctx->esz = sizeof(double2);
+  ctx->vsz = ctx->precision == 1 ? sizeof(float2) : sizeof(double2);
   s = alloc_common(ctx);
   if (s == SEED_OK) s = dalloc(ctx, &ctx->nbr, sizeof(int32_t) * 8 * vol);
+  if (s == SEED_OK && ctx->precision == 1) {
+    const int64_t nl = 4 * vol * 9;
+    s = dalloc(ctx, &ctx->op32, sizeof(float2) * (size_t)nl);
+    if (s == SEED_OK) {
+      launch_to_low<double2, float2>((const double2 *)A->links, nl, (float2 *)ctx->op32, nl, nl, 1, ctx->cs);
+      ctx->stats.kernel_launches += 1;
+    }
+  }
   if (s == SEED_OK) {
     launch_wilson_neighbors(A->dims, ctx->nbr, ctx->cs);
     ctx->stats.kernel_launches += 1;
@@ -840,6 +1149,12 @@ seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_
     ctx->wil.bc_t = A->bc_t;
     ctx->wil.links = (const double2 *)A->links;
     ctx->wil.nbr = ctx->nbr;
+    for (int k = 0; k < 4; ++k) ctx->wil32.dims[k] = A->dims[k];
+    ctx->wil32.sites = vol;
+    ctx->wil32.kappa = A->kappa;
+    ctx->wil32.bc_t = A->bc_t;
+    ctx->wil32.links = (const float2 *)ctx->op32;
+    ctx->wil32.nbr = ctx->nbr;
     if (cudaStreamSynchronize(ctx->cs) != cudaSuccess || cudaGetLastError() != cudaSuccess)
       s = fail(ctx, SEED_ECUDA, "neighbour table build failed");
   }
@@ -855,6 +1170,10 @@ seed_status seed_solve_first(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   TRY(check_block(ctx, X, ldx, nrhs, "X"));
   if (overlap(B, ldb, X, ldx, nrhs, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
   StreamScope scope(ctx);
+  if (ctx->precision == 1) {
+    if (ctx->kind == 0) return solve_first_mixed<double, float>(ctx, B, ldb, X, ldx, nrhs, info);
+    return solve_first_mixed<double2, float2>(ctx, B, ldb, X, ldx, nrhs, info);
+  }
   if (ctx->kind == 0) return solve_first_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
   return solve_first_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
 }
@@ -866,6 +1185,10 @@ seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
   TRY(check_block(ctx, X, ldx, nrhs, "X"));
   if (overlap(B, ldb, X, ldx, nrhs, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
   StreamScope scope(ctx);
+  if (ctx->precision == 1) {
+    if (ctx->kind == 0) return solve_rest_mixed<double, float>(ctx, B, ldb, X, ldx, nrhs, info);
+    return solve_rest_mixed<double2, float2>(ctx, B, ldb, X, ldx, nrhs, info);
+  }
   if (ctx->kind == 0) return solve_rest_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
   return solve_rest_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
 }
@@ -918,13 +1241,22 @@ seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int
 
 seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, void *Y, int64_t ldy, int32_t ncols) {
   if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
-  if (op < 0 || op > 2 || (op > 0 && ctx->kind != 1)) return fail(ctx, SEED_EINVAL, "op must be 0 (A), or 1 (D) / 2 (D^H) for Wilson");
+  if (op < 0 || op > 5 || ((op == 1 || op == 2 || op == 4 || op == 5) && ctx->kind != 1))
+    return fail(ctx, SEED_EINVAL, "op must be 0 (A), or 1 (D) / 2 (D^H) for Wilson; 3..5 in FP32");
+  if (op >= 3 && ctx->precision != 1) return fail(ctx, SEED_EINVAL, "ops 3..5 need a mixed-precision context");
   TRY(check_block(ctx, X, ldx, ncols, "X"));
   TRY(check_block(ctx, Y, ldy, ncols, "Y"));
-  if (overlap(X, ldx, Y, ldy, ncols, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "X and Y overlap");
+  const size_t es = op >= 3 ? ctx->vsz : ctx->esz;
+  if (overlap(X, ldx, Y, ldy, ncols, ctx->n, es)) return fail(ctx, SEED_EINVAL, "X and Y overlap");
   TRY(ensure_cols(ctx, ncols));
   StreamScope scope(ctx);
-  if (op == 0) {
+  if (op == 3) {
+    ctx->stats.kernel_launches += apply_A32(ctx, X, ldx, Y, ldy, ncols, nullptr);
+  } else if (op >= 4) {
+    launch_wilson_dslash32(ctx->wil32, op == 4 ? +1 : -1, (const float2 *)X, ldx, (float2 *)Y, ldy, ncols, nullptr,
+                           ctx->cs);
+    ctx->stats.kernel_launches += 1;
+  } else if (op == 0) {
     ctx->stats.kernel_launches += apply_A(ctx, X, ldx, Y, ldy, ncols, nullptr);
     ctx->stats.mvps += ncols;
   } else {
@@ -967,6 +1299,7 @@ seed_status seed_get_basis(const seed_ctx *cctx, void *V_host, int32_t ncols) {
   seed_ctx *ctx = const_cast<seed_ctx *>(cctx);
   if (!ctx || !V_host) return fail(ctx, SEED_EINVAL, "NULL argument");
   if (!ctx->seeded || ncols < 0 || ncols > ctx->last_m) return fail(ctx, SEED_EINVAL, "ncols out of range");
+  if (ctx->precision == 1) return fail(ctx, SEED_ESTATE, "the basis of a mixed-precision context is FP32");
   CU(cudaMemcpy2D(V_host, ctx->n * ctx->esz, ctx->V, ctx->ldv * ctx->esz, ctx->n * ctx->esz, ncols,
                   cudaMemcpyDeviceToHost));
   return SEED_OK;
@@ -974,16 +1307,25 @@ seed_status seed_get_basis(const seed_ctx *cctx, void *V_host, int32_t ncols) {
 
 seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t reps, double *ms_per_apply) {
   if (!ctx || !ms_per_apply) return fail(ctx, SEED_EINVAL, "NULL argument");
-  if (op < 0 || op > 2 || (op > 0 && ctx->kind != 1)) return fail(ctx, SEED_EINVAL, "bad op");
+  if (op < 0 || op > 5 || ((op == 1 || op == 2 || op == 4 || op == 5) && ctx->kind != 1))
+    return fail(ctx, SEED_EINVAL, "bad op");
+  if (op >= 3 && ctx->precision != 1) return fail(ctx, SEED_EINVAL, "ops 3..5 need a mixed-precision context");
   if (ncols < 1 || ncols > kMaxRhs || reps < 1 || reps > 100000) return fail(ctx, SEED_EINVAL, "bad ncols / reps");
   TRY(ensure_cols(ctx, ncols));
   StreamScope scope(ctx);
   CU(cudaMemsetAsync(ctx->P, 0x3F, (size_t)ctx->ldv * ncols * ctx->esz, ctx->cs));   // normal doubles ~4.8e-4
+  if (op >= 3) CU(cudaMemsetAsync(ctx->P32, 0x3F, (size_t)ctx->ldv * ncols * ctx->vsz, ctx->cs));   // floats ~0.75
   // one untimed launch, then the timed ones
   for (int r = 0; r <= reps; ++r) {
     if (r == 1) CU(cudaEventRecord(ctx->t0, ctx->cs));
     if (op == 0) {
       ctx->stats.kernel_launches += apply_A(ctx, ctx->P, ctx->ldv, ctx->Q, ctx->ldv, ncols, nullptr);
+    } else if (op == 3) {
+      ctx->stats.kernel_launches += apply_A32(ctx, ctx->P32, ctx->ldv, ctx->Q32, ctx->ldv, ncols, nullptr);
+    } else if (op >= 4) {
+      launch_wilson_dslash32(ctx->wil32, op == 4 ? +1 : -1, (const float2 *)ctx->P32, ctx->ldv, (float2 *)ctx->Q32,
+                             ctx->ldv, ncols, nullptr, ctx->cs);
+      ctx->stats.kernel_launches += 1;
     } else {
       launch_wilson_dslash(ctx->wil, op == 1 ? +1 : -1, (const double2 *)ctx->P, ctx->ldv, (double2 *)ctx->Q,
                            ctx->ldv, ncols, nullptr, ctx->cs);

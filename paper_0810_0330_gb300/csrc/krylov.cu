@@ -797,6 +797,7 @@ void launch_cg_check(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq
 
 SEED_INSTANTIATE(double)
 SEED_INSTANTIATE(double2)
+SEED_INSTANTIATE(float)
 SEED_INSTANTIATE(float2)
 
 }  // namespace seedk

@@ -85,14 +85,17 @@ struct ReorthBufs {
   double2 *H;              // [m_max+1][2]
 };
 
-// Per-column CG state (lockstep CG over nc columns).
+// Per-column CG state (lockstep CG over nc columns).  rupd, upd and delta are
+// used by the mixed-precision reliable updates only.
 struct CgCols {
   int32_t nc;
-  double *rho, *alpha, *beta, *bnorm, *relres;
-  int32_t *active, *iters, *reached, *restarts, *converged, *needs_check, *mvps;
-  double tol, tol_check;
+  double *rho, *alpha, *beta, *bnorm, *relres, *rupd;
+  int32_t *active, *iters, *reached, *restarts, *converged, *needs_check, *mvps, *upd;
+  double tol, tol_check, delta;
   int32_t maxit, max_restarts;
 };
+constexpr int kCgDoubles = 6;   // arrays of kMaxRhs doubles in CgCols
+constexpr int kCgInts = 8;      // arrays of kMaxRhs int32 in CgCols
 
 // Grid barrier of the persistent kernels (all zeroed before every launch).
 constexpr int kGridSyncWords = 4 + 256;
@@ -129,13 +132,18 @@ void launch_wilson_dslash32(const WilsonOp32 &op, int sign, const float2 *in, in
                             int ncols, const int32_t *col_active, cudaStream_t s);
 
 // CSR (csr.cu)
-struct CsrOp {
+template <class R>
+struct CsrOpT {
   int64_t n;
   const int32_t *row_ptr, *col_idx;
-  const double *vals;
+  const R *vals;
 };
+using CsrOp = CsrOpT<double>;
+using CsrOp32 = CsrOpT<float>;
 void launch_csr_spmv(const CsrOp &op, const double *in, int64_t ldi, double *out, int64_t ldo, int ncols,
                      const int32_t *col_active, cudaStream_t s);
+void launch_csr_spmv32(const CsrOp32 &op, const float *in, int64_t ldi, float *out, int64_t ldo, int ncols,
+                       const int32_t *col_active, cudaStream_t s);
 
 // Seed recurrence, reorthogonalization, CG (krylov.cu)
 int vec_blocks(int64_t n);
@@ -168,6 +176,19 @@ template <class T> void launch_project(int64_t n, const T *V, int64_t ldv, int m
 template <class T> void launch_copy_cols(const T *src, int64_t lds, T *dst, int64_t ldd, int64_t n, int ncols,
                                          cudaStream_t s);
 template <class T> void launch_zero_cols(T *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
+
+// Mixed precision (mixed.cu): T64 / T32 = double / float or double2 / float2.
+template <class T64, class T32>
+void launch_to_low(const T64 *src, int64_t lds, T32 *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
+template <class T64, class T32>   // X += E, E = 0 (columns with mask set; mask NULL = all)
+void launch_fold(T64 *X, int64_t ldx, T32 *E, int64_t lde, int64_t n, int ncols, const int32_t *mask, cudaStream_t s);
+template <class T64, class T32>
+void launch_mixed_init(int64_t n, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P, T32 *E,
+                       int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s);
+void launch_mixed_flag(const CgCols &c, cudaStream_t s);
+template <class T64, class T32>
+void launch_mixed_residual(int64_t n, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P,
+                           int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s);
 
 // Persistent cooperative kernels (persistent.cu).  Seed: runs Lanczos steps
 // i < i_stop (none of which reorthogonalizes) while the recurrence is active;

@@ -29,10 +29,13 @@ def test_library_exports_every_declared_symbol(seedlib):
 
 def test_abi_version_and_defaults(seedlib):
     L = seedlib.lib()
-    assert L.seed_abi_version() == 1
+    assert L.seed_abi_version() == 2
     p = seedlib.seed_params_default()
     assert p.m_max == 1000 and p.reorth_passes == 2 and p.x0_zero == 1
     assert p.tol_seed == 1e-12 and p.tol_rest == 1e-8
+    assert p.precision == 0 and p.reliable_delta == 0.0 and p.kernel_path == 0
+    # the ctypes mirror has the C struct's size (4 + 8 int32, 3 doubles, 4 int32, 1 double)
+    assert C.sizeof(seedlib.seed_params) == 4 * 8 + 8 * 3 + 4 * 4 + 8
 
 
 def test_argument_errors_are_status_codes(seedlib):
@@ -60,6 +63,10 @@ def test_argument_errors_are_status_codes(seedlib):
     bad = P.seed_params_default(reorth_passes=3)
     w.bc_t = 0
     assert L.seed_create_wilson(C.byref(h), C.byref(w), C.byref(bad), None) == P.SEED_EINVAL
+    for kw in (dict(precision=2), dict(precision=-1), dict(reliable_delta=1.0), dict(reliable_delta=-0.5),
+               dict(kernel_path=3)):
+        bad = P.seed_params_default(**kw)
+        assert L.seed_create_wilson(C.byref(h), C.byref(w), C.byref(bad), None) == P.SEED_EINVAL, kw
     # NULL context
     assert L.seed_solve_first(None, None, 0, None, 0, 1, None) == P.SEED_EINVAL
     assert L.seed_solve_rest(None, None, 0, None, 0, 1, None) == P.SEED_EINVAL
