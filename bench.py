@@ -280,6 +280,18 @@ def run_sweep(args):
                         "tflops": fl / (ms * 1e-3) / 1e12, "frac_fp64": fl / (ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
                         "l2_resident": b < L2_BYTES, "reps": reps})
         S.seed_destroy(ctx)
+        # the FP32 copy of the operator (mixed-precision iterations): bound by memory traffic
+        ctx = S.seed_create_wilson(dims, WL["kappa"], U, S.seed_params_default(m_max=4, precision=1))
+        for ncols in (1, 11):
+            b = wilson_bytes(sites, ncols, fp32=True)
+            reps = max(10, min(500, int(4e9 / b)))
+            ms = S.seed_time_operator(ctx, 4, ncols, reps)
+            fl = FLOPS_PER_SITE_D * sites * ncols
+            pts.append({"op": "wilson_D_fp32", "kernel": "k_dslash32<+1>", "dims": dims, "n": 12 * sites,
+                        "ncols": ncols, "ms": ms, "bytes": b, "gbs": b / (ms * 1e-3) / 1e9,
+                        "frac_hbm": b / (ms * 1e-3) / 1e9 / hbm, "tflops": fl / (ms * 1e-3) / 1e12,
+                        "l2_resident": b < L2_BYTES, "reps": reps})
+        S.seed_destroy(ctx)
         del U
         torch.cuda.empty_cache()
     for p in pts:

@@ -190,10 +190,8 @@ seed_status alloc_common(seed_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->eta, sizeof(double2) * kMaxRhs));
   TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs)));
   TRY(dalloc(ctx, &ctx->colnorm, sizeof(double) * kMaxRhs));
-  const int nb = vec_blocks(n);
-  // block partials: seed dots use ceil(63/15) = 5 chunks x nb x 32; lockstep kernels nc x blocks x 2
-  (void)nb;
-  TRY(dalloc(ctx, &ctx->partials, sizeof(double) * 65536));
+  // block partials: seed dots use up to 5 chunks x vec_blocks(n) x 32; lockstep kernels nc x blocks x 2
+  TRY(dalloc(ctx, &ctx->partials, sizeof(double) * kPartials));
   TRY(dalloc(ctx, &ctx->tickets, sizeof(unsigned) * 256));
   // reorthogonalization tiles: ~32 row blocks of >= 256 rows
   int64_t rows = (n + 31) / 32;
@@ -1136,7 +1134,7 @@ seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_
     const int64_t nl = 4 * vol * 9;
     s = dalloc(ctx, &ctx->op32, sizeof(float2) * (size_t)nl);
     if (s == SEED_OK) {
-      launch_to_low<double2, float2>((const double2 *)A->links, nl, (float2 *)ctx->op32, nl, nl, 1, ctx->cs);
+      launch_links_soa32((const double2 *)A->links, (float2 *)ctx->op32, vol, ctx->cs);
       ctx->stats.kernel_launches += 1;
     }
   }

@@ -25,12 +25,17 @@ constexpr int kColTicket = 16;     // tickets[16 + c]: per-column kernels
 #define GRID_STRIDE(e, n) \
   for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < (n); e += (int64_t)gridDim.x * NT)
 
-// Single-vector kernels: at most one block per SM (152), a few elements per
-// thread; the FP64 work of these kernels is a few microseconds, so what
-// matters is few blocks, independent loads per thread and a short tail.
+// Single-vector kernels: one block per SM (152) while that leaves each thread
+// at most 8 elements -- there the work is a few microseconds and what matters
+// is few blocks, independent loads per thread and a short reduction tail --
+// and beyond that up to 8 blocks per SM, so that enough loads are in flight to
+// keep HBM busy on long vectors.
 int vec_blocks(int64_t n) {
-  int64_t b = (n + NT - 1) / NT;
-  if (b > 152) b = 152;
+  int64_t b = (n + NT * 8 - 1) / (NT * 8);
+  if (b < 152) b = 152;
+  const int64_t bmax = (n + NT - 1) / NT;
+  if (b > bmax) b = bmax;
+  if (b > kVecBlocksMax) b = kVecBlocksMax;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -198,7 +203,16 @@ __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
     b.w[e] = we;
     T *x = X + e;
     x[0] = Sc<T>::axpy(zeta, we, x[0]);
-    for (int j = 1; j < b.nrhs; ++j) x[j * ldx] = Sc<T>::caxpy2(s_eta[j], we, x[j * ldx]);
+    // x^j += eta^j w_i, four columns at a time with the loads issued before the stores
+    int j = 1;
+    for (; j + 3 < b.nrhs; j += 4) {
+      const T x0 = x[j * ldx], x1 = x[(j + 1) * ldx], x2 = x[(j + 2) * ldx], x3 = x[(j + 3) * ldx];
+      x[j * ldx] = Sc<T>::caxpy2(s_eta[j], we, x0);
+      x[(j + 1) * ldx] = Sc<T>::caxpy2(s_eta[j + 1], we, x1);
+      x[(j + 2) * ldx] = Sc<T>::caxpy2(s_eta[j + 2], we, x2);
+      x[(j + 3) * ldx] = Sc<T>::caxpy2(s_eta[j + 3], we, x3);
+    }
+    for (; j < b.nrhs; ++j) x[j * ldx] = Sc<T>::caxpy2(s_eta[j], we, x[j * ldx]);
     if (NORM) acc = Sc<T>::nrm2(fe, acc);
   }
   if (!NORM) return;

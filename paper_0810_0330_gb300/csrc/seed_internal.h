@@ -8,6 +8,9 @@ namespace seedk {
 
 constexpr int kMaxRhs = 64;       // right-hand sides per call
 constexpr int kVecThreads = 128;  // threads per block of the vector kernels
+constexpr int kVecBlocksMax = 152 * 8;   // blocks of the single-vector kernels on long vectors
+// device scratch for block partials: the seed dot kernel's 5 chunks x 32 values per block
+constexpr int kPartials = 5 * kVecBlocksMax * 32 + 4096;
 
 // Stop reasons of the seed recurrence (SeedState::stop_reason)
 enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4, STOP_TIMEOUT = 5 };
@@ -67,7 +70,7 @@ struct SeedBufs {
   double *beta_hist;   // [m_max+1], beta_i at index i (beta_0 at 0)
   double *delta_hist;  // [m_max+1]
   double2 *eta;        // [kMaxRhs]
-  double *partials;    // >= nblocks * (2*nrhs + 2) doubles
+  double *partials;    // kPartials doubles
   unsigned *tickets;   // >= 4 counters, zero between launches
 };
 
@@ -119,7 +122,7 @@ struct WilsonOpT {
   int64_t sites;
   double kappa;
   int32_t bc_t;
-  const C *links;         // [4][sites][3][3]
+  const C *links;         // FP64: [4][sites][3][3];  FP32 copy: [4][9][sites]
   const int32_t *nbr;     // [sites][8]
 };
 using WilsonOp = WilsonOpT<double2>;
@@ -128,8 +131,10 @@ void launch_wilson_neighbors(const int32_t dims[4], int32_t *nbr, cudaStream_t s
 void launch_wilson_dslash(const WilsonOp &op, int sign, const double2 *in, int64_t ldi, double2 *out,
                           int64_t ldo, int ncols, const int32_t *col_active, cudaStream_t s);
 int wilson_kernels_per_apply();
+// FP32 copy (links in structure-of-arrays order, see wilson.cu)
 void launch_wilson_dslash32(const WilsonOp32 &op, int sign, const float2 *in, int64_t ldi, float2 *out, int64_t ldo,
                             int ncols, const int32_t *col_active, cudaStream_t s);
+void launch_links_soa32(const double2 *links, float2 *out, int64_t sites, cudaStream_t s);
 
 // CSR (csr.cu)
 template <class R>

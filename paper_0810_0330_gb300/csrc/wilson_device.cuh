@@ -53,26 +53,21 @@ __host__ __device__ constexpr int bP(int mu, int k) {
 }
 
 // One hop of (1 - S g_MU) M psi(nb) into acc[spin*3 + colour];  M = U (FWD) or
-// U^H.  FIRST: acc is overwritten instead of accumulated.  neg: boundary sign
-// mask (0 or the sign bit).
-template <int MU, int S, bool FWD, bool FIRST, bool NC = true, class C>
-SEED_DEV void hop(const C *__restrict__ psi, const C *__restrict__ U, typename CxBits<C>::U neg, C (&acc)[12]) {
+// U^H; psi and U already in registers.  FIRST: acc is overwritten instead of
+// accumulated.  neg: boundary sign mask (0 or the sign bit).
+template <int MU, int S, bool FWD, bool FIRST, class C>
+SEED_DEV void hop_r(const C (&psi)[12], const C (&u)[9], typename CxBits<C>::U neg, C (&acc)[12]) {
   // h_k = psi_k - S * P(k) psi_{2+J(k)}
   constexpr int c0 = S > 0 ? ph_neg(bP(MU, 0)) : bP(MU, 0);
   constexpr int c1 = S > 0 ? ph_neg(bP(MU, 1)) : bP(MU, 1);
   C h0[3], h1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const C p0 = ldv<NC>(psi + a), p1 = ldv<NC>(psi + 3 + a);
-    const C q0 = ldv<NC>(psi + 3 * (2 + bJ(MU, 0)) + a), q1 = ldv<NC>(psi + 3 * (2 + bJ(MU, 1)) + a);
-    h0[a] = ph_add<c0>(p0, q0);
-    h1[a] = ph_add<c1>(p1, q1);
+    h0[a] = ph_add<c0>(psi[a], psi[3 * (2 + bJ(MU, 0)) + a]);
+    h1[a] = ph_add<c1>(psi[3 + a], psi[3 * (2 + bJ(MU, 1)) + a]);
     h0[a].x = xsign(h0[a].x, neg); h0[a].y = xsign(h0[a].y, neg);
     h1[a].x = xsign(h1[a].x, neg); h1[a].y = xsign(h1[a].y, neg);
   }
-  C u[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) u[k] = __ldg(U + k);
   // chi_k = M h_k
   C x0[3], x1[3];
 #pragma unroll
@@ -112,6 +107,17 @@ SEED_DEV void hop(const C *__restrict__ psi, const C *__restrict__ U, typename C
       acc[3 * s1 + a] = ph_add<l1>(acc[3 * s1 + a], x1[a]);
     }
   }
+}
+
+// The same hop with psi and the link read from memory (link as 9 consecutive elements).
+template <int MU, int S, bool FWD, bool FIRST, bool NC = true, class C>
+SEED_DEV void hop(const C *__restrict__ psi, const C *__restrict__ U, typename CxBits<C>::U neg, C (&acc)[12]) {
+  C ps[12], u[9];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) ps[k] = ldv<NC>(psi + k);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = __ldg(U + k);
+  hop_r<MU, S, FWD, FIRST>(ps, u, neg, acc);
 }
 
 template <int MU, int S, bool NC = true, class C>
