@@ -343,13 +343,14 @@ def run_ours(args):
     n = 12 * vol
     U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
     if args.kernel_only:
-        prm = S.seed_params_default(m_max=4)
+        prm = S.seed_params_default(m_max=4, precision=1 if mixed else 0)
         ctx = S.seed_create_wilson(dims, kappa, U, prm)
         ncols = args.ncols or nrhs - 1
-        ms = S.seed_time_operator(ctx, 1, ncols, args.reps)
+        ms = S.seed_time_operator(ctx, 4 if mixed else 1, ncols, args.reps)
         flops = FLOPS_PER_SITE_D * vol * ncols
-        print(json.dumps({"kernel": "k_dslash", "dims": dims, "ncols": ncols, "ms": ms,
-                          "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
+        b = wilson_bytes(vol, ncols, fp32=mixed)
+        print(json.dumps({"kernel": "k_dslash32" if mixed else "k_dslash", "dims": dims, "ncols": ncols, "ms": ms,
+                          "tflops": flops / (ms * 1e-3) / 1e12, "gbs": b / (ms * 1e-3) / 1e9}), flush=True)
         S.seed_destroy(ctx)
         return 0
     prm = S.seed_params_default(m_max=WL["m_max"], reorth_freq=WL["reorth_freq"],

@@ -95,6 +95,8 @@ struct seed_ctx {
   // mixed precision: V, vcur, u, f, w hold FP32 vectors (vsz bytes per element)
   int precision = 0;
   size_t vsz = 8;
+  int64_t nv = 0;                      // length of the Krylov vectors (n, or the tiled FP32 length)
+  Layout32 lay{0};                     // FP32 vector layout of the mixed path (tiled for Wilson)
   WilsonOp32 wil32{};
   CsrOp32 csr32{};
   void *op32 = nullptr;                // FP32 copy of the links / matrix values
@@ -174,8 +176,9 @@ seed_status dalloc(seed_ctx *ctx, Tp **p, size_t bytes) {
   } while (0)
 
 seed_status alloc_common(seed_ctx *ctx) {
-  const int64_t n = ctx->n;
-  const size_t es = ctx->vsz;   // Krylov vectors: FP64, or FP32 in mixed precision
+  // Krylov vectors: FP64 of length n, or FP32 of length nv (tiled by 32 sites for Wilson)
+  const int64_t n = ctx->nv;
+  const size_t es = ctx->vsz;
   const int m = ctx->prm.m_max;
   ctx->ldv = (n + 31) / 32 * 32;   // 256-byte aligned columns for complex, 256 B for real
   TRY(dalloc(ctx, &ctx->V, (size_t)ctx->ldv * (m + 1) * es));
@@ -270,13 +273,17 @@ int apply_A(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, int
 }
 
 // Y = A X with the FP32 copy of the operator (mixed precision).  Returns the kernel count.
-int apply_A32(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, int ncols, const int32_t *mask) {
+// tiled: X and Y in the solver's tiled FP32 layout (else the caller's site-major one).
+int apply_A32(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, int ncols, const int32_t *mask,
+              bool tiled = true) {
   if (ctx->kind == 0) {
     launch_csr_spmv32(ctx->csr32, (const float *)X, ldx, (float *)Y, ldy, ncols, mask, ctx->cs);
     return 1;
   }
-  launch_wilson_dslash32(ctx->wil32, +1, (const float2 *)X, ldx, (float2 *)ctx->T32, ctx->ldv, ncols, mask, ctx->cs);
-  launch_wilson_dslash32(ctx->wil32, -1, (const float2 *)ctx->T32, ctx->ldv, (float2 *)Y, ldy, ncols, mask, ctx->cs);
+  launch_wilson_dslash32(ctx->wil32, +1, (const float2 *)X, ldx, (float2 *)ctx->T32, ctx->ldv, ncols, mask, tiled,
+                         ctx->cs);
+  launch_wilson_dslash32(ctx->wil32, -1, (const float2 *)ctx->T32, ctx->ldv, (float2 *)Y, ldy, ncols, mask, tiled,
+                         ctx->cs);
   return 2;
 }
 
@@ -288,7 +295,7 @@ template <class T> T *E_cols(seed_ctx *ctx) { return (T *)ctx->E32 + ctx->ldv; }
 template <class T>
 SeedBufs<T> seed_bufs(seed_ctx *ctx, int nrhs) {
   SeedBufs<T> b;
-  b.n = ctx->n;
+  b.n = kLow<T> ? ctx->nv : ctx->n;
   b.nrhs = nrhs;
   b.nblocks = vec_blocks(ctx->n);
   b.V = (T *)ctx->V;
@@ -317,7 +324,7 @@ SeedBufs<T> seed_bufs(seed_ctx *ctx, int nrhs) {
 template <class T>
 ReorthBufs<T> reorth_bufs(seed_ctx *ctx) {
   ReorthBufs<T> r;
-  r.n = ctx->n;
+  r.n = kLow<T> ? ctx->nv : ctx->n;
   r.rows_per_item = ctx->rows_per_item;
   r.nrb = ctx->nrb;
   r.nitems_grid = 152 * 4;
@@ -750,7 +757,7 @@ seed_status run_graph(seed_ctx *ctx, const std::string &key, F issue) {
 // FP64 alpha / beta / norms); x is the FP32 correction E (call32[1]).
 template <class T32>
 int issue_mixed_iter(seed_ctx *ctx, const CgCols &c) {
-  const int64_t n = ctx->n, ld = ctx->ldv;
+  const int64_t n = ctx->nv, ld = ctx->ldv;
   int k = apply_A32(ctx, ctx->P32, ld, ctx->Q32, ld, c.nc, c.active);
   launch_cg_alpha<T32>(n, (const T32 *)ctx->P32, (const T32 *)ctx->Q32, ld, c, ctx->partials, ctx->tickets, ctx->cs);
   launch_cg_update<T32>(n, ctx->call32 + 1, (T32 *)ctx->R32, (const T32 *)ctx->P32, (const T32 *)ctx->Q32, ld, c,
@@ -765,7 +772,8 @@ int issue_mixed_iter(seed_ctx *ctx, const CgCols &c) {
 template <class T64, class T32>
 seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t ldx, int c0, int nc, double tol,
                      CgCols *cols_out) {
-  const int64_t n = ctx->n, ld = ctx->ldv;
+  const int64_t nv = ctx->nv, ld = ctx->ldv;
+  const Layout32 lay = ctx->lay;
   CgCols c = cg_cols(ctx, nc);
   c.tol = tol;
   c.tol_check = tol;
@@ -773,7 +781,7 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
   const CallArgs ca{(void *)(E - ld), ld};   // k_cg_update writes column col+1 of call->X
   CU(cudaMemcpyAsync(ctx->call32 + 1, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
   int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
-  launch_mixed_init<T64, T32>(n, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, E, ld, c,
+  launch_mixed_init<T64, T32>(nv, lay, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, E, ld, c,
                               ctx->partials, ctx->tickets, ctx->cs);
   ctx->stats.kernel_launches += kern + 1;
   ctx->stats.mvps += nc;
@@ -790,10 +798,10 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
     }));
     // reliable updates (direct launches: B and X are this call's buffers)
     launch_mixed_flag(c, ctx->cs);
-    launch_fold<T64, T32>(Xc, ldx, E, ld, n, nc, c.upd, ctx->cs);
+    launch_fold<T64, T32>(Xc, ldx, E, ld, nv, lay, nc, c.upd, ctx->cs);
     kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, c.upd);
-    launch_mixed_residual<T64, T32>(n, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, ld, c,
-                                    ctx->partials, ctx->tickets, ctx->cs);
+    launch_mixed_residual<T64, T32>(nv, lay, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, ld,
+                                    c, ctx->partials, ctx->tickets, ctx->cs);
     ctx->stats.kernel_launches += kern + 3;
     CU(cudaMemcpyAsync(ctx->h_flags + slot * kMaxRhs, c.active, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost,
                        ctx->cs));
@@ -862,18 +870,19 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
 
   // Step 1 in FP64: r_0^j = b^j - A x_0^j, rounded to FP32 (column 0 starts the Lanczos run)
   int kern = 0;
+  const int64_t nv = ctx->nv;
   if (p.x0_zero) {
     launch_zero_cols<T64>((T64 *)X, ldx, n, nrhs, ctx->cs);
-    launch_to_low<T64, T32>((const T64 *)B, ldb, (T32 *)ctx->R32, ld, n, nrhs, ctx->cs);
+    launch_to_low<T64, T32>((const T64 *)B, ldb, (T32 *)ctx->R32, ld, nv, ctx->lay, nrhs, ctx->cs);
     kern += 2;
   } else {
     kern += apply_A(ctx, X, ldx, ctx->Q, ld, nrhs, nullptr);
     ctx->stats.mvps += nrhs;
     launch_sub_from<T64>((const T64 *)B, ldb, (const T64 *)ctx->Q, ld, (T64 *)ctx->P, ld, n, nrhs, ctx->cs);
-    launch_to_low<T64, T32>((const T64 *)ctx->P, ld, (T32 *)ctx->R32, ld, n, nrhs, ctx->cs);
+    launch_to_low<T64, T32>((const T64 *)ctx->P, ld, (T32 *)ctx->R32, ld, nv, ctx->lay, nrhs, ctx->cs);
     kern += 2;
   }
-  launch_zero_cols<T32>(E, ld, n, nrhs, ctx->cs);
+  launch_zero_cols<T32>(E, ld, nv, nrhs, ctx->cs);
   launch_colnorms<T64>(n, (const T64 *)B, ldb, 1, &ctx->st->bnorm1, ctx->partials, ctx->tickets, ctx->cs);
   SeedBufs<T32> b = seed_bufs<T32>(ctx, nrhs);
   launch_seed_start<T32>(b, (const T32 *)ctx->R32, ctx->cs);
@@ -898,7 +907,7 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
                                        ": operator not positive definite in floating point");
   }
   // x^j += e^j (the FP32 Lanczos corrections), then system 1 to tol_seed
-  launch_fold<T64, T32>((T64 *)X, ldx, E, ld, n, nrhs, nullptr, ctx->cs);
+  launch_fold<T64, T32>((T64 *)X, ldx, E, ld, nv, ctx->lay, nrhs, nullptr, ctx->cs);
   ctx->stats.kernel_launches += 1;
   TRY((mixed_cg<T64, T32>(ctx, (const T64 *)B, ldb, (T64 *)X, ldx, 0, 1, p.tol_seed, nullptr)));
   CU(cudaEventRecord(ctx->t1, ctx->cs));
@@ -1088,12 +1097,15 @@ seed_status seed_create_csr(seed_ctx **out, const seed_csr *A, const seed_params
   ctx->n = A->n;
   ctx->esz = sizeof(double);
   ctx->vsz = ctx->precision == 1 ? sizeof(float) : sizeof(double);
+  ctx->nv = A->n;
+  ctx->lay = Layout32{0};
   ctx->csr = CsrOp{A->n, A->row_ptr, A->col_idx, A->vals};
   s = alloc_common(ctx);
   if (s == SEED_OK && ctx->precision == 1) {
     s = dalloc(ctx, &ctx->op32, sizeof(float) * (size_t)(A->nnz > 0 ? A->nnz : 1));
     if (s == SEED_OK) {
-      if (A->nnz > 0) launch_to_low<double, float>(A->vals, A->nnz, (float *)ctx->op32, A->nnz, A->nnz, 1, ctx->cs);
+      if (A->nnz > 0)
+        launch_to_low<double, float>(A->vals, A->nnz, (float *)ctx->op32, A->nnz, A->nnz, Layout32{0}, 1, ctx->cs);
       ctx->stats.kernel_launches += A->nnz > 0;
       ctx->csr32 = CsrOp32{A->n, A->row_ptr, A->col_idx, (const float *)ctx->op32};
     }
@@ -1128,6 +1140,8 @@ seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_
   ctx->n = 12 * vol;
   ctx->esz = sizeof(double2);
   ctx->vsz = ctx->precision == 1 ? sizeof(float2) : sizeof(double2);
+  ctx->lay = Layout32{ctx->precision == 1 ? vol : 0};
+  ctx->nv = ctx->lay.length(ctx->n);
   s = alloc_common(ctx);
   if (s == SEED_OK) s = dalloc(ctx, &ctx->nbr, sizeof(int32_t) * 8 * vol);
   if (s == SEED_OK && ctx->precision == 1) {
@@ -1249,10 +1263,10 @@ seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, vo
   TRY(ensure_cols(ctx, ncols));
   StreamScope scope(ctx);
   if (op == 3) {
-    ctx->stats.kernel_launches += apply_A32(ctx, X, ldx, Y, ldy, ncols, nullptr);
+    ctx->stats.kernel_launches += apply_A32(ctx, X, ldx, Y, ldy, ncols, nullptr, false);
   } else if (op >= 4) {
     launch_wilson_dslash32(ctx->wil32, op == 4 ? +1 : -1, (const float2 *)X, ldx, (float2 *)Y, ldy, ncols, nullptr,
-                           ctx->cs);
+                           false, ctx->cs);
     ctx->stats.kernel_launches += 1;
   } else if (op == 0) {
     ctx->stats.kernel_launches += apply_A(ctx, X, ldx, Y, ldy, ncols, nullptr);
@@ -1322,7 +1336,7 @@ seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t
       ctx->stats.kernel_launches += apply_A32(ctx, ctx->P32, ctx->ldv, ctx->Q32, ctx->ldv, ncols, nullptr);
     } else if (op >= 4) {
       launch_wilson_dslash32(ctx->wil32, op == 4 ? +1 : -1, (const float2 *)ctx->P32, ctx->ldv, (float2 *)ctx->Q32,
-                             ctx->ldv, ncols, nullptr, ctx->cs);
+                             ctx->ldv, ncols, nullptr, true, ctx->cs);
       ctx->stats.kernel_launches += 1;
     } else {
       launch_wilson_dslash(ctx->wil, op == 1 ? +1 : -1, (const double2 *)ctx->P, ctx->ldv, (double2 *)ctx->Q,

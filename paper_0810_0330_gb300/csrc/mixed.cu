@@ -27,34 +27,42 @@ SEED_DEV float2 lo(double2 x) { return make_float2((float)x.x, (float)x.y); }
 SEED_DEV double hi(float x) { return (double)x; }
 SEED_DEV double2 hi(float2 x) { return make_double2((double)x.x, (double)x.y); }
 
-// dst = FP32 rounding of src (grid.y columns; also used once for the links / values)
+// In every kernel below t runs over the FP32 vector (length n32, Layout32 L)
+// and e = L.to_user(t) is the caller's element (-1: padding, kept zero).
+
+// dst = FP32 rounding of src (grid.y columns; also used once for the CSR values)
 template <class T64, class T32>
-__global__ void __launch_bounds__(NT) k_to_low(const T64 *src, int64_t lds, T32 *dst, int64_t ldd, int64_t n) {
+__global__ void __launch_bounds__(NT) k_to_low(const T64 *src, int64_t lds, T32 *dst, int64_t ldd, int64_t n32,
+                                               Layout32 L) {
   src += (int64_t)blockIdx.y * lds;
   dst += (int64_t)blockIdx.y * ldd;
-  GRID_STRIDE(e, n) dst[e] = lo(src[e]);
+  GRID_STRIDE(t, n32) {
+    const int64_t e = L.to_user(t);
+    dst[t] = e >= 0 ? lo(src[e]) : Sc<T32>::zero();
+  }
 }
 
 // X += E (FP64 += FP32), then E = 0; mask: only columns whose flag is set (NULL: all)
 template <class T64, class T32>
-__global__ void __launch_bounds__(NT) k_fold(T64 *X, int64_t ldx, T32 *E, int64_t lde, int64_t n,
+__global__ void __launch_bounds__(NT) k_fold(T64 *X, int64_t ldx, T32 *E, int64_t lde, int64_t n32, Layout32 L,
                                              const int32_t *mask) {
   const int col = blockIdx.y;
   if (mask != nullptr && mask[col] == 0) return;
   X += (int64_t)col * ldx;
   E += (int64_t)col * lde;
-  GRID_STRIDE(e, n) {
-    X[e] = Sc<T64>::add(X[e], hi(E[e]));
-    E[e] = Sc<T32>::zero();
+  GRID_STRIDE(t, n32) {
+    const int64_t e = L.to_user(t);
+    if (e >= 0) X[e] = Sc<T64>::add(X[e], hi(E[t]));
+    E[t] = Sc<T32>::zero();
   }
 }
 
 // Start of mixed CG on nc columns: r = b - q (q = A x in FP64), R32 = lo(r),
 // P32 = R32, E = 0; rho = ||r||^2, ||b||; a column already within tol is done.
 template <class T64, class T32>
-__global__ void __launch_bounds__(NT) k_mixed_init(int64_t n, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq,
-                                                   T32 *R, T32 *P, T32 *E, int64_t ld, CgCols c, double *partials,
-                                                   unsigned *tickets) {
+__global__ void __launch_bounds__(NT) k_mixed_init(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, const T64 *Q,
+                                                   int64_t ldq, T32 *R, T32 *P, T32 *E, int64_t ld, CgCols c,
+                                                   double *partials, unsigned *tickets) {
   __shared__ double sm[2 * NT / 32];
   const int col = blockIdx.y;
   B += (int64_t)col * ldb;
@@ -63,13 +71,14 @@ __global__ void __launch_bounds__(NT) k_mixed_init(int64_t n, const T64 *B, int6
   P += (int64_t)col * ld;
   E += (int64_t)col * ld;
   double rr = 0.0, bb = 0.0;
-  GRID_STRIDE(e, n) {
-    const T64 bv = B[e];
-    const T64 r = Sc<T64>::sub(bv, Q[e]);
+  GRID_STRIDE(t, n32) {
+    const int64_t e = L.to_user(t);
+    const T64 bv = e >= 0 ? B[e] : Sc<T64>::zero();
+    const T64 r = e >= 0 ? Sc<T64>::sub(bv, Q[e]) : Sc<T64>::zero();
     const T32 r32 = lo(r);
-    R[e] = r32;
-    P[e] = r32;
-    E[e] = Sc<T32>::zero();
+    R[t] = r32;
+    P[t] = r32;
+    E[t] = Sc<T32>::zero();
     rr = Sc<T64>::nrm2(r, rr);
     bb = Sc<T64>::nrm2(bv, bb);
   }
@@ -120,9 +129,9 @@ __global__ void k_mixed_flag(CgCols c) {
 // stopped restart with p = r; the others keep p.  Converged when the FP64
 // true residual meets tol.
 template <class T64, class T32>
-__global__ void __launch_bounds__(NT) k_mixed_residual(int64_t n, const T64 *B, int64_t ldb, const T64 *Q,
-                                                       int64_t ldq, T32 *R, T32 *P, int64_t ld, CgCols c,
-                                                       double *partials, unsigned *tickets) {
+__global__ void __launch_bounds__(NT) k_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb,
+                                                       const T64 *Q, int64_t ldq, T32 *R, T32 *P, int64_t ld,
+                                                       CgCols c, double *partials, unsigned *tickets) {
   __shared__ double sm[NT / 32];
   const int col = blockIdx.y;
   if (!c.upd[col]) return;
@@ -132,11 +141,12 @@ __global__ void __launch_bounds__(NT) k_mixed_residual(int64_t n, const T64 *B, 
   R += (int64_t)col * ld;
   P += (int64_t)col * ld;
   double rr = 0.0;
-  GRID_STRIDE(e, n) {
-    const T64 r = Sc<T64>::sub(B[e], Q[e]);
+  GRID_STRIDE(t, n32) {
+    const int64_t e = L.to_user(t);
+    const T64 r = e >= 0 ? Sc<T64>::sub(B[e], Q[e]) : Sc<T64>::zero();
     const T32 r32 = lo(r);
-    R[e] = r32;
-    if (restart) P[e] = r32;
+    R[t] = r32;
+    if (restart) P[t] = r32;
     rr = Sc<T64>::nrm2(r, rr);
   }
   double v[1] = {rr};
@@ -172,38 +182,43 @@ __global__ void __launch_bounds__(NT) k_mixed_residual(int64_t n, const T64 *B, 
 // launchers
 // ---------------------------------------------------------------------------
 template <class T64, class T32>
-void launch_to_low(const T64 *src, int64_t lds, T32 *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s) {
-  int64_t b = (n + NT * 4 - 1) / (NT * 4);
+void launch_to_low(const T64 *src, int64_t lds, T32 *dst, int64_t ldd, int64_t n32, Layout32 L, int ncols,
+                   cudaStream_t s) {
+  int64_t b = (n32 + NT * 4 - 1) / (NT * 4);
   if (b > 152 * 8) b = 152 * 8;
   if (b < 1) b = 1;
-  k_to_low<T64, T32><<<dim3((unsigned)b, (unsigned)ncols), NT, 0, s>>>(src, lds, dst, ldd, n);
+  k_to_low<T64, T32><<<dim3((unsigned)b, (unsigned)ncols), NT, 0, s>>>(src, lds, dst, ldd, n32, L);
 }
 template <class T64, class T32>
-void launch_fold(T64 *X, int64_t ldx, T32 *E, int64_t lde, int64_t n, int ncols, const int32_t *mask, cudaStream_t s) {
-  k_fold<T64, T32><<<dim3((unsigned)col_blocks(n, ncols), (unsigned)ncols), NT, 0, s>>>(X, ldx, E, lde, n, mask);
+void launch_fold(T64 *X, int64_t ldx, T32 *E, int64_t lde, int64_t n32, Layout32 L, int ncols, const int32_t *mask,
+                 cudaStream_t s) {
+  k_fold<T64, T32><<<dim3((unsigned)col_blocks(n32, ncols), (unsigned)ncols), NT, 0, s>>>(X, ldx, E, lde, n32, L,
+                                                                                         mask);
 }
 template <class T64, class T32>
-void launch_mixed_init(int64_t n, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P, T32 *E,
-                       int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s) {
-  k_mixed_init<T64, T32><<<dim3((unsigned)col_blocks(n, c.nc), (unsigned)c.nc), NT, 0, s>>>(
-      n, B, ldb, Q, ldq, R, P, E, ld, c, partials, tickets);
+void launch_mixed_init(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P,
+                       T32 *E, int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s) {
+  k_mixed_init<T64, T32><<<dim3((unsigned)col_blocks(n32, c.nc), (unsigned)c.nc), NT, 0, s>>>(
+      n32, L, B, ldb, Q, ldq, R, P, E, ld, c, partials, tickets);
 }
 void launch_mixed_flag(const CgCols &c, cudaStream_t s) { k_mixed_flag<<<1, kMaxRhs, 0, s>>>(c); }
 template <class T64, class T32>
-void launch_mixed_residual(int64_t n, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P,
-                           int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s) {
-  k_mixed_residual<T64, T32><<<dim3((unsigned)col_blocks(n, c.nc), (unsigned)c.nc), NT, 0, s>>>(
-      n, B, ldb, Q, ldq, R, P, ld, c, partials, tickets);
+void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R,
+                           T32 *P, int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s) {
+  k_mixed_residual<T64, T32><<<dim3((unsigned)col_blocks(n32, c.nc), (unsigned)c.nc), NT, 0, s>>>(
+      n32, L, B, ldb, Q, ldq, R, P, ld, c, partials, tickets);
 }
 
-#define MIXED_INSTANTIATE(T64, T32)                                                                            \
-  template void launch_to_low<T64, T32>(const T64 *, int64_t, T32 *, int64_t, int64_t, int, cudaStream_t);     \
-  template void launch_fold<T64, T32>(T64 *, int64_t, T32 *, int64_t, int64_t, int, const int32_t *,           \
-                                      cudaStream_t);                                                           \
-  template void launch_mixed_init<T64, T32>(int64_t, const T64 *, int64_t, const T64 *, int64_t, T32 *, T32 *,  \
-                                            T32 *, int64_t, const CgCols &, double *, unsigned *, cudaStream_t); \
-  template void launch_mixed_residual<T64, T32>(int64_t, const T64 *, int64_t, const T64 *, int64_t, T32 *,    \
-                                                T32 *, int64_t, const CgCols &, double *, unsigned *,          \
+#define MIXED_INSTANTIATE(T64, T32)                                                                              \
+  template void launch_to_low<T64, T32>(const T64 *, int64_t, T32 *, int64_t, int64_t, Layout32, int,           \
+                                        cudaStream_t);                                                           \
+  template void launch_fold<T64, T32>(T64 *, int64_t, T32 *, int64_t, int64_t, Layout32, int, const int32_t *,   \
+                                      cudaStream_t);                                                             \
+  template void launch_mixed_init<T64, T32>(int64_t, Layout32, const T64 *, int64_t, const T64 *, int64_t, T32 *, \
+                                            T32 *, T32 *, int64_t, const CgCols &, double *, unsigned *,        \
+                                            cudaStream_t);                                                       \
+  template void launch_mixed_residual<T64, T32>(int64_t, Layout32, const T64 *, int64_t, const T64 *, int64_t,    \
+                                                T32 *, T32 *, int64_t, const CgCols &, double *, unsigned *,     \
                                                 cudaStream_t);
 
 MIXED_INSTANTIATE(double, float)

@@ -131,9 +131,11 @@ void launch_wilson_neighbors(const int32_t dims[4], int32_t *nbr, cudaStream_t s
 void launch_wilson_dslash(const WilsonOp &op, int sign, const double2 *in, int64_t ldi, double2 *out,
                           int64_t ldo, int ncols, const int32_t *col_active, cudaStream_t s);
 int wilson_kernels_per_apply();
-// FP32 copy (links in structure-of-arrays order, see wilson.cu)
+// FP32 copy (links in structure-of-arrays order, see wilson.cu).  tiled: the
+// spinor vectors use the mixed path's 32-site tiled layout (Layout32), else the
+// caller's site-major layout.
 void launch_wilson_dslash32(const WilsonOp32 &op, int sign, const float2 *in, int64_t ldi, float2 *out, int64_t ldo,
-                            int ncols, const int32_t *col_active, cudaStream_t s);
+                            int ncols, const int32_t *col_active, bool tiled, cudaStream_t s);
 void launch_links_soa32(const double2 *links, float2 *out, int64_t sites, cudaStream_t s);
 
 // CSR (csr.cu)
@@ -182,18 +184,37 @@ template <class T> void launch_copy_cols(const T *src, int64_t lds, T *dst, int6
                                          cudaStream_t s);
 template <class T> void launch_zero_cols(T *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
 
+// Index map from the mixed path's FP32 vectors to the caller's vectors.  For a
+// Wilson operator the FP32 vectors are tiled by 32 sites: component k (0..11)
+// of site s lives at ((s / 32) * 12 + k) * 32 + s % 32, so that a warp reading
+// one component of 32 consecutive sites reads 256 contiguous bytes; the
+// vector length is 12 * 32 * ceil(sites / 32) and sites beyond the lattice are
+// zero padding.  For CSR (sites == 0) the map is the identity.
+struct Layout32 {
+  int64_t sites;
+  __host__ __device__ int64_t to_user(int64_t t) const {   // -1 for padding
+    if (sites == 0) return t;
+    const int64_t blk = t / 384, rem = t - blk * 384, s = blk * 32 + (rem & 31);
+    return s < sites ? 12 * s + (rem >> 5) : -1;
+  }
+  __host__ __device__ int64_t length(int64_t n) const { return sites == 0 ? n : 384 * ((sites + 31) / 32); }
+};
+
 // Mixed precision (mixed.cu): T64 / T32 = double / float or double2 / float2.
+// n32: length of the FP32 vectors (Layout32::length); user vectors follow L.
 template <class T64, class T32>
-void launch_to_low(const T64 *src, int64_t lds, T32 *dst, int64_t ldd, int64_t n, int ncols, cudaStream_t s);
+void launch_to_low(const T64 *src, int64_t lds, T32 *dst, int64_t ldd, int64_t n32, Layout32 L, int ncols,
+                   cudaStream_t s);
 template <class T64, class T32>   // X += E, E = 0 (columns with mask set; mask NULL = all)
-void launch_fold(T64 *X, int64_t ldx, T32 *E, int64_t lde, int64_t n, int ncols, const int32_t *mask, cudaStream_t s);
+void launch_fold(T64 *X, int64_t ldx, T32 *E, int64_t lde, int64_t n32, Layout32 L, int ncols, const int32_t *mask,
+                 cudaStream_t s);
 template <class T64, class T32>
-void launch_mixed_init(int64_t n, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P, T32 *E,
-                       int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s);
+void launch_mixed_init(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P,
+                       T32 *E, int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s);
 void launch_mixed_flag(const CgCols &c, cudaStream_t s);
 template <class T64, class T32>
-void launch_mixed_residual(int64_t n, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R, T32 *P,
-                           int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s);
+void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, const T64 *Q, int64_t ldq, T32 *R,
+                           T32 *P, int64_t ld, const CgCols &c, double *partials, unsigned *tickets, cudaStream_t s);
 
 // Persistent cooperative kernels (persistent.cu).  Seed: runs Lanczos steps
 // i < i_stop (none of which reorthogonalizes) while the recurrence is active;
