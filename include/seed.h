@@ -202,6 +202,26 @@ seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int
 seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
                             int32_t nrhs, seed_info *info);
 
+/* Lockstep CG (Sec. 1; the iteration of seed_solve_rest) on ALL ncols columns
+ * of B from the initial guesses in X, to ||b^j - A x^j|| <= tol_rest ||b^j||
+ * (mixed-precision contexts: FP32 iterations with FP64 reliable updates).
+ * This finishes systems whose guesses come from elsewhere, e.g. seed_project
+ * over a kept basis (the backward solves of an adjoint, Sec. 2.1's projection
+ * reused for new right-hand sides).  The paper has no separate entry for it.
+ *   B, X: device, column-major n x ncols; X in = guesses, out = solutions.
+ *   info: NULL or ncols entries.  Returns SEED_OK or SEED_ENOTCONV. */
+seed_status seed_solve_cg(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t ncols,
+                          seed_info *info);
+
+/* Adjoint helper for Wilson contexts (no counterpart in the paper):
+ *   *out = sum_j Re <Lambda_j, (dA/dkappa) X_j>,   A = D^H D, D = 1 - kappa H,
+ * so dA/dkappa = -(H^H D + D^H H).  With x^j = A^{-1} b^j, a real loss L and
+ * lambda^j = A^{-1} (dL/dx^j) (the conjugate-Wirtinger gradient convention),
+ * dL/dkappa = -(*out).  Lambda, X: device, column-major n x ncols (complex
+ * double).  Synchronises.  SEED_EINVAL on a CSR context. */
+seed_status seed_grad_kappa(seed_ctx *ctx, const void *Lambda, int64_t ldl, const void *X, int64_t ldx,
+                            int32_t ncols, double *out);
+
 /* Y = op(X) for ncols columns: op 0 = A; for Wilson contexts op 1 = D and
  * op 2 = D^H (used e.g. to form normal-equation right-hand sides b = D^H eta,
  * Sec. 4).  On a mixed-precision context ops 3 = A, 4 = D, 5 = D^H apply the

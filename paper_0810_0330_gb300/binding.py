@@ -31,7 +31,7 @@ STATUS_NAMES = ["SEED_OK", "SEED_EINVAL", "SEED_ENOMEM", "SEED_ECUDA", "SEED_ENO
 EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_create_wilson",
            "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
-           "seed_destroy", "seed_wilson_apply_noalloc"]
+           "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa"]
 
 
 class SeedError(RuntimeError):
@@ -100,6 +100,8 @@ def lib():
             L.seed_get_stats.argtypes = [P, C.POINTER(seed_stats)]
             L.seed_time_operator.argtypes = [P, I32, I32, I32, C.POINTER(C.c_double)]
             L.seed_wilson_apply_noalloc.argtypes = [C.POINTER(seed_wilson), P, I64, P, I64, I32, P]
+            L.seed_solve_cg.argtypes = [P, P, I64, P, I64, I32, P]
+            L.seed_grad_kappa.argtypes = [P, P, I64, P, I64, I32, C.POINTER(C.c_double)]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
             L.seed_destroy.argtypes = [P]
@@ -207,6 +209,28 @@ def seed_solve_rest(ctx: Context, B: torch.Tensor, X: torch.Tensor):
     info = _infos(nb)
     _check(lib().seed_solve_rest(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_rest", ctx.handle)
     return [i.as_dict() for i in info]
+
+
+def seed_solve_cg(ctx: Context, B: torch.Tensor, X: torch.Tensor):
+    """CG on every column of B from the guesses in X (X is overwritten with the solutions)."""
+    pb, ldb, nb = _block(B, ctx.n, "B")
+    px, ldx, nx = _block(X, ctx.n, "X")
+    if nb != nx:
+        raise ValueError("B and X must have the same number of columns")
+    info = _infos(nb)
+    _check(lib().seed_solve_cg(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_cg", ctx.handle)
+    return [i.as_dict() for i in info]
+
+
+def seed_grad_kappa(ctx: Context, Lam: torch.Tensor, X: torch.Tensor) -> float:
+    """sum_j Re <Lam_j, (dA/dkappa) X_j> for a Wilson context."""
+    pl, ldl, nl = _block(Lam, ctx.n, "Lambda")
+    px, ldx, nx = _block(X, ctx.n, "X")
+    if nl != nx:
+        raise ValueError("Lambda and X must have the same number of columns")
+    out = C.c_double()
+    _check(lib().seed_grad_kappa(ctx.handle, pl, ldl, px, ldx, nl, C.byref(out)), "seed_grad_kappa", ctx.handle)
+    return out.value
 
 
 def seed_project(ctx: Context, B: torch.Tensor, X: torch.Tensor):

@@ -476,7 +476,7 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   ctx->seeded = false;
   CU(cudaEventRecord(ctx->t0, ctx->cs));
 
-  CallArgs ca{X, ldx};
+  CallArgs ca{X, ldx, 0};
   CU(cudaMemcpyAsync(ctx->call, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
   SeedState s0{};
   s0.tol_rel = p.tol_seed;
@@ -618,21 +618,20 @@ seed_status launch_cg_run(seed_ctx *ctx, const CgCols &c, int len) {
   return SEED_OK;
 }
 
+// Lockstep CG (Sec. 1, Sec. 2.2) on the nc columns of Bc / Xc from the guesses
+// in Xc; info: NULL or nc entries.
 template <class T>
-seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
-                            seed_info *info) {
+seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx, int nc, seed_info *info) {
   const int64_t n = ctx->n, ld = ctx->ldv;
-  const int nc = nrhs - 1;
-  if (info) std::memset(info + 1, 0, sizeof(seed_info) * nc);
+  if (info) std::memset(info, 0, sizeof(seed_info) * nc);
   if (nc <= 0) return SEED_OK;
-  TRY(ensure_cols(ctx, nrhs));
+  TRY(ensure_cols(ctx, nc));
   CU(cudaEventRecord(ctx->t2, ctx->cs));
-  CallArgs ca{X, ldx};
+  CallArgs ca{Xc, ldx, 0};
   CU(cudaMemcpyAsync(ctx->call, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
   const CgCols c = cg_cols(ctx, nc);
-  const T *Bc = (const T *)B + ldb;
   // K7: true residual of the seeded systems, then p = r
-  int kern = apply_A(ctx, (const T *)X + ldx, ldx, ctx->Q, ld, nc, nullptr);
+  int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
   launch_cg_init<T>(n, Bc, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, (T *)ctx->P, ld, c, ctx->partials, ctx->tickets,
                     false, ctx->cs);
   ctx->stats.kernel_launches += kern + 1;
@@ -685,7 +684,7 @@ seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
         if (e) cudaEventDestroy(e);
     }
     // true residuals of the columns that stopped; restarts where needed
-    kern = apply_A(ctx, (const T *)X + ldx, ldx, ctx->Q, ld, nc, c.needs_check);
+    kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, c.needs_check);
     launch_cg_check<T>(n, Bc, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, ld, c, ctx->partials, ctx->tickets, ctx->cs);
     launch_cg_init<T>(n, Bc, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, (T *)ctx->P, ld, c, ctx->partials,
                       ctx->tickets, true, ctx->cs);
@@ -714,7 +713,7 @@ seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
     all &= conv != 0;
     mv += hi[6 * kMaxRhs + j];
     if (info) {
-      seed_info &o = info[j + 1];
+      seed_info &o = info[j];
       o.iters = hi[kMaxRhs + j];
       o.mvps = hi[6 * kMaxRhs + j];
       o.restarts = hi[3 * kMaxRhs + j];
@@ -726,6 +725,18 @@ seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
   ctx->stats.mvps += mv - nc;   // the initial residual was counted above
   if (!all) return fail(ctx, SEED_ENOTCONV, "CG did not reach tol_rest on every system within maxit_rest");
   return SEED_OK;
+}
+
+template <class T>
+seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
+                            seed_info *info) {
+  const int nc = nrhs - 1;
+  if (nc <= 0) {
+    if (info && nrhs > 1) std::memset(info + 1, 0, sizeof(seed_info) * (nrhs - 1));
+    return SEED_OK;
+  }
+  TRY(ensure_cols(ctx, nrhs));
+  return cg_impl<T>(ctx, (const T *)B + ldb, ldb, (T *)X + ldx, ldx, nc, info ? info + 1 : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -778,7 +789,7 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
   c.tol = tol;
   c.tol_check = tol;
   T32 *E = E_cols<T32>(ctx) + (int64_t)c0 * ld;
-  const CallArgs ca{(void *)(E - ld), ld};   // k_cg_update writes column col+1 of call->X
+  const CallArgs ca{(void *)E_cols<T32>(ctx), ld, c0};   // CG column c corrects system c0 + c + 1
   CU(cudaMemcpyAsync(ctx->call32 + 1, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
   int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
   launch_mixed_init<T64, T32>(nv, lay, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, E, ld, c,
@@ -856,7 +867,7 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   ctx->seeded = false;
   CU(cudaEventRecord(ctx->t0, ctx->cs));
   T32 *E = E_cols<T32>(ctx);
-  const CallArgs ca{(void *)E, ld};
+  const CallArgs ca{(void *)E, ld, 0};
   CU(cudaMemcpyAsync(ctx->call32, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
   SeedState s0{};
   s0.tol_rel = p.tol_seed;
@@ -1203,6 +1214,69 @@ seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
   }
   if (ctx->kind == 0) return solve_rest_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
   return solve_rest_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
+}
+
+seed_status seed_solve_cg(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t ncols,
+                          seed_info *info) {
+  if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
+  TRY(check_block(ctx, B, ldb, ncols, "B"));
+  TRY(check_block(ctx, X, ldx, ncols, "X"));
+  if (overlap(B, ldb, X, ldx, ncols, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
+  StreamScope scope(ctx);
+  TRY(ensure_cols(ctx, ncols));
+  if (ctx->precision == 1) {
+    if (info) std::memset(info, 0, sizeof(seed_info) * ncols);
+    CU(cudaEventRecord(ctx->t2, ctx->cs));
+    seed_status st;
+    if (ctx->kind == 0)
+      st = mixed_cg<double, float>(ctx, (const double *)B, ldb, (double *)X, ldx, 0, ncols, ctx->prm.tol_rest, nullptr);
+    else
+      st = mixed_cg<double2, float2>(ctx, (const double2 *)B, ldb, (double2 *)X, ldx, 0, ncols, ctx->prm.tol_rest,
+                                     nullptr);
+    TRY(st);
+    CU(cudaEventRecord(ctx->t3, ctx->cs));
+    CgHost h;
+    TRY(read_cg(ctx, &h));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->t2, ctx->t3);
+    ctx->stats.ms_rest = ms;
+    bool all = true;
+    for (int j = 0; j < ncols; ++j) {
+      all &= h.converged(j) != 0;
+      ctx->stats.mvps += h.mvps(j);
+      if (info) {
+        info[j].iters = h.iters(j);
+        info[j].mvps = h.mvps(j);
+        info[j].restarts = h.restarts(j);
+        info[j].converged = h.converged(j);
+        info[j].est_relres = info[j].true_relres = h.relres(j);
+      }
+    }
+    if (!all) return fail(ctx, SEED_ENOTCONV, "CG did not reach tol_rest on every system within maxit_rest");
+    return SEED_OK;
+  }
+  if (ctx->kind == 0) return cg_impl<double>(ctx, (const double *)B, ldb, (double *)X, ldx, ncols, info);
+  return cg_impl<double2>(ctx, (const double2 *)B, ldb, (double2 *)X, ldx, ncols, info);
+}
+
+seed_status seed_grad_kappa(seed_ctx *ctx, const void *Lambda, int64_t ldl, const void *X, int64_t ldx, int32_t ncols,
+                            double *out) {
+  if (!ctx || !out) return fail(ctx, SEED_EINVAL, "NULL argument");
+  if (ctx->kind != 1) return fail(ctx, SEED_EINVAL, "seed_grad_kappa needs a Wilson context");
+  TRY(check_block(ctx, Lambda, ldl, ncols, "Lambda"));
+  TRY(check_block(ctx, X, ldx, ncols, "X"));
+  StreamScope scope(ctx);
+  launch_dkappa_inner(ctx->wil, (const double2 *)Lambda, ldl, (const double2 *)X, ldx, ncols, ctx->partials,
+                      ctx->tickets, ctx->colnorm, ctx->cs);
+  ctx->stats.kernel_launches += 1;
+  std::vector<double> v(ncols);
+  CU(cudaMemcpyAsync(v.data(), ctx->colnorm, sizeof(double) * ncols, cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  CU(cudaGetLastError());
+  double t = 0.0;
+  for (int j = 0; j < ncols; ++j) t += v[j];
+  *out = t;
+  return SEED_OK;
 }
 
 seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t ncols) {

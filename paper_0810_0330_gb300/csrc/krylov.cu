@@ -661,8 +661,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(int64_t n, const CallArgs *cal
   __shared__ double sm[NT / 32];
   const int col = blockIdx.y;
   if (!c.active[col]) return;
-  // system col+2 of the call: column col+1 of X
-  T *X = reinterpret_cast<T *>(call->X) + (int64_t)(col + 1) * call->ldx;
+  T *X = reinterpret_cast<T *>(call->X) + (int64_t)(col + call->col0) * call->ldx;
   R += (int64_t)col * ld;
   P += (int64_t)col * ld;
   Q += (int64_t)col * ld;

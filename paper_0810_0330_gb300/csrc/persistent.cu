@@ -513,7 +513,7 @@ SEED_DEV bool cg_vector_phases(const CallArgs *call, T *R, T *P, const T *Q, int
   constexpr int kElem = elems_per_thread<T>(), kChunk = PT * kElem;
   const int nc = c.nc;
   const int nchunks = (int)((n + kChunk - 1) / kChunk);
-  T *const X = reinterpret_cast<T *>(call->X) + call->ldx;   // systems 2.. are columns 1.. of X
+  T *const X = reinterpret_cast<T *>(call->X) + call->col0 * call->ldx;   // CG column c is column c + col0 of X
   const int64_t ldx = call->ldx;
   for (int j = threadIdx.x; j < nc; j += PT) {
     s_a[j] = __ldcg(c.alpha + j);

@@ -48,6 +48,7 @@ struct SeedState {
 struct CallArgs {
   void *X;             // x^1..x^nrhs, column-major
   int64_t ldx;
+  int64_t col0;        // lockstep CG: CG column c updates column c + col0 of X
 };
 
 // Buffers of one seed solve; T = double (real) or double2 (complex).
@@ -199,6 +200,11 @@ struct Layout32 {
   }
   __host__ __device__ int64_t length(int64_t n) const { return sites == 0 ? n : 384 * ((sites + 31) / 32); }
 };
+
+// Adjoint (adjoint.cu): out[j] = Re <L_j, (dA/dkappa) X_j> for the Wilson normal
+// operator A = D^H D (device array of ncols doubles).
+void launch_dkappa_inner(const WilsonOp &op, const double2 *L, int64_t ldl, const double2 *X, int64_t ldx, int ncols,
+                         double *partials, unsigned *tickets, double *out, cudaStream_t s);
 
 // Mixed precision (mixed.cu): T64 / T32 = double / float or double2 / float2.
 // n32: length of the FP32 vectors (Layout32::length); user vectors follow L.
