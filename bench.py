@@ -82,6 +82,9 @@ def parse():
                     help="right-hand sides: 12 unit point sources at site 0, or 12 Z4 noise vectors (seed 0)")
     ap.add_argument("--csr-side", type=int, default=None,
                     help="--kernel-only on the 2-d Laplacian CSR of this side instead of the Wilson operator")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="forward + backward of the differentiable solve: 16^4, kappa 0.150, 8 Gaussian b and t")
+    ap.add_argument("--reorth-freq", type=int, default=None, help="reorthogonalization frequency for --adjoint")
     ap.add_argument("--sweep", action="store_true",
                     help="operator-apply bandwidth sweep (CSR Laplacian and Wilson D at growing sizes)")
     ap.add_argument("--sweep-max", type=int, default=3, help="sweep points per operator (1..4)")
@@ -487,10 +490,67 @@ def run_ours(args):
     return 0
 
 
+def run_adjoint(args):
+    """Loss sum_j ||x_j - t_j||^2, x = A(kappa)^{-1} b through the autograd
+    Function: forward (context, seed solve, CG) and backward (adjoint solves
+    seeded from the forward basis, or from zero for comparison, and the kappa
+    gradient), each timed with CUDA events."""
+    import torch
+    from paper_0810_0330_gb300 import inputs as I
+    from paper_0810_0330_gb300.adjoint import WilsonSeedSolve
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    dims = tuple(int(x) for x in args.lattice.split(",")) if args.lattice else (16, 16, 16, 16)
+    kappa, nrhs = 0.150, 8
+    n = 12 * int(np.prod(dims))
+    U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
+    B = torch.from_numpy(np.ascontiguousarray(I.gaussian_rhs(n, nrhs, seed=0, complex_=True).T)).to(dev).t()
+    T = torch.from_numpy(np.ascontiguousarray(I.gaussian_rhs(n, nrhs, seed=1, complex_=True).T)).to(dev).t()
+    freq = args.reorth_freq if args.reorth_freq is not None else 100
+    prm = dict(m_max=1000, reorth_freq=freq, reorth_passes=2, tol_seed=1e-10, tol_rest=1e-8)
+    res = {}
+    for seeded in (True, False):
+        fw, bw, its, fits = [], [], [], []
+        for step in range(args.warmup + args.steps):
+            k = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            torch.cuda.synchronize()
+            e[0].record()
+            X = WilsonSeedSolve.apply(k, B, U, dims, 0, prm, seeded)
+            loss = ((X - T).abs() ** 2).sum()
+            e[1].record()
+            loss.backward()
+            e[2].record()
+            torch.cuda.synchronize()
+            if step >= args.warmup:
+                fw.append(e[0].elapsed_time(e[1]))
+                bw.append(e[1].elapsed_time(e[2]))
+                its.append(sum(i["iters"] for i in X.grad_fn.info_backward))
+                fits.append([i["iters"] for i in X.grad_fn.info_forward])
+            del X, loss
+        res[seeded] = dict(fw=statistics.mean(fw), bw=statistics.mean(bw), bw_iters=its[-1], fw_iters=fits[-1],
+                           grad_kappa=float(k.grad))
+    s_, u_ = res[True], res[False]
+    out = {"metric": "adjoint forward+backward time (loss and gradients for b and kappa)",
+           "value": round(s_["fw"] + s_["bw"], 3), "unit": "ms", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "wilson-dirac %s kappa=%.3f A=D^H D, %d Gaussian b and t (seeds 0, 1), seed tol "
+                                  "1e-10 reorth/%d, CG tol 1e-8" % ("x".join(map(str, dims)), kappa, nrhs, freq),
+                      "forward_ms": round(s_["fw"], 3), "backward_seeded_ms": round(s_["bw"], 3),
+                      "backward_unseeded_ms": round(u_["bw"], 3),
+                      "backward_cg_iters_seeded": s_["bw_iters"], "backward_cg_iters_unseeded": u_["bw_iters"],
+                      "forward_iters": s_["fw_iters"], "grad_kappa": s_["grad_kappa"],
+                      "grad_kappa_unseeded": u_["grad_kappa"]}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.sweep:
         return run_sweep(args)
+    if args.adjoint:
+        return run_adjoint(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -6,7 +6,9 @@ library and its binding) never imports this package, and this package never
 imports the product path; the two share only the seeded input generators.
 
 Every function here is a thin marshalling layer; the arithmetic is in
-``seed_oracle.c`` (see its header for the passage each routine follows).
+``seed_oracle.c`` (see its header for the passage each routine follows),
+except ``adjoint_reference``, which assembles a loss and its gradients from
+the oracle's CG solves and operator applies with numpy inner products.
 """
 from __future__ import annotations
 
@@ -74,6 +76,8 @@ def _declare(lib):
     lib.orc_csr_apply.argtypes = [C.c_int64, P, P, P, P, P]
     lib.orc_wilson_neighbors.argtypes = [P, P]
     lib.orc_wilson_dslash.argtypes = [P, C.c_double, C.c_int32, C.c_int32, P, P, P]
+    lib.orc_wilson_dA_dkappa.argtypes = [P, C.c_double, C.c_int32, P, P, P]
+    lib.orc_wilson_dA_dkappa.restype = C.c_int
     lib.orc_op_apply.argtypes = [C.POINTER(_Op), P, P]
     lib.orc_op_apply.restype = C.c_int
     lib.orc_seed_first.argtypes = [C.POINTER(_Op), C.c_int32, P, P, C.POINTER(_SeedParams),
@@ -163,6 +167,41 @@ def wilson_dslash(dims, kappa, bc_t, sign, links, x) -> np.ndarray:
     y = np.empty_like(x)
     _load().orc_wilson_dslash(_p(d), float(kappa), int(bc_t), int(sign), _p(lk), _p(x), _p(y))
     return y
+
+
+def wilson_dA_dkappa(dims, kappa, bc_t, links, x) -> np.ndarray:
+    """(dA/dkappa) x for the Wilson normal operator A = D^H D."""
+    d = np.asarray(dims, dtype=np.int32)
+    lk = np.ascontiguousarray(links, dtype=np.complex128)
+    x = _zvec(x)
+    y = np.empty_like(x)
+    rc = _load().orc_wilson_dA_dkappa(_p(d), float(kappa), int(bc_t), _p(lk), _p(x), _p(y))
+    if rc != 0:
+        raise MemoryError("orc_wilson_dA_dkappa")
+    return y
+
+
+def adjoint_reference(dims, kappa, links, B, T, bc_t: int = 0, tol: float = 1e-12) -> dict:
+    """Loss L = sum_j ||x_j - t_j||^2 with x_j = A^{-1} b_j (A = D^H D) and its
+    gradients by the chain rule, from CG solves to ``tol``:
+      dL/db_j = lambda_j = A^{-1} g_j,  g_j = 2 (x_j - t_j)   (A Hermitian; the
+        conjugate-Wirtinger convention, dL = Re <dL/db, db>),
+      dL/dkappa = -sum_j Re <lambda_j, (dA/dkappa) x_j>.
+    Returns L, X, Lambda (= dL/dB) and dL/dkappa."""
+    op = Operator.wilson(dims, kappa, links, bc_t=bc_t)
+    B = np.asfortranarray(B, dtype=np.complex128)
+    T = np.asfortranarray(T, dtype=np.complex128)
+    n, p = B.shape
+    X = np.zeros((n, p), dtype=np.complex128, order="F")
+    Lam = np.zeros((n, p), dtype=np.complex128, order="F")
+    loss, gk = 0.0, 0.0
+    for j in range(p):
+        X[:, j] = cg(op, B[:, j], np.zeros(n, dtype=np.complex128), tol=tol)["x"]
+        d = X[:, j] - T[:, j]
+        loss += float(np.vdot(d, d).real)
+        Lam[:, j] = cg(op, 2.0 * d, np.zeros(n, dtype=np.complex128), tol=tol)["x"]
+        gk -= float(np.vdot(Lam[:, j], wilson_dA_dkappa(dims, kappa, bc_t, links, X[:, j])).real)
+    return dict(loss=loss, X=X, grad_B=Lam, grad_kappa=gk)
 
 
 def wilson_neighbors(dims) -> np.ndarray:

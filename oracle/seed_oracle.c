@@ -30,6 +30,9 @@
  *   orc_tridiag_eigs ..... eigenvalues of the Lanczos tridiagonal by Sturm
  *                          bisection (pin only)
  *   orc_wilson_neighbors . site -> 8 neighbour table (x fastest, periodic)
+ *   orc_wilson_dA_dkappa . y = (dA/dkappa) x for A = D^H D (no passage: the
+ *                          chain rule for the adjoint of a solve; pinned by
+ *                          finite differences of the operator and of a loss)
  */
 #include <math.h>
 #include <stdint.h>
@@ -183,6 +186,26 @@ void orc_wilson_dslash(const int32_t dims[4], double kappa, int32_t bc_t, int32_
         out[12 * s + 3 * sp + a] = zsub(in[12 * s + 3 * sp + a], zscale(kappa, acc[sp][a]));
   }
   free(nbr);
+}
+
+/* y = (dA/dkappa) x for A = D^H D.  D = 1 - kappa H with H the hopping sum
+ * of orc_wilson_dslash (sign +1); D^H = 1 - kappa H^H with H^H the sign -1
+ * sum.  So dA/dkappa = -(H^H D + D^H H).  H v is formed as v - D(kappa=1) v
+ * and H^H v as v - D^H(kappa=1) v.  Returns 0 or ORC_ENOMEM. */
+int orc_wilson_dA_dkappa(const int32_t dims[4], double kappa, int32_t bc_t, const zc *links, const zc *x, zc *y) {
+  int64_t n = 12 * (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  zc *t1 = (zc *)malloc(sizeof(zc) * n), *t2 = (zc *)malloc(sizeof(zc) * n);
+  if (!t1 || !t2) { free(t1); free(t2); return 2; }
+  orc_wilson_dslash(dims, kappa, bc_t, +1, links, x, t1);       /* t1 = D x */
+  orc_wilson_dslash(dims, 1.0, bc_t, -1, links, t1, t2);        /* t2 = D x - H^H D x */
+  for (int64_t i = 0; i < n; ++i) y[i] = zsub(t2[i], t1[i]);    /* y = -H^H D x */
+  orc_wilson_dslash(dims, 1.0, bc_t, +1, links, x, t1);         /* t1 = x - H x */
+  for (int64_t i = 0; i < n; ++i) t1[i] = zsub(x[i], t1[i]);    /* t1 = H x */
+  orc_wilson_dslash(dims, kappa, bc_t, -1, links, t1, t2);      /* t2 = D^H H x */
+  for (int64_t i = 0; i < n; ++i) y[i] = zsub(y[i], t2[i]);
+  free(t1);
+  free(t2);
+  return 0;
 }
 
 /* Operator description passed from the test harness. */

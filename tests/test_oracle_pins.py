@@ -396,3 +396,56 @@ def test_seeded_vectors_roundoff_sensitivity(orc):
         b = orc.seed_first(op, B * (1 + 2.2e-16), m_max=600, reorth_freq=freq, tol=1e-12)["X"][:, 1:]
         sens[freq] = np.linalg.norm(a - b) / np.linalg.norm(a)
     assert sens[5] < 1e-12 and sens[0] > 1e3 * sens[5], sens
+
+
+# --------------------------------------------------------------------------
+# adjoint (the kappa derivative of A = D^H D and the loss gradients)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,bc_t", [((2, 2, 2, 4), 1), ((3, 2, 2, 2), 0)])
+def test_dA_dkappa_central_difference(orc, dims, bc_t):
+    """A(kappa) = (1 - kappa H)^H (1 - kappa H) is quadratic in kappa, so the
+    central difference (A(k+h) - A(k-h)) / 2h equals dA/dkappa up to rounding;
+    the second difference is the constant 2 H^H H (its value pins H)."""
+    U = I.random_su3_links(dims, 0.3, seed=1)
+    n = 12 * I.lattice_sites(dims)
+    x = I.gaussian_rhs(n, 1, seed=2, complex_=True)[:, 0]
+    k, h = 0.13, 1e-3
+
+    def Ax(kk):
+        return orc.Operator.wilson(dims, kk, U, bc_t=bc_t).apply(x)
+
+    fd = (Ax(k + h) - Ax(k - h)) / (2 * h)
+    an = orc.wilson_dA_dkappa(dims, k, bc_t, U, x)
+    assert np.abs(fd - an).max() <= 1e-10 * np.abs(an).max()
+    # second difference vs 2 H^H H x, H from D at kappa = 1 (D1 = 1 - H) by its own definition
+    sd = (Ax(k + h) - 2 * Ax(k) + Ax(k - h)) / h ** 2
+    Hx = x - orc.wilson_dslash(dims, 1.0, bc_t, +1, U, x)
+    HHHx = Hx - orc.wilson_dslash(dims, 1.0, bc_t, -1, U, Hx)
+    assert np.abs(sd - 2 * HHHx).max() <= 1e-6 * np.abs(HHHx).max()
+
+
+def test_adjoint_reference_gradients_finite_differences(orc):
+    """dL/dkappa and the directional derivative of L along a random complex
+    dB from central differences of L itself (each L from CG solves to 1e-13):
+    the difference quotient's truncation error is O(h^2) and its rounding
+    error ~ 1e-13 |L| / h."""
+    dims, bc_t = (2, 2, 2, 4), 1
+    U = I.random_su3_links(dims, 0.3, seed=3)
+    n = 12 * I.lattice_sites(dims)
+    B = I.gaussian_rhs(n, 2, seed=4, complex_=True)
+    T = I.gaussian_rhs(n, 2, seed=5, complex_=True)
+    k = 0.12
+    ref = orc.adjoint_reference(dims, k, U, B, T, bc_t=bc_t, tol=1e-13)
+    h = 1e-5
+    lp = orc.adjoint_reference(dims, k + h, U, B, T, bc_t=bc_t, tol=1e-13)["loss"]
+    lm = orc.adjoint_reference(dims, k - h, U, B, T, bc_t=bc_t, tol=1e-13)["loss"]
+    fd = (lp - lm) / (2 * h)
+    assert abs(fd - ref["grad_kappa"]) <= 1e-6 * abs(ref["grad_kappa"]), (fd, ref["grad_kappa"])
+    dB = I.gaussian_rhs(n, 2, seed=6, complex_=True)
+    hb = 1e-4
+    lp = orc.adjoint_reference(dims, k, U, B + hb * dB, T, bc_t=bc_t, tol=1e-13)["loss"]
+    lm = orc.adjoint_reference(dims, k, U, B - hb * dB, T, bc_t=bc_t, tol=1e-13)["loss"]
+    fdb = (lp - lm) / (2 * hb)
+    an = float(np.vdot(ref["grad_B"], dB).real)
+    assert abs(fdb - an) <= 1e-6 * abs(an), (fdb, an)
