@@ -202,6 +202,21 @@ seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int
 seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
                             int32_t nrhs, seed_info *info);
 
+/* Sec. 2.3 "Single Seeding of Related Right-hand Sides", steps 3-4, after
+ * seed_solve_first (step 2) on the same B and X: the remaining systems are
+ * projected over x^1 (x^1_bcg = 0, r^1_bcg = b^1); then for j = 2..nrhs, CG
+ * runs on system j from its current approximation x^j_bcg (residual r^j_bcg)
+ * to tol_rest, and every later system i receives the Galerkin projection over
+ * the CG correction x_cg = x^j - x^j_bcg:
+ *   delta = (x_cg^H r^i) / (x_cg^H r^j_bcg),  x^i += delta x_cg,  r^i -= delta r^j_bcg.
+ * The systems are solved one after another (not in lockstep).  FP64 contexts
+ * with x0_zero = 1 only (the paper assumes no initial guesses): SEED_EINVAL
+ * otherwise; SEED_ESTATE before seed_solve_first.
+ *   info: NULL or nrhs entries; entries 1..nrhs-1 are filled as by seed_solve_rest.
+ * Returns SEED_OK or SEED_ENOTCONV. */
+seed_status seed_solve_related(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t nrhs,
+                               seed_info *info);
+
 /* Lockstep CG (Sec. 1; the iteration of seed_solve_rest) on ALL ncols columns
  * of B from the initial guesses in X, to ||b^j - A x^j|| <= tol_rest ||b^j||
  * (mixed-precision contexts: FP32 iterations with FP64 reliable updates).

@@ -270,6 +270,34 @@ def seed_solve_all(op: Operator, B, *, m_max: int, reorth_freq: int, reorth_pass
     return dict(seed=s, rest=rest, X=X, X_seeded=X_seeded)
 
 
+def seed_solve_related(op: Operator, B, *, m_max: int, reorth_freq: int, reorth_passes: int = 2,
+                       tol_seed: float = 1e-12, tol_rest: float = 1e-8, maxit_rest: int = 100000) -> dict:
+    """Sec. 2.3, "Single Seeding of Related Right-hand Sides": step 2 by the
+    Sec. 3 seed solve (no initial guesses), then steps 3-4: project the
+    remaining systems over x^1 (x^1_bcg = 0, r^1_bcg = b^1); for j = 2..nrhs run
+    CG on system j from its current approximation and project the later
+    systems over that CG's correction x^j - x^j_bcg (orc_related_project)."""
+    s = seed_first(op, B, m_max=m_max, reorth_freq=reorth_freq, reorth_passes=reorth_passes, tol=tol_seed)
+    B = np.asfortranarray(B, dtype=np.complex128)
+    X = s["X"]
+    n, p = B.shape
+    R = np.zeros((n, p), dtype=np.complex128, order="F")
+    for i in range(1, p):
+        R[:, i] = B[:, i] - op.apply(X[:, i])
+    for i in range(1, p):
+        X[:, i], R[:, i] = related_project(X[:, 0], B[:, 0], X[:, i], R[:, i])
+    rest = []
+    for j in range(1, p):
+        xb, rb = X[:, j].copy(), R[:, j].copy()
+        r = cg(op, B[:, j], X[:, j], tol=tol_rest, maxit=maxit_rest)
+        X[:, j] = r["x"]
+        rest.append(r)
+        xcg = X[:, j] - xb
+        for i in range(j + 1, p):
+            X[:, i], R[:, i] = related_project(xcg, rb, X[:, i], R[:, i])
+    return dict(seed=s, rest=rest, X=X)
+
+
 def related_project(x_cg, r_bcg, x_bpr, r_bpr):
     """Sec. 2.3 step 3, in place on copies; returns (x_new, r_new)."""
     x_cg = _zvec(x_cg)

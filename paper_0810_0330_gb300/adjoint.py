@@ -12,8 +12,12 @@ right-hand sides), finished by lockstep CG (seed_solve_cg).  Then
     dL/dB     = Lambda,
     dL/dkappa = -sum_j Re <Lambda_j, (dA/dkappa) X_j>   (seed_grad_kappa),
 
-in PyTorch's conjugate-Wirtinger convention (dL = Re <grad, dz>).  Every step
-runs in the library's kernels; this module only marshals tensors.
+in PyTorch's conjugate-Wirtinger convention (dL = Re <grad, dz>).  With
+params["precision"] = 1 both the forward and the adjoint solves run in mixed
+precision (FP32 iterations, FP64 reliable updates, the same FP64 tolerances);
+the FP32 basis is not used for the backward projection, so those adjoint
+solves start from zero.  Every step runs in the library's kernels; this module
+only marshals tensors.
 """
 from __future__ import annotations
 
@@ -39,7 +43,7 @@ class WilsonSeedSolve(torch.autograd.Function):
         X = torch.empty((Bc.shape[1], Bc.shape[0]), dtype=Bc.dtype, device=Bc.device).t()
         ctx.info_forward = [S.seed_solve_first(sc, Bc, X)[0]] + S.seed_solve_rest(sc, Bc, X)[1:]
         ctx.sc = sc
-        ctx.seeded = seeded_backward
+        ctx.seeded = seeded_backward and int(prm.get("precision", 0)) == 0
         ctx.kappa_meta = (kappa.dtype, kappa.device) if isinstance(kappa, torch.Tensor) else (torch.float64, "cpu")
         ctx.save_for_backward(X)
         return X

@@ -31,7 +31,7 @@ STATUS_NAMES = ["SEED_OK", "SEED_EINVAL", "SEED_ENOMEM", "SEED_ECUDA", "SEED_ENO
 EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_create_wilson",
            "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
-           "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa"]
+           "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related"]
 
 
 class SeedError(RuntimeError):
@@ -101,6 +101,7 @@ def lib():
             L.seed_time_operator.argtypes = [P, I32, I32, I32, C.POINTER(C.c_double)]
             L.seed_wilson_apply_noalloc.argtypes = [C.POINTER(seed_wilson), P, I64, P, I64, I32, P]
             L.seed_solve_cg.argtypes = [P, P, I64, P, I64, I32, P]
+            L.seed_solve_related.argtypes = [P, P, I64, P, I64, I32, P]
             L.seed_grad_kappa.argtypes = [P, P, I64, P, I64, I32, C.POINTER(C.c_double)]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
@@ -208,6 +209,17 @@ def seed_solve_rest(ctx: Context, B: torch.Tensor, X: torch.Tensor):
         raise ValueError("B and X must have the same number of columns")
     info = _infos(nb)
     _check(lib().seed_solve_rest(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_rest", ctx.handle)
+    return [i.as_dict() for i in info]
+
+
+def seed_solve_related(ctx: Context, B: torch.Tensor, X: torch.Tensor):
+    """Sec. 2.3 steps 3-4 after seed_solve_first (systems 2.. solved one after another)."""
+    pb, ldb, nb = _block(B, ctx.n, "B")
+    px, ldx, nx = _block(X, ctx.n, "X")
+    if nb != nx:
+        raise ValueError("B and X must have the same number of columns")
+    info = _infos(nb)
+    _check(lib().seed_solve_related(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_related", ctx.handle)
     return [i.as_dict() for i in info]
 
 

@@ -104,6 +104,11 @@ struct seed_ctx {
   void *E32 = nullptr;                 // FP32 corrections, cap_cols + 1 columns (column 0 spare)
   CallArgs *call32 = nullptr;          // [0]: seed run (X = E), [1]: mixed CG
 
+  // Sec. 2.3 related right-hand sides: tracked residuals, x_bcg / x_cg, r_bcg, dots and deltas
+  void *Rrel = nullptr, *xrel = nullptr, *rrel = nullptr;
+  int rel_cap = 0;
+  double2 *reldots = nullptr;          // [2 * kMaxRhs]
+
   std::map<std::string, GraphEntry> graphs;
   std::string err;
   seed_stats stats{};
@@ -740,6 +745,73 @@ seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
 }
 
 // ---------------------------------------------------------------------------
+// Sec. 2.3: single seeding of related right-hand sides
+// ---------------------------------------------------------------------------
+seed_status ensure_related(seed_ctx *ctx, int nc) {
+  if (nc <= ctx->rel_cap) return SEED_OK;
+  cudaStreamSynchronize(ctx->cs);
+  cudaFree(ctx->Rrel); cudaFree(ctx->xrel); cudaFree(ctx->rrel);
+  ctx->Rrel = ctx->xrel = ctx->rrel = nullptr;
+  ctx->rel_cap = 0;
+  TRY(dalloc(ctx, &ctx->Rrel, (size_t)ctx->ldv * nc * ctx->esz));
+  TRY(dalloc(ctx, &ctx->xrel, (size_t)ctx->ldv * ctx->esz));
+  TRY(dalloc(ctx, &ctx->rrel, (size_t)ctx->ldv * ctx->esz));
+  if (!ctx->reldots) TRY(dalloc(ctx, &ctx->reldots, sizeof(double2) * 2 * kMaxRhs));
+  ctx->rel_cap = nc;
+  return SEED_OK;
+}
+
+// Steps 3-4 after the seed solve of system 1 (step 2): project the remaining
+// systems over x^1 (x^1_bcg = 0, r^1_bcg = b^1), then for j = 2, 3, ...: CG on
+// system j from its current approximation, and project the systems after it
+// over that CG's correction.
+template <class T>
+seed_status solve_related_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
+                               seed_info *info) {
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  const int nc = nrhs - 1;
+  if (info && nc > 0) std::memset(info + 1, 0, sizeof(seed_info) * nc);
+  if (nc <= 0) return SEED_OK;
+  TRY(ensure_cols(ctx, nrhs));
+  TRY(ensure_related(ctx, nc));
+  const T *Bt = (const T *)B;
+  T *Xt = (T *)X;
+  T *R = (T *)ctx->Rrel, *xb = (T *)ctx->xrel, *rb = (T *)ctx->rrel;
+  double2 *dots = ctx->reldots, *delta = ctx->reldots + kMaxRhs;
+  CU(cudaEventRecord(ctx->t2, ctx->cs));
+  // residuals of the seeded systems 2..nrhs
+  int kern = apply_A(ctx, Xt + ldx, ldx, ctx->Q, ld, nc, nullptr);
+  launch_sub_from<T>(Bt + ldb, ldb, (const T *)ctx->Q, ld, R, ld, n, nc, ctx->cs);
+  ctx->stats.mvps += nc;
+  // step 3 for system 1: x_cg = x^1, r_bcg = b^1
+  launch_related_project<T>(n, Xt, Bt, Xt + ldx, ldx, R, ld, nc, dots, delta, ctx->partials, ctx->tickets, ctx->cs);
+  ctx->stats.kernel_launches += kern + 4;
+  float ms_total = 0.f;
+  for (int j = 0; j < nc; ++j) {
+    T *xj = Xt + (int64_t)(1 + j) * ldx;
+    // step 4: x_bcg, r_bcg of system j + 2, then CG
+    launch_copy_cols<T>(xj, ldx, xb, ld, n, 1, ctx->cs);
+    launch_copy_cols<T>(R + (int64_t)j * ld, ld, rb, ld, n, 1, ctx->cs);
+    ctx->stats.kernel_launches += 2;
+    TRY(cg_impl<T>(ctx, Bt + (int64_t)(1 + j) * ldb, ldb, xj, ldx, 1, info ? info + 1 + j : nullptr));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->t2, ctx->t3);
+    ms_total += ms;
+    if (j + 1 < nc) {
+      // step 3: x_cg = x^j - x^j_bcg; project the systems after j over it
+      launch_sub_from<T>(xj, ldx, xb, ld, xb, ld, n, 1, ctx->cs);
+      launch_related_project<T>(n, xb, rb, xj + ldx, ldx, R + (int64_t)(j + 1) * ld, ld, nc - j - 1, dots, delta,
+                                ctx->partials, ctx->tickets, ctx->cs);
+      ctx->stats.kernel_launches += 4;
+    }
+  }
+  CU(cudaStreamSynchronize(ctx->cs));
+  CU(cudaGetLastError());
+  ctx->stats.ms_rest = ms_total;
+  return SEED_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Mixed precision: FP32 iterations, FP64 scalars and reliable updates
 // ---------------------------------------------------------------------------
 
@@ -1029,7 +1101,7 @@ void destroy(seed_ctx *ctx) {
                   ctx->delta_hist, ctx->eta, ctx->partials, ctx->tickets, ctx->Hpart, ctx->H, ctx->call,
                   ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
                   ctx->gsync, ctx->f2, ctx->gbuf, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
-                  ctx->T32, ctx->E32, ctx->call32};
+                  ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
@@ -1257,6 +1329,20 @@ seed_status seed_solve_cg(seed_ctx *ctx, const void *B, int64_t ldb, void *X, in
   }
   if (ctx->kind == 0) return cg_impl<double>(ctx, (const double *)B, ldb, (double *)X, ldx, ncols, info);
   return cg_impl<double2>(ctx, (const double2 *)B, ldb, (double2 *)X, ldx, ncols, info);
+}
+
+seed_status seed_solve_related(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t nrhs,
+                               seed_info *info) {
+  if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
+  if (ctx->precision != 0) return fail(ctx, SEED_EINVAL, "seed_solve_related runs in FP64 (precision = 0)");
+  if (!ctx->prm.x0_zero) return fail(ctx, SEED_EINVAL, "seed_solve_related assumes no initial guesses (x0_zero = 1)");
+  if (!ctx->seeded) return fail(ctx, SEED_ESTATE, "seed_solve_related follows seed_solve_first");
+  TRY(check_block(ctx, B, ldb, nrhs, "B"));
+  TRY(check_block(ctx, X, ldx, nrhs, "X"));
+  if (overlap(B, ldb, X, ldx, nrhs, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
+  StreamScope scope(ctx);
+  if (ctx->kind == 0) return solve_related_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
+  return solve_related_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
 }
 
 seed_status seed_grad_kappa(seed_ctx *ctx, const void *Lambda, int64_t ldl, const void *X, int64_t ldx, int32_t ncols,

@@ -201,6 +201,12 @@ struct Layout32 {
   __host__ __device__ int64_t length(int64_t n) const { return sites == 0 ? n : 384 * ((sites + 31) / 32); }
 };
 
+// Sec. 2.3 step 3 (related.cu): X[:, c] += delta_c xcg, R[:, c] -= delta_c rbcg with
+// delta_c = (xcg^H R[:, c]) / (xcg^H rbcg), c < nrem.  dots: nrem + 1, delta: nrem device scratch.
+template <class T>
+void launch_related_project(int64_t n, const T *xcg, const T *rbcg, T *X, int64_t ldx, T *R, int64_t ldr, int nrem,
+                            double2 *dots, double2 *delta, double *partials, unsigned *tickets, cudaStream_t s);
+
 // Adjoint (adjoint.cu): out[j] = Re <L_j, (dA/dkappa) X_j> for the Wilson normal
 // operator A = D^H D (device array of ncols doubles).
 void launch_dkappa_inner(const WilsonOp &op, const double2 *L, int64_t ldl, const double2 *X, int64_t ldx, int ncols,

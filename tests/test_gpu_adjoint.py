@@ -136,3 +136,24 @@ def test_autograd_kappa_central_difference_on_gpu(seedlib):
     _, g = loss(kappa, grad=True)
     fd = (loss(kappa + h) - loss(kappa - h)) / (2 * h)
     assert abs(fd - g) <= 1e-6 * abs(g), (fd, g)
+
+
+def test_autograd_mixed_precision_gradients_match_oracle(seedlib, orc):
+    """Forward and adjoint solves in mixed precision (FP32 iterations, FP64
+    reliable updates to the same 1e-12 tolerances): the same 1e-8 bound."""
+    from paper_0810_0330_gb300.adjoint import WilsonSeedSolve
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = I.random_su3_links(dims, 0.3, seed=21)
+    n = 12 * I.lattice_sites(dims)
+    B = I.gaussian_rhs(n, 3, seed=22, complex_=True)
+    T = I.gaussian_rhs(n, 3, seed=23, complex_=True)
+    ref = orc.adjoint_reference(dims, kappa, U, B, T, tol=1e-13)
+    k = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    Bd = dev(B).requires_grad_(True)
+    prm = dict(m_max=2000, reorth_freq=10, tol_seed=1e-12, tol_rest=1e-12, precision=1)
+    X = WilsonSeedSolve.apply(k, Bd, torch.from_numpy(U).cuda(), dims, 0, prm, True)
+    loss = ((X - dev(T)).abs() ** 2).sum()
+    loss.backward()
+    assert abs(loss.item() - ref["loss"]) <= 1e-9 * ref["loss"]
+    assert abs(float(k.grad) - ref["grad_kappa"]) <= 1e-8 * abs(ref["grad_kappa"])
+    assert np.linalg.norm(host(Bd.grad) - ref["grad_B"]) <= 1e-8 * np.linalg.norm(ref["grad_B"])
