@@ -126,7 +126,10 @@ typedef struct {
                              seed_solve_first), tol_rest for the others.  The paper runs FP64 only;
                              this is the GPU extension.  seed_project and seed_get_basis use the
                              FP64 path only (SEED_ESTATE after a mixed seed solve). */
-  int32_t reserved;
+  int32_t autotune;       /* CSR contexts: 1 = time the sparse matrix-vector kernel's launch shapes
+                             (threads per row 1/2/4/8, block size) on the matrix at creation and
+                             keep the fastest (cached per process by size); 0 = one thread per row,
+                             256-thread blocks.  Results are reproducible for a given shape. */
   double reliable_delta;  /* mixed only: a reliable update is made when the FP32 recursive residual
                              has fallen below reliable_delta times its value at the last update
                              (checked every 16 iterations), and whenever it meets the tolerance;
@@ -151,13 +154,14 @@ typedef struct {
   int64_t mvps;              /* operator applications */
   int64_t reorth_events;
   double ms_seed, ms_project, ms_rest;   /* device time of the last call of each kind */
+  int32_t csr_tpr, csr_block;            /* CSR launch shape in use (threads per row, block size) */
 } seed_stats;
 
 int32_t seed_abi_version(void);
 
 /* Fill p with defaults: m_max 1000, reorth_freq 0, passes 2, extra 0,
  * keep_basis 0, x0_zero 1, maxit_rest 100000, max_restarts 3, tol_seed 1e-12,
- * tol_rest 1e-8, breakdown_rel 1e-14, kernel_path 0, precision 0,
+ * tol_rest 1e-8, breakdown_rel 1e-14, kernel_path 0, precision 0, autotune 0,
  * reliable_delta 0.  Returns SEED_EINVAL if p is NULL. */
 seed_status seed_params_default(seed_params *p);
 
@@ -265,6 +269,23 @@ seed_status seed_get_tridiag(const seed_ctx *ctx, double *alpha, double *beta, i
 seed_status seed_get_basis(const seed_ctx *ctx, void *V_host, int32_t ncols);
 
 seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out);
+
+/* Batched uneven problems (no counterpart in the paper): for each problem i,
+ * seed_solve_first then seed_solve_rest on ctxs[i] with B[i], X[i] (ldb[i],
+ * ldx[i], nrhs[i] columns, info[i] NULL or nrhs[i] entries), all problems
+ * concurrently on the GPU.  Every context has its own stream; a pool of
+ * `workers` host threads (0 = min(nprob, 32)) drives the solves, largest
+ * problem (n x nrhs) first, so the launches and CUDA graphs of many small
+ * problems overlap on the GPU instead of running one after another.  The
+ * contexts must be distinct and must not be used by other threads meanwhile.
+ * Each problem runs exactly the arithmetic of a solo solve with kernel_path
+ * 1 (the persistent cooperative kernels are not used inside a batch), so its
+ * results are bitwise those of that solo solve.  Returns SEED_OK, or the
+ * status of the first failing problem (in problem order; the others still
+ * run), with seed_last_error(NULL) naming it. */
+seed_status seed_batch_solve(seed_ctx *const *ctxs, const void *const *B, const int64_t *ldb, void *const *X,
+                             const int64_t *ldx, const int32_t *nrhs, int32_t nprob, int32_t workers,
+                             seed_info *const *info);
 
 /* Measurement helper (not part of the method): launch op(X) (op as in
  * seed_apply; on a mixed-precision context also 3 = A, 4 = D, 5 = D^H with the

@@ -31,7 +31,8 @@ STATUS_NAMES = ["SEED_OK", "SEED_EINVAL", "SEED_ENOMEM", "SEED_ECUDA", "SEED_ENO
 EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_create_wilson",
            "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
-           "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related"]
+           "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related",
+           "seed_batch_solve"]
 
 
 class SeedError(RuntimeError):
@@ -56,7 +57,7 @@ class seed_params(C.Structure):
                 ("extra_iters", C.c_int32), ("keep_basis", C.c_int32), ("x0_zero", C.c_int32),
                 ("maxit_rest", C.c_int32), ("max_restarts", C.c_int32), ("tol_seed", C.c_double),
                 ("tol_rest", C.c_double), ("breakdown_rel", C.c_double), ("kernel_path", C.c_int32),
-                ("precision", C.c_int32), ("reserved", C.c_int32), ("reliable_delta", C.c_double)]
+                ("precision", C.c_int32), ("autotune", C.c_int32), ("reliable_delta", C.c_double)]
 
 
 class seed_info(C.Structure):
@@ -70,7 +71,7 @@ class seed_info(C.Structure):
 class seed_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("graph_launches", C.c_int64), ("mvps", C.c_int64),
                 ("reorth_events", C.c_int64), ("ms_seed", C.c_double), ("ms_project", C.c_double),
-                ("ms_rest", C.c_double)]
+                ("ms_rest", C.c_double), ("csr_tpr", C.c_int32), ("csr_block", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +103,7 @@ def lib():
             L.seed_wilson_apply_noalloc.argtypes = [C.POINTER(seed_wilson), P, I64, P, I64, I32, P]
             L.seed_solve_cg.argtypes = [P, P, I64, P, I64, I32, P]
             L.seed_solve_related.argtypes = [P, P, I64, P, I64, I32, P]
+            L.seed_batch_solve.argtypes = [P, P, P, P, P, P, I32, I32, P]
             L.seed_grad_kappa.argtypes = [P, P, I64, P, I64, I32, C.POINTER(C.c_double)]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
@@ -210,6 +212,28 @@ def seed_solve_rest(ctx: Context, B: torch.Tensor, X: torch.Tensor):
     info = _infos(nb)
     _check(lib().seed_solve_rest(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_rest", ctx.handle)
     return [i.as_dict() for i in info]
+
+
+def seed_batch_solve(ctxs, Bs, Xs, workers: int = 0):
+    """seed_solve_first + seed_solve_rest for every (ctx, B, X), all problems
+    concurrently; returns one info list per problem."""
+    k = len(ctxs)
+    if not (len(Bs) == len(Xs) == k):
+        raise ValueError("ctxs, Bs and Xs must have the same length")
+    hs = (C.c_void_p * k)(*[c.handle.value for c in ctxs])
+    pb, ldb, px, ldx, nr = (C.c_void_p * k)(), (C.c_int64 * k)(), (C.c_void_p * k)(), (C.c_int64 * k)(), \
+        (C.c_int32 * k)()
+    infos = []
+    for i, (c, B, X) in enumerate(zip(ctxs, Bs, Xs)):
+        b, lb, nb = _block(B, c.n, "B")
+        x, lx, nx = _block(X, c.n, "X")
+        if nb != nx:
+            raise ValueError("B and X must have the same number of columns (problem %d)" % i)
+        pb[i], ldb[i], px[i], ldx[i], nr[i] = b, lb, x, lx, nb
+        infos.append(_infos(nb))
+    ip = (C.c_void_p * k)(*[C.cast(inf, C.c_void_p).value for inf in infos])
+    _check(lib().seed_batch_solve(hs, pb, ldb, px, ldx, nr, int(k), int(workers), ip), "seed_batch_solve")
+    return [[i.as_dict() for i in inf] for inf in infos]
 
 
 def seed_solve_related(ctx: Context, B: torch.Tensor, X: torch.Tensor):

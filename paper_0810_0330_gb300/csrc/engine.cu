@@ -17,8 +17,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <mutex>
+#include <set>
+#include <thread>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -116,6 +121,7 @@ struct seed_ctx {
   bool basis_valid = false;
   bool seeded = false;
   bool timing_project = false;
+  bool in_batch = false;               // inside seed_batch_solve (stream ordering done by the batch)
 };
 
 namespace {
@@ -157,6 +163,7 @@ seed_status check_params(seed_ctx *ctx, const seed_params *p) {
     return fail(ctx, SEED_EINVAL, "tolerances must be >= 0");
   if (p->kernel_path < 0 || p->kernel_path > 2) return fail(ctx, SEED_EINVAL, "kernel_path must be 0, 1 or 2");
   if (p->precision < 0 || p->precision > 1) return fail(ctx, SEED_EINVAL, "precision must be 0 or 1");
+  if (p->autotune < 0 || p->autotune > 1) return fail(ctx, SEED_EINVAL, "autotune must be 0 or 1");
   if (!(p->reliable_delta >= 0.0 && p->reliable_delta < 1.0))
     return fail(ctx, SEED_EINVAL, "reliable_delta must be in [0, 1)");
   return SEED_OK;
@@ -745,6 +752,66 @@ seed_status solve_rest_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
 }
 
 // ---------------------------------------------------------------------------
+// CSR launch-shape autotuner: times every shape of kCsrShape on the matrix
+// itself (10 launches after 2 untimed ones, CUDA events on the context's
+// stream) and keeps the fastest; choices are cached per process by (device,
+// n, nnz, precision) so that a batch of equal-sized problems tunes once.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t, int>, int> g_tune_cache;
+
+template <class R>
+seed_status time_csr_shape(seed_ctx *ctx, CsrOpT<R> &op, const R *x, R *y, int shape, float *ms) {
+  op.tpr = kCsrShape[shape][0];
+  op.block = kCsrShape[shape][1];
+  for (int r = 0; r < 12; ++r) {
+    if (r == 2) CU(cudaEventRecord(ctx->t0, ctx->cs));
+    if constexpr (sizeof(R) == sizeof(double)) launch_csr_spmv(op, x, ctx->ldv, y, ctx->ldv, 1, nullptr, ctx->cs);
+    else launch_csr_spmv32(op, x, ctx->ldv, y, ctx->ldv, 1, nullptr, ctx->cs);
+  }
+  CU(cudaEventRecord(ctx->t1, ctx->cs));
+  CU(cudaEventSynchronize(ctx->t1));
+  CU(cudaGetLastError());
+  CU(cudaEventElapsedTime(ms, ctx->t0, ctx->t1));
+  ctx->stats.kernel_launches += 12;
+  return SEED_OK;
+}
+
+seed_status autotune_csr(seed_ctx *ctx, int64_t nnz) {
+  const auto key = std::make_tuple(ctx->device, ctx->n, nnz, ctx->precision);
+  int best = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) best = it->second;
+  }
+  if (best < 0) {
+    TRY(ensure_cols(ctx, 1));
+    float best_ms = 0.f;
+    for (int sh = 0; sh < kCsrShapes; ++sh) {
+      float ms = 0.f;
+      if (ctx->precision == 1) {
+        CU(cudaMemsetAsync(ctx->P32, 0, (size_t)ctx->ldv * ctx->vsz, ctx->cs));
+        TRY(time_csr_shape<float>(ctx, ctx->csr32, (const float *)ctx->P32, (float *)ctx->Q32, sh, &ms));
+      } else {
+        CU(cudaMemsetAsync(ctx->P, 0, (size_t)ctx->ldv * ctx->esz, ctx->cs));
+        TRY(time_csr_shape<double>(ctx, ctx->csr, (const double *)ctx->P, (double *)ctx->Q, sh, &ms));
+      }
+      if (best < 0 || ms < best_ms) {
+        best = sh;
+        best_ms = ms;
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  // the FP64 operator (true residuals) and its FP32 copy share the chosen shape
+  ctx->csr.tpr = ctx->csr32.tpr = kCsrShape[best][0];
+  ctx->csr.block = ctx->csr32.block = kCsrShape[best][1];
+  return SEED_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Sec. 2.3: single seeding of related right-hand sides
 // ---------------------------------------------------------------------------
 seed_status ensure_related(seed_ctx *ctx, int nc) {
@@ -1063,13 +1130,19 @@ bool overlap(const void *a, int64_t lda, const void *b, int64_t ldb, int cols, i
   return a0 < b1 && b0 < a1;
 }
 
-struct StreamScope {   // order the internal stream after the caller's, and back
+// Order the internal stream after the caller's, and back.  Inside
+// seed_batch_solve the ordering is done once for the whole batch instead:
+// several contexts usually share the caller's stream, and per-call ordering
+// through it would make every problem wait for the ones before it.
+struct StreamScope {
   seed_ctx *ctx;
   explicit StreamScope(seed_ctx *c) : ctx(c) {
+    if (ctx->in_batch) return;
     cudaEventRecord(ctx->ev_in, ctx->user_stream);
     cudaStreamWaitEvent(ctx->cs, ctx->ev_in, 0);
   }
   ~StreamScope() {
+    if (ctx->in_batch) return;
     cudaEventRecord(ctx->ev_in, ctx->cs);
     cudaStreamWaitEvent(ctx->user_stream, ctx->ev_in, 0);
   }
@@ -1143,7 +1216,7 @@ seed_status seed_params_default(seed_params *p) {
   p->breakdown_rel = 1e-14;
   p->kernel_path = 0;
   p->precision = 0;
-  p->reserved = 0;
+  p->autotune = 0;
   p->reliable_delta = 0.0;
   return SEED_OK;
 }
@@ -1193,6 +1266,7 @@ seed_status seed_create_csr(seed_ctx **out, const seed_csr *A, const seed_params
       ctx->csr32 = CsrOp32{A->n, A->row_ptr, A->col_idx, (const float *)ctx->op32};
     }
   }
+  if (s == SEED_OK && ctx->prm.autotune) s = autotune_csr(ctx, A->nnz);
   if (s == SEED_OK && cudaStreamSynchronize(ctx->cs) != cudaSuccess) s = fail(ctx, SEED_ECUDA, "set-up failed");
   if (s != SEED_OK) { g_last_error = ctx->err; destroy(ctx); return s; }
   *out = ctx;
@@ -1513,9 +1587,81 @@ seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t
   return SEED_OK;
 }
 
+seed_status seed_batch_solve(seed_ctx *const *ctxs, const void *const *B, const int64_t *ldb, void *const *X,
+                             const int64_t *ldx, const int32_t *nrhs, int32_t nprob, int32_t workers,
+                             seed_info *const *info) {
+  if (!ctxs || !B || !ldb || !X || !ldx || !nrhs) return fail(nullptr, SEED_EINVAL, "NULL argument");
+  if (nprob < 1 || nprob > 4096) return fail(nullptr, SEED_EINVAL, "nprob must be in [1, 4096]");
+  if (workers < 0) return fail(nullptr, SEED_EINVAL, "workers must be >= 0");
+  std::set<const seed_ctx *> seen;
+  for (int i = 0; i < nprob; ++i) {
+    if (!ctxs[i]) return fail(nullptr, SEED_EINVAL, "a context is NULL");
+    if (!seen.insert(ctxs[i]).second) return fail(nullptr, SEED_EINVAL, "a context appears twice in the batch");
+  }
+  // largest problems first (longest-processing-time order), so that the small
+  // ones fill the GPU around them
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return ctxs[a]->n * (int64_t)nrhs[a] > ctxs[b]->n * (int64_t)nrhs[b];
+  });
+  const int W = workers > 0 ? std::min<int>(workers, nprob) : std::min<int>(nprob, 32);
+  // every context starts after the work already queued on its caller's stream ...
+  for (int i = 0; i < nprob; ++i) {
+    seed_ctx *c = ctxs[i];
+    if (cudaSetDevice(c->device) != cudaSuccess || cudaEventRecord(c->ev_in, c->user_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->cs, c->ev_in, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, SEED_ECUDA, "stream ordering at the start of the batch failed");
+    }
+    c->in_batch = true;
+  }
+  std::vector<seed_status> st(nprob, SEED_OK);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int k = next.fetch_add(1); k < nprob; k = next.fetch_add(1)) {
+      const int i = order[k];
+      seed_ctx *c = ctxs[i];
+      if (cudaSetDevice(c->device) != cudaSuccess) {
+        cudaGetLastError();
+        st[i] = fail(c, SEED_ECUDA, "cudaSetDevice failed in a batch worker");
+        continue;
+      }
+      // cooperative (persistent) kernels of different problems are not run side by side
+      const bool p0 = c->allow_persistent, p1 = c->allow_persistent_cg;
+      c->allow_persistent = c->allow_persistent_cg = false;
+      seed_info *inf = info ? info[i] : nullptr;
+      st[i] = seed_solve_first(c, B[i], ldb[i], X[i], ldx[i], nrhs[i], inf);
+      if (st[i] == SEED_OK) st[i] = seed_solve_rest(c, B[i], ldb[i], X[i], ldx[i], nrhs[i], inf);
+      c->allow_persistent = p0;
+      c->allow_persistent_cg = p1;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < W; ++w) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+  // ... and the callers' streams continue after every context's work
+  for (int i = 0; i < nprob; ++i) {
+    seed_ctx *c = ctxs[i];
+    c->in_batch = false;
+    cudaSetDevice(c->device);
+    cudaEventRecord(c->ev_in, c->cs);
+    cudaStreamWaitEvent(c->user_stream, c->ev_in, 0);
+  }
+  for (int i = 0; i < nprob; ++i)
+    if (st[i] != SEED_OK) {
+      g_last_error = "problem " + std::to_string(i) + ": " + ctxs[i]->err;
+      return st[i];
+    }
+  return SEED_OK;
+}
+
 seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out) {
   if (!ctx || !out) return fail(nullptr, SEED_EINVAL, "NULL argument");
   *out = ctx->stats;
+  out->csr_tpr = ctx->kind == 0 ? ctx->csr.tpr : 0;
+  out->csr_block = ctx->kind == 0 ? ctx->csr.block : 0;
   return SEED_OK;
 }
 

@@ -145,6 +145,8 @@ struct CsrOpT {
   int64_t n;
   const int32_t *row_ptr, *col_idx;
   const R *vals;
+  int32_t tpr = 1;        // threads per row (1, 2, 4 or 8); see csr.cu
+  int32_t block = 256;    // threads per block
 };
 using CsrOp = CsrOpT<double>;
 using CsrOp32 = CsrOpT<float>;
@@ -152,6 +154,9 @@ void launch_csr_spmv(const CsrOp &op, const double *in, int64_t ldi, double *out
                      const int32_t *col_active, cudaStream_t s);
 void launch_csr_spmv32(const CsrOp32 &op, const float *in, int64_t ldi, float *out, int64_t ldo, int ncols,
                        const int32_t *col_active, cudaStream_t s);
+// launch shapes the CSR autotuner chooses from: {threads per row, block size}
+constexpr int kCsrShapes = 6;
+extern const int32_t kCsrShape[kCsrShapes][2];
 
 // Seed recurrence, reorthogonalization, CG (krylov.cu)
 int vec_blocks(int64_t n);

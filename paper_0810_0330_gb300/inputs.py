@@ -62,13 +62,40 @@ def laplacian_3d_csr(n1: int, n2: int, n3: int, shift: float = 0.0):
 
 
 def shifted_laplacian_2d_csr(n1: int, n2: int, shift: float):
+    """laplacian_2d_csr plus ``shift`` on the diagonal."""
     row_ptr, col_idx, vals = laplacian_2d_csr(n1, n2)
+    rows = np.repeat(np.arange(n1 * n2, dtype=np.int64), np.diff(row_ptr))
     vals = vals.copy()
-    for r in range(n1 * n2):
-        for k in range(row_ptr[r], row_ptr[r + 1]):
-            if col_idx[k] == r:
-                vals[k] += shift
+    vals[col_idx == rows] += shift
     return row_ptr, col_idx, vals
+
+
+def batch_problems(count: int = 32, n_min: float = 1e4, n_max: float = 1e6, seed: int = 0):
+    """Uneven batch of SPD problems: each a 2-d (side round(sqrt n)) or 3-d
+    (side round(cbrt n)) Dirichlet Laplacian plus a diagonal shift U(0.01, 1),
+    n log-uniform in [n_min, n_max], 4..16 right-hand sides.  Returns a list of
+    dicts (kind, sides, shift, nrhs, rhs_seed); ``batch_problem_arrays`` builds
+    the CSR arrays and right-hand sides of one entry."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        kind = "2d" if rng.uniform() < 0.5 else "3d"
+        side = max(2, int(round(n ** 0.5 if kind == "2d" else n ** (1.0 / 3.0))))
+        shift = float(rng.uniform(0.01, 1.0))
+        nrhs = int(rng.integers(4, 17))
+        out.append(dict(kind=kind, sides=(side,) * (2 if kind == "2d" else 3), shift=shift, nrhs=nrhs,
+                        rhs_seed=seed * 1000 + i))
+    return out
+
+
+def batch_problem_arrays(p):
+    """(row_ptr, col_idx, vals, B) of one batch_problems entry; B Gaussian N(0,1), column-major."""
+    if p["kind"] == "2d":
+        rp, ci, v = shifted_laplacian_2d_csr(p["sides"][0], p["sides"][1], p["shift"])
+    else:
+        rp, ci, v = laplacian_3d_csr(*p["sides"], shift=p["shift"])
+    return rp, ci, v, gaussian_rhs(rp.shape[0] - 1, p["nrhs"], seed=p["rhs_seed"])
 
 
 def diagonal_csr(d: np.ndarray):
