@@ -21,6 +21,8 @@ namespace seedk {
 constexpr int NT = kVecThreads;
 constexpr int kSeedTicket = 0;     // tickets[0..15]: seed / reorth kernels
 constexpr int kColTicket = 16;     // tickets[16 + c]: per-column kernels
+constexpr int kGroupTicket = 128;  // tickets[128 + g]: groups of 32 blocks (two-level reductions)
+constexpr int kOneLevelBlocks = 152;   // reductions over more blocks than this use two levels
 
 #define GRID_STRIDE(e, n) \
   for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < (n); e += (int64_t)gridDim.x * NT)
@@ -159,10 +161,44 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
           ((sred[0][lane] + sred[1][lane]) + sred[2][lane]) + sred[3][lane];
     __syncthreads();
   }
-  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  // The last block reduces the block partials; on long vectors (more than one
+  // block per SM) in two levels: the last block of every group of 32 blocks
+  // sums its group, then the last group sums the group partials, so no single
+  // block reads all 32 x gridDim.x partials.  Both orders are fixed.
+  const int nb = gridDim.x;
+  const double *fin = b.partials;   // partials of the final level: [ch][nfin][32]
+  int nfin = nb;
+  if (nb > kOneLevelBlocks) {
+    const int grp = blockIdx.x >> 5, ngrp = (nb + 31) >> 5, gsz = min(32, nb - grp * 32);
+    if (!last_block_done(b.tickets + kGroupTicket + grp, gsz)) return;
+    double *gpart = b.partials + (int64_t)nch * nb * 32;
+    for (int v0 = warp * 8; v0 < 32 * nch; v0 += (NT / 32) * 8) {
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int val = v0 + u, ch = val >> 5, q = val & 31;
+        x[u] = (val < 32 * nch && lane < gsz) ? __ldcg(b.partials + ((int64_t)ch * nb + grp * 32 + lane) * 32 + q)
+                                              : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = warp_sum(x[u]);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int val = v0 + u;
+          if (val < 32 * nch) gpart[((int64_t)(val >> 5) * ngrp + grp) * 32 + (val & 31)] = x[u];
+        }
+      }
+    }
+    if (!last_block_done(b.tickets + kSeedTicket, ngrp)) return;
+    fin = gpart;
+    nfin = ngrp;
+  } else if (!last_block_done(b.tickets + kSeedTicket, nb)) {
+    return;
+  }
   for (int val = warp; val < 32 * nch; val += NT / 32) {
     const int ch = val >> 5, q = val & 31;
-    const double sv = warp_sum_partials(b.partials + (int64_t)ch * gridDim.x * 32, gridDim.x, 32, q);
+    const double sv = warp_sum_partials(fin + (int64_t)ch * nfin * 32, nfin, 32, q);
     if (lane == 0) {
       if (q == 0) {
         if (ch == 0) s_alpha = sv;

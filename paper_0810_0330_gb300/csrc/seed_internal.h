@@ -10,7 +10,8 @@ constexpr int kMaxRhs = 64;       // right-hand sides per call
 constexpr int kVecThreads = 128;  // threads per block of the vector kernels
 constexpr int kVecBlocksMax = 152 * 8;   // blocks of the single-vector kernels on long vectors
 // device scratch for block partials: the seed dot kernel's 5 chunks x 32 values per block
-constexpr int kPartials = 5 * kVecBlocksMax * 32 + 4096;
+// (plus its group partials, 5 chunks x ceil(kVecBlocksMax / 32) x 32)
+constexpr int kPartials = 5 * kVecBlocksMax * 32 + 5 * ((kVecBlocksMax + 31) / 32) * 32 + 4096;
 
 // Stop reasons of the seed recurrence (SeedState::stop_reason)
 enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4, STOP_TIMEOUT = 5 };

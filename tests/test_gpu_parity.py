@@ -379,3 +379,29 @@ def test_host_pointer_rejected(seedlib):
     Bd = dev_cols(np.ones((64, 1)))
     st = L.seed_solve_first(ctx.handle, Bd.data_ptr(), 32, Bd.data_ptr(), 64, 1, None)
     assert st == seedlib.SEED_EINVAL   # ld < n
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_long_vectors_two_level_reductions(seedlib, orc, precision):
+    """n = 512^2 (shifted 2-d Laplacian, shift 0.5): the single-vector kernels
+    run with more than one block per SM and the seed dot products reduce in
+    two levels (groups of 32 blocks, then the groups).  FP64: the seed steps
+    equal and x^1 within 1e-9 of the oracle's; both precisions: every true
+    residual within its tolerance and the seeded CG counts within 5 %."""
+    rp, ci, v = I.shifted_laplacian_2d_csr(512, 512, 0.5)
+    n = 512 * 512
+    B = I.gaussian_rhs(n, 3, seed=9)
+    prm = dict(m_max=400, reorth_freq=20, tol_seed=1e-10, tol_rest=1e-8, precision=precision, kernel_path=1)
+    ctx = csr_ctx(seedlib, rp, ci, v, **prm)
+    info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
+    op = orc.Operator.csr(rp, ci, v)
+    ref = orc.seed_solve_all(op, B, m_max=400, reorth_freq=20, tol_seed=1e-10, tol_rest=1e-8)
+    if precision == 0:
+        assert info1[0]["iters"] == ref["seed"]["iters"]
+        assert relerr(X[:, 0].real, ref["seed"]["X"][:, 0].real) < REL_X
+    for j in range(3):
+        tol = 1e-10 if j == 0 else 1e-8
+        rr = np.linalg.norm(B[:, j] - op.apply(X[:, j].real).real) / np.linalg.norm(B[:, j])
+        assert rr <= 1.5 * tol, (j, rr)
+    for j, r in enumerate(ref["rest"], start=1):
+        assert abs(info2[j]["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (j, info2[j]["iters"], r["iters"])
