@@ -221,6 +221,18 @@ seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, 
 seed_status seed_solve_related(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t nrhs,
                                seed_info *info);
 
+/* Multiple seeding, the seed CG that Sec. 2.1 compares single seeding with:
+ * the systems are solved in order by CG from zero (tol_rest); every CG step of
+ * system j, with direction p and q = A p, also projects each later system i:
+ *   eta = (p^H r^i) / (p^H q),  x^i += eta p,  r^i -= eta q  (r^i tracked).
+ * Each system's CG starts from its projected x^j with the residual recomputed
+ * (one mvp) and ends with a true-residual check (one mvp, no restart).  Kept
+ * as the comparison baseline; FP64 contexts only.  X: out, all solutions;
+ * info: NULL or nrhs entries (iters, mvps, converged, true_relres per system).
+ * Returns SEED_OK or SEED_ENOTCONV. */
+seed_status seed_solve_multiple(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t nrhs,
+                                seed_info *info);
+
 /* Lockstep CG (Sec. 1; the iteration of seed_solve_rest) on ALL ncols columns
  * of B from the initial guesses in X, to ||b^j - A x^j|| <= tol_rest ||b^j||
  * (mixed-precision contexts: FP32 iterations with FP64 reliable updates).

@@ -76,6 +76,8 @@ def _declare(lib):
     lib.orc_csr_apply.argtypes = [C.c_int64, P, P, P, P, P]
     lib.orc_wilson_neighbors.argtypes = [P, P]
     lib.orc_wilson_dslash.argtypes = [P, C.c_double, C.c_int32, C.c_int32, P, P, P]
+    lib.orc_seed_multiple.argtypes = [C.POINTER(_Op), C.c_int32, P, P, C.c_double, C.c_int32, P, P, P]
+    lib.orc_seed_multiple.restype = C.c_int
     lib.orc_wilson_dA_dkappa.argtypes = [P, C.c_double, C.c_int32, P, P, P]
     lib.orc_wilson_dA_dkappa.restype = C.c_int
     lib.orc_op_apply.argtypes = [C.POINTER(_Op), P, P]
@@ -268,6 +270,19 @@ def seed_solve_all(op: Operator, B, *, m_max: int, reorth_freq: int, reorth_pass
         X[:, j] = r["x"]
         rest.append(r)
     return dict(seed=s, rest=rest, X=X, X_seeded=X_seeded)
+
+
+def seed_multiple(op: Operator, B, *, tol: float = 1e-8, maxit: int = 100000) -> dict:
+    """Multiple seeding, the seed CG that Sec. 2.1 compares against (see orc_seed_multiple)."""
+    B = np.asfortranarray(B, dtype=np.complex128)
+    n, p = B.shape
+    X = np.zeros((n, p), dtype=np.complex128, order="F")
+    iters = np.zeros(p, dtype=np.int32)
+    mvps = np.zeros(p, dtype=np.int32)
+    relres = np.zeros(p, dtype=np.float64)
+    rc = _load().orc_seed_multiple(C.byref(op.s), p, _p(B), _p(X), float(tol), int(maxit), _p(iters), _p(mvps),
+                                   _p(relres))
+    return dict(status=STATUS.get(rc, rc), X=X, iters=iters.tolist(), mvps=mvps.tolist(), relres=relres.tolist())
 
 
 def seed_solve_related(op: Operator, B, *, m_max: int, reorth_freq: int, reorth_passes: int = 2,

@@ -30,6 +30,9 @@
  *   orc_tridiag_eigs ..... eigenvalues of the Lanczos tridiagonal by Sturm
  *                          bisection (pin only)
  *   orc_wilson_neighbors . site -> 8 neighbour table (x fastest, periodic)
+ *   orc_seed_multiple .... multiple seeding, the seed CG that Sec. 2.1 compares
+ *                          against: systems solved in order by CG, each CG
+ *                          step also projecting every later system
  *   orc_wilson_dA_dkappa . y = (dA/dkappa) x for A = D^H D (no passage: the
  *                          chain rule for the adjoint of a solve; pinned by
  *                          finite differences of the operator and of a loss)
@@ -485,6 +488,71 @@ int orc_cg(const orc_op *A, const zc *b, zc *x, double tol, int32_t maxit,
   }
 done:
   free(r); free(p); free(q);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multiple seeding (Sec. 2.1, the comparison method)                       */
+/* ------------------------------------------------------------------------ */
+
+/* No initial guesses.  For j = 1..nrhs: CG on system j from its current x^j
+ * (residual recomputed, one mvp); every CG step, with direction p and
+ * q = A p, first projects each later system i over p:
+ *   eta = (p^H r^i) / (p^H q),  x^i += eta p,  r^i -= eta q,
+ * where r^i is the tracked residual of system i (r^i = b^i at the start).
+ * CG stops at ||r^j|| <= tol ||b^j||, then the true residual is computed
+ * (one mvp).  iters[j], mvps[j] and relres[j] receive each system's counts. */
+int orc_seed_multiple(const orc_op *A, int32_t nrhs, const zc *B, zc *X, double tol, int32_t maxit,
+                      int32_t *iters, int32_t *mvps, double *relres) {
+  int64_t n = A->n;
+  zc *R = (zc *)malloc(sizeof(zc) * n * nrhs), *r = (zc *)malloc(sizeof(zc) * n),
+     *p = (zc *)malloc(sizeof(zc) * n), *q = (zc *)malloc(sizeof(zc) * n);
+  if (!R || !r || !p || !q) { free(R); free(r); free(p); free(q); return ORC_ENOMEM; }
+  memset(X, 0, sizeof(zc) * n * nrhs);
+  memcpy(R, B, sizeof(zc) * n * nrhs);
+  int status = ORC_OK;
+  for (int32_t j = 0; j < nrhs; ++j) {
+    const zc *b = B + (int64_t)j * n;
+    zc *x = X + (int64_t)j * n;
+    double bn = vnorm(n, b);
+    iters[j] = 0;
+    mvps[j] = 1;
+    orc_op_apply(A, x, q);
+    for (int64_t k = 0; k < n; ++k) r[k] = zsub(b[k], q[k]);
+    double rn = vnorm(n, r);
+    if (rn > tol * bn) {
+      memcpy(p, r, sizeof(zc) * n);
+      double rho = rn * rn;
+      while (iters[j] < maxit) {
+        orc_op_apply(A, p, q);
+        mvps[j]++;
+        iters[j]++;
+        zc pqz = vdot(n, p, q);
+        double al = rho / pqz.re;
+        for (int32_t i = j + 1; i < nrhs; ++i) {
+          zc *xi = X + (int64_t)i * n, *ri = R + (int64_t)i * n;
+          zc num = vdot(n, p, ri);
+          double d = pqz.re * pqz.re + pqz.im * pqz.im;
+          zc eta = zmk((num.re * pqz.re + num.im * pqz.im) / d, (num.im * pqz.re - num.re * pqz.im) / d);
+          vaxpy(n, eta, p, xi);
+          vaxpy(n, zmk(-eta.re, -eta.im), q, ri);
+        }
+        vaxpy(n, zmk(al, 0.0), p, x);
+        vaxpy(n, zmk(-al, 0.0), q, r);
+        rn = vnorm(n, r);
+        if (rn <= tol * bn) break;
+        double be = (rn * rn) / rho;
+        for (int64_t k = 0; k < n; ++k) p[k] = zadd(r[k], zscale(be, p[k]));
+        rho = rn * rn;
+      }
+    }
+    orc_op_apply(A, x, q);
+    mvps[j]++;
+    for (int64_t k = 0; k < n; ++k) r[k] = zsub(b[k], q[k]);
+    relres[j] = bn > 0.0 ? vnorm(n, r) / bn : 0.0;
+    if (relres[j] > 1.5 * tol) status = ORC_ENOTCONV;
+  }
+  free(R); free(r); free(p); free(q);
   return status;
 }
 

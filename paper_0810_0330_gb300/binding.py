@@ -32,7 +32,7 @@ EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_c
            "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
            "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related",
-           "seed_batch_solve"]
+           "seed_batch_solve", "seed_solve_multiple"]
 
 
 class SeedError(RuntimeError):
@@ -103,6 +103,7 @@ def lib():
             L.seed_wilson_apply_noalloc.argtypes = [C.POINTER(seed_wilson), P, I64, P, I64, I32, P]
             L.seed_solve_cg.argtypes = [P, P, I64, P, I64, I32, P]
             L.seed_solve_related.argtypes = [P, P, I64, P, I64, I32, P]
+            L.seed_solve_multiple.argtypes = [P, P, I64, P, I64, I32, P]
             L.seed_batch_solve.argtypes = [P, P, P, P, P, P, I32, I32, P]
             L.seed_grad_kappa.argtypes = [P, P, I64, P, I64, I32, C.POINTER(C.c_double)]
             L.seed_last_error.argtypes = [P]
@@ -234,6 +235,17 @@ def seed_batch_solve(ctxs, Bs, Xs, workers: int = 0):
     ip = (C.c_void_p * k)(*[C.cast(inf, C.c_void_p).value for inf in infos])
     _check(lib().seed_batch_solve(hs, pb, ldb, px, ldx, nr, int(k), int(workers), ip), "seed_batch_solve")
     return [[i.as_dict() for i in inf] for inf in infos]
+
+
+def seed_solve_multiple(ctx: Context, B: torch.Tensor, X: torch.Tensor):
+    """Multiple seeding (the Sec. 2.1 comparison method): all systems, in order."""
+    pb, ldb, nb = _block(B, ctx.n, "B")
+    px, ldx, nx = _block(X, ctx.n, "X")
+    if nb != nx:
+        raise ValueError("B and X must have the same number of columns")
+    info = _infos(nb)
+    _check(lib().seed_solve_multiple(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_multiple", ctx.handle)
+    return [i.as_dict() for i in info]
 
 
 def seed_solve_related(ctx: Context, B: torch.Tensor, X: torch.Tensor):

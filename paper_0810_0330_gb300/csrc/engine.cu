@@ -113,6 +113,8 @@ struct seed_ctx {
   void *Rrel = nullptr, *xrel = nullptr, *rrel = nullptr;
   int rel_cap = 0;
   double2 *reldots = nullptr;          // [2 * kMaxRhs]
+  void *msX = nullptr, *msR = nullptr; // multiple seeding: solutions and tracked residuals
+  int ms_cap = 0;
 
   std::map<std::string, GraphEntry> graphs;
   std::string err;
@@ -609,6 +611,25 @@ CgCols cg_cols(seed_ctx *ctx, int nc) {
   return c;
 }
 
+struct CgHost {
+  std::vector<int32_t> i;
+  std::vector<double> d;
+  int32_t iters(int j) const { return i[kMaxRhs + j]; }
+  int32_t restarts(int j) const { return i[3 * kMaxRhs + j]; }
+  int32_t converged(int j) const { return i[4 * kMaxRhs + j]; }
+  int32_t mvps(int j) const { return i[6 * kMaxRhs + j]; }
+  double relres(int j) const { return d[4 * kMaxRhs + j]; }
+};
+
+seed_status read_cg(seed_ctx *ctx, CgHost *h) {
+  h->i.resize(kCgInts * kMaxRhs);
+  h->d.resize(kCgDoubles * kMaxRhs);
+  CU(cudaMemcpyAsync(h->i.data(), ctx->cg_i, sizeof(int32_t) * kCgInts * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaMemcpyAsync(h->d.data(), ctx->cg_d, sizeof(double) * kCgDoubles * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  return SEED_OK;
+}
+
 template <class T>
 seed_status launch_cg_run(seed_ctx *ctx, const CgCols &c, int len) {
   std::string key = "C" + std::to_string(c.nc) + ":" + std::to_string(len);
@@ -879,6 +900,115 @@ seed_status solve_related_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *
 }
 
 // ---------------------------------------------------------------------------
+// Multiple seeding (the comparison method of Sec. 2.1)
+// ---------------------------------------------------------------------------
+seed_status ensure_multiple(seed_ctx *ctx, int nrhs) {
+  if (nrhs <= ctx->ms_cap) return SEED_OK;
+  cudaStreamSynchronize(ctx->cs);
+  cudaFree(ctx->msX); cudaFree(ctx->msR);
+  ctx->msX = ctx->msR = nullptr;
+  ctx->ms_cap = 0;
+  TRY(dalloc(ctx, &ctx->msX, (size_t)ctx->ldv * nrhs * ctx->esz));
+  TRY(dalloc(ctx, &ctx->msR, (size_t)ctx->ldv * nrhs * ctx->esz));
+  if (!ctx->reldots) TRY(dalloc(ctx, &ctx->reldots, sizeof(double2) * 2 * kMaxRhs));
+  ctx->ms_cap = nrhs;
+  return SEED_OK;
+}
+
+// Systems solved in order by CG from zero; every CG step of system j projects
+// each later system i over its direction p (eta = p^H r^i / p^H q, x^i += eta p,
+// r^i -= eta q), with the tracked residuals r^i (b^i at the start).  All on
+// internal copies (so the captured graphs stay valid), copied to X at the end.
+template <class T>
+seed_status solve_multiple_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
+                                seed_info *info) {
+  const int64_t n = ctx->n, ld = ctx->ldv;
+  if (info) std::memset(info, 0, sizeof(seed_info) * nrhs);
+  TRY(ensure_cols(ctx, nrhs));
+  TRY(ensure_multiple(ctx, nrhs));
+  T *Xw = (T *)ctx->msX, *Rw = (T *)ctx->msR;
+  const T *Bt = (const T *)B;
+  double2 *dots = ctx->reldots, *delta = ctx->reldots + kMaxRhs;
+  CU(cudaEventRecord(ctx->t2, ctx->cs));
+  launch_zero_cols<T>(Xw, ld, n, nrhs, ctx->cs);
+  launch_copy_cols<T>(Bt, ldb, Rw, ld, n, nrhs, ctx->cs);
+  ctx->stats.kernel_launches += 2;
+  CgCols c = cg_cols(ctx, 1);
+  c.max_restarts = 0;
+  c.tol_check = 1.5 * c.tol;
+  const int L = 16;
+  for (int j = 0; j < nrhs; ++j) {
+    const CallArgs ca{Xw, ld, j};
+    CU(cudaMemcpyAsync(ctx->call, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+    int kern = apply_A(ctx, Xw + (int64_t)j * ld, ld, ctx->Q, ld, 1, nullptr);
+    launch_cg_init<T>(n, Bt + (int64_t)j * ldb, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, (T *)ctx->P, ld, c,
+                      ctx->partials, ctx->tickets, false, ctx->cs);
+    ctx->stats.kernel_launches += kern + 1;
+    const int nrem = nrhs - j - 1;
+    const std::string key = "MS" + std::to_string(nrhs) + ":" + std::to_string(j) + ":" + std::to_string(L);
+    int slot = 0, pending = -1;
+    cudaEvent_t evs[2] = {nullptr, nullptr};
+    for (;;) {
+      TRY(run_graph(ctx, key, [&] {
+        int k = 0;
+        for (int q = 0; q < L; ++q) {
+          k += apply_A(ctx, ctx->P, ld, ctx->Q, ld, 1, c.active);
+          launch_cg_alpha<T>(n, (const T *)ctx->P, (const T *)ctx->Q, ld, c, ctx->partials, ctx->tickets, ctx->cs);
+          launch_related_project<T>(n, (const T *)ctx->P, (const T *)ctx->Q, Xw + (int64_t)(j + 1) * ld, ld,
+                                    Rw + (int64_t)(j + 1) * ld, ld, nrem, dots, delta, ctx->partials, ctx->tickets,
+                                    ctx->cs, c.active);
+          launch_cg_update<T>(n, ctx->call, (T *)ctx->R, (const T *)ctx->P, (const T *)ctx->Q, ld, c, ctx->partials,
+                              ctx->tickets, ctx->cs);
+          launch_cg_p<T>(n, (const T *)ctx->R, (T *)ctx->P, ld, c, ctx->cs);
+          k += 3 + (nrem > 0 ? 3 : 0);
+        }
+        return k;
+      }));
+      CU(cudaMemcpyAsync(ctx->h_flags + slot * kMaxRhs, c.active, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->cs));
+      if (!evs[slot]) CU(cudaEventCreateWithFlags(&evs[slot], cudaEventDisableTiming));
+      CU(cudaEventRecord(evs[slot], ctx->cs));
+      bool any = true;
+      if (pending >= 0) {
+        CU(cudaEventSynchronize(evs[pending]));
+        any = ctx->h_flags[pending * kMaxRhs] != 0;
+      }
+      pending = slot;
+      slot ^= 1;
+      if (!any) break;
+    }
+    CU(cudaStreamSynchronize(ctx->cs));
+    for (auto &e : evs)
+      if (e) cudaEventDestroy(e);
+    // true residual of system j
+    kern = apply_A(ctx, Xw + (int64_t)j * ld, ld, ctx->Q, ld, 1, c.needs_check);
+    launch_cg_check<T>(n, Bt + (int64_t)j * ldb, ldb, (const T *)ctx->Q, ld, (T *)ctx->R, ld, c, ctx->partials,
+                       ctx->tickets, ctx->cs);
+    ctx->stats.kernel_launches += kern + 1;
+    CgHost h;
+    TRY(read_cg(ctx, &h));
+    ctx->stats.mvps += h.mvps(0);
+    if (info) {
+      info[j].iters = h.iters(0);
+      info[j].mvps = h.mvps(0);
+      info[j].converged = h.converged(0);
+      info[j].est_relres = info[j].true_relres = h.relres(0);
+    }
+  }
+  launch_copy_cols<T>(Xw, ld, (T *)X, ldx, n, nrhs, ctx->cs);
+  ctx->stats.kernel_launches += 1;
+  CU(cudaEventRecord(ctx->t3, ctx->cs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  CU(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->t2, ctx->t3);
+  ctx->stats.ms_rest = ms;
+  if (info)
+    for (int j = 0; j < nrhs; ++j)
+      if (!info[j].converged) return fail(ctx, SEED_ENOTCONV, "multiple seeding: a system did not reach tol_rest");
+  return SEED_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Mixed precision: FP32 iterations, FP64 scalars and reliable updates
 // ---------------------------------------------------------------------------
 
@@ -972,25 +1102,6 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
     if (e) cudaEventDestroy(e);
   CU(cudaGetLastError());
   if (cols_out) *cols_out = c;
-  return SEED_OK;
-}
-
-struct CgHost {
-  std::vector<int32_t> i;
-  std::vector<double> d;
-  int32_t iters(int j) const { return i[kMaxRhs + j]; }
-  int32_t restarts(int j) const { return i[3 * kMaxRhs + j]; }
-  int32_t converged(int j) const { return i[4 * kMaxRhs + j]; }
-  int32_t mvps(int j) const { return i[6 * kMaxRhs + j]; }
-  double relres(int j) const { return d[4 * kMaxRhs + j]; }
-};
-
-seed_status read_cg(seed_ctx *ctx, CgHost *h) {
-  h->i.resize(kCgInts * kMaxRhs);
-  h->d.resize(kCgDoubles * kMaxRhs);
-  CU(cudaMemcpyAsync(h->i.data(), ctx->cg_i, sizeof(int32_t) * kCgInts * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
-  CU(cudaMemcpyAsync(h->d.data(), ctx->cg_d, sizeof(double) * kCgDoubles * kMaxRhs, cudaMemcpyDeviceToHost, ctx->cs));
-  CU(cudaStreamSynchronize(ctx->cs));
   return SEED_OK;
 }
 
@@ -1174,7 +1285,8 @@ void destroy(seed_ctx *ctx) {
                   ctx->delta_hist, ctx->eta, ctx->partials, ctx->tickets, ctx->Hpart, ctx->H, ctx->call,
                   ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
                   ctx->gsync, ctx->f2, ctx->gbuf, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
-                  ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots};
+                  ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots,
+                  ctx->msX, ctx->msR};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
@@ -1417,6 +1529,18 @@ seed_status seed_solve_related(seed_ctx *ctx, const void *B, int64_t ldb, void *
   StreamScope scope(ctx);
   if (ctx->kind == 0) return solve_related_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
   return solve_related_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
+}
+
+seed_status seed_solve_multiple(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int32_t nrhs,
+                                seed_info *info) {
+  if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
+  if (ctx->precision != 0) return fail(ctx, SEED_EINVAL, "seed_solve_multiple runs in FP64 (precision = 0)");
+  TRY(check_block(ctx, B, ldb, nrhs, "B"));
+  TRY(check_block(ctx, X, ldx, nrhs, "X"));
+  if (overlap(B, ldb, X, ldx, nrhs, ctx->n, ctx->esz)) return fail(ctx, SEED_EINVAL, "B and X overlap");
+  StreamScope scope(ctx);
+  if (ctx->kind == 0) return solve_multiple_impl<double>(ctx, B, ldb, X, ldx, nrhs, info);
+  return solve_multiple_impl<double2>(ctx, B, ldb, X, ldx, nrhs, info);
 }
 
 seed_status seed_grad_kappa(seed_ctx *ctx, const void *Lambda, int64_t ldl, const void *X, int64_t ldx, int32_t ncols,

@@ -7,6 +7,12 @@
 // (r^j_bcg, the residual of system j before its CG, stands for A x_cg: the
 // two differ by the final residual of system j, which CG has made small.)
 // Reductions are deterministic: block partials summed in block order.
+//
+// The same two kernels give multiple seeding (the comparison method of Sec.
+// 2.1): there every CG step of the current system projects each later system
+// over its direction, with (p, q = A p) in place of (x_cg, r^j_bcg).  `gate`
+// (NULL = always) is that CG's active flag, so steps issued after it has
+// converged change nothing.
 #include "seed_device.cuh"
 
 namespace seedk {
@@ -23,8 +29,9 @@ int col_blocks(int64_t n, int nc);
 template <class T>
 __global__ void __launch_bounds__(NT) k_rel_dots(int64_t n, const T *__restrict__ xcg, const T *__restrict__ rbcg,
                                                  const T *__restrict__ R, int64_t ldr, int nrem, double2 *dots,
-                                                 double *partials, unsigned *tickets) {
+                                                 double *partials, unsigned *tickets, const int32_t *gate) {
   __shared__ double sm[2 * NT / 32];
+  if (gate != nullptr && gate[0] == 0) return;
   const int col = blockIdx.y;
   const T *y = col < nrem ? R + (int64_t)col * ldr : rbcg;
   typename Sc<T>::A2 acc = Sc<T>::zero2();
@@ -43,9 +50,9 @@ __global__ void __launch_bounds__(NT) k_rel_dots(int64_t n, const T *__restrict_
 }
 
 // delta_c = dots[c] / dots[nrem] (complex division), one thread per column
-__global__ void k_rel_delta(int nrem, const double2 *dots, double2 *delta) {
+__global__ void k_rel_delta(int nrem, const double2 *dots, double2 *delta, const int32_t *gate) {
   const int c = threadIdx.x;
-  if (c >= nrem) return;
+  if (c >= nrem || (gate != nullptr && gate[0] == 0)) return;
   const double2 a = dots[c], b = dots[nrem];
   const double d = b.x * b.x + b.y * b.y;
   delta[c] = d > 0.0 ? c2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d) : c2(0.0, 0.0);
@@ -54,7 +61,9 @@ __global__ void k_rel_delta(int nrem, const double2 *dots, double2 *delta) {
 // X[:, c] += delta_c x_cg;  R[:, c] -= delta_c r_bcg   (grid (blocks, nrem))
 template <class T>
 __global__ void __launch_bounds__(NT) k_rel_update(int64_t n, const T *__restrict__ xcg, const T *__restrict__ rbcg,
-                                                   T *X, int64_t ldx, T *R, int64_t ldr, const double2 *delta) {
+                                                   T *X, int64_t ldx, T *R, int64_t ldr, const double2 *delta,
+                                                   const int32_t *gate) {
+  if (gate != nullptr && gate[0] == 0) return;
   const int col = blockIdx.y;
   const double2 d = delta[col], md = c2(-d.x, -d.y);
   X += (int64_t)col * ldx;
@@ -67,20 +76,22 @@ __global__ void __launch_bounds__(NT) k_rel_update(int64_t n, const T *__restric
 
 template <class T>
 void launch_related_project(int64_t n, const T *xcg, const T *rbcg, T *X, int64_t ldx, T *R, int64_t ldr, int nrem,
-                            double2 *dots, double2 *delta, double *partials, unsigned *tickets, cudaStream_t s) {
+                            double2 *dots, double2 *delta, double *partials, unsigned *tickets, cudaStream_t s,
+                            const int32_t *gate) {
   if (nrem <= 0) return;
   const int b = col_blocks(n, nrem + 1);
   k_rel_dots<T><<<dim3((unsigned)b, (unsigned)(nrem + 1)), NT, 0, s>>>(n, xcg, rbcg, R, ldr, nrem, dots, partials,
-                                                                       tickets);
-  k_rel_delta<<<1, kMaxRhs, 0, s>>>(nrem, dots, delta);
+                                                                       tickets, gate);
+  k_rel_delta<<<1, kMaxRhs, 0, s>>>(nrem, dots, delta, gate);
   const int b2 = col_blocks(n, nrem);
-  k_rel_update<T><<<dim3((unsigned)b2, (unsigned)nrem), NT, 0, s>>>(n, xcg, rbcg, X, ldx, R, ldr, delta);
+  k_rel_update<T><<<dim3((unsigned)b2, (unsigned)nrem), NT, 0, s>>>(n, xcg, rbcg, X, ldx, R, ldr, delta, gate);
 }
 
 template void launch_related_project<double>(int64_t, const double *, const double *, double *, int64_t, double *,
-                                             int64_t, int, double2 *, double2 *, double *, unsigned *, cudaStream_t);
+                                             int64_t, int, double2 *, double2 *, double *, unsigned *, cudaStream_t,
+                                             const int32_t *);
 template void launch_related_project<double2>(int64_t, const double2 *, const double2 *, double2 *, int64_t,
                                               double2 *, int64_t, int, double2 *, double2 *, double *, unsigned *,
-                                              cudaStream_t);
+                                              cudaStream_t, const int32_t *);
 
 }  // namespace seedk

@@ -211,7 +211,8 @@ struct Layout32 {
 // delta_c = (xcg^H R[:, c]) / (xcg^H rbcg), c < nrem.  dots: nrem + 1, delta: nrem device scratch.
 template <class T>
 void launch_related_project(int64_t n, const T *xcg, const T *rbcg, T *X, int64_t ldx, T *R, int64_t ldr, int nrem,
-                            double2 *dots, double2 *delta, double *partials, unsigned *tickets, cudaStream_t s);
+                            double2 *dots, double2 *delta, double *partials, unsigned *tickets, cudaStream_t s,
+                            const int32_t *gate = nullptr);
 
 // Adjoint (adjoint.cu): out[j] = Re <L_j, (dA/dkappa) X_j> for the Wilson normal
 // operator A = D^H D (device array of ncols doubles).

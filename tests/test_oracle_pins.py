@@ -474,3 +474,27 @@ def test_paper_example3_related_rhs(orc):
     for j, r in enumerate(rel["rest"], start=1):
         assert r["converged"] and r["true_relres"] <= 1.5e-8
         assert np.linalg.norm(B[:, j] - op.apply(rel["X"][:, j])) <= 1.5e-8 * np.linalg.norm(B[:, j])
+
+
+@pytest.mark.slow
+def test_paper_multiple_seeding_trends(orc):
+    """Sec. 2.1-2.2 with multiple seeding (every system's CG projects all later
+    systems): it saves mvps against no seeding (Table 2.1: 3978 vs 4935, ratio
+    0.81), single seeding saves more (2439), and the third system after multiple
+    seeding needs more iterations than the second (Example 1: 598 vs 269, the
+    rounding effect Sec. 2.1 describes).  The draws are not the paper's; over 4
+    draws the ratio was 0.81-0.90, so each must be below 0.95."""
+    g = _golden()
+    n = g["example1"]["n"]
+    for seed in range(4):
+        op = orc.Operator.csr(*I.diagonal_csr(I.paper_diagonal(n, seed=seed)))
+        B = I.gaussian_rhs(n, 8, seed=100 + seed)
+        none = sum(orc.cg(op, B[:, j], np.zeros(n), tol=1e-8)["iters"] for j in range(8))
+        ms = orc.seed_multiple(op, B, tol=1e-8)
+        res = orc.seed_solve_all(op, B, m_max=5000, reorth_freq=0, tol_seed=1e-8, tol_rest=1e-8)
+        single = res["seed"]["iters"] + sum(r["iters"] for r in res["rest"])
+        multiple = sum(ms["iters"])
+        assert ms["status"] == "OK" and max(ms["relres"]) <= 1.5e-8
+        assert multiple < 0.95 * none, (seed, multiple, none)
+        assert single < multiple, (seed, single, multiple)
+        assert ms["iters"][2] > ms["iters"][1], (seed, ms["iters"])
