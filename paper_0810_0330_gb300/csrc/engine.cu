@@ -92,7 +92,6 @@ struct seed_ctx {
   unsigned *gsync = nullptr;           // GridSync: count, release, error
   int32_t *h_gerr = nullptr;           // pinned copy of the error flag
   void *f2 = nullptr;                  // second Lanczos-vector buffer (CSR persistent run)
-  double2 *gbuf = nullptr;             // g^j of the next step (persistent seed run)
   double *tpart = nullptr;             // per-tile partial sums (persistent Wilson seed run)
   bool allow_persistent = true;        // persistent seed runs
   bool allow_persistent_cg = false;    // persistent CG
@@ -227,7 +226,6 @@ seed_status alloc_common(seed_ctx *ctx) {
   CU(cudaMallocHost(&ctx->h_status, sizeof(HostStatus) * 2));
   TRY(dalloc(ctx, &ctx->gsync, sizeof(unsigned) * kGridSyncWords));
   TRY(dalloc(ctx, &ctx->f2, n * es));
-  TRY(dalloc(ctx, &ctx->gbuf, sizeof(double2) * kPersistMaxRhs));
   TRY(dalloc(ctx, &ctx->tpart, sizeof(double) * (size_t)((n / 12 + 31) / 32 + 1)));
   CU(cudaMallocHost(&ctx->h_gerr, sizeof(int32_t) * 2));
   CU(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -467,10 +465,10 @@ seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
     SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
     cudaError_t e;
     if constexpr (sizeof(T) == sizeof(double2))
-      e = launch_seed_run_wilson(b, ctx->wil, (double2 *)ctx->T, ctx->gbuf, g, ctx->partials, ctx->tpart, i_stop,
-                                 ctx->pgrid, ctx->cs);
+      e = launch_seed_run_wilson(b, ctx->wil, (double2 *)ctx->T, g, ctx->partials, ctx->tpart, i_stop, ctx->pgrid,
+                                 ctx->cs);
     else
-      e = launch_seed_run_csr(b, ctx->csr, (double *)ctx->f2, ctx->gbuf, g, ctx->partials, i_stop, ctx->pgrid, ctx->cs);
+      e = launch_seed_run_csr(b, ctx->csr, (double *)ctx->f2, g, ctx->partials, i_stop, ctx->pgrid, ctx->cs);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, SEED_ECUDA, std::string("persistent seed launch: ") + cudaGetErrorString(e));
@@ -1284,7 +1282,7 @@ void destroy(seed_ctx *ctx) {
   void *ptrs[] = {ctx->V, ctx->vcur, ctx->u, ctx->f, ctx->w, ctx->st, ctx->alpha_hist, ctx->beta_hist,
                   ctx->delta_hist, ctx->eta, ctx->partials, ctx->tickets, ctx->Hpart, ctx->H, ctx->call,
                   ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
-                  ctx->gsync, ctx->f2, ctx->gbuf, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
+                  ctx->gsync, ctx->f2, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
                   ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots,
                   ctx->msX, ctx->msR};
   for (void *q : ptrs)

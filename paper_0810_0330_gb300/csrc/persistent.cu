@@ -202,14 +202,50 @@ SEED_DEV double2 tile_sum(double (*sacc)[24][kWilsonSites + 1], int cc, int sl) 
 // Seed runs.  Per step i (paper notation):
 //   phase 1 (tiles): v_i = f / beta_{i-1} into V; t = D v_i        [Wilson only]
 //   phase 2 (tiles): u = A v_i; f = u - beta_{i-1} v_{i-1}; partial alpha_i
-//   reduce: alpha_i -> gamma_{i-1}, delta_i, zeta_i, eta^j (steps 3/4, 6/7),
-//           with g^j = v_i^H r_0^j formed in the previous step's update
+//   barrier; every block: alpha_i -> gamma_{i-1}, delta_i, zeta_i, eta^j
+//           (steps 3/4, 6/7), with g^j = v_i^H r_0^j formed in the previous step
 //   phase 3 (all blocks): f -= alpha_i v_i; w_i; x^1, x^j; partials ||f||^2
 //           and f^H r_0^j
-//   reduce: beta_i, stopping test (step 9); g^j of step i+1 =
+//   barrier; every block: beta_i, stopping test (step 9); g^j of step i+1 =
 //           (f^H r_0^j) / beta_i, since v_{i+1} = f / beta_i.
 // A pre-phase at the start of a run forms g^j of its first step the same way.
+//
+// Every block keeps its own shared-memory copy of the recurrence scalars
+// (SeedState, eta^j, g^j).  After each barrier every block reduces the same
+// partials in the same fixed order and runs the same scalar code, so the
+// copies stay identical and no block waits for another to publish scalars:
+// the barriers are plain arrivals, with no serial reduce-then-release hop.
+// Block 0 writes the step histories and, on leaving, the state back.
 // ---------------------------------------------------------------------------
+struct LocalSeed {
+  SeedState st;
+  double2 eta[kPersistMaxRhs];
+  double2 g[kPersistMaxRhs];
+};
+
+template <class T>
+SEED_DEV SeedBufs<T> local_bufs(const SeedBufs<T> &b, LocalSeed &L) {
+  SeedBufs<T> l = b;
+  l.st = &L.st;
+  l.eta = L.eta;
+  if (blockIdx.x != 0) l.alpha_hist = l.beta_hist = l.delta_hist = nullptr;
+  return l;
+}
+
+template <class T>
+SEED_DEV void local_load(const SeedBufs<T> &b, LocalSeed &L) {
+  if (threadIdx.x == 0) L.st = *b.st;
+  for (int j = threadIdx.x; j < b.nrhs; j += PT) L.eta[j] = b.eta[j];
+  __syncthreads();
+}
+
+template <class T>
+SEED_DEV void local_store(const SeedBufs<T> &b, const LocalSeed &L) {
+  __syncthreads();
+  if (blockIdx.x != 0) return;
+  if (threadIdx.x == 0) *b.st = L.st;
+  for (int j = threadIdx.x; j < b.nrhs; j += PT) b.eta[j] = L.eta[j];
+}
 
 // partial of f^H r_0^j (slots 1 + 2(j-1), 2 + 2(j-1)) for element e
 template <class T>
@@ -225,16 +261,15 @@ SEED_DEV void add_fr0(const SeedBufs<T> &b, int64_t e, T fe, double (&acc)[32]) 
   }
 }
 
-// g^j = scale * (reduced f^H r_0^j) into gbuf
-template <class T>
-SEED_DEV void store_g(const SeedBufs<T> &b, const double *s_vals, double scale, double2 *gbuf) {
-  for (int j = 1 + (int)threadIdx.x; j < b.nrhs; j += PT)
-    gbuf[j] = c2(scale * s_vals[1 + 2 * (j - 1)], scale * s_vals[2 + 2 * (j - 1)]);
+// g^j = scale * (reduced f^H r_0^j)
+SEED_DEV void local_g(int nrhs, const double *s_vals, double scale, LocalSeed &L) {
+  for (int j = 1 + (int)threadIdx.x; j < nrhs; j += PT)
+    L.g[j] = c2(scale * s_vals[1 + 2 * (j - 1)], scale * s_vals[2 + 2 * (j - 1)]);
 }
 
 // pre-phase: g^j of the first step from the current f
 template <class T>
-SEED_DEV bool seed_pre_dots(const SeedBufs<T> &b, const T *f, double2 *gbuf, const GridSync &g, unsigned &epoch,
+SEED_DEV bool seed_pre_dots(const SeedBufs<T> &b, const T *f, LocalSeed &L, const GridSync &g, unsigned &epoch,
                             double *bpart, double (*sred)[32], double *s_vals) {
   double acc[32];
 #pragma unroll
@@ -242,40 +277,35 @@ SEED_DEV bool seed_pre_dots(const SeedBufs<T> &b, const T *f, double2 *gbuf, con
   for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT)
     add_fr0<T>(b, e, f[e], acc);
   write_row32(acc, bpart, sred);
-  return grid_reduce_sync(g, epoch, [&]() {
-    reduce_rows32(bpart, gridDim.x, s_vals, sred);
-    store_g<T>(b, s_vals, __ldcg(&b.st->inv_beta), gbuf);
-  });
+  if (!grid_sync(g, epoch)) return false;
+  reduce_rows32(bpart, gridDim.x, s_vals, sred);
+  local_g(b.nrhs, s_vals, L.st.inv_beta, L);
+  __syncthreads();
+  return true;
 }
 
-// reduce alpha_i from parts[k * stride], k < nparts (written by the caller, in
-// an order that does not depend on which block ran which tile) and form the
+// barrier, then in every block: alpha_i from parts[k * stride], k < nparts (a
+// fixed order that does not depend on which block ran which tile), and the
 // step's scalars
 template <class T>
-SEED_DEV bool seed_alpha_barrier(const SeedBufs<T> &b, const double *parts, int nparts, int stride,
-                                 const double2 *gbuf, int i, const GridSync &g, unsigned &epoch, double *s_red,
-                                 double2 *s_sums) {
-  return grid_reduce_sync(g, epoch, [&]() {
-    for (int j = 1 + (int)threadIdx.x; j < b.nrhs; j += PT) s_sums[j] = __ldcg(gbuf + j);
-    if (threadIdx.x < 32) {
-      const double a = warp_sum_partials(parts, nparts, stride, 0);
-      __syncwarp();
-      if (threadIdx.x == 0) s_red[0] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) seed_step_scalars(b, i, s_red[0], s_sums);
-  });
+SEED_DEV bool seed_alpha_step(const SeedBufs<T> &bl, const double *parts, int nparts, int stride, int i,
+                              LocalSeed &L, const GridSync &g, unsigned &epoch) {
+  if (!grid_sync(g, epoch)) return false;
+  if (threadIdx.x < 32) {
+    const double a = warp_sum_partials(parts, nparts, stride, 0);
+    if (threadIdx.x == 0) seed_step_scalars<T, false>(bl, i, a, L.g);
+  }
+  __syncthreads();
+  return true;
 }
 
-// phase 3 and the step-9 barrier
+// phase 3, the barrier, and step 9 in every block
 template <class T>
-SEED_DEV bool seed_update_phase(const SeedBufs<T> &b, T *f, const T *vi, int i, double2 *gbuf, const GridSync &g,
-                                unsigned &epoch, double *bpart, double (*sred)[32], double *s_vals, double2 *s_eta) {
-  SeedState *st = b.st;
-  const double a = vload(&st->alpha), zeta = vload(&st->zeta), inv_d = 1.0 / vload(&st->delta);
-  const double bp = (i > 1) ? vload(&st->beta_prev) : 0.0;
-  for (int j = threadIdx.x; j < b.nrhs; j += PT) s_eta[j] = __ldcg(b.eta + j);
-  __syncthreads();
+SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i, LocalSeed &L,
+                               const GridSync &g, unsigned &epoch, double *bpart, double (*sred)[32],
+                               double *s_vals) {
+  const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+  const double bp = (i > 1) ? L.st.beta_prev : 0.0;
   T *const X = reinterpret_cast<T *>(b.call->X);
   const int64_t ldx = b.call->ldx;
   const int nr = b.nrhs;
@@ -296,7 +326,7 @@ SEED_DEV bool seed_update_phase(const SeedBufs<T> &b, T *f, const T *vi, int i, 
     xv[0] = Sc<T>::axpy(zeta, we, xv[0]);
 #pragma unroll
     for (int j = 1; j < kPersistMaxRhs; ++j)
-      if (j < nr) xv[j] = Sc<T>::caxpy(s_eta[j], we, xv[j]);
+      if (j < nr) xv[j] = Sc<T>::caxpy(L.eta[j], we, xv[j]);
 #pragma unroll
     for (int j = 0; j < kPersistMaxRhs; ++j)
       if (j < nr) X[j * ldx + e] = xv[j];
@@ -304,20 +334,20 @@ SEED_DEV bool seed_update_phase(const SeedBufs<T> &b, T *f, const T *vi, int i, 
     add_fr0<T>(b, e, fe, acc);
   }
   write_row32(acc, bpart, sred);
-  return grid_reduce_sync(g, epoch, [&]() {
-    reduce_rows32(bpart, gridDim.x, s_vals, sred);
-    if (threadIdx.x == 0) seed_finish(b, s_vals[0]);
-    __syncthreads();
-    if (vload(&st->active)) store_g<T>(b, s_vals, vload(&st->inv_beta), gbuf);
-  });
+  if (!grid_sync(g, epoch)) return false;
+  reduce_rows32(bpart, gridDim.x, s_vals, sred);
+  if (threadIdx.x == 0) seed_finish<T, false>(bl, s_vals[0]);
+  __syncthreads();
+  if (L.st.active) local_g(b.nrhs, s_vals, L.st.inv_beta, L);
+  __syncthreads();
+  return true;
 }
 
 // On leaving at a reorthogonalization step: v_i = f / beta_{i-1} into V and vcur.
 template <class T>
-SEED_DEV void seed_leave(const SeedBufs<T> &b, const T *f, int i_stop) {
-  SeedState *st = b.st;
-  if (!vload(&st->active) || vload(&st->i) != i_stop) return;
-  const double inv_b = vload(&st->inv_beta);
+SEED_DEV void seed_leave(const SeedBufs<T> &b, const LocalSeed &L, const T *f, int i_stop) {
+  if (!L.st.active || L.st.i != i_stop) return;
+  const double inv_b = L.st.inv_beta;
   T *vi = b.V + (int64_t)(i_stop - 1) * b.ldv;
   for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
     const T fe = __ldcg(f + e);
@@ -329,27 +359,26 @@ SEED_DEV void seed_leave(const SeedBufs<T> &b, const T *f, int i_stop) {
 }
 
 __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, WilsonOp op, double2 *tbuf,
-                                                         double2 *gbuf, GridSync g, double *bpart, double *tpart,
-                                                         int i_stop) {
+                                                         GridSync g, double *bpart, double *tpart, int i_stop) {
   __shared__ double sacc[4][24][kWilsonSites + 1];
   __shared__ double sred[PT / 32][32];
   __shared__ double s_vals[32];
   __shared__ double s_red[PT / 32];
-  __shared__ double2 s_sums[kPersistMaxRhs];
-  __shared__ double2 s_eta[kPersistMaxRhs];
-  SeedState *st = b.st;
+  __shared__ LocalSeed L;
   const int64_t sites = op.sites;
   const int tiles = (int)((sites + kWilsonSites - 1) / kWilsonSites);
   const double kappa = op.kappa;
   unsigned epoch = 0;
+  local_load(b, L);
+  const SeedBufs<double2> bl = local_bufs(b, L);
   Owners own;
   if (!register_owner(g, epoch, own)) return;
-  if (vload(&st->active) && vload(&st->i) < i_stop)
-    if (!seed_pre_dots<double2>(b, b.f, gbuf, g, epoch, bpart, sred, s_vals)) return;
+  if (L.st.active && L.st.i < i_stop)
+    if (!seed_pre_dots<double2>(b, b.f, L, g, epoch, bpart, sred, s_vals)) return;
   for (;;) {
-    const int i = vload(&st->i);
-    if (!vload(&st->active) || i >= i_stop) break;
-    const double inv_b = vload(&st->inv_beta);
+    const int i = L.st.i;
+    if (!L.st.active || i >= i_stop) break;
+    const double inv_b = L.st.inv_beta;
     double2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
     if (own.rank >= 0) {
       for (int tile = own.rank; tile < tiles; tile += own.count) {
@@ -373,7 +402,7 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
     }
     if (!grid_sync(g, epoch)) return;
 
-    const double bp = (i > 1) ? vload(&st->beta_prev) : 0.0;
+    const double bp = (i > 1) ? L.st.beta_prev : 0.0;
     const double2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
     if (own.rank >= 0) {
       for (int tile = own.rank; tile < tiles; tile += own.count) {
@@ -400,32 +429,33 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
         if (threadIdx.x == 0) tpart[tile] = vv[0];   // per tile: the sum order is fixed
       }
     }
-    if (!seed_alpha_barrier<double2>(b, tpart, tiles, 1, gbuf, i, g, epoch, s_red, s_sums)) return;
-    if (!vload(&st->active)) break;   // delta_i <= 0
-    if (!seed_update_phase<double2>(b, b.f, vi, i, gbuf, g, epoch, bpart, sred, s_vals, s_eta)) return;
+    if (!seed_alpha_step<double2>(bl, tpart, tiles, 1, i, L, g, epoch)) return;
+    if (!L.st.active) break;   // delta_i <= 0
+    if (!seed_update_step<double2>(b, bl, b.f, vi, i, L, g, epoch, bpart, sred, s_vals)) return;
   }
-  seed_leave<double2>(b, b.f, i_stop);
+  seed_leave<double2>(b, L, b.f, i_stop);
+  local_store(b, L);
 }
 
 // real CSR operator: the apply reads f_cur (two buffers alternate, since a row
 // reads other rows' entries while writing its own)
-__global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp op, double *f2, double2 *gbuf,
-                                                      GridSync g, double *bpart, int i_stop) {
+__global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp op, double *f2, GridSync g,
+                                                      double *bpart, int i_stop) {
   __shared__ double sred[PT / 32][32];
   __shared__ double s_vals[32];
   __shared__ double s_red[PT / 32];
-  __shared__ double2 s_sums[kPersistMaxRhs];
-  __shared__ double2 s_eta[kPersistMaxRhs];
-  SeedState *st = b.st;
+  __shared__ LocalSeed L;
   unsigned epoch = 0;
   int par = 0;
-  if (vload(&st->active) && vload(&st->i) < i_stop)
-    if (!seed_pre_dots<double>(b, b.f, gbuf, g, epoch, bpart, sred, s_vals)) return;
+  local_load(b, L);
+  const SeedBufs<double> bl = local_bufs(b, L);
+  if (L.st.active && L.st.i < i_stop)
+    if (!seed_pre_dots<double>(b, b.f, L, g, epoch, bpart, sred, s_vals)) return;
   for (;;) {
-    const int i = vload(&st->i);
-    if (!vload(&st->active) || i >= i_stop) break;
-    const double inv_b = vload(&st->inv_beta);
-    const double bp = (i > 1) ? vload(&st->beta_prev) : 0.0;
+    const int i = L.st.i;
+    if (!L.st.active || i >= i_stop) break;
+    const double inv_b = L.st.inv_beta;
+    const double bp = (i > 1) ? L.st.beta_prev : 0.0;
     double *fc = par ? f2 : b.f, *fn = par ? b.f : f2;
     double *vi = b.V + (int64_t)(i - 1) * b.ldv;
     const double *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
@@ -441,17 +471,21 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp o
       fn[r] = u;
       apart = fma(v, u, apart);
     }
+    // alpha partials after the update rows (every block reads them after the
+    // barrier, while a faster block may already be writing its update row)
+    double *apartials = bpart + (int64_t)gridDim.x * 32;
     {
       double vv[1] = {apart};
       block_sum<1, PT>(vv, s_red);
-      if (threadIdx.x == 0) bpart[(int64_t)blockIdx.x * 32] = vv[0];   // rows follow blockIdx: fixed order
+      if (threadIdx.x == 0) apartials[blockIdx.x] = vv[0];   // by blockIdx: fixed order
     }
-    if (!seed_alpha_barrier<double>(b, bpart, gridDim.x, 32, gbuf, i, g, epoch, s_red, s_sums)) return;
-    if (!vload(&st->active)) break;
-    if (!seed_update_phase<double>(b, fn, vi, i, gbuf, g, epoch, bpart, sred, s_vals, s_eta)) return;
+    if (!seed_alpha_step<double>(bl, apartials, gridDim.x, 1, i, L, g, epoch)) return;
+    if (!L.st.active) break;
+    if (!seed_update_step<double>(b, bl, fn, vi, i, L, g, epoch, bpart, sred, s_vals)) return;
     par ^= 1;
   }
-  seed_leave<double>(b, par ? f2 : b.f, i_stop);
+  seed_leave<double>(b, L, par ? f2 : b.f, i_stop);
+  local_store(b, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -736,18 +770,18 @@ int persistent_grid(int kind, int sm_count) {
   return b * sm_count;
 }
 
-cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, double2 *gbuf,
-                                   GridSync g, double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s) {
+cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, GridSync g,
+                                   double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s) {
   SeedBufs<double2> bb = b;
   WilsonOp o = op;
-  void *args[] = {&bb, &o, &tbuf, &gbuf, &g, &bpart, &tpart, &i_stop};
+  void *args[] = {&bb, &o, &tbuf, &g, &bpart, &tpart, &i_stop};
   return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson, dim3(grid), dim3(PT), args, 0, s);
 }
-cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, double2 *gbuf, GridSync g,
-                                double *bpart, int i_stop, int grid, cudaStream_t s) {
+cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g, double *bpart,
+                                int i_stop, int grid, cudaStream_t s) {
   SeedBufs<double> bb = b;
   CsrOp o = op;
-  void *args[] = {&bb, &o, &f2, &gbuf, &g, &bpart, &i_stop};
+  void *args[] = {&bb, &o, &f2, &g, &bpart, &i_stop};
   return cudaLaunchCooperativeKernel((const void *)k_seed_run_csr, dim3(grid), dim3(PT), args, 0, s);
 }
 cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,

@@ -1,10 +1,12 @@
 // seed_device.cuh -- the scalar part of the Sec. 3 recurrence, shared by the
 // step-by-step kernels (krylov.cu) and the persistent kernels (persistent.cu).
-// Both run in thread 0 of the one block that holds the reduced sums.  In the
-// persistent kernels that block changes from step to step (it is whichever
-// block reaches the barrier last, on any SM), so state is read with L2 loads
-// (never from a stale L1 line written by another SM); all loads are issued
-// before their values are used, so their L2 round trips overlap.
+// It runs in thread 0 of a block that holds the reduced sums.  G = true: the
+// state (SeedState, eta) is in global memory and the block is whichever block
+// finished a reduction last, on any SM, so state is read with L2 loads (never
+// from a stale L1 line written by another SM), all issued before their values
+// are used so that their round trips overlap.  G = false: the state is the
+// block's own shared-memory copy (the persistent kernels keep one per block).
+// History arrays that are NULL are not written.
 #pragma once
 #include <math.h>
 
@@ -13,17 +15,22 @@
 
 namespace seedk {
 
+template <bool G, class P> SEED_DEV P sld(const P *p) {
+  if constexpr (G) return __ldcg(p);
+  else return *p;
+}
+
 // Steps 3/6 (delta_i, gamma_{i-1}, zeta_i) and 4/7 (eta^j) from alpha_i and
 // g^j = v_i^H r_0^j (sums[j], j = 1..nrhs-1); beta_{i-1} is st->beta_prev.
-template <class T>
+template <class T, bool G = true>
 SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const double2 *sums) {
   SeedState *st = b.st;
-  const double bp = __ldcg(&st->beta_prev), dprev = __ldcg(&st->delta), zprev = __ldcg(&st->zeta),
-               beta0 = __ldcg(&st->beta0);
+  const double bp = sld<G>(&st->beta_prev), dprev = sld<G>(&st->delta), zprev = sld<G>(&st->zeta),
+               beta0 = sld<G>(&st->beta0);
   const int nr = b.nrhs;
   double2 e[kMaxRhs];
 #pragma unroll 16
-  for (int j = 1; j < nr; ++j) e[j] = __ldcg(b.eta + j);
+  for (int j = 1; j < nr; ++j) e[j] = sld<G>(b.eta + j);
   double gam, del, zet;
   if (i == 1) {           // step 3: delta_1 = alpha_1, zeta_1 = beta_0
     gam = 0.0;
@@ -43,8 +50,8 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
   st->gamma = gam;
   st->delta = del;
   st->zeta = zet;
-  b.alpha_hist[i] = a;
-  b.delta_hist[i] = del;
+  if (b.alpha_hist) b.alpha_hist[i] = a;
+  if (b.delta_hist) b.delta_hist[i] = del;
   if (!(del > 0.0) || !isfinite(del)) {
     st->active = 0;
     st->stop_reason = STOP_NOTSPD;
@@ -52,17 +59,17 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
 }
 
 // Sec. 3 step 9: beta_i = ||f||, residual estimate and the stopping test.
-template <class T>
+template <class T, bool G = true>
 SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
   SeedState *st = b.st;
-  const int i = __ldcg(&st->i);
-  const double alpha = __ldcg(&st->alpha), bp = __ldcg(&st->beta_prev), tnorm = __ldcg(&st->tnorm),
-               zeta = __ldcg(&st->zeta), delta = __ldcg(&st->delta), tol_abs = __ldcg(&st->tol_abs),
-               brel = __ldcg(&st->breakdown_rel);
-  int converged_at = __ldcg(&st->converged_at), stop_at = __ldcg(&st->stop_at);
-  const int extra = __ldcg(&st->extra_iters), m_max = __ldcg(&st->m_max);
+  const int i = sld<G>(&st->i);
+  const double alpha = sld<G>(&st->alpha), bp = sld<G>(&st->beta_prev), tnorm = sld<G>(&st->tnorm),
+               zeta = sld<G>(&st->zeta), delta = sld<G>(&st->delta), tol_abs = sld<G>(&st->tol_abs),
+               brel = sld<G>(&st->breakdown_rel);
+  int converged_at = sld<G>(&st->converged_at), stop_at = sld<G>(&st->stop_at);
+  const int extra = sld<G>(&st->extra_iters), m_max = sld<G>(&st->m_max);
   const double beta = sqrt(sumsq);
-  b.beta_hist[i] = beta;
+  if (b.beta_hist) b.beta_hist[i] = beta;
   const double row = fabs(alpha) + (i > 1 ? bp : 0.0) + beta;
   const double tn = row > tnorm ? row : tnorm;
   const double rho = beta * fabs(zeta) / delta;

@@ -244,12 +244,11 @@ void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, c
 constexpr int kPersistMaxRhs = 16;
 constexpr int kPersistMaxCols = 32;
 int persistent_grid(int kind, int sm_count);
-// gbuf: [kPersistMaxRhs] device scratch for g^j of the next step.
 // tpart: one double per 32-site tile
-cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, double2 *gbuf,
-                                   GridSync g, double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
-cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, double2 *gbuf, GridSync g,
-                                double *bpart, int i_stop, int grid, cudaStream_t s);
+cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, GridSync g,
+                                   double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
+cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g, double *bpart,
+                                int i_stop, int grid, cudaStream_t s);
 cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,
                                  double2 *tbuf, int64_t ld, const CgCols &c, GridSync g, double *bpart, int grid,
                                  cudaStream_t s);
