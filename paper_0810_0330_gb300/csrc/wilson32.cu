@@ -53,13 +53,15 @@ SEED_DEV void load_spinor_tiled(const float2 *__restrict__ in, int64_t q, float2
 template <int MU, int S, bool VEC, bool TILED>
 SEED_DEV void hops32(const float2 *__restrict__ in, int32_t nf, int32_t nb, const float2 (&uf)[9],
                      const float2 (&ub)[9], unsigned negf, unsigned negb, float2 (&acc)[12]) {
-  float2 ps[12];
-  if constexpr (TILED) load_spinor_tiled(in, nf, ps);
-  else load_spinor<VEC>(in + 12 * (int64_t)nf, ps);
-  hop_r<MU, S, true, true>(ps, uf, negf, acc);
-  if constexpr (TILED) load_spinor_tiled(in, nb, ps);
-  else load_spinor<VEC>(in + 12 * (int64_t)nb, ps);
-  hop_r<MU, -S, false, false>(ps, ub, negb, acc);
+  float2 pf[12], pb[12];
+  if constexpr (TILED) {
+    load_spinor_tiled(in, nf, pf);
+    load_spinor_tiled(in, nb, pb);
+  } else {
+    load_spinor<VEC>(in + 12 * (int64_t)nf, pf);
+    load_spinor<VEC>(in + 12 * (int64_t)nb, pb);
+  }
+  hop_pair_r<MU, S>(pf, uf, negf, pb, ub, negb, acc);
 }
 
 template <int S, bool VEC, bool TILED>
