@@ -299,7 +299,27 @@ SEED_DEV bool seed_alpha_step(const SeedBufs<T> &bl, const double *parts, int np
   return true;
 }
 
-// phase 3, the barrier, and step 9 in every block
+// The update partials (one 32-value row per block) reach every block in two
+// levels: blocks 0..nseg-1 each sum a segment of 16 rows in order, then after
+// a second barrier every block sums the nseg segment rows in order (instead
+// of every block reading every row: 304 x 256 B from L2 per block).
+constexpr int kRowSeg = 16;
+SEED_DEV double *seg_rows(double *bpart) { return bpart + (int64_t)gridDim.x * 40; }
+SEED_DEV bool reduce_rows_2level(double *bpart, const GridSync &g, unsigned &epoch, double *s_vals,
+                                 double (*sred)[32]) {
+  const int nseg = (gridDim.x + kRowSeg - 1) / kRowSeg;
+  double *seg = seg_rows(bpart);
+  if ((int)blockIdx.x < nseg) {
+    const int r0 = blockIdx.x * kRowSeg, nr = min(kRowSeg, (int)gridDim.x - r0);
+    reduce_rows32(bpart + (int64_t)r0 * 32, nr, s_vals, sred);
+    if (threadIdx.x < 32) seg[(int64_t)blockIdx.x * 32 + threadIdx.x] = s_vals[threadIdx.x];
+  }
+  if (!grid_sync(g, epoch)) return false;
+  reduce_rows32(seg, nseg, s_vals, sred);
+  return true;
+}
+
+// phase 3, the barriers, and step 9 in every block
 template <class T>
 SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i, LocalSeed &L,
                                const GridSync &g, unsigned &epoch, double *bpart, double (*sred)[32],
@@ -335,7 +355,7 @@ SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f
   }
   write_row32(acc, bpart, sred);
   if (!grid_sync(g, epoch)) return false;
-  reduce_rows32(bpart, gridDim.x, s_vals, sred);
+  if (!reduce_rows_2level(bpart, g, epoch, s_vals, sred)) return false;
   if (threadIdx.x == 0) seed_finish<T, false>(bl, s_vals[0]);
   __syncthreads();
   if (L.st.active) local_g(b.nrhs, s_vals, L.st.inv_beta, L);
