@@ -88,7 +88,8 @@ struct seed_ctx {
 
   // persistent kernels
   int sm_count = 0;
-  int pgrid = 0;                       // blocks of a persistent launch (0: not available)
+  int pgrid = 0;                       // blocks of a persistent seed launch (0: not available)
+  int pgrid_cg = 0;                    // blocks of a persistent CG launch
   unsigned *gsync = nullptr;           // GridSync: count, release, error
   int32_t *h_gerr = nullptr;           // pinned copy of the error flag
   void *f2 = nullptr;                  // second Lanczos-vector buffer (CSR persistent run)
@@ -231,7 +232,8 @@ seed_status alloc_common(seed_ctx *ctx) {
   CU(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
   int coop = 0;
   CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
-  ctx->pgrid = coop ? persistent_grid(ctx->kind, ctx->sm_count) : 0;
+  ctx->pgrid = coop ? persistent_grid(ctx->kind, ctx->sm_count, false) : 0;
+  ctx->pgrid_cg = coop ? persistent_grid(ctx->kind, ctx->sm_count, true) : 0;
   return SEED_OK;
 }
 
@@ -668,7 +670,7 @@ seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx,
   ctx->stats.kernel_launches += kern + 1;
   ctx->stats.mvps += nc;
 
-  const bool persist = ctx->allow_persistent_cg && ctx->pgrid > 0 && nc <= kPersistMaxCols;
+  const bool persist = ctx->allow_persistent_cg && ctx->pgrid_cg > 0 && nc <= kPersistMaxCols;
   const GridSync g = grid_sync_bufs(ctx);
   const int L = 16;
   for (int round = 0;; ++round) {
@@ -678,10 +680,10 @@ seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx,
       cudaError_t e;
       if constexpr (sizeof(T) == sizeof(double2))
         e = launch_cg_run_wilson(ctx->wil, ctx->call, (double2 *)ctx->R, (double2 *)ctx->P, (double2 *)ctx->Q,
-                                 (double2 *)ctx->T, ld, c, g, ctx->partials, ctx->pgrid, ctx->cs);
+                                 (double2 *)ctx->T, ld, c, g, ctx->partials, ctx->pgrid_cg, ctx->cs);
       else
         e = launch_cg_run_csr(ctx->csr, ctx->call, (double *)ctx->R, (double *)ctx->P, (double *)ctx->Q, ld, c, g,
-                              ctx->partials, ctx->pgrid, ctx->cs);
+                              ctx->partials, ctx->pgrid_cg, ctx->cs);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, SEED_ECUDA, std::string("persistent CG launch: ") + cudaGetErrorString(e));

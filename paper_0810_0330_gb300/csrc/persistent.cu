@@ -772,22 +772,24 @@ __global__ void __launch_bounds__(PT) k_cg_run_csr(CsrOp op, const CallArgs *cal
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-int persistent_grid(int kind, int sm_count) {
-  int per_sm = 0, per_sm2 = 0;
+// Up to 2 blocks per SM (3 for the seed runs, with the kernel bounded to fit,
+// measured no faster on the 8^4 workload); 0 when the occupancy query fails.
+int persistent_grid(int kind, int sm_count, bool cg) {
+  int per_sm = 0;
   cudaError_t e;
-  if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed_run_csr, PT, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed_run_wilson, PT, 0);
-  if (e == cudaSuccess) {
-    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_run_csr, PT, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_cg_run_wilson, PT, 0);
-  }
+  if (!cg) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kind == 0 ? (const void *)k_seed_run_csr
+                                                                               : (const void *)k_seed_run_wilson,
+                                                             PT, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kind == 0 ? (const void *)k_cg_run_csr
+                                                                           : (const void *)k_cg_run_wilson,
+                                                         PT, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  int b = per_sm < per_sm2 ? per_sm : per_sm2;
-  if (b > 2) b = 2;
-  return b * sm_count;
+  const int cap = 2;
+  if (per_sm > cap) per_sm = cap;
+  return per_sm * sm_count;
 }
 
 cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, GridSync g,

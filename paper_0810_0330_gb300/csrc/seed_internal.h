@@ -243,7 +243,7 @@ void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, c
 // barrier time-out through GridSync::error.  nrhs <= kPersistMaxRhs, nc <= 32.
 constexpr int kPersistMaxRhs = 16;
 constexpr int kPersistMaxCols = 32;
-int persistent_grid(int kind, int sm_count);
+int persistent_grid(int kind, int sm_count, bool cg);
 // tpart: one double per 32-site tile
 cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, GridSync g,
                                    double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
