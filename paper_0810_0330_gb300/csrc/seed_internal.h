@@ -132,7 +132,6 @@ using WilsonOp32 = WilsonOpT<float2>;
 void launch_wilson_neighbors(const int32_t dims[4], int32_t *nbr, cudaStream_t s);
 void launch_wilson_dslash(const WilsonOp &op, int sign, const double2 *in, int64_t ldi, double2 *out,
                           int64_t ldo, int ncols, const int32_t *col_active, cudaStream_t s);
-int wilson_kernels_per_apply();
 // FP32 copy (links in structure-of-arrays order, see wilson.cu).  tiled: the
 // spinor vectors use the mixed path's 32-site tiled layout (Layout32), else the
 // caller's site-major layout.

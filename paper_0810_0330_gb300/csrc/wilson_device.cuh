@@ -152,17 +152,6 @@ SEED_DEV void hop_pair_r(const C (&pf)[12], const C (&uf)[9], typename CxBits<C>
   }
 }
 
-// The same hop with psi and the link read from memory (link as 9 consecutive elements).
-template <int MU, int S, bool FWD, bool FIRST, bool NC = true, class C>
-SEED_DEV void hop(const C *__restrict__ psi, const C *__restrict__ U, typename CxBits<C>::U neg, C (&acc)[12]) {
-  C ps[12], u[9];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) ps[k] = ldv<NC>(psi + k);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) u[k] = __ldg(U + k);
-  hop_r<MU, S, FWD, FIRST>(ps, u, neg, acc);
-}
-
 template <int MU, int S, bool NC = true, class C>
 SEED_DEV void site_mu(const WilsonOpT<C> &op, const C *__restrict__ in, int64_t s, C (&acc)[12]) {
   const int32_t nf = __ldg(op.nbr + 8 * s + 2 * MU);
