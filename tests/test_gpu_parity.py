@@ -405,3 +405,39 @@ def test_long_vectors_two_level_reductions(seedlib, orc, precision):
         assert rr <= 1.5 * tol, (j, rr)
     for j, r in enumerate(ref["rest"], start=1):
         assert abs(info2[j]["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (j, info2[j]["iters"], r["iters"])
+
+
+@pytest.mark.parametrize("nrhs", [17, 64])
+def test_many_rhs_multichunk_dots(seedlib, orc, nrhs):
+    """nrhs = 17 (just past the persistent kernels' 16) and 64 (the maximum):
+    the seed dot products run in chunks of 15 systems (5 chunks at 64).  20x19
+    Laplacian (distinct eigenvalues), Gaussian right-hand sides, full
+    reorthogonalization: the seed's steps equal and x^1 within 1e-9; every
+    seeded x^j within max(1e-9, 10 x the oracle's one-ulp sensitivity); every
+    CG count within 5 % and every true residual within 1.5 tol."""
+    rp, ci, v = I.laplacian_2d_csr(20, 19)
+    n = 380
+    B = I.gaussian_rhs(n, nrhs, seed=11)
+    prm = dict(m_max=400, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8)
+    ctx = csr_ctx(seedlib, rp, ci, v, **prm)
+    info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
+    op = orc.Operator.csr(rp, ci, v)
+    ref = orc.seed_solve_all(op, B, m_max=400, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8)
+    assert info1[0]["iters"] == ref["seed"]["iters"]
+    assert relerr(X[:, 0].real, ref["seed"]["X"][:, 0].real) < REL_X
+    sens = seeded_only_sensitivity(orc, op, B, m_max=400, reorth_freq=1, tol=1e-12)
+    assert relerr(Xs[:, 1:].real, ref["X_seeded"][:, 1:].real) < max(REL_X, 10 * sens)
+    for j, r in enumerate(ref["rest"], start=1):
+        assert abs(info2[j]["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (j, info2[j]["iters"], r["iters"])
+        rr = np.linalg.norm(B[:, j] - op.apply(X[:, j].real).real) / np.linalg.norm(B[:, j])
+        assert rr <= 1.5e-8, (j, rr)
+
+
+def test_too_many_rhs_rejected(seedlib):
+    rp, ci, v = I.laplacian_2d_csr(8, 8)
+    ctx = csr_ctx(seedlib, rp, ci, v, m_max=10)
+    B = dev_cols(I.gaussian_rhs(64, 65, seed=1))
+    X = dev_cols(np.zeros((64, 65)))
+    with pytest.raises(seedlib.SeedError) as e:
+        seedlib.seed_solve_first(ctx, B, X)
+    assert e.value.status == seedlib.SEED_EINVAL
