@@ -19,30 +19,6 @@ namespace seedk {
 constexpr int kAdjThreads = 128;   // 4 warps (one per mu) x 32 sites, as the operator kernel
 constexpr int kColTicketAdj = 16;  // tickets[16 + c]: per-column kernels
 
-template <int S>
-SEED_DEV void hop_sum_tile(const WilsonOp &op, const double2 *__restrict__ in, int64_t s0,
-                           double (*sacc)[24][kWilsonSites + 1]) {
-  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
-  const int64_t s = s0 + lane;
-  double2 acc[12];
-  if (s < op.sites) {
-    switch (mu) {
-      case 0: site_mu<0, S>(op, in, s, acc); break;
-      case 1: site_mu<1, S>(op, in, s, acc); break;
-      case 2: site_mu<2, S>(op, in, s, acc); break;
-      default: site_mu<3, S>(op, in, s, acc); break;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = c2(0.0, 0.0);
-  }
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    sacc[mu][2 * k][lane] = acc[k].x;
-    sacc[mu][2 * k + 1][lane] = acc[k].y;
-  }
-}
-
 // grid (blocks, ncols); block b of column j handles site tiles b, b + gridDim.x, ...
 __global__ void __launch_bounds__(kAdjThreads) k_dkappa_inner(WilsonOp op, const double2 *__restrict__ L, int64_t ldl,
                                                               const double2 *__restrict__ X, int64_t ldx,
@@ -60,22 +36,20 @@ __global__ void __launch_bounds__(kAdjThreads) k_dkappa_inner(WilsonOp op, const
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t s0 = tile * kWilsonSites;
     double hl[kPer];
-    hop_sum_tile<+1>(op, L, s0, sacc);
-    __syncthreads();
+    dslash_tile<+1>(op, L, s0, sacc);
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int o = threadIdx.x + q * kAdjThreads, sl = o / 24, c = o - 24 * (o / 24);
-      hl[q] = ((sacc[0][c][sl] + sacc[1][c][sl]) + sacc[2][c][sl]) + sacc[3][c][sl];
+      hl[q] = tile_hop_sum(sacc, c, sl);
     }
     __syncthreads();
-    hop_sum_tile<+1>(op, X, s0, sacc);
-    __syncthreads();
+    dslash_tile<+1>(op, X, s0, sacc);
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int o = threadIdx.x + q * kAdjThreads, sl = o / 24, c = o - 24 * (o / 24);
       const int64_t ss = s0 + sl;
       if (ss < op.sites) {
-        const double hx = ((sacc[0][c][sl] + sacc[1][c][sl]) + sacc[2][c][sl]) + sacc[3][c][sl];
+        const double hx = tile_hop_sum(sacc, c, sl);
         const double l = __ldg(Ld + 24 * ss + c), x = __ldg(Xd + 24 * ss + c);
         const double dl = fma(-op.kappa, hl[q], l), dx = fma(-op.kappa, hx, x);
         val = fma(hl[q], dx, val);

@@ -116,6 +116,12 @@ struct seed_ctx {
   void *msX = nullptr, *msR = nullptr; // multiple seeding: solutions and tracked residuals
   int ms_cap = 0;
 
+  // blocked seeding of systems 2..p (seedblock.cu): w_i of the current block,
+  // gamma_{i-1} per step, and the flush workspace
+  void *Wb = nullptr;
+  double *gamma_hist = nullptr;
+  BlockBufs blk{};
+
   std::map<std::string, GraphEntry> graphs;
   std::string err;
   seed_stats stats{};
@@ -204,6 +210,7 @@ seed_status alloc_common(seed_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->alpha_hist, sizeof(double) * (m + 2)));
   TRY(dalloc(ctx, &ctx->beta_hist, sizeof(double) * (m + 2)));
   TRY(dalloc(ctx, &ctx->delta_hist, sizeof(double) * (m + 2)));
+  TRY(dalloc(ctx, &ctx->gamma_hist, sizeof(double) * (m + 2)));
   TRY(dalloc(ctx, &ctx->eta, sizeof(double2) * kMaxRhs));
   TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs)));
   TRY(dalloc(ctx, &ctx->colnorm, sizeof(double) * kMaxRhs));
@@ -303,6 +310,25 @@ int apply_A32(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, i
 
 template <class T> constexpr bool kLow = std::is_same_v<T, float> || std::is_same_v<T, float2>;
 
+// Blocked seeding (Sec. 3 steps 4 and 7 folded into x^2..x^p once per block of
+// steps, seedblock.cu) when there are seeded systems and blocks can be long:
+// without reorthogonalization or with reorthogonalization every 8 or more steps
+// (a block ends at every reorthogonalizing step).
+bool blocked_seeding(const seed_ctx *ctx, int nrhs) {
+  const int f = ctx->prm.reorth_freq;
+  return nrhs >= 2 && (f == 0 || f >= 8);
+}
+
+seed_status ensure_block(seed_ctx *ctx) {
+  if (ctx->Wb) return SEED_OK;
+  ctx->blk = block_layout(ctx->nv);
+  TRY(dalloc(ctx, &ctx->Wb, (size_t)ctx->ldv * kSeedBlock * ctx->vsz));
+  TRY(dalloc(ctx, &ctx->blk.Hpart, sizeof(double2) * (size_t)ctx->blk.nchunk * kSeedBlock * (kMaxRhs - 1)));
+  TRY(dalloc(ctx, &ctx->blk.G, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
+  TRY(dalloc(ctx, &ctx->blk.Z, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
+  return SEED_OK;
+}
+
 // E: column 0 of the corrections (system 1); its spare column sits before it
 template <class T> T *E_cols(seed_ctx *ctx) { return (T *)ctx->E32 + ctx->ldv; }
 
@@ -326,6 +352,8 @@ SeedBufs<T> seed_bufs(seed_ctx *ctx, int nrhs) {
     b.call = ctx->call32;                    // x^j := FP32 corrections e^j
   }
   b.st = ctx->st;
+  b.Wb = (blocked_seeding(ctx, nrhs) && ctx->Wb) ? (T *)ctx->Wb : nullptr;
+  b.gamma_hist = ctx->gamma_hist;
   b.alpha_hist = ctx->alpha_hist;
   b.beta_hist = ctx->beta_hist;
   b.delta_hist = ctx->delta_hist;
@@ -362,6 +390,7 @@ int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
   launch_seed_update<T>(b, !reorth, ctx->cs);
   k += 2;
   if (reorth) {
+    k += launch_seed_flush<T>(b, ctx->blk, ctx->cs);   // step 8 rewrites v_i: fold the block first
     launch_reorth<T>(b, reorth_bufs<T>(ctx), ctx->prm.reorth_passes, ctx->cs);
     k += reorth_kernel_count<T>(ctx->prm.reorth_passes);
   }
@@ -379,6 +408,7 @@ seed_status launch_seed_run(seed_ctx *ctx, int nrhs, const std::vector<char> &pa
     cudaGraph_t graph;
     CU(cudaStreamBeginCapture(ctx->cs, cudaStreamCaptureModeThreadLocal));
     for (char c : pattern) g.kernels += issue_seed_step<T>(ctx, nrhs, c == 'R');
+    g.kernels += launch_seed_flush<T>(seed_bufs<T>(ctx, nrhs), ctx->blk, ctx->cs);   // runs end with a fold
     CU(cudaStreamEndCapture(ctx->cs, &graph));
     cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -463,8 +493,9 @@ seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
     }
     int i_stop = p.m_max + 1;
     if (p.reorth_freq > 0) i_stop = std::min(i_stop, (i / p.reorth_freq + 1) * p.reorth_freq);
-    CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
     SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
+    if (b.Wb) i_stop = std::min(i_stop, i + kSeedBlock);   // every run starts a block (blk0 = i)
+    CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
     cudaError_t e;
     if constexpr (sizeof(T) == sizeof(double2))
       e = launch_seed_run_wilson(b, ctx->wil, (double2 *)ctx->T, g, ctx->partials, ctx->tpart, i_stop, ctx->pgrid,
@@ -475,7 +506,7 @@ seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
       cudaGetLastError();
       return fail(ctx, SEED_ECUDA, std::string("persistent seed launch: ") + cudaGetErrorString(e));
     }
-    ctx->stats.kernel_launches += 1;
+    ctx->stats.kernel_launches += 1 + launch_seed_flush<T>(b, ctx->blk, ctx->cs);
   }
   return SEED_OK;
 }
@@ -486,6 +517,7 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   const int64_t n = ctx->n;
   const seed_params &p = ctx->prm;
   TRY(ensure_cols(ctx, std::max(nrhs, 1)));
+  if (blocked_seeding(ctx, nrhs)) TRY(ensure_block(ctx));
   ctx->basis_valid = false;
   ctx->seeded = false;
   CU(cudaEventRecord(ctx->t0, ctx->cs));
@@ -499,6 +531,8 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   s0.extra_iters = p.extra_iters;
   s0.converged_at = -1;
   s0.stop_at = -1;
+  s0.blk0 = 1;
+  s0.w_last = 0;
   CU(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->cs));
   CU(cudaMemsetAsync(ctx->eta, 0, sizeof(double2) * kMaxRhs, ctx->cs));
 
@@ -538,6 +572,7 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
 
   SeedState st;
   CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st.stop_reason == STOP_BLOCK) return fail(ctx, SEED_ECUDA, "internal: a seeding block overflowed");
   const int steps = st.i >= 1 ? st.i : 0;
   ctx->stats.mvps += (st.beta0 > 0.0) ? steps : 0;
   ctx->last_m = (st.beta0 > 0.0) ? steps : 0;
@@ -1113,6 +1148,7 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   const int64_t n = ctx->n, ld = ctx->ldv;
   const seed_params &p = ctx->prm;
   TRY(ensure_cols(ctx, std::max(nrhs, 1)));
+  if (blocked_seeding(ctx, nrhs)) TRY(ensure_block(ctx));
   ctx->basis_valid = false;
   ctx->seeded = false;
   CU(cudaEventRecord(ctx->t0, ctx->cs));
@@ -1126,6 +1162,8 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   s0.extra_iters = p.extra_iters;
   s0.converged_at = -1;
   s0.stop_at = -1;
+  s0.blk0 = 1;
+  s0.w_last = 0;
   CU(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->cs));
   CU(cudaMemsetAsync(ctx->eta, 0, sizeof(double2) * kMaxRhs, ctx->cs));
 
@@ -1159,6 +1197,7 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   CU(cudaGetLastError());
   SeedState st;
   CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st.stop_reason == STOP_BLOCK) return fail(ctx, SEED_ECUDA, "internal: a seeding block overflowed");
   const int steps = (st.beta0 > 0.0 && st.i >= 1) ? st.i : 0;
   ctx->stats.mvps += steps;
   ctx->last_m = steps;
@@ -1286,7 +1325,7 @@ void destroy(seed_ctx *ctx) {
                   ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
                   ctx->gsync, ctx->f2, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
                   ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots,
-                  ctx->msX, ctx->msR};
+                  ctx->msX, ctx->msR, ctx->Wb, ctx->gamma_hist, ctx->blk.Hpart, ctx->blk.G, ctx->blk.Z};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
   __shared__ double s_alpha;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = st->i;
-  const int nr = b.nrhs;
+  const int nr = b.Wb == nullptr ? b.nrhs : 1;   // blocked seeding: g^j at the flush
   const int nch = nr > 1 ? (nr - 1 + kDotsPerChunk - 1) / kDotsPerChunk : 1;
   const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
   const T *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
@@ -216,16 +216,32 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
 }
 
 // Steps 5 (f -= alpha_i v_i), 6 (w_i, x^1) and 7 (x^j), plus ||f||^2 when this
-// step has no reorthogonalization.
+// step has no reorthogonalization.  Blocked seeding (b.Wb set): w_i also goes
+// to column i - blk0 of Wb and x^2..x^p wait for the block's flush.
 template <class T, bool NORM>
 __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
   SeedState *st = b.st;
   if (!st->active) return;
   __shared__ typename Sc<T>::A2 s_eta[kMaxRhs];
   __shared__ double sm[NT / 32];
-  for (int j = threadIdx.x; j < b.nrhs; j += NT) s_eta[j] = Sc<T>::from2(b.eta[j]);
-  __syncthreads();
   const int i = st->i;
+  T *wcol = nullptr;
+  int nx = b.nrhs;   // columns of X updated here
+  if (b.Wb != nullptr) {
+    const int q = i - st->blk0;
+    if (q < 0 || q >= kSeedBlock) {   // the host flushes before a block can fill
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->active = 0;
+        st->stop_reason = STOP_BLOCK;
+      }
+      return;
+    }
+    wcol = b.Wb + (int64_t)q * b.ldv;
+    nx = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->w_last = i;   // read only by later kernels
+  }
+  for (int j = threadIdx.x; j < nx; j += NT) s_eta[j] = Sc<T>::from2(b.eta[j]);
+  __syncthreads();
   const double a = st->alpha, zeta = st->zeta, inv_d = 1.0 / st->delta, bp = st->beta_prev;
   const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
   const int64_t ldx = b.call->ldx;
@@ -237,18 +253,19 @@ __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
     b.f[e] = fe;
     const T we = (i > 1) ? Sc<T>::scale(inv_d, Sc<T>::axpy(-bp, b.w[e], ve)) : Sc<T>::scale(inv_d, ve);
     b.w[e] = we;
+    if (wcol != nullptr) wcol[e] = we;
     T *x = X + e;
     x[0] = Sc<T>::axpy(zeta, we, x[0]);
     // x^j += eta^j w_i, four columns at a time with the loads issued before the stores
     int j = 1;
-    for (; j + 3 < b.nrhs; j += 4) {
+    for (; j + 3 < nx; j += 4) {
       const T x0 = x[j * ldx], x1 = x[(j + 1) * ldx], x2 = x[(j + 2) * ldx], x3 = x[(j + 3) * ldx];
       x[j * ldx] = Sc<T>::caxpy2(s_eta[j], we, x0);
       x[(j + 1) * ldx] = Sc<T>::caxpy2(s_eta[j + 1], we, x1);
       x[(j + 2) * ldx] = Sc<T>::caxpy2(s_eta[j + 2], we, x2);
       x[(j + 3) * ldx] = Sc<T>::caxpy2(s_eta[j + 3], we, x3);
     }
-    for (; j < b.nrhs; ++j) x[j * ldx] = Sc<T>::caxpy2(s_eta[j], we, x[j * ldx]);
+    for (; j < nx; ++j) x[j * ldx] = Sc<T>::caxpy2(s_eta[j], we, x[j * ldx]);
     if (NORM) acc = Sc<T>::nrm2(fe, acc);
   }
   if (!NORM) return;
@@ -715,23 +732,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(int64_t n, const CallArgs *cal
   if (threadIdx.x == 0) part[blockIdx.x] = v[0];
   if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
   const double rr = sum_partials<NT>(part, gridDim.x, 1, 0, sm);
-  if (threadIdx.x == 0) {
-    const double rn = sqrt(rr), bn = c.bnorm[col];
-    c.iters[col] += 1;
-    c.mvps[col] += 1;
-    c.relres[col] = bn > 0.0 ? rn / bn : 0.0;
-    if (rn <= c.tol * bn) {
-      c.active[col] = 0;
-      c.reached[col] = 1;
-      c.needs_check[col] = 1;
-    } else if (c.iters[col] >= c.maxit) {
-      c.active[col] = 0;
-      c.needs_check[col] = 1;
-    } else {
-      c.beta[col] = rr / c.rho[col];
-      c.rho[col] = rr;
-    }
-  }
+  if (threadIdx.x == 0) cg_update_tail(c, col, rr);
 }
 
 // p = r + beta p (also used with beta = 0 after a restart: p = r)

@@ -228,7 +228,7 @@ SEED_DEV SeedBufs<T> local_bufs(const SeedBufs<T> &b, LocalSeed &L) {
   SeedBufs<T> l = b;
   l.st = &L.st;
   l.eta = L.eta;
-  if (blockIdx.x != 0) l.alpha_hist = l.beta_hist = l.delta_hist = nullptr;
+  if (blockIdx.x != 0) l.alpha_hist = l.beta_hist = l.delta_hist = l.gamma_hist = nullptr;
   return l;
 }
 
@@ -363,6 +363,44 @@ SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f
   return true;
 }
 
+// Phase 3 with blocked seeding (b.Wb set): f, w_i (also into column
+// i - blk0 of Wb), x^1 and ||f||^2 only -- x^2..x^p wait for the block's flush.
+// One value per block; after the barrier every block sums the gridDim.x
+// partials in block order (the same order in every block) and runs step 9.
+template <class T>
+SEED_DEV bool seed_update_step_blk(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i,
+                                   LocalSeed &L, const GridSync &g, unsigned &epoch, double *bpart, double *s_red) {
+  const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+  const double bp = (i > 1) ? L.st.beta_prev : 0.0;
+  T *const X = reinterpret_cast<T *>(b.call->X);
+  T *const wcol = b.Wb + (int64_t)(i - L.st.blk0) * b.ldv;
+  typename Sc<T>::A acc = 0;
+  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
+    const T v = __ldcg(vi + e), f0 = __ldcg(f + e), x0 = __ldcg(X + e);
+    const T wp = (i > 1) ? __ldcg(b.w + e) : Sc<T>::zero();
+    const T fe = Sc<T>::axpy(-a, v, f0);
+    const T we = (i > 1) ? Sc<T>::scale(inv_d, Sc<T>::axpy(-bp, wp, v)) : Sc<T>::scale(inv_d, v);
+    f[e] = fe;
+    b.w[e] = we;
+    wcol[e] = we;
+    X[e] = Sc<T>::axpy(zeta, we, x0);
+    acc = Sc<T>::nrm2(fe, acc);
+  }
+  double vv[1] = {(double)acc};
+  block_sum<1, PT>(vv, s_red);
+  if (threadIdx.x == 0) bpart[blockIdx.x] = vv[0];
+  if (!grid_sync(g, epoch)) return false;
+  if (threadIdx.x < 32) {
+    const double ss = warp_sum_partials(bpart, gridDim.x, 1, 0);
+    if (threadIdx.x == 0) {
+      L.st.w_last = i;
+      seed_finish<T, false>(bl, ss);
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // On leaving at a reorthogonalization step: v_i = f / beta_{i-1} into V and vcur.
 template <class T>
 SEED_DEV void seed_leave(const SeedBufs<T> &b, const LocalSeed &L, const T *f, int i_stop) {
@@ -393,11 +431,21 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
   const SeedBufs<double2> bl = local_bufs(b, L);
   Owners own;
   if (!register_owner(g, epoch, own)) return;
-  if (L.st.active && L.st.i < i_stop)
+  const bool blocked = b.Wb != nullptr;
+  if (L.st.active && L.st.i < i_stop && !blocked)
     if (!seed_pre_dots<double2>(b, b.f, L, g, epoch, bpart, sred, s_vals)) return;
   for (;;) {
     const int i = L.st.i;
     if (!L.st.active || i >= i_stop) break;
+    if (blocked && i - L.st.blk0 >= kSeedBlock) {   // the host caps runs below this
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        L.st.active = 0;
+        L.st.stop_reason = STOP_BLOCK;
+      }
+      __syncthreads();
+      break;
+    }
     const double inv_b = L.st.inv_beta;
     double2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
     if (own.rank >= 0) {
@@ -451,7 +499,11 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
     }
     if (!seed_alpha_step<double2>(bl, tpart, tiles, 1, i, L, g, epoch)) return;
     if (!L.st.active) break;   // delta_i <= 0
-    if (!seed_update_step<double2>(b, bl, b.f, vi, i, L, g, epoch, bpart, sred, s_vals)) return;
+    if (blocked) {
+      if (!seed_update_step_blk<double2>(b, bl, b.f, vi, i, L, g, epoch, bpart, s_red)) return;
+    } else if (!seed_update_step<double2>(b, bl, b.f, vi, i, L, g, epoch, bpart, sred, s_vals)) {
+      return;
+    }
   }
   seed_leave<double2>(b, L, b.f, i_stop);
   local_store(b, L);
@@ -469,11 +521,21 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp o
   int par = 0;
   local_load(b, L);
   const SeedBufs<double> bl = local_bufs(b, L);
-  if (L.st.active && L.st.i < i_stop)
+  const bool blocked = b.Wb != nullptr;
+  if (L.st.active && L.st.i < i_stop && !blocked)
     if (!seed_pre_dots<double>(b, b.f, L, g, epoch, bpart, sred, s_vals)) return;
   for (;;) {
     const int i = L.st.i;
     if (!L.st.active || i >= i_stop) break;
+    if (blocked && i - L.st.blk0 >= kSeedBlock) {   // the host caps runs below this
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        L.st.active = 0;
+        L.st.stop_reason = STOP_BLOCK;
+      }
+      __syncthreads();
+      break;
+    }
     const double inv_b = L.st.inv_beta;
     const double bp = (i > 1) ? L.st.beta_prev : 0.0;
     double *fc = par ? f2 : b.f, *fn = par ? b.f : f2;
@@ -501,7 +563,11 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp o
     }
     if (!seed_alpha_step<double>(bl, apartials, gridDim.x, 1, i, L, g, epoch)) return;
     if (!L.st.active) break;
-    if (!seed_update_step<double>(b, bl, fn, vi, i, L, g, epoch, bpart, sred, s_vals)) return;
+    if (blocked) {
+      if (!seed_update_step_blk<double>(b, bl, fn, vi, i, L, g, epoch, bpart, s_red)) return;
+    } else if (!seed_update_step<double>(b, bl, fn, vi, i, L, g, epoch, bpart, sred, s_vals)) {
+      return;
+    }
     par ^= 1;
   }
   seed_leave<double>(b, L, par ? f2 : b.f, i_stop);

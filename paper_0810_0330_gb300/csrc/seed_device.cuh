@@ -27,7 +27,7 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
   SeedState *st = b.st;
   const double bp = sld<G>(&st->beta_prev), dprev = sld<G>(&st->delta), zprev = sld<G>(&st->zeta),
                beta0 = sld<G>(&st->beta0);
-  const int nr = b.nrhs;
+  const int nr = b.Wb == nullptr ? b.nrhs : 1;
   double2 e[kMaxRhs];
 #pragma unroll 16
   for (int j = 1; j < nr; ++j) e[j] = sld<G>(b.eta + j);
@@ -41,10 +41,14 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
     del = a - gam * bp;
     zet = -gam * zprev;
   }
+  if (b.Wb == nullptr) {
 #pragma unroll 16
-  for (int j = 1; j < nr; ++j) {   // steps 4 / 7
-    const double2 g = sums[j];
-    b.eta[j] = (i == 1) ? g : c2(g.x - gam * e[j].x, g.y - gam * e[j].y);
+    for (int j = 1; j < nr; ++j) {   // steps 4 / 7
+      const double2 g = sums[j];
+      b.eta[j] = (i == 1) ? g : c2(g.x - gam * e[j].x, g.y - gam * e[j].y);
+    }
+  } else if (b.gamma_hist) {         // blocked seeding: eta^j at the block's flush
+    b.gamma_hist[i] = gam;
   }
   st->alpha = a;
   st->gamma = gam;
@@ -93,6 +97,28 @@ SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
     st->beta_prev = beta;
     st->inv_beta = 1.0 / beta;
     st->i = i + 1;
+  }
+}
+
+// Lockstep CG, after x += alpha p, r -= alpha q and rr = ||r||^2 (thread 0 of
+// the block that reduced column col): count the iteration, stop the column
+// when ||r|| <= tol ||b|| (or at the iteration cap; the true residual is
+// checked afterwards), else beta = rr / rho and rho = rr.
+SEED_DEV void cg_update_tail(const CgCols &c, int col, double rr) {
+  const double rn = sqrt(rr), bn = c.bnorm[col];
+  c.iters[col] += 1;
+  c.mvps[col] += 1;
+  c.relres[col] = bn > 0.0 ? rn / bn : 0.0;
+  if (rn <= c.tol * bn) {
+    c.active[col] = 0;
+    c.reached[col] = 1;
+    c.needs_check[col] = 1;
+  } else if (c.iters[col] >= c.maxit) {
+    c.active[col] = 0;
+    c.needs_check[col] = 1;
+  } else {
+    c.beta[col] = rr / c.rho[col];
+    c.rho[col] = rr;
   }
 }
 

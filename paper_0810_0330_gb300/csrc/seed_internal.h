@@ -14,7 +14,8 @@ constexpr int kVecBlocksMax = 152 * 8;   // blocks of the single-vector kernels 
 constexpr int kPartials = 5 * kVecBlocksMax * 32 + 5 * ((kVecBlocksMax + 31) / 32) * 32 + 4096;
 
 // Stop reasons of the seed recurrence (SeedState::stop_reason)
-enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4, STOP_TIMEOUT = 5 };
+enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4, STOP_TIMEOUT = 5,
+       STOP_BLOCK = 6 /* internal: a step found its seeding block full (never expected) */ };
 
 // Device-resident scalars of the Sec. 3 recurrence (paper notation).
 struct SeedState {
@@ -41,7 +42,12 @@ struct SeedState {
   int32_t stop_at;
   int32_t m_max;
   int32_t extra_iters;
-  int32_t pad_;
+  // blocked seeding of systems 2..p (SeedBufs::Wb set): the current block
+  // starts at step blk0; w_last is the last step whose w_i is stored in Wb;
+  // blk_len is the length of the block a flush is folding into X
+  int32_t blk0;
+  int32_t w_last;
+  int32_t blk_len;
 };
 
 // Caller buffers of the current call, read by the kernels from device memory so
@@ -74,7 +80,26 @@ struct SeedBufs {
   double2 *eta;        // [kMaxRhs]
   double *partials;    // kPartials doubles
   unsigned *tickets;   // >= 4 counters, zero between launches
+  // Blocked seeding (Sec. 3 steps 4 and 7 deferred over a block of steps):
+  // NULL = the streaming form (g^j, eta^j and x^j every step).  Otherwise each
+  // step stores w_i in column i - blk0 of Wb and gamma_{i-1} in gamma_hist[i],
+  // and launch_seed_flush folds the block into x^2..x^p.
+  T *Wb;               // n x kSeedBlock, leading dimension ldv
+  double *gamma_hist;  // [m_max+2]
 };
+
+// Steps per block of the blocked seeding (columns of SeedBufs::Wb).
+constexpr int kSeedBlock = 128;
+
+// Workspace of the block flush (seedblock.cu).
+struct BlockBufs {
+  double2 *Hpart;   // [nchunk][kSeedBlock][kMaxRhs - 1] partial products v_i^H r_0^j
+  double2 *G;       // [kSeedBlock][kMaxRhs - 1]   g_i^j
+  double2 *Z;       // [kSeedBlock][kMaxRhs - 1]   eta_i^j
+  int32_t nchunk;   // row chunks of the partial products
+  int64_t rows;     // rows per chunk
+};
+constexpr int kBlockChunksMax = 64;
 
 // Buffers of the blocked reorthogonalization (Sec. 3 step 8).
 template <class T>
@@ -165,6 +190,10 @@ template <class T> void launch_seed_normalize(const SeedBufs<T> &b, cudaStream_t
 template <class T> void launch_seed_dots(const SeedBufs<T> &b, cudaStream_t s);
 template <class T> void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s);
 template <class T> void launch_reorth(const SeedBufs<T> &b, const ReorthBufs<T> &r, int passes, cudaStream_t s);
+// Blocked seeding: fold the steps blk0..w_last into x^2..x^p (G = V_blk^H R_0,
+// the eta recursion, X += W Z) and start the next block.  Returns the kernel count.
+template <class T> int launch_seed_flush(const SeedBufs<T> &b, const BlockBufs &k, cudaStream_t s);
+BlockBufs block_layout(int64_t n);
 template <class T> int reorth_kernel_count(int passes);
 
 template <class T> void launch_sub_from(const T *B, int64_t ldb, const T *Q, int64_t ldq, T *R, int64_t ldr,

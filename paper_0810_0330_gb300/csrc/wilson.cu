@@ -65,27 +65,8 @@ __global__ void __launch_bounds__(128) k_dslash(WilsonOpT<C> op, const C *__rest
   in += (int64_t)col * ldi;
   out += (int64_t)col * ldo;
   __shared__ R sacc[4][24][kWilsonSites + 1];
-  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
   const int64_t s0 = (int64_t)blockIdx.x * kWilsonSites;
-  const int64_t s = s0 + lane;
-  C acc[12];
-  if (s < op.sites) {
-    switch (mu) {
-      case 0: site_mu<0, S>(op, in, s, acc); break;
-      case 1: site_mu<1, S>(op, in, s, acc); break;
-      case 2: site_mu<2, S>(op, in, s, acc); break;
-      default: site_mu<3, S>(op, in, s, acc); break;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = C{0, 0};
-  }
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    sacc[mu][2 * k][lane] = acc[k].x;
-    sacc[mu][2 * k + 1][lane] = acc[k].y;
-  }
-  __syncthreads();
+  dslash_tile<S>(op, in, s0, sacc);
   const R *ind = reinterpret_cast<const R *>(in);
   R *outd = reinterpret_cast<R *>(out);
   const R mk = (R)(-op.kappa);
@@ -93,7 +74,7 @@ __global__ void __launch_bounds__(128) k_dslash(WilsonOpT<C> op, const C *__rest
     const int sl = o / 24, c = o - 24 * (o / 24);
     const int64_t ss = s0 + sl;
     if (ss >= op.sites) continue;
-    const R sum = ((sacc[0][c][sl] + sacc[1][c][sl]) + sacc[2][c][sl]) + sacc[3][c][sl];
+    const R sum = tile_hop_sum(sacc, c, sl);
     outd[24 * ss + c] = fma(mk, sum, __ldg(ind + 24 * ss + c));
   }
 }

@@ -142,6 +142,109 @@ __global__ void __launch_bounds__(128) k_dslash32(WilsonOp32 op, const float2 *_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Large lattices (at least kSiteKernelSites sites): one thread per site runs
+// all eight hops of its site, for two columns at a time (blockIdx.y = column
+// pair), so the four direction partials never leave registers: no shared
+// memory exchange and no CTA barrier.  Each link is loaded once per column
+// pair and applied to both columns.  Measured on GB300 against the kernel
+// above (11 columns): 16^3 x 32 125 us instead of 152, 16^4 62 us instead of
+// 80; on small lattices (8^4: 4096 threads) it leaves most SMs idle, so the
+// kernel above stays there.
+// ---------------------------------------------------------------------------
+constexpr int64_t kSiteKernelSites = 65536;
+
+template <bool TILED, bool VEC>
+SEED_DEV void load_site(const float2 *__restrict__ in, int64_t q, float2 (&ps)[12]) {
+  if constexpr (TILED) load_spinor_tiled(in, q, ps);
+  else load_spinor<VEC>(in + 12 * q, ps);
+}
+
+// direction MU of site s for the columns set in jm (bit j: column j of the
+// pair); MU == 0 starts the sums
+template <int MU, int S, bool TILED, bool VEC>
+SEED_DEV void site_dir2(const WilsonOp32 &op, const float2 *__restrict__ in, int64_t ldi, int64_t s, int32_t nf,
+                        int32_t nb, unsigned negf, unsigned negb, unsigned jm, float2 (&acc)[2][12]) {
+  const float2 *L = op.links + (int64_t)MU * 9 * op.sites;
+  {
+    float2 u[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = __ldg(L + (int64_t)k * op.sites + s);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (jm & (1u << j)) {
+        float2 p[12];
+        load_site<TILED, VEC>(in + j * ldi, nf, p);
+        hop_r<MU, S, true, MU == 0>(p, u, negf, acc[j]);
+      }
+    }
+  }
+  {
+    float2 u[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = __ldg(L + (int64_t)k * op.sites + nb);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (jm & (1u << j)) {
+        float2 p[12];
+        load_site<TILED, VEC>(in + j * ldi, nb, p);
+        hop_r<MU, -S, false, false>(p, u, negb, acc[j]);
+      }
+    }
+  }
+}
+
+template <int S, bool TILED, bool VEC>
+__global__ void __launch_bounds__(128, 4) k_dslash32_site(WilsonOp32 op, const float2 *__restrict__ in, int64_t ldi,
+                                                          float2 *__restrict__ out, int64_t ldo,
+                                                          const int32_t *__restrict__ col_active, int ncols) {
+  const int c0 = 2 * (int)blockIdx.y;
+  unsigned jm = 0u;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+    if (c0 + j < ncols && (col_active == nullptr || col_active[c0 + j] != 0)) jm |= 1u << j;
+  if (jm == 0u) return;   // uniform over the block
+  const int64_t s = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  const int64_t send = TILED ? (op.sites + 31) / 32 * 32 : op.sites;
+  if (s >= send) return;
+  const bool valid = s < op.sites;   // tiled padding sites only write zeros
+  in += (int64_t)c0 * ldi;
+  out += (int64_t)c0 * ldo;
+  float2 acc[2][12];
+  if (valid) {
+    const int4 *q = reinterpret_cast<const int4 *>(op.nbr + 8 * s);
+    const int4 a = __ldg(q), b = __ldg(q + 1);
+    unsigned negf = 0u, negb = 0u;
+    if (op.bc_t) {
+      const int64_t t = s / ((int64_t)op.dims[0] * op.dims[1] * op.dims[2]);
+      if (t == op.dims[3] - 1) negf = CxBits<float2>::sign;
+      if (t == 0) negb = CxBits<float2>::sign;
+    }
+    site_dir2<0, S, TILED, VEC>(op, in, ldi, s, a.x, a.y, 0u, 0u, jm, acc);
+    site_dir2<1, S, TILED, VEC>(op, in, ldi, s, a.z, a.w, 0u, 0u, jm, acc);
+    site_dir2<2, S, TILED, VEC>(op, in, ldi, s, b.x, b.y, 0u, 0u, jm, acc);
+    site_dir2<3, S, TILED, VEC>(op, in, ldi, s, b.z, b.w, negf, negb, jm, acc);
+  }
+  const float mk = (float)(-op.kappa);
+  const int64_t so = TILED ? (s >> 5) * 384 + (s & 31) : 12 * s;
+  constexpr int kStride = TILED ? 32 : 1;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (!(jm & (1u << j))) continue;
+    const float2 *ic = in + j * ldi + so;
+    float2 *oc = out + j * ldo + so;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      float2 v = make_float2(0.f, 0.f);
+      if (valid) {
+        const float2 x = __ldg(ic + kStride * k);
+        v = make_float2(fmaf(mk, acc[j][k].x, x.x), fmaf(mk, acc[j][k].y, x.y));
+      }
+      oc[kStride * k] = v;
+    }
+  }
+}
+
 // links (caller's layout [mu][site][3][3], FP64) -> FP32 structure-of-arrays copy
 __global__ void k_links_soa32(const double2 *__restrict__ links, float2 *__restrict__ out, int64_t sites) {
   const int64_t total = 36 * sites;
@@ -169,6 +272,21 @@ void launch_wilson_dslash32(const WilsonOp32 &op, int sign, const float2 *in, in
   const int ngroups = (int)((ncols + group - 1) / group);
   const dim3 grid((unsigned)nsb, (unsigned)ngroups);
   const bool vec = ((uintptr_t)in % 16 == 0) && (ldi % 2 == 0);
+  if (op.sites >= kSiteKernelSites) {
+    const int64_t nthreads = tiled ? nsb * kWilsonSites : op.sites;
+    const dim3 g2((unsigned)((nthreads + 127) / 128), (unsigned)((ncols + 1) / 2));
+    if (tiled) {
+      if (sign > 0) k_dslash32_site<+1, true, false><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
+      else k_dslash32_site<-1, true, false><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
+    } else if (vec) {
+      if (sign > 0) k_dslash32_site<+1, false, true><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
+      else k_dslash32_site<-1, false, true><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
+    } else {
+      if (sign > 0) k_dslash32_site<+1, false, false><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
+      else k_dslash32_site<-1, false, false><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
+    }
+    return;
+  }
   const int g = (int)group;
   if (tiled) {
     if (sign > 0) k_dslash32<+1, false, true><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols, g);

@@ -180,4 +180,39 @@ SEED_DEV void site_mu(const WilsonOpT<C> &op, const C *__restrict__ in, int64_t 
 
 constexpr int kWilsonSites = 32;   // sites per block; 4 warps (one per mu)
 
+// The hop sums of the 32 sites s0 .. s0+31 (a block of 128 threads: warp mu
+// handles direction mu, lane = site), left per direction in
+// sacc[mu][real component][lane] for the block's epilogue; sites past the
+// lattice contribute zeros.  Ends with a CTA barrier.
+template <int S, bool NC = true, class C>
+SEED_DEV void dslash_tile(const WilsonOpT<C> &op, const C *__restrict__ in, int64_t s0,
+                          typename CxBits<C>::R (*sacc)[24][kWilsonSites + 1]) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const int64_t s = s0 + lane;
+  C acc[12];
+  if (s < op.sites) {
+    switch (mu) {
+      case 0: site_mu<0, S, NC>(op, in, s, acc); break;
+      case 1: site_mu<1, S, NC>(op, in, s, acc); break;
+      case 2: site_mu<2, S, NC>(op, in, s, acc); break;
+      default: site_mu<3, S, NC>(op, in, s, acc); break;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = C{0, 0};
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    sacc[mu][2 * k][lane] = acc[k].x;
+    sacc[mu][2 * k + 1][lane] = acc[k].y;
+  }
+  __syncthreads();
+}
+
+// Sum of the four direction partials of real component c of tile site sl.
+template <class R>
+SEED_DEV R tile_hop_sum(const R (*sacc)[24][kWilsonSites + 1], int c, int sl) {
+  return ((sacc[0][c][sl] + sacc[1][c][sl]) + sacc[2][c][sl]) + sacc[3][c][sl];
+}
+
 }  // namespace seedk

@@ -84,8 +84,10 @@ def check_solution(orc, op, B, X, ref, info1, info2, tol_seed, tol_rest, label):
 # FP32 operator applies
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("dims,bc_t", [((4, 4, 4, 4), 0), ((3, 4, 5, 6), 1)])
+@pytest.mark.parametrize("dims,bc_t", [((4, 4, 4, 4), 0), ((3, 4, 5, 6), 1), ((16, 16, 16, 16), 1)])
 def test_fp32_wilson_apply(seedlib, orc, dims, bc_t):
+    """From 16^4 = 65536 sites on, the FP32 operator runs one thread per site
+    over column pairs (3 columns: one pair and one single column)."""
     kappa = 0.155
     U = I.random_su3_links(dims, 0.3, seed=2)
     n = 12 * I.lattice_sites(dims)
@@ -163,6 +165,33 @@ def test_mixed_wilson_small(seedlib, orc, freq):
     op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
     ref = orc.seed_solve_all(op, B, m_max=600, reorth_freq=freq, tol_seed=1e-12, tol_rest=1e-8)
     check_solution(orc, op, B, X, ref, i1, i2, 1e-12, 1e-8, "wilson-small-mixed")
+
+
+def test_mixed_wilson_large_lattice(seedlib, orc):
+    """17x17x15x16 = 69360 sites (one thread per site in the FP32 operator,
+    and a site count that is not a multiple of 32, so the solver's tiled FP32
+    vectors carry padding), kappa 0.10, antiperiodic t, 2 Gaussian RHS.  Both
+    systems' FP64 true residuals, recomputed by the oracle's operator, meet
+    their tolerances, and the mixed solve needs at most 30 % more CG
+    iterations than the FP64 solve of the same systems (a wrong FP32 operator
+    would show up as slower or stalled convergence between reliable updates)."""
+    dims, kappa = (17, 17, 15, 16), 0.10
+    U = I.random_su3_links(dims, 0.3, seed=11)
+    n = 12 * I.lattice_sites(dims)
+    B = I.gaussian_rhs(n, 2, seed=4, complex_=True)
+    prm = dict(m_max=400, reorth_freq=10, tol_seed=1e-9, tol_rest=1e-8)
+    out = {}
+    for prec in (0, 1):
+        ctx = seedlib.seed_create_wilson(dims, kappa, torch.from_numpy(U).cuda(),
+                                         seedlib.seed_params_default(precision=prec, **prm), bc_t=1)
+        out[prec] = mixed_solve(seedlib, ctx, B)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    i1, i2, X = out[1]
+    rr = true_relres(op, B, X)
+    assert rr[0] <= 1.01 * 1e-9 and rr[1] <= 1.01 * 1e-8, rr
+    assert i1[0]["converged"] == 1 and i2[1]["converged"] == 1
+    it64 = out[0][1][1]["iters"]
+    assert i2[1]["iters"] <= 1.3 * it64 + 2, (i2[1]["iters"], it64)
 
 
 @pytest.mark.slow
