@@ -44,7 +44,7 @@ except (OSError, ValueError):
     MEASURED_PEAKS = {}
 # DRAM bytes of one k_dslash launch (8^4, 11 columns) from an ncu capture of these sources of the kernel
 # (profiles/k_dslash_wilson_8x4_11cols.md); reported only while the source is unchanged.
-DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0}
+DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0, "6e70bd4a297626c1": 11.207424e6 + 0.0}
 
 
 def dslash_source_hash():

@@ -194,17 +194,21 @@ SEED_DEV void site_dir2(const WilsonOp32 &op, const float2 *__restrict__ in, int
   }
 }
 
+// Grid: one block per (128 sites, column pair), the pair fastest, so that the
+// pairs of one site block run together and their link loads hit L2.
 template <int S, bool TILED, bool VEC>
 __global__ void __launch_bounds__(128, 4) k_dslash32_site(WilsonOp32 op, const float2 *__restrict__ in, int64_t ldi,
                                                           float2 *__restrict__ out, int64_t ldo,
                                                           const int32_t *__restrict__ col_active, int ncols) {
-  const int c0 = 2 * (int)blockIdx.y;
+  const int npairs = (ncols + 1) / 2;
+  const int64_t sblock = (int64_t)blockIdx.x / npairs;
+  const int c0 = 2 * (int)(blockIdx.x - sblock * npairs);
   unsigned jm = 0u;
 #pragma unroll
   for (int j = 0; j < 2; ++j)
     if (c0 + j < ncols && (col_active == nullptr || col_active[c0 + j] != 0)) jm |= 1u << j;
   if (jm == 0u) return;   // uniform over the block
-  const int64_t s = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  const int64_t s = sblock * 128 + threadIdx.x;
   const int64_t send = TILED ? (op.sites + 31) / 32 * 32 : op.sites;
   if (s >= send) return;
   const bool valid = s < op.sites;   // tiled padding sites only write zeros
@@ -274,7 +278,7 @@ void launch_wilson_dslash32(const WilsonOp32 &op, int sign, const float2 *in, in
   const bool vec = ((uintptr_t)in % 16 == 0) && (ldi % 2 == 0);
   if (op.sites >= kSiteKernelSites) {
     const int64_t nthreads = tiled ? nsb * kWilsonSites : op.sites;
-    const dim3 g2((unsigned)((nthreads + 127) / 128), (unsigned)((ncols + 1) / 2));
+    const unsigned g2 = (unsigned)(((nthreads + 127) / 128) * ((ncols + 1) / 2));
     if (tiled) {
       if (sign > 0) k_dslash32_site<+1, true, false><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
       else k_dslash32_site<-1, true, false><<<g2, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
