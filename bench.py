@@ -47,6 +47,11 @@ except (OSError, ValueError):
 DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0, "6e70bd4a297626c1": 11.207424e6 + 0.0}
 
 
+def fp32_kernel_name(sites):
+    """The FP32 hopping kernel the library runs on a lattice of this many sites."""
+    return "k_dslash32_site" if sites >= 65536 else "k_dslash32"
+
+
 def dslash_source_hash():
     """Hash of the hopping kernel's sources (the .cu and its device header)."""
     import hashlib
@@ -270,12 +275,15 @@ def run_sweep(args):
                     "l2_resident": b < L2_BYTES, "reps": reps})
         S.seed_destroy(ctx)
         del rp, ci, v
-    for L in (8, 16, 24)[:args.sweep_max]:
-        dims = (L, L, L, L)
-        sites = L ** 4
+    # FP64 and FP32 on L^4, then FP32 only on the two mixed-precision lattice sizes
+    lattices = [((L, L, L, L), True) for L in (8, 16, 24)[:args.sweep_max]]
+    if args.sweep_max >= 3:
+        lattices += [((16, 16, 16, 32), False), ((32, 32, 32, 64), False)]
+    for dims, with_fp64 in lattices:
+        sites = int(np.prod(dims))
         U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
         ctx = S.seed_create_wilson(dims, WL["kappa"], U, S.seed_params_default(m_max=4))
-        for ncols in (1, 11):
+        for ncols in ((1, 11) if with_fp64 else ()):
             b = wilson_bytes(sites, ncols)
             reps = max(10, min(500, int(4e9 / b)))
             ms = S.seed_time_operator(ctx, 1, ncols, reps)
@@ -292,7 +300,7 @@ def run_sweep(args):
             reps = max(10, min(500, int(4e9 / b)))
             ms = S.seed_time_operator(ctx, 4, ncols, reps)
             fl = FLOPS_PER_SITE_D * sites * ncols
-            pts.append({"op": "wilson_D_fp32", "kernel": "k_dslash32<+1>", "dims": dims, "n": 12 * sites,
+            pts.append({"op": "wilson_D_fp32", "kernel": fp32_kernel_name(sites) + "<+1>", "dims": dims, "n": 12 * sites,
                         "ncols": ncols, "ms": ms, "bytes": b, "gbs": b / (ms * 1e-3) / 1e9,
                         "frac_hbm": b / (ms * 1e-3) / 1e9 / hbm, "tflops": fl / (ms * 1e-3) / 1e12,
                         "l2_resident": b < L2_BYTES, "reps": reps})
@@ -354,7 +362,7 @@ def run_ours(args):
         ms = S.seed_time_operator(ctx, 4 if mixed else 1, ncols, args.reps)
         flops = FLOPS_PER_SITE_D * vol * ncols
         b = wilson_bytes(vol, ncols, fp32=mixed)
-        print(json.dumps({"kernel": "k_dslash32" if mixed else "k_dslash", "dims": dims, "ncols": ncols, "ms": ms,
+        print(json.dumps({"kernel": fp32_kernel_name(vol) if mixed else "k_dslash", "dims": dims, "ncols": ncols, "ms": ms,
                           "tflops": flops / (ms * 1e-3) / 1e12, "gbs": b / (ms * 1e-3) / 1e9}), flush=True)
         S.seed_destroy(ctx)
         return 0
@@ -434,7 +442,7 @@ def run_ours(args):
         peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_dslash<+1, float2> (Wilson D, FP32 complex), %d columns" % ncols,
+                "kernel": "%s<+1> (Wilson D, FP32 complex), %d columns" % (fp32_kernel_name(vol), ncols),
                 "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
                 "bytes_per_launch": b, "l2_resident": b < L2_BYTES,
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
