@@ -51,6 +51,8 @@ struct seed_ctx {
   int device = 0;
   cudaStream_t user_stream = nullptr;
   cudaStream_t cs = nullptr;           // internal stream (capturable)
+  cudaStream_t cs2 = nullptr;          // second branch of the lockstep CG graphs
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;
   int kind = 0;                        // 0 = CSR, 1 = Wilson
@@ -212,7 +214,7 @@ seed_status alloc_common(seed_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->delta_hist, sizeof(double) * (m + 2)));
   TRY(dalloc(ctx, &ctx->gamma_hist, sizeof(double) * (m + 2)));
   TRY(dalloc(ctx, &ctx->eta, sizeof(double2) * kMaxRhs));
-  TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs)));
+  TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs) * 2));   // [1]: second branch of the CG graphs
   TRY(dalloc(ctx, &ctx->colnorm, sizeof(double) * kMaxRhs));
   // block partials: seed dots use up to 5 chunks x vec_blocks(n) x 32; lockstep kernels nc x blocks x 2
   TRY(dalloc(ctx, &ctx->partials, sizeof(double) * kPartials));
@@ -227,14 +229,15 @@ seed_status alloc_common(seed_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->H, sizeof(double2) * (size_t)(m + 1) * 2));
   TRY(dalloc(ctx, &ctx->cg_d, sizeof(double) * kCgDoubles * kMaxRhs));
   TRY(dalloc(ctx, &ctx->cg_i, sizeof(int32_t) * kCgInts * kMaxRhs));
-  if (ctx->precision == 1) TRY(dalloc(ctx, &ctx->call32, sizeof(CallArgs) * 2));
+  // call32: [0] seed run (X = E), [1] mixed CG, [2] its second graph branch
+  if (ctx->precision == 1) TRY(dalloc(ctx, &ctx->call32, sizeof(CallArgs) * 3));
   CU(cudaMemsetAsync(ctx->tickets, 0, sizeof(unsigned) * 256, ctx->cs));
   CU(cudaMemsetAsync(ctx->w, 0, n * es, ctx->cs));
   CU(cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * 2 * kMaxRhs));
   CU(cudaMallocHost(&ctx->h_status, sizeof(HostStatus) * 2));
   TRY(dalloc(ctx, &ctx->gsync, sizeof(unsigned) * kGridSyncWords));
   TRY(dalloc(ctx, &ctx->f2, n * es));
-  TRY(dalloc(ctx, &ctx->tpart, sizeof(double) * (size_t)((n / 12 + 31) / 32 + 1)));
+  TRY(dalloc(ctx, &ctx->tpart, sizeof(double) * (size_t)(3 * ((n / 12 + 31) / 32) + 3)));
   CU(cudaMallocHost(&ctx->h_gerr, sizeof(int32_t) * 2));
   CU(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
   int coop = 0;
@@ -432,7 +435,7 @@ int run_length(const seed_params &p) {
 
 bool use_persistent_seed(seed_ctx *ctx, int nrhs) {
   const int f = ctx->prm.reorth_freq;
-  return ctx->allow_persistent && ctx->pgrid > 0 && nrhs <= kPersistMaxRhs && (f == 0 || f >= 8);
+  return ctx->allow_persistent && ctx->pgrid > 0 && (f == 0 || f >= 8);
 }
 
 // Runs of Lanczos steps from CUDA graphs, status polled one run behind.
@@ -608,16 +611,45 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   return SEED_OK;
 }
 
+// One lockstep CG iteration on the CG columns c0 .. c0 + c.nc - 1 (c: the view
+// of those columns), on stream s, with its own CallArgs slot, partials and
+// tickets (two branches of a graph run at the same time on disjoint columns).
 template <class T>
-int issue_cg_iter(seed_ctx *ctx, const CgCols &c) {
+int issue_cg_iter(seed_ctx *ctx, const CgCols &c, int c0, cudaStream_t s, const CallArgs *call, double *partials,
+                  unsigned *tickets) {
   const int64_t n = ctx->n, ld = ctx->ldv;
-  int k = apply_A(ctx, ctx->P, ld, ctx->Q, ld, c.nc, c.active);
-  launch_cg_alpha<T>(n, (const T *)ctx->P, (const T *)ctx->Q, ld, c, ctx->partials, ctx->tickets, ctx->cs);
-  launch_cg_update<T>(n, ctx->call, (T *)ctx->R, (const T *)ctx->P, (const T *)ctx->Q, ld, c, ctx->partials,
-                      ctx->tickets, ctx->cs);
-  launch_cg_p<T>(n, (const T *)ctx->R, (T *)ctx->P, ld, c, ctx->cs);
+  T *P = (T *)ctx->P + (int64_t)c0 * ld, *Q = (T *)ctx->Q + (int64_t)c0 * ld, *R = (T *)ctx->R + (int64_t)c0 * ld;
+  int k;
+  if (ctx->kind == 0) {
+    launch_csr_spmv(ctx->csr, (const double *)P, ld, (double *)Q, ld, c.nc, c.active, s);
+    k = 1;
+  } else {
+    double2 *Tb = (double2 *)ctx->T + (int64_t)c0 * ld;
+    launch_wilson_dslash(ctx->wil, +1, (const double2 *)P, ld, Tb, ld, c.nc, c.active, s);
+    launch_wilson_dslash(ctx->wil, -1, Tb, ld, (double2 *)Q, ld, c.nc, c.active, s);
+    k = 2;
+  }
+  launch_cg_alpha<T>(n, P, Q, ld, c, partials, tickets, s);
+  launch_cg_update<T>(n, call, R, P, Q, ld, c, partials, tickets, s);
+  launch_cg_p<T>(n, R, P, ld, c, s);
   return k + 3;
 }
+
+// The columns c0 .. c0 + nc - 1 of the per-column CG state.
+CgCols cg_sub(const CgCols &c, int c0, int nc) {
+  CgCols v = c;
+  v.nc = nc;
+  for (double **p : {&v.rho, &v.alpha, &v.beta, &v.bnorm, &v.relres, &v.rupd}) *p += c0;
+  for (int32_t **p : {&v.active, &v.iters, &v.reached, &v.restarts, &v.converged, &v.needs_check, &v.mvps, &v.upd})
+    *p += c0;
+  return v;
+}
+
+// Lockstep CG graphs split the columns into two independent branches (kCgSplit
+// columns or more): the branches drift against each other, so one branch's
+// vector kernels and kernel tails overlap the other's operator applies.
+constexpr int kCgSplit = 4;
+int cg_split_at(int nc) { return nc >= kCgSplit ? (nc + 1) / 2 : nc; }
 
 CgCols cg_cols(seed_ctx *ctx, int nc) {
   CgCols c;
@@ -672,8 +704,23 @@ seed_status launch_cg_run(seed_ctx *ctx, const CgCols &c, int len) {
   if (it == ctx->graphs.end()) {
     GraphEntry g;
     cudaGraph_t graph;
+    const int h = cg_split_at(c.nc);
     CU(cudaStreamBeginCapture(ctx->cs, cudaStreamCaptureModeThreadLocal));
-    for (int q = 0; q < len; ++q) g.kernels += issue_cg_iter<T>(ctx, c);
+    if (h < c.nc) {
+      // branch 2 on cs2: columns h .. nc-1, CallArgs slot 1, the upper half of
+      // the partials and tickets shifted past branch 1's columns
+      CU(cudaEventRecord(ctx->ev_fork, ctx->cs));
+      CU(cudaStreamWaitEvent(ctx->cs2, ctx->ev_fork, 0));
+      const CgCols cb = cg_sub(c, h, c.nc - h);
+      for (int q = 0; q < len; ++q)
+        g.kernels += issue_cg_iter<T>(ctx, cb, h, ctx->cs2, ctx->call + 1, ctx->partials + kPartials / 2,
+                                      ctx->tickets + h);
+      CU(cudaEventRecord(ctx->ev_join, ctx->cs2));
+    }
+    const CgCols ca = cg_sub(c, 0, h);
+    for (int q = 0; q < len; ++q)
+      g.kernels += issue_cg_iter<T>(ctx, ca, 0, ctx->cs, ctx->call, ctx->partials, ctx->tickets);
+    if (h < c.nc) CU(cudaStreamWaitEvent(ctx->cs, ctx->ev_join, 0));
     CU(cudaStreamEndCapture(ctx->cs, &graph));
     cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -695,8 +742,9 @@ seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx,
   if (nc <= 0) return SEED_OK;
   TRY(ensure_cols(ctx, nc));
   CU(cudaEventRecord(ctx->t2, ctx->cs));
-  CallArgs ca{Xc, ldx, 0};
-  CU(cudaMemcpyAsync(ctx->call, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  // slot 1: the second branch of the CG graphs (columns from cg_split_at(nc) on)
+  const CallArgs ca[2] = {{Xc, ldx, 0}, {Xc, ldx, cg_split_at(nc)}};
+  CU(cudaMemcpyAsync(ctx->call, ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
   const CgCols c = cg_cols(ctx, nc);
   // K7: true residual of the seeded systems, then p = r
   int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
@@ -1069,15 +1117,28 @@ seed_status run_graph(seed_ctx *ctx, const std::string &key, F issue) {
 }
 
 // One lockstep CG iteration in FP32 (the operator's FP32 copy, FP32 vectors,
-// FP64 alpha / beta / norms); x is the FP32 correction E (call32[1]).
+// FP64 alpha / beta / norms) on the CG columns c0 .. c0 + c.nc - 1 (c: their
+// view); x is the FP32 correction E (CallArgs `call`).  Stream, partials and
+// tickets as in issue_cg_iter.
 template <class T32>
-int issue_mixed_iter(seed_ctx *ctx, const CgCols &c) {
+int issue_mixed_iter(seed_ctx *ctx, const CgCols &c, int c0, cudaStream_t s, const CallArgs *call,
+                     double *partials, unsigned *tickets) {
   const int64_t n = ctx->nv, ld = ctx->ldv;
-  int k = apply_A32(ctx, ctx->P32, ld, ctx->Q32, ld, c.nc, c.active);
-  launch_cg_alpha<T32>(n, (const T32 *)ctx->P32, (const T32 *)ctx->Q32, ld, c, ctx->partials, ctx->tickets, ctx->cs);
-  launch_cg_update<T32>(n, ctx->call32 + 1, (T32 *)ctx->R32, (const T32 *)ctx->P32, (const T32 *)ctx->Q32, ld, c,
-                        ctx->partials, ctx->tickets, ctx->cs);
-  launch_cg_p<T32>(n, (const T32 *)ctx->R32, (T32 *)ctx->P32, ld, c, ctx->cs);
+  T32 *P = (T32 *)ctx->P32 + (int64_t)c0 * ld, *Q = (T32 *)ctx->Q32 + (int64_t)c0 * ld;
+  T32 *R = (T32 *)ctx->R32 + (int64_t)c0 * ld;
+  int k;
+  if (ctx->kind == 0) {
+    launch_csr_spmv32(ctx->csr32, (const float *)P, ld, (float *)Q, ld, c.nc, c.active, s);
+    k = 1;
+  } else {
+    float2 *Tb = (float2 *)ctx->T32 + (int64_t)c0 * ld;
+    launch_wilson_dslash32(ctx->wil32, +1, (const float2 *)P, ld, Tb, ld, c.nc, c.active, true, s);
+    launch_wilson_dslash32(ctx->wil32, -1, Tb, ld, (float2 *)Q, ld, c.nc, c.active, true, s);
+    k = 2;
+  }
+  launch_cg_alpha<T32>(n, P, Q, ld, c, partials, tickets, s);
+  launch_cg_update<T32>(n, call, R, P, Q, ld, c, partials, tickets, s);
+  launch_cg_p<T32>(n, R, P, ld, c, s);
   return k + 3;
 }
 
@@ -1093,8 +1154,10 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
   c.tol = tol;
   c.tol_check = tol;
   T32 *E = E_cols<T32>(ctx) + (int64_t)c0 * ld;
-  const CallArgs ca{(void *)E_cols<T32>(ctx), ld, c0};   // CG column c corrects system c0 + c + 1
-  CU(cudaMemcpyAsync(ctx->call32 + 1, &ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  // CG column c corrects system c0 + c + 1; slot 2: the graphs' second branch
+  const int h = cg_split_at(nc);
+  const CallArgs ca[2] = {{(void *)E_cols<T32>(ctx), ld, c0}, {(void *)E_cols<T32>(ctx), ld, c0 + h}};
+  CU(cudaMemcpyAsync(ctx->call32 + 1, ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
   int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
   launch_mixed_init<T64, T32>(nv, lay, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, E, ld, c,
                               ctx->partials, ctx->tickets, ctx->cs);
@@ -1107,8 +1170,22 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
   cudaEvent_t evs[2] = {nullptr, nullptr};
   for (;;) {
     TRY(run_graph(ctx, key, [&] {
+      // two branches on disjoint columns (see cg_split_at); a failed call here
+      // invalidates the capture, which cudaStreamEndCapture reports
       int k = 0;
-      for (int q = 0; q < L; ++q) k += issue_mixed_iter<T32>(ctx, c);
+      if (h < nc) {
+        cudaEventRecord(ctx->ev_fork, ctx->cs);
+        cudaStreamWaitEvent(ctx->cs2, ctx->ev_fork, 0);
+        const CgCols cb = cg_sub(c, h, nc - h);
+        for (int q = 0; q < L; ++q)
+          k += issue_mixed_iter<T32>(ctx, cb, h, ctx->cs2, ctx->call32 + 2, ctx->partials + kPartials / 2,
+                                     ctx->tickets + h);
+        cudaEventRecord(ctx->ev_join, ctx->cs2);
+      }
+      const CgCols ca0 = cg_sub(c, 0, h);
+      for (int q = 0; q < L; ++q)
+        k += issue_mixed_iter<T32>(ctx, ca0, 0, ctx->cs, ctx->call32 + 1, ctx->partials, ctx->tickets);
+      if (h < nc) cudaStreamWaitEvent(ctx->cs, ctx->ev_join, 0);
       return k;
     }));
     // reliable updates (direct launches: B and X are this call's buffers)
@@ -1308,6 +1385,9 @@ seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream strea
   CU(cudaGetDevice(&ctx->device));
   ctx->user_stream = (cudaStream_t)stream;
   CU(cudaStreamCreateWithFlags(&ctx->cs, cudaStreamNonBlocking));
+  CU(cudaStreamCreateWithFlags(&ctx->cs2, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  CU(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
   CU(cudaEventCreate(&ctx->t0));
   CU(cudaEventCreate(&ctx->t1));
@@ -1331,9 +1411,10 @@ void destroy(seed_ctx *ctx) {
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->h_gerr) cudaFreeHost(ctx->h_gerr);
-  cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3};
+  cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3, ctx->ev_fork, ctx->ev_join};
   for (auto e : evs)
     if (e) cudaEventDestroy(e);
+  if (ctx->cs2) cudaStreamDestroy(ctx->cs2);
   if (ctx->cs) cudaStreamDestroy(ctx->cs);
   delete ctx;
 }

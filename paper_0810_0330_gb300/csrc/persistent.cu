@@ -158,16 +158,6 @@ SEED_DEV void reduce_rows32(const double *part, int nrows, double *s_vals, doubl
   __syncthreads();
 }
 
-// Block partial of 32 values: reduce-scatter and one row of bpart.
-SEED_DEV void write_row32(double (&acc)[32], double *bpart, double (*sred)[32]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double mine = warp_reduce_scatter32(acc);
-  sred[warp][lane] = mine;
-  __syncthreads();
-  if (threadIdx.x < 32)
-    bpart[(int64_t)blockIdx.x * 32 + lane] = ((sred[0][lane] + sred[1][lane]) + sred[2][lane]) + sred[3][lane];
-}
-
 // Hopping sums of one 32-site tile into sacc[mu][component][site] (S = +1: D, -1: D^H).
 template <int S>
 SEED_DEV void wilson_tile(const WilsonOp &op, const double2 *in, int64_t s0, double (*sacc)[24][kWilsonSites + 1]) {
@@ -199,35 +189,36 @@ SEED_DEV double2 tile_sum(double (*sacc)[24][kWilsonSites + 1], int cc, int sl) 
 }
 
 // ---------------------------------------------------------------------------
-// Seed runs.  Per step i (paper notation):
-//   phase 1 (tiles): v_i = f / beta_{i-1} into V; t = D v_i        [Wilson only]
-//   phase 2 (tiles): u = A v_i; f = u - beta_{i-1} v_{i-1}; partial alpha_i
-//   barrier; every block: alpha_i -> gamma_{i-1}, delta_i, zeta_i, eta^j
-//           (steps 3/4, 6/7), with g^j = v_i^H r_0^j formed in the previous step
-//   phase 3 (all blocks): f -= alpha_i v_i; w_i; x^1, x^j; partials ||f||^2
-//           and f^H r_0^j
-//   barrier; every block: beta_i, stopping test (step 9); g^j of step i+1 =
-//           (f^H r_0^j) / beta_i, since v_{i+1} = f / beta_i.
-// A pre-phase at the start of a run forms g^j of its first step the same way.
+// Seed runs (Sec. 3 steps 2-9 between two reorthogonalizing steps).  The
+// seeding of systems 2..p is blocked (SeedBufs::Wb, seedblock.cu): a step only
+// stores w_i, so the recurrence of system 1 is all that runs here.
 //
-// Every block keeps its own shared-memory copy of the recurrence scalars
-// (SeedState, eta^j, g^j).  After each barrier every block reduces the same
-// partials in the same fixed order and runs the same scalar code, so the
-// copies stay identical and no block waits for another to publish scalars:
-// the barriers are plain arrivals, with no serial reduce-then-release hop.
-// Block 0 writes the step histories and, on leaving, the state back.
+// Wilson, two phases and two grid barriers per step i:
+//   phase 1 (tiles): v_i = f / beta_{i-1} into V; t = D v_i; per tile the
+//           partial sums of ||t||^2 and Re(v_i^H v_{i-1})
+//   barrier; every block: alpha_i = ||D v_i||^2 - beta_{i-1} Re(v_i^H v_{i-1}),
+//           then gamma_{i-1}, delta_i, zeta_i (steps 3/6)
+//   phase 2 (tiles): u = D^H t; f = u - beta_{i-1} v_{i-1} - alpha_i v_i (step
+//           5); w_i and x^1 += zeta_i w_i (step 6); w_i into Wb; partial ||f||^2
+//   barrier; every block: beta_i and the stopping test (step 9).
+// alpha_i is the paper's v_i^H (A v_i - beta_{i-1} v_{i-1}) with v_i^H A v_i
+// written as ||D v_i||^2 (A = D^H D): the same number up to rounding, available
+// one barrier earlier, so that the update runs in the D^H tiles' epilogue.
+//
+// Every block keeps its own shared-memory copy of the recurrence scalars.
+// After each barrier every block reduces the same per-tile partials in the same
+// fixed order (tile order, not block order) and runs the same scalar code, so
+// the copies stay identical; block 0 writes the step histories and, on leaving,
+// the state back.
 // ---------------------------------------------------------------------------
 struct LocalSeed {
   SeedState st;
-  double2 eta[kPersistMaxRhs];
-  double2 g[kPersistMaxRhs];
 };
 
 template <class T>
 SEED_DEV SeedBufs<T> local_bufs(const SeedBufs<T> &b, LocalSeed &L) {
   SeedBufs<T> l = b;
   l.st = &L.st;
-  l.eta = L.eta;
   if (blockIdx.x != 0) l.alpha_hist = l.beta_hist = l.delta_hist = l.gamma_hist = nullptr;
   return l;
 }
@@ -235,165 +226,57 @@ SEED_DEV SeedBufs<T> local_bufs(const SeedBufs<T> &b, LocalSeed &L) {
 template <class T>
 SEED_DEV void local_load(const SeedBufs<T> &b, LocalSeed &L) {
   if (threadIdx.x == 0) L.st = *b.st;
-  for (int j = threadIdx.x; j < b.nrhs; j += PT) L.eta[j] = b.eta[j];
   __syncthreads();
 }
 
 template <class T>
 SEED_DEV void local_store(const SeedBufs<T> &b, const LocalSeed &L) {
   __syncthreads();
-  if (blockIdx.x != 0) return;
-  if (threadIdx.x == 0) *b.st = L.st;
-  for (int j = threadIdx.x; j < b.nrhs; j += PT) b.eta[j] = L.eta[j];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *b.st = L.st;
 }
 
-// partial of f^H r_0^j (slots 1 + 2(j-1), 2 + 2(j-1)) for element e
+// Stops the run (in every block alike) when step i would not fit in Wb; the
+// host caps runs below this, so it only guards the buffer.
 template <class T>
-SEED_DEV void add_fr0(const SeedBufs<T> &b, int64_t e, T fe, double (&acc)[32]) {
-  const int nr = b.nrhs;
-#pragma unroll
-  for (int q = 0; q < kPersistMaxRhs - 1; ++q) {
-    if (q < nr - 1) {
-      const double2 d = Sc<T>::dotc(fe, __ldg(b.R0 + (int64_t)q * b.ldr + e), c2(acc[1 + 2 * q], acc[2 + 2 * q]));
-      acc[1 + 2 * q] = d.x;
-      acc[2 + 2 * q] = d.y;
+SEED_DEV bool block_full(const SeedBufs<T> &b, LocalSeed &L, int i) {
+  if (b.Wb == nullptr || i - L.st.blk0 < kSeedBlock) return false;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    L.st.active = 0;
+    L.st.stop_reason = STOP_BLOCK;
+  }
+  __syncthreads();
+  return true;
+}
+
+// barrier, then in every block: alpha_i from parts[k * stride] (k < nparts, a
+// fixed order that does not depend on which block ran which tile) minus
+// beta_{i-1} times parts[k * stride + 1] when `with_vm`, and the step's scalars
+template <class T>
+SEED_DEV bool seed_alpha_step(const SeedBufs<T> &bl, const double *parts, int nparts, int stride, bool with_vm,
+                              int i, LocalSeed &L, const GridSync &g, unsigned &epoch) {
+  if (!grid_sync(g, epoch)) return false;
+  if (threadIdx.x < 32) {
+    double a = warp_sum_partials(parts, nparts, stride, 0);
+    if (with_vm) {
+      const double vm = warp_sum_partials(parts, nparts, stride, 1);
+      a = a - L.st.beta_prev * vm;
     }
+    if (threadIdx.x == 0) seed_step_scalars<T, false>(bl, i, a, nullptr);
   }
-}
-
-// g^j = scale * (reduced f^H r_0^j)
-SEED_DEV void local_g(int nrhs, const double *s_vals, double scale, LocalSeed &L) {
-  for (int j = 1 + (int)threadIdx.x; j < nrhs; j += PT)
-    L.g[j] = c2(scale * s_vals[1 + 2 * (j - 1)], scale * s_vals[2 + 2 * (j - 1)]);
-}
-
-// pre-phase: g^j of the first step from the current f
-template <class T>
-SEED_DEV bool seed_pre_dots(const SeedBufs<T> &b, const T *f, LocalSeed &L, const GridSync &g, unsigned &epoch,
-                            double *bpart, double (*sred)[32], double *s_vals) {
-  double acc[32];
-#pragma unroll
-  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT)
-    add_fr0<T>(b, e, f[e], acc);
-  write_row32(acc, bpart, sred);
-  if (!grid_sync(g, epoch)) return false;
-  reduce_rows32(bpart, gridDim.x, s_vals, sred);
-  local_g(b.nrhs, s_vals, L.st.inv_beta, L);
   __syncthreads();
   return true;
 }
 
-// barrier, then in every block: alpha_i from parts[k * stride], k < nparts (a
-// fixed order that does not depend on which block ran which tile), and the
-// step's scalars
+// barrier, then in every block: beta_i from the partials of ||f||^2 and step 9
 template <class T>
-SEED_DEV bool seed_alpha_step(const SeedBufs<T> &bl, const double *parts, int nparts, int stride, int i,
-                              LocalSeed &L, const GridSync &g, unsigned &epoch) {
+SEED_DEV bool seed_beta_step(const SeedBufs<T> &bl, const double *parts, int nparts, int i, LocalSeed &L,
+                             const GridSync &g, unsigned &epoch) {
   if (!grid_sync(g, epoch)) return false;
   if (threadIdx.x < 32) {
-    const double a = warp_sum_partials(parts, nparts, stride, 0);
-    if (threadIdx.x == 0) seed_step_scalars<T, false>(bl, i, a, L.g);
-  }
-  __syncthreads();
-  return true;
-}
-
-// The update partials (one 32-value row per block) reach every block in two
-// levels: blocks 0..nseg-1 each sum a segment of 16 rows in order, then after
-// a second barrier every block sums the nseg segment rows in order (instead
-// of every block reading every row: 304 x 256 B from L2 per block).
-constexpr int kRowSeg = 16;
-SEED_DEV double *seg_rows(double *bpart) { return bpart + (int64_t)gridDim.x * 40; }
-SEED_DEV bool reduce_rows_2level(double *bpart, const GridSync &g, unsigned &epoch, double *s_vals,
-                                 double (*sred)[32]) {
-  const int nseg = (gridDim.x + kRowSeg - 1) / kRowSeg;
-  double *seg = seg_rows(bpart);
-  if ((int)blockIdx.x < nseg) {
-    const int r0 = blockIdx.x * kRowSeg, nr = min(kRowSeg, (int)gridDim.x - r0);
-    reduce_rows32(bpart + (int64_t)r0 * 32, nr, s_vals, sred);
-    if (threadIdx.x < 32) seg[(int64_t)blockIdx.x * 32 + threadIdx.x] = s_vals[threadIdx.x];
-  }
-  if (!grid_sync(g, epoch)) return false;
-  reduce_rows32(seg, nseg, s_vals, sred);
-  return true;
-}
-
-// phase 3, the barriers, and step 9 in every block
-template <class T>
-SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i, LocalSeed &L,
-                               const GridSync &g, unsigned &epoch, double *bpart, double (*sred)[32],
-                               double *s_vals) {
-  const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
-  const double bp = (i > 1) ? L.st.beta_prev : 0.0;
-  T *const X = reinterpret_cast<T *>(b.call->X);
-  const int64_t ldx = b.call->ldx;
-  const int nr = b.nrhs;
-  double acc[32];
-#pragma unroll
-  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
-    T xv[kPersistMaxRhs];
-#pragma unroll
-    for (int j = 0; j < kPersistMaxRhs; ++j)
-      if (j < nr) xv[j] = __ldcg(X + j * ldx + e);
-    const T v = __ldcg(vi + e), f0 = __ldcg(f + e);
-    const T wp = (i > 1) ? __ldcg(b.w + e) : Sc<T>::zero();
-    const T fe = Sc<T>::axpy(-a, v, f0);
-    const T we = (i > 1) ? Sc<T>::scale(inv_d, Sc<T>::axpy(-bp, wp, v)) : Sc<T>::scale(inv_d, v);
-    f[e] = fe;
-    b.w[e] = we;
-    xv[0] = Sc<T>::axpy(zeta, we, xv[0]);
-#pragma unroll
-    for (int j = 1; j < kPersistMaxRhs; ++j)
-      if (j < nr) xv[j] = Sc<T>::caxpy(L.eta[j], we, xv[j]);
-#pragma unroll
-    for (int j = 0; j < kPersistMaxRhs; ++j)
-      if (j < nr) X[j * ldx + e] = xv[j];
-    acc[0] = Sc<T>::nrm2(fe, acc[0]);
-    add_fr0<T>(b, e, fe, acc);
-  }
-  write_row32(acc, bpart, sred);
-  if (!grid_sync(g, epoch)) return false;
-  if (!reduce_rows_2level(bpart, g, epoch, s_vals, sred)) return false;
-  if (threadIdx.x == 0) seed_finish<T, false>(bl, s_vals[0]);
-  __syncthreads();
-  if (L.st.active) local_g(b.nrhs, s_vals, L.st.inv_beta, L);
-  __syncthreads();
-  return true;
-}
-
-// Phase 3 with blocked seeding (b.Wb set): f, w_i (also into column
-// i - blk0 of Wb), x^1 and ||f||^2 only -- x^2..x^p wait for the block's flush.
-// One value per block; after the barrier every block sums the gridDim.x
-// partials in block order (the same order in every block) and runs step 9.
-template <class T>
-SEED_DEV bool seed_update_step_blk(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i,
-                                   LocalSeed &L, const GridSync &g, unsigned &epoch, double *bpart, double *s_red) {
-  const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
-  const double bp = (i > 1) ? L.st.beta_prev : 0.0;
-  T *const X = reinterpret_cast<T *>(b.call->X);
-  T *const wcol = b.Wb + (int64_t)(i - L.st.blk0) * b.ldv;
-  typename Sc<T>::A acc = 0;
-  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
-    const T v = __ldcg(vi + e), f0 = __ldcg(f + e), x0 = __ldcg(X + e);
-    const T wp = (i > 1) ? __ldcg(b.w + e) : Sc<T>::zero();
-    const T fe = Sc<T>::axpy(-a, v, f0);
-    const T we = (i > 1) ? Sc<T>::scale(inv_d, Sc<T>::axpy(-bp, wp, v)) : Sc<T>::scale(inv_d, v);
-    f[e] = fe;
-    b.w[e] = we;
-    wcol[e] = we;
-    X[e] = Sc<T>::axpy(zeta, we, x0);
-    acc = Sc<T>::nrm2(fe, acc);
-  }
-  double vv[1] = {(double)acc};
-  block_sum<1, PT>(vv, s_red);
-  if (threadIdx.x == 0) bpart[blockIdx.x] = vv[0];
-  if (!grid_sync(g, epoch)) return false;
-  if (threadIdx.x < 32) {
-    const double ss = warp_sum_partials(bpart, gridDim.x, 1, 0);
+    const double ss = warp_sum_partials(parts, nparts, 1, 0);
     if (threadIdx.x == 0) {
-      L.st.w_last = i;
+      if (bl.Wb != nullptr) L.st.w_last = i;
       seed_finish<T, false>(bl, ss);
     }
   }
@@ -416,42 +299,37 @@ SEED_DEV void seed_leave(const SeedBufs<T> &b, const LocalSeed &L, const T *f, i
   }
 }
 
+// tpart: 3 x tiles doubles (phase-1 pairs, then the phase-2 norms)
 __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, WilsonOp op, double2 *tbuf,
                                                          GridSync g, double *bpart, double *tpart, int i_stop) {
   __shared__ double sacc[4][24][kWilsonSites + 1];
-  __shared__ double sred[PT / 32][32];
-  __shared__ double s_vals[32];
-  __shared__ double s_red[PT / 32];
+  __shared__ double s_red[2 * (PT / 32)];
   __shared__ LocalSeed L;
+  (void)bpart;
   const int64_t sites = op.sites;
   const int tiles = (int)((sites + kWilsonSites - 1) / kWilsonSites);
   const double kappa = op.kappa;
+  double *part1 = tpart, *part2 = tpart + 2 * (int64_t)tiles;
   unsigned epoch = 0;
   local_load(b, L);
   const SeedBufs<double2> bl = local_bufs(b, L);
   Owners own;
   if (!register_owner(g, epoch, own)) return;
-  const bool blocked = b.Wb != nullptr;
-  if (L.st.active && L.st.i < i_stop && !blocked)
-    if (!seed_pre_dots<double2>(b, b.f, L, g, epoch, bpart, sred, s_vals)) return;
+  double2 *const X = reinterpret_cast<double2 *>(b.call->X);
   for (;;) {
     const int i = L.st.i;
     if (!L.st.active || i >= i_stop) break;
-    if (blocked && i - L.st.blk0 >= kSeedBlock) {   // the host caps runs below this
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        L.st.active = 0;
-        L.st.stop_reason = STOP_BLOCK;
-      }
-      __syncthreads();
-      break;
-    }
+    if (block_full(b, L, i)) break;
     const double inv_b = L.st.inv_beta;
+    const double bp = (i > 1) ? L.st.beta_prev : 0.0;
     double2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
+    const double2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+    // phase 1: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
     if (own.rank >= 0) {
       for (int tile = own.rank; tile < tiles; tile += own.count) {
         const int64_t s0 = (int64_t)tile * kWilsonSites;
         wilson_tile<+1>(op, b.f, s0, sacc);
+        double ptt = 0.0, pvm = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
@@ -462,21 +340,33 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
             const double2 fe = b.f[e];
             const double2 v = c2(inv_b * fe.x, inv_b * fe.y);
             vi[e] = v;
-            tbuf[e] = c2(fma(-kappa, inv_b * sum.x, v.x), fma(-kappa, inv_b * sum.y, v.y));
+            const double2 t = c2(fma(-kappa, inv_b * sum.x, v.x), fma(-kappa, inv_b * sum.y, v.y));
+            tbuf[e] = t;
+            ptt = fma(t.y, t.y, fma(t.x, t.x, ptt));
+            if (i > 1) {
+              const double2 m = vm[e];
+              pvm = fma(v.y, m.y, fma(v.x, m.x, pvm));
+            }
           }
         }
-        __syncthreads();
+        double vv[2] = {ptt, pvm};
+        block_sum<2, PT>(vv, s_red);   // ends with a CTA barrier: sacc is free again
+        if (threadIdx.x == 0) {
+          part1[2 * tile] = vv[0];
+          part1[2 * tile + 1] = vv[1];
+        }
       }
     }
-    if (!grid_sync(g, epoch)) return;
-
-    const double bp = (i > 1) ? L.st.beta_prev : 0.0;
-    const double2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+    if (!seed_alpha_step<double2>(bl, part1, tiles, 2, i > 1, i, L, g, epoch)) return;
+    if (!L.st.active) break;   // delta_i <= 0
+    // phase 2: u = D^H t, f, w_i, x^1, w_i into Wb, partials of ||f||^2
+    const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+    double2 *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
     if (own.rank >= 0) {
       for (int tile = own.rank; tile < tiles; tile += own.count) {
         const int64_t s0 = (int64_t)tile * kWilsonSites;
         wilson_tile<-1>(op, tbuf, s0, sacc);
-        double apart = 0.0;
+        double pff = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
@@ -485,57 +375,81 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
             const double2 sum = tile_sum(sacc, cc, sl);
             const int64_t e = 12 * ss + cc;
             const double2 tv = tbuf[e], v = vi[e];
-            const double2 m = (i > 1) ? vm[e] : c2(0.0, 0.0);
-            double2 u = c2(fma(-kappa, sum.x, tv.x), fma(-kappa, sum.y, tv.y));
-            if (i > 1) u = c2(fma(-bp, m.x, u.x), fma(-bp, m.y, u.y));
-            b.f[e] = u;
-            apart = fma(v.y, u.y, fma(v.x, u.x, apart));
+            double2 f = c2(fma(-kappa, sum.x, tv.x), fma(-kappa, sum.y, tv.y));
+            if (i > 1) {
+              const double2 m = vm[e];
+              f = c2(fma(-bp, m.x, f.x), fma(-bp, m.y, f.y));
+            }
+            f = c2(fma(-a, v.x, f.x), fma(-a, v.y, f.y));
+            double2 w;
+            if (i > 1) {
+              const double2 wp = b.w[e];
+              w = c2(inv_d * fma(-bp, wp.x, v.x), inv_d * fma(-bp, wp.y, v.y));
+            } else {
+              w = c2(inv_d * v.x, inv_d * v.y);
+            }
+            b.f[e] = f;
+            b.w[e] = w;
+            if (wcol != nullptr) wcol[e] = w;
+            const double2 x = X[e];
+            X[e] = c2(fma(zeta, w.x, x.x), fma(zeta, w.y, x.y));
+            pff = fma(f.y, f.y, fma(f.x, f.x, pff));
           }
         }
-        double vv[1] = {apart};
+        double vv[1] = {pff};
         block_sum<1, PT>(vv, s_red);
-        if (threadIdx.x == 0) tpart[tile] = vv[0];   // per tile: the sum order is fixed
+        if (threadIdx.x == 0) part2[tile] = vv[0];
       }
     }
-    if (!seed_alpha_step<double2>(bl, tpart, tiles, 1, i, L, g, epoch)) return;
-    if (!L.st.active) break;   // delta_i <= 0
-    if (blocked) {
-      if (!seed_update_step_blk<double2>(b, bl, b.f, vi, i, L, g, epoch, bpart, s_red)) return;
-    } else if (!seed_update_step<double2>(b, bl, b.f, vi, i, L, g, epoch, bpart, sred, s_vals)) {
-      return;
-    }
+    if (!seed_beta_step<double2>(bl, part2, tiles, i, L, g, epoch)) return;
   }
   seed_leave<double2>(b, L, b.f, i_stop);
   local_store(b, L);
 }
 
-// real CSR operator: the apply reads f_cur (two buffers alternate, since a row
-// reads other rows' entries while writing its own)
+// Phase 3 of the CSR run: f -= alpha_i v_i, w_i (also into column i - blk0 of
+// Wb), x^1 and ||f||^2; one value per block, reduced in block order by every
+// block after the barrier, then step 9.
+template <class T>
+SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i, LocalSeed &L,
+                               const GridSync &g, unsigned &epoch, double *bpart, double *s_red) {
+  const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+  const double bp = (i > 1) ? L.st.beta_prev : 0.0;
+  T *const X = reinterpret_cast<T *>(b.call->X);
+  T *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
+  typename Sc<T>::A acc = 0;
+  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
+    const T v = __ldcg(vi + e), f0 = __ldcg(f + e), x0 = __ldcg(X + e);
+    const T wp = (i > 1) ? __ldcg(b.w + e) : Sc<T>::zero();
+    const T fe = Sc<T>::axpy(-a, v, f0);
+    const T we = (i > 1) ? Sc<T>::scale(inv_d, Sc<T>::axpy(-bp, wp, v)) : Sc<T>::scale(inv_d, v);
+    f[e] = fe;
+    b.w[e] = we;
+    if (wcol != nullptr) wcol[e] = we;
+    X[e] = Sc<T>::axpy(zeta, we, x0);
+    acc = Sc<T>::nrm2(fe, acc);
+  }
+  double vv[1] = {(double)acc};
+  block_sum<1, PT>(vv, s_red);
+  if (threadIdx.x == 0) bpart[blockIdx.x] = vv[0];
+  return seed_beta_step<T>(bl, bpart, gridDim.x, i, L, g, epoch);
+}
+
+// real CSR operator, three barriers per step: the apply reads f_cur (two
+// buffers alternate, since a row reads other rows' entries while writing its
+// own); alpha_i from block partials; then the update.
 __global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp op, double *f2, GridSync g,
                                                       double *bpart, int i_stop) {
-  __shared__ double sred[PT / 32][32];
-  __shared__ double s_vals[32];
   __shared__ double s_red[PT / 32];
   __shared__ LocalSeed L;
   unsigned epoch = 0;
   int par = 0;
   local_load(b, L);
   const SeedBufs<double> bl = local_bufs(b, L);
-  const bool blocked = b.Wb != nullptr;
-  if (L.st.active && L.st.i < i_stop && !blocked)
-    if (!seed_pre_dots<double>(b, b.f, L, g, epoch, bpart, sred, s_vals)) return;
   for (;;) {
     const int i = L.st.i;
     if (!L.st.active || i >= i_stop) break;
-    if (blocked && i - L.st.blk0 >= kSeedBlock) {   // the host caps runs below this
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        L.st.active = 0;
-        L.st.stop_reason = STOP_BLOCK;
-      }
-      __syncthreads();
-      break;
-    }
+    if (block_full(b, L, i)) break;
     const double inv_b = L.st.inv_beta;
     const double bp = (i > 1) ? L.st.beta_prev : 0.0;
     double *fc = par ? f2 : b.f, *fn = par ? b.f : f2;
@@ -553,21 +467,18 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp o
       fn[r] = u;
       apart = fma(v, u, apart);
     }
-    // alpha partials after the update rows (every block reads them after the
-    // barrier, while a faster block may already be writing its update row)
+    // alpha partials apart from the update partials (every block reads them
+    // after the barrier, while a faster block may already be writing its
+    // update partial)
     double *apartials = bpart + (int64_t)gridDim.x * 32;
     {
       double vv[1] = {apart};
       block_sum<1, PT>(vv, s_red);
       if (threadIdx.x == 0) apartials[blockIdx.x] = vv[0];   // by blockIdx: fixed order
     }
-    if (!seed_alpha_step<double>(bl, apartials, gridDim.x, 1, i, L, g, epoch)) return;
+    if (!seed_alpha_step<double>(bl, apartials, gridDim.x, 1, false, i, L, g, epoch)) return;
     if (!L.st.active) break;
-    if (blocked) {
-      if (!seed_update_step_blk<double>(b, bl, fn, vi, i, L, g, epoch, bpart, s_red)) return;
-    } else if (!seed_update_step<double>(b, bl, fn, vi, i, L, g, epoch, bpart, sred, s_vals)) {
-      return;
-    }
+    if (!seed_update_step<double>(b, bl, fn, vi, i, L, g, epoch, bpart, s_red)) return;
     par ^= 1;
   }
   seed_leave<double>(b, L, par ? f2 : b.f, i_stop);
@@ -853,7 +764,9 @@ int persistent_grid(int kind, int sm_count, bool cg) {
     cudaGetLastError();
     return 0;
   }
-  const int cap = 2;
+  // the Wilson seed run works in operator tiles only (one owner block per SM):
+  // more blocks would only add barrier arrivals
+  const int cap = (!cg && kind == 1) ? 1 : 2;
   if (per_sm > cap) per_sm = cap;
   return per_sm * sm_count;
 }

@@ -268,11 +268,10 @@ void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, c
 // on leaving with i == i_stop it forms v_i in V and vcur for the step-by-step
 // path.  CG: runs lockstep iterations until no column is active.  Both return
 // cudaErrorCooperativeLaunchTooLarge and friends from the launch, and report a
-// barrier time-out through GridSync::error.  nrhs <= kPersistMaxRhs, nc <= 32.
-constexpr int kPersistMaxRhs = 16;
+// barrier time-out through GridSync::error.  CG: nc <= 32.
 constexpr int kPersistMaxCols = 32;
 int persistent_grid(int kind, int sm_count, bool cg);
-// tpart: one double per 32-site tile
+// tpart: three doubles per 32-site tile
 cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, GridSync g,
                                    double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
 cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g, double *bpart,
