@@ -45,14 +45,17 @@ struct HostStatus {   // pinned, written by cudaMemcpyAsync from SeedState
   int32_t i, active, stop_reason, converged_at;
 };
 
+constexpr int kCgBranches = 3;   // concurrent branches of a lockstep CG graph (cg_branches)
+
 }  // namespace
 
 struct seed_ctx {
   int device = 0;
   cudaStream_t user_stream = nullptr;
   cudaStream_t cs = nullptr;           // internal stream (capturable)
-  cudaStream_t cs2 = nullptr;          // second branch of the lockstep CG graphs
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t csb[kCgBranches - 1] = {};   // further branches of the lockstep CG graphs
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kCgBranches - 1] = {};
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;
   int kind = 0;                        // 0 = CSR, 1 = Wilson
@@ -214,7 +217,7 @@ seed_status alloc_common(seed_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->delta_hist, sizeof(double) * (m + 2)));
   TRY(dalloc(ctx, &ctx->gamma_hist, sizeof(double) * (m + 2)));
   TRY(dalloc(ctx, &ctx->eta, sizeof(double2) * kMaxRhs));
-  TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs) * 2));   // [1]: second branch of the CG graphs
+  TRY(dalloc(ctx, &ctx->call, sizeof(CallArgs) * kCgBranches));   // [b]: branch b of the CG graphs
   TRY(dalloc(ctx, &ctx->colnorm, sizeof(double) * kMaxRhs));
   // block partials: seed dots use up to 5 chunks x vec_blocks(n) x 32; lockstep kernels nc x blocks x 2
   TRY(dalloc(ctx, &ctx->partials, sizeof(double) * kPartials));
@@ -229,8 +232,8 @@ seed_status alloc_common(seed_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->H, sizeof(double2) * (size_t)(m + 1) * 2));
   TRY(dalloc(ctx, &ctx->cg_d, sizeof(double) * kCgDoubles * kMaxRhs));
   TRY(dalloc(ctx, &ctx->cg_i, sizeof(int32_t) * kCgInts * kMaxRhs));
-  // call32: [0] seed run (X = E), [1] mixed CG, [2] its second graph branch
-  if (ctx->precision == 1) TRY(dalloc(ctx, &ctx->call32, sizeof(CallArgs) * 3));
+  // call32: [0] seed run (X = E), [1 + b] branch b of the mixed CG graphs
+  if (ctx->precision == 1) TRY(dalloc(ctx, &ctx->call32, sizeof(CallArgs) * (1 + kCgBranches)));
   CU(cudaMemsetAsync(ctx->tickets, 0, sizeof(unsigned) * 256, ctx->cs));
   CU(cudaMemsetAsync(ctx->w, 0, n * es, ctx->cs));
   CU(cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * 2 * kMaxRhs));
@@ -645,11 +648,43 @@ CgCols cg_sub(const CgCols &c, int c0, int nc) {
   return v;
 }
 
-// Lockstep CG graphs split the columns into two independent branches (kCgSplit
-// columns or more): the branches drift against each other, so one branch's
-// vector kernels and kernel tails overlap the other's operator applies.
-constexpr int kCgSplit = 4;
-int cg_split_at(int nc) { return nc >= kCgSplit ? (nc + 1) / 2 : nc; }
+// Lockstep CG graphs split the columns into up to kCgBranches independent
+// branches (two columns or more each), one stream each: the branches drift
+// against each other, so one branch's vector kernels and kernel tails overlap
+// the others' operator applies.  Branch b owns columns start[b] .. start[b+1]-1,
+// CallArgs slot b, the b-th part of the partials and the tickets shifted by
+// start[b].
+int cg_branches(int nc, int start[kCgBranches + 1]) {
+  int nb = nc / 2;
+  if (nb > kCgBranches) nb = kCgBranches;
+  if (nb < 1) nb = 1;
+  for (int b = 0; b <= nb; ++b) start[b] = b * nc / nb;
+  return nb;
+}
+
+// Captures `len` iterations of issue(view, first column, stream, branch) on
+// every branch: a fork from cs, the branches, a join back into cs.
+template <class F>
+int issue_cg_branches(seed_ctx *ctx, const CgCols &c, int len, F &&issue) {
+  int start[kCgBranches + 1];
+  const int nb = cg_branches(c.nc, start);
+  int k = 0;
+  if (nb > 1) {
+    cudaEventRecord(ctx->ev_fork, ctx->cs);   // a failed call invalidates the capture (reported at its end)
+    for (int b = 1; b < nb; ++b) {
+      cudaStream_t s = ctx->csb[b - 1];
+      cudaStreamWaitEvent(s, ctx->ev_fork, 0);
+      const CgCols v = cg_sub(c, start[b], start[b + 1] - start[b]);
+      for (int q = 0; q < len; ++q) k += issue(v, start[b], s, b);
+      cudaEventRecord(ctx->ev_join[b - 1], s);
+    }
+  }
+  const CgCols v0 = cg_sub(c, 0, start[1]);
+  for (int q = 0; q < len; ++q) k += issue(v0, 0, ctx->cs, 0);
+  for (int b = 1; b < nb; ++b) cudaStreamWaitEvent(ctx->cs, ctx->ev_join[b - 1], 0);
+  return k;
+}
+double *branch_partials(seed_ctx *ctx, int b) { return ctx->partials + (int64_t)b * (kPartials / kCgBranches); }
 
 CgCols cg_cols(seed_ctx *ctx, int nc) {
   CgCols c;
@@ -704,23 +739,10 @@ seed_status launch_cg_run(seed_ctx *ctx, const CgCols &c, int len) {
   if (it == ctx->graphs.end()) {
     GraphEntry g;
     cudaGraph_t graph;
-    const int h = cg_split_at(c.nc);
     CU(cudaStreamBeginCapture(ctx->cs, cudaStreamCaptureModeThreadLocal));
-    if (h < c.nc) {
-      // branch 2 on cs2: columns h .. nc-1, CallArgs slot 1, the upper half of
-      // the partials and tickets shifted past branch 1's columns
-      CU(cudaEventRecord(ctx->ev_fork, ctx->cs));
-      CU(cudaStreamWaitEvent(ctx->cs2, ctx->ev_fork, 0));
-      const CgCols cb = cg_sub(c, h, c.nc - h);
-      for (int q = 0; q < len; ++q)
-        g.kernels += issue_cg_iter<T>(ctx, cb, h, ctx->cs2, ctx->call + 1, ctx->partials + kPartials / 2,
-                                      ctx->tickets + h);
-      CU(cudaEventRecord(ctx->ev_join, ctx->cs2));
-    }
-    const CgCols ca = cg_sub(c, 0, h);
-    for (int q = 0; q < len; ++q)
-      g.kernels += issue_cg_iter<T>(ctx, ca, 0, ctx->cs, ctx->call, ctx->partials, ctx->tickets);
-    if (h < c.nc) CU(cudaStreamWaitEvent(ctx->cs, ctx->ev_join, 0));
+    g.kernels += issue_cg_branches(ctx, c, len, [&](const CgCols &v, int c0, cudaStream_t s, int b) {
+      return issue_cg_iter<T>(ctx, v, c0, s, ctx->call + b, branch_partials(ctx, b), ctx->tickets + c0);
+    });
     CU(cudaStreamEndCapture(ctx->cs, &graph));
     cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -742,9 +764,12 @@ seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx,
   if (nc <= 0) return SEED_OK;
   TRY(ensure_cols(ctx, nc));
   CU(cudaEventRecord(ctx->t2, ctx->cs));
-  // slot 1: the second branch of the CG graphs (columns from cg_split_at(nc) on)
-  const CallArgs ca[2] = {{Xc, ldx, 0}, {Xc, ldx, cg_split_at(nc)}};
-  CU(cudaMemcpyAsync(ctx->call, ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  // slot b: branch b of the CG graphs (its first column)
+  int start[kCgBranches + 1];
+  const int nb = cg_branches(nc, start);
+  CallArgs ca[kCgBranches];
+  for (int b = 0; b < nb; ++b) ca[b] = CallArgs{Xc, ldx, start[b]};
+  CU(cudaMemcpyAsync(ctx->call, ca, sizeof(CallArgs) * nb, cudaMemcpyHostToDevice, ctx->cs));
   const CgCols c = cg_cols(ctx, nc);
   // K7: true residual of the seeded systems, then p = r
   int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
@@ -1154,10 +1179,12 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
   c.tol = tol;
   c.tol_check = tol;
   T32 *E = E_cols<T32>(ctx) + (int64_t)c0 * ld;
-  // CG column c corrects system c0 + c + 1; slot 2: the graphs' second branch
-  const int h = cg_split_at(nc);
-  const CallArgs ca[2] = {{(void *)E_cols<T32>(ctx), ld, c0}, {(void *)E_cols<T32>(ctx), ld, c0 + h}};
-  CU(cudaMemcpyAsync(ctx->call32 + 1, ca, sizeof(ca), cudaMemcpyHostToDevice, ctx->cs));
+  // CG column c corrects system c0 + c + 1; slot 1 + b: branch b of the graphs
+  int start[kCgBranches + 1];
+  const int nb = cg_branches(nc, start);
+  CallArgs ca[kCgBranches];
+  for (int b = 0; b < nb; ++b) ca[b] = CallArgs{(void *)E_cols<T32>(ctx), ld, c0 + start[b]};
+  CU(cudaMemcpyAsync(ctx->call32 + 1, ca, sizeof(CallArgs) * nb, cudaMemcpyHostToDevice, ctx->cs));
   int kern = apply_A(ctx, Xc, ldx, ctx->Q, ld, nc, nullptr);
   launch_mixed_init<T64, T32>(nv, lay, Bc, ldb, (const T64 *)ctx->Q, ld, (T32 *)ctx->R32, (T32 *)ctx->P32, E, ld, c,
                               ctx->partials, ctx->tickets, ctx->cs);
@@ -1170,23 +1197,9 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
   cudaEvent_t evs[2] = {nullptr, nullptr};
   for (;;) {
     TRY(run_graph(ctx, key, [&] {
-      // two branches on disjoint columns (see cg_split_at); a failed call here
-      // invalidates the capture, which cudaStreamEndCapture reports
-      int k = 0;
-      if (h < nc) {
-        cudaEventRecord(ctx->ev_fork, ctx->cs);
-        cudaStreamWaitEvent(ctx->cs2, ctx->ev_fork, 0);
-        const CgCols cb = cg_sub(c, h, nc - h);
-        for (int q = 0; q < L; ++q)
-          k += issue_mixed_iter<T32>(ctx, cb, h, ctx->cs2, ctx->call32 + 2, ctx->partials + kPartials / 2,
-                                     ctx->tickets + h);
-        cudaEventRecord(ctx->ev_join, ctx->cs2);
-      }
-      const CgCols ca0 = cg_sub(c, 0, h);
-      for (int q = 0; q < L; ++q)
-        k += issue_mixed_iter<T32>(ctx, ca0, 0, ctx->cs, ctx->call32 + 1, ctx->partials, ctx->tickets);
-      if (h < nc) cudaStreamWaitEvent(ctx->cs, ctx->ev_join, 0);
-      return k;
+      return issue_cg_branches(ctx, c, L, [&](const CgCols &v, int cb0, cudaStream_t s, int b) {
+        return issue_mixed_iter<T32>(ctx, v, cb0, s, ctx->call32 + 1 + b, branch_partials(ctx, b), ctx->tickets + cb0);
+      });
     }));
     // reliable updates (direct launches: B and X are this call's buffers)
     launch_mixed_flag(c, ctx->cs);
@@ -1385,9 +1398,11 @@ seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream strea
   CU(cudaGetDevice(&ctx->device));
   ctx->user_stream = (cudaStream_t)stream;
   CU(cudaStreamCreateWithFlags(&ctx->cs, cudaStreamNonBlocking));
-  CU(cudaStreamCreateWithFlags(&ctx->cs2, cudaStreamNonBlocking));
+  for (int b = 0; b < kCgBranches - 1; ++b) {
+    CU(cudaStreamCreateWithFlags(&ctx->csb[b], cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
+  }
   CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-  CU(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
   CU(cudaEventCreate(&ctx->t0));
   CU(cudaEventCreate(&ctx->t1));
@@ -1411,10 +1426,13 @@ void destroy(seed_ctx *ctx) {
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->h_gerr) cudaFreeHost(ctx->h_gerr);
-  cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3, ctx->ev_fork, ctx->ev_join};
+  cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3, ctx->ev_fork};
   for (auto e : evs)
     if (e) cudaEventDestroy(e);
-  if (ctx->cs2) cudaStreamDestroy(ctx->cs2);
+  for (int b = 0; b < kCgBranches - 1; ++b) {
+    if (ctx->ev_join[b]) cudaEventDestroy(ctx->ev_join[b]);
+    if (ctx->csb[b]) cudaStreamDestroy(ctx->csb[b]);
+  }
   if (ctx->cs) cudaStreamDestroy(ctx->cs);
   delete ctx;
 }
