@@ -47,6 +47,13 @@ except (OSError, ValueError):
 DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0, "6e70bd4a297626c1": 11.207424e6 + 0.0}
 
 
+def cg_branch_cols(nc, branches=3):
+    """Columns per branch of the library's lockstep CG graphs (two or more columns per branch)."""
+    nb = max(1, min(branches, nc // 2))
+    start = [b * nc // nb for b in range(nb + 1)]
+    return [start[b + 1] - start[b] for b in range(nb)]
+
+
 def fp32_kernel_name(sites):
     """The FP32 hopping kernel the library runs on a lattice of this many sites."""
     return "k_dslash32_site" if sites >= 65536 else "k_dslash32"
@@ -429,7 +436,9 @@ def run_ours(args):
         peak = FP64_PEAK_GFLOPS / 1e3
         roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": dslash_traffic() if dims == WL["dims"] else None,
-                "kernel": "k_dslash<+1> (Wilson D, FP64 complex), %d columns" % ncols,
+                "kernel": "k_dslash<+1> (Wilson D, FP64 complex), %d columns in one launch: the work of one "
+                          "CG half-iteration, which the CG graphs issue as %s-column launches on concurrent "
+                          "streams" % (ncols, "+".join(str(x) for x in cg_branch_cols(ncols))),
                 "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
                 "flops_per_launch": flops,
                 "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from unit counts and "
@@ -442,7 +451,9 @@ def run_ours(args):
         peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "%s<+1> (Wilson D, FP32 complex), %d columns" % (fp32_kernel_name(vol), ncols),
+                "kernel": "%s<+1> (Wilson D, FP32 complex), %d columns in one launch: the work of one CG "
+                          "half-iteration, which the CG graphs issue as %s-column launches on concurrent streams"
+                          % (fp32_kernel_name(vol), ncols, "+".join(str(x) for x in cg_branch_cols(ncols))),
                 "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
                 "bytes_per_launch": b, "l2_resident": b < L2_BYTES,
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
@@ -489,6 +500,8 @@ def run_ours(args):
                           "parallelism": "replicas" if world > 1 else "single-gpu",
                           "l2": "flushed (512 MB write) before every step, outside the timed events",
                           "seed_steps": i1[0]["iters"], "cg_iters": [i["iters"] for i in i2[1:]],
+                          "last_step_phase_ms": {"seed_solve_first": round(st1["ms_seed"], 3),
+                                                 "seed_solve_rest": round(st1["ms_rest"], 3)},
                           "wall_s_timed_region": round(t_wall1 - t_wall0, 3),
                           "step_ms": [round(x, 3) for x in step_ms], "converged": ok},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
