@@ -160,7 +160,10 @@ def tridiag_dev(a, b, a_ref, b_ref):
     return max(da, db)
 
 
-def compare_full(orc_res, info1, info2, Xs, X, label, seeded_tol=REL_X, final_tol=REL_X):
+def compare_full(orc_res, info1, info2, Xs, X, label, seeded_tol=REL_X, final_tol=REL_X, min_counted=0):
+    """min_counted: compare CG iteration counts only where the oracle's is at
+    least this (a system whose seeded residual is already near the tolerance
+    can need 1 or 6 iterations depending on rounding of the seeding)."""
     s = orc_res["seed"]
     assert info1[0]["iters"] == s["iters"], (label, info1[0]["iters"], s["iters"])
     assert relerr(X[:, 0], s["X"][:, 0]) < REL_X
@@ -169,11 +172,12 @@ def compare_full(orc_res, info1, info2, Xs, X, label, seeded_tol=REL_X, final_to
     for j, r in enumerate(orc_res["rest"], start=1):
         g = info2[j]
         assert g["converged"] == 1
-        assert abs(g["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (label, j, g["iters"], r["iters"])
+        if r["iters"] >= min_counted:
+            assert abs(g["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (label, j, g["iters"], r["iters"])
         if g["iters"] == r["iters"]:
             assert relerr(X[:, j], r["x"]) < final_tol, (label, j, relerr(X[:, j], r["x"]), final_tol)
         else:
-            # one iteration apart: both meet the tolerance; solutions agree to the CG accuracy
+            # counts apart: both meet the tolerance; solutions agree to the CG accuracy
             assert relerr(X[:, j], r["x"]) < max(1e-6, final_tol), (label, j)
         assert g["true_relres"] <= 1.5e-8
 
@@ -222,6 +226,32 @@ def test_seed_wilson_small(seedlib, orc, freq, passes, kernel_path):
                                        reorth_passes=passes, tol=1e-12)
     compare_full(ref, info1, info2, Xs, X, "wilson-small-%d" % freq, seeded_tol=max(REL_X, 10 * s_seed),
                  final_tol=max(REL_X, 10 * s_final))
+
+
+@pytest.mark.parametrize("kernel_path", [0, 1])
+def test_blocked_seeding_long_run_many_rhs(seedlib, orc, kernel_path):
+    """Without reorthogonalization the 3x4x5x6 lattice at kappa 0.15 needs 219
+    seed steps: on path 0 the persistent run is cut into segments of at most
+    128 steps (one seeding block each), on path 1 into graph runs of 16; 20
+    right-hand sides (19 seeded systems: five 4-column tiles of G, five
+    4-column chunks of the X update).  Everything against the oracle as in
+    test_seed_wilson_small, except that CG counts are compared only where the
+    oracle needs 20 or more: without reorthogonalization the seeded vectors
+    carry the oracle's own one-ulp sensitivity (checked), and systems seeded
+    almost to tolerance finish in anywhere from 1 to a few iterations."""
+    dims, kappa = (3, 4, 5, 6), 0.15
+    U = I.random_su3_links(dims, 0.3, seed=7)
+    eta = I.point_sources(dims, 20, site=17)
+    B = np.stack([orc.wilson_dslash(dims, kappa, 1, -1, U, eta[:, j]) for j in range(20)], axis=1)
+    ctx = wilson_ctx(seedlib, dims, kappa, U, bc_t=1, m_max=3000, reorth_freq=0, tol_seed=1e-12, tol_rest=1e-8,
+                     kernel_path=kernel_path)
+    info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    ref = orc.seed_solve_all(op, B, m_max=3000, reorth_freq=0, tol_seed=1e-12, tol_rest=1e-8)
+    assert ref["seed"]["iters"] > 128
+    s_seed, s_final = self_sensitivity(orc, op, B, ref, cols=(1, 19), m_max=3000, reorth_freq=0, tol=1e-12)
+    compare_full(ref, info1, info2, Xs, X, "wilson-long-%d" % kernel_path, seeded_tol=max(REL_X, 10 * s_seed),
+                 final_tol=max(REL_X, 10 * s_final), min_counted=20)
 
 
 _WORKLOAD_REF = {}
@@ -407,25 +437,27 @@ def test_long_vectors_two_level_reductions(seedlib, orc, precision):
         assert abs(info2[j]["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (j, info2[j]["iters"], r["iters"])
 
 
-@pytest.mark.parametrize("nrhs", [17, 64])
-def test_many_rhs_multichunk_dots(seedlib, orc, nrhs):
+@pytest.mark.parametrize("nrhs,freq", [(17, 1), (64, 1), (64, 10)])
+def test_many_rhs_multichunk_dots(seedlib, orc, nrhs, freq):
     """nrhs = 17 (just past the persistent kernels' 16) and 64 (the maximum):
     the seed dot products run in chunks of 15 systems (5 chunks at 64).  20x19
     Laplacian (distinct eigenvalues), Gaussian right-hand sides, full
-    reorthogonalization: the seed's steps equal and x^1 within 1e-9; every
+    reorthogonalization (freq 1: the streaming seeding) or every 10 steps (the
+    blocked seeding: 63 seeded systems in sixteen 4-column tiles of G, on the
+    persistent CSR run): the seed's steps equal and x^1 within 1e-9; every
     seeded x^j within max(1e-9, 10 x the oracle's one-ulp sensitivity); every
     CG count within 5 % and every true residual within 1.5 tol."""
     rp, ci, v = I.laplacian_2d_csr(20, 19)
     n = 380
     B = I.gaussian_rhs(n, nrhs, seed=11)
-    prm = dict(m_max=400, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8)
+    prm = dict(m_max=400, reorth_freq=freq, tol_seed=1e-12, tol_rest=1e-8)
     ctx = csr_ctx(seedlib, rp, ci, v, **prm)
     info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
     op = orc.Operator.csr(rp, ci, v)
-    ref = orc.seed_solve_all(op, B, m_max=400, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8)
+    ref = orc.seed_solve_all(op, B, m_max=400, reorth_freq=freq, tol_seed=1e-12, tol_rest=1e-8)
     assert info1[0]["iters"] == ref["seed"]["iters"]
     assert relerr(X[:, 0].real, ref["seed"]["X"][:, 0].real) < REL_X
-    sens = seeded_only_sensitivity(orc, op, B, m_max=400, reorth_freq=1, tol=1e-12)
+    sens = seeded_only_sensitivity(orc, op, B, m_max=400, reorth_freq=freq, tol=1e-12)
     assert relerr(Xs[:, 1:].real, ref["X_seeded"][:, 1:].real) < max(REL_X, 10 * sens)
     for j, r in enumerate(ref["rest"], start=1):
         assert abs(info2[j]["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (j, info2[j]["iters"], r["iters"])
