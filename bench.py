@@ -481,7 +481,7 @@ def run_ours(args):
         e2e_v = statistics.mean(e2e_ms)
         e2e_v = max_over_ranks(e2e_v, dist, dev)
         e2e = {"value": round(e2e_v, 3), "unit": "ms", "h2d_bytes_per_step": int(eta_pin.numel() * 16),
-               "d2h_bytes_per_step": int(x_pin.numel() * 16)}
+               "d2h_bytes_per_step": int(x_pin.numel() * 16), "step_ms": [round(x, 3) for x in e2e_ms]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and default_wl:
