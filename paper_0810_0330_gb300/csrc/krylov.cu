@@ -215,6 +215,32 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
   if (threadIdx.x == 0) seed_step_scalars(b, i, s_alpha, sums);
 }
 
+// Step 5 and the scalars of steps 3/6 when no g^j is formed here (blocked
+// seeding, or system 1 alone): f = A v_i - beta_{i-1} v_{i-1},
+// alpha_i = Re(v_i^H f), one value per block summed in block order by the last.
+template <class T>
+__global__ void __launch_bounds__(NT) k_seed_alpha(SeedBufs<T> b) {
+  SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double sm[NT / 32];
+  const int i = st->i;
+  const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
+  const T *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+  const double bp = (i > 1) ? st->beta_prev : 0.0;
+  typename Sc<T>::A acc = 0;
+  GRID_STRIDE(e, b.n) {
+    const T fe = (i > 1) ? Sc<T>::axpy(-bp, vm[e], b.u[e]) : b.u[e];
+    b.f[e] = fe;
+    acc = Sc<T>::redot(vi[e], fe, acc);
+  }
+  double v[1] = {(double)acc};
+  block_sum<1, NT>(v, sm);
+  if (threadIdx.x == 0) b.partials[blockIdx.x] = v[0];
+  if (!last_block_done(b.tickets + kSeedTicket, gridDim.x)) return;
+  const double a = sum_partials<NT>(b.partials, gridDim.x, 1, 0, sm);
+  if (threadIdx.x == 0) seed_step_scalars(b, i, a, nullptr);
+}
+
 // Steps 5 (f -= alpha_i v_i), 6 (w_i, x^1) and 7 (x^j), plus ||f||^2 when this
 // step has no reorthogonalization.  Blocked seeding (b.Wb set): w_i also goes
 // to column i - blk0 of Wb and x^2..x^p wait for the block's flush.
@@ -482,7 +508,8 @@ void launch_seed_normalize(const SeedBufs<T> &b, cudaStream_t s) {
 }
 template <class T>
 void launch_seed_dots(const SeedBufs<T> &b, cudaStream_t s) {
-  k_seed_dots<T><<<b.nblocks, NT, 0, s>>>(b);
+  if (b.Wb != nullptr || b.nrhs <= 1) k_seed_alpha<T><<<b.nblocks, NT, 0, s>>>(b);
+  else k_seed_dots<T><<<b.nblocks, NT, 0, s>>>(b);
 }
 template <class T>
 void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s) {

@@ -64,16 +64,26 @@ __global__ void __launch_bounds__(NT) k_blk_dots(SeedBufs<T> b, BlockBufs k) {
     for (int qq = 0; qq < kBQ; ++qq)
 #pragma unroll
       for (int jj = 0; jj < kBJ; ++jj) acc[qq][jj] = Sc<T>::zero2();
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += NT) {
-      T r[kBJ];
+    // two rows per thread and iteration: twice the loads in flight
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += 2 * NT) {
+      const int64_t row2 = row + NT;
+      const bool two = row2 < r1;
+      T r[kBJ], r2[kBJ];
 #pragma unroll
-      for (int jj = 0; jj < kBJ; ++jj) r[jj] = jj < njj ? Rj[(int64_t)jj * b.ldr + row] : Sc<T>::zero();
+      for (int jj = 0; jj < kBJ; ++jj) {
+        r[jj] = jj < njj ? Rj[(int64_t)jj * b.ldr + row] : Sc<T>::zero();
+        r2[jj] = (two && jj < njj) ? Rj[(int64_t)jj * b.ldr + row2] : Sc<T>::zero();
+      }
 #pragma unroll
       for (int qq = 0; qq < kBQ; ++qq) {
         if (qq < nq) {
           const T v = Vq[(int64_t)qq * b.ldv + row];
+          const T v2 = two ? Vq[(int64_t)qq * b.ldv + row2] : Sc<T>::zero();
 #pragma unroll
-          for (int jj = 0; jj < kBJ; ++jj) acc[qq][jj] = Sc<T>::dotc(v, r[jj], acc[qq][jj]);
+          for (int jj = 0; jj < kBJ; ++jj) {
+            acc[qq][jj] = Sc<T>::dotc(v, r[jj], acc[qq][jj]);
+            acc[qq][jj] = Sc<T>::dotc(v2, r2[jj], acc[qq][jj]);
+          }
         }
       }
     }
