@@ -170,15 +170,15 @@ def test_mixed_wilson_small(seedlib, orc, freq):
 def test_mixed_wilson_large_lattice(seedlib, orc):
     """17x17x15x16 = 69360 sites (one thread per site in the FP32 operator,
     and a site count that is not a multiple of 32, so the solver's tiled FP32
-    vectors carry padding), kappa 0.10, antiperiodic t, 2 Gaussian RHS.  Both
-    systems' FP64 true residuals, recomputed by the oracle's operator, meet
-    their tolerances, and the mixed solve needs at most 30 % more CG
+    vectors carry padding), kappa 0.10, antiperiodic t, 3 Gaussian RHS.
+    Every system's FP64 true residual, recomputed by the oracle's operator,
+    meets its tolerance, and the mixed solve needs at most 30 % more CG
     iterations than the FP64 solve of the same systems (a wrong FP32 operator
     would show up as slower or stalled convergence between reliable updates)."""
     dims, kappa = (17, 17, 15, 16), 0.10
     U = I.random_su3_links(dims, 0.3, seed=11)
     n = 12 * I.lattice_sites(dims)
-    B = I.gaussian_rhs(n, 2, seed=4, complex_=True)
+    B = I.gaussian_rhs(n, 3, seed=4, complex_=True)
     prm = dict(m_max=400, reorth_freq=10, tol_seed=1e-9, tol_rest=1e-8)
     out = {}
     for prec in (0, 1):
@@ -188,10 +188,11 @@ def test_mixed_wilson_large_lattice(seedlib, orc):
     op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
     i1, i2, X = out[1]
     rr = true_relres(op, B, X)
-    assert rr[0] <= 1.01 * 1e-9 and rr[1] <= 1.01 * 1e-8, rr
-    assert i1[0]["converged"] == 1 and i2[1]["converged"] == 1
-    it64 = out[0][1][1]["iters"]
-    assert i2[1]["iters"] <= 1.3 * it64 + 2, (i2[1]["iters"], it64)
+    assert rr[0] <= 1.01 * 1e-9 and np.all(rr[1:] <= 1.01 * 1e-8), rr
+    assert i1[0]["converged"] == 1 and all(i["converged"] for i in i2[1:])
+    for j in (1, 2):
+        it64 = out[0][1][j]["iters"]
+        assert i2[j]["iters"] <= 1.3 * it64 + 2, (j, i2[j]["iters"], it64)
 
 
 @pytest.mark.slow
