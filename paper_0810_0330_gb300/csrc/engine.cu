@@ -436,6 +436,16 @@ int run_length(const seed_params &p) {
   return best >= 8 ? best : 16;
 }
 
+// Blocks of a persistent CSR seed run: about 8 rows per thread, at least 16
+// blocks, at most the occupancy-derived grid.  Small problems get small grids
+// (cheaper barriers, and in a batch several problems' runs fit side by side).
+int csr_seed_grid(const seed_ctx *ctx) {
+  int64_t b = (ctx->n + 128 * 8 - 1) / (128 * 8);
+  if (b < 16) b = 16;
+  if (b > ctx->pgrid) b = ctx->pgrid;
+  return (int)b;
+}
+
 bool use_persistent_seed(seed_ctx *ctx, int nrhs) {
   const int f = ctx->prm.reorth_freq;
   return ctx->allow_persistent && ctx->pgrid > 0 && (f == 0 || f >= 8);
@@ -507,7 +517,7 @@ seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
       e = launch_seed_run_wilson(b, ctx->wil, (double2 *)ctx->T, g, ctx->partials, ctx->tpart, i_stop, ctx->pgrid,
                                  ctx->cs);
     else
-      e = launch_seed_run_csr(b, ctx->csr, (double *)ctx->f2, g, ctx->partials, i_stop, ctx->pgrid, ctx->cs);
+      e = launch_seed_run_csr(b, ctx->csr, (double *)ctx->f2, g, ctx->partials, i_stop, csr_seed_grid(ctx), ctx->cs);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, SEED_ECUDA, std::string("persistent seed launch: ") + cudaGetErrorString(e));
@@ -1889,9 +1899,10 @@ seed_status seed_batch_solve(seed_ctx *const *ctxs, const void *const *B, const 
         st[i] = fail(c, SEED_ECUDA, "cudaSetDevice failed in a batch worker");
         continue;
       }
-      // cooperative (persistent) kernels of different problems are not run side by side
+      // persistent seed runs of different problems may run side by side (each
+      // waits only on its own blocks); the persistent CG stays off in a batch
       const bool p0 = c->allow_persistent, p1 = c->allow_persistent_cg;
-      c->allow_persistent = c->allow_persistent_cg = false;
+      c->allow_persistent_cg = false;
       seed_info *inf = info ? info[i] : nullptr;
       st[i] = seed_solve_first(c, B[i], ldb[i], X[i], ldx[i], nrhs[i], inf);
       if (st[i] == SEED_OK) st[i] = seed_solve_rest(c, B[i], ldb[i], X[i], ldx[i], nrhs[i], inf);

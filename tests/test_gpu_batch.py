@@ -2,8 +2,9 @@
 
  * A batch of independent shifted 2-d / 3-d Laplacians with different sizes
    and right-hand side counts gives, problem by problem, bitwise the results
-   of solving each problem alone with the same parameters on the step-kernel
-   path (kernel_path 1): the batch only changes when the work runs.
+   of solving each problem alone with the same parameters, on the step-kernel
+   path (kernel_path 1) and with persistent seed runs side by side
+   (kernel_path 0): the batch only changes when the work runs.
  * Two problems of the batch against the oracle: seed step counts equal,
    CG iteration counts within 5 %, true residuals <= 1.5 tol_rest.
  * Every autotuned launch shape gives the apply to 1e-13 of the oracle's.
@@ -34,18 +35,20 @@ def make(seedlib, p, **prm):
     return ctx, (rp, ci, v), B
 
 
-def test_batch_equals_solo_solves_and_oracle(seedlib, orc):
+@pytest.mark.parametrize("kernel_path", [1, 0])
+def test_batch_equals_solo_solves_and_oracle(seedlib, orc, kernel_path):
     probs = I.batch_problems(count=7, n_min=300, n_max=20000, seed=3)
     probs[1] = dict(probs[1], nrhs=1)          # a single right-hand side in the mix
+    prm = dict(PRM, kernel_path=kernel_path)
     ctxs, ops, Bs, Xs = [], [], [], []
     for p in probs:
-        c, op, B = make(seedlib, p, **PRM)
+        c, op, B = make(seedlib, p, **prm)
         ctxs.append(c), ops.append(op), Bs.append(dev(B))
         Xs.append(torch.full_like(Bs[-1].t(), 7.0).t())   # overwritten (x0_zero)
     infos = seedlib.seed_batch_solve(ctxs, Bs, Xs, workers=4)
     torch.cuda.synchronize()
     for i, p in enumerate(probs):
-        c, _, _ = make(seedlib, p, **PRM)
+        c, _, _ = make(seedlib, p, **prm)
         X = torch.zeros_like(Bs[i].t()).t()
         a = seedlib.seed_solve_first(c, Bs[i], X)
         b = seedlib.seed_solve_rest(c, Bs[i], X)
