@@ -239,13 +239,16 @@ seed_status alloc_common(seed_ctx *ctx) {
   CU(cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * 2 * kMaxRhs));
   CU(cudaMallocHost(&ctx->h_status, sizeof(HostStatus) * 2));
   TRY(dalloc(ctx, &ctx->gsync, sizeof(unsigned) * kGridSyncWords));
+  // zeroed here too: the error flag is read after every persistent run, and
+  // cudaMalloc memory may hold an earlier allocation's bytes
+  CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
   TRY(dalloc(ctx, &ctx->f2, n * es));
   TRY(dalloc(ctx, &ctx->tpart, sizeof(double) * (size_t)(3 * ((n / 12 + 31) / 32) + 3)));
   CU(cudaMallocHost(&ctx->h_gerr, sizeof(int32_t) * 2));
   CU(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
   int coop = 0;
   CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
-  ctx->pgrid = coop ? persistent_grid(ctx->kind, ctx->sm_count, false) : 0;
+  ctx->pgrid = coop ? persistent_grid(ctx->kind, ctx->sm_count, false, ctx->precision == 1) : 0;
   ctx->pgrid_cg = coop ? persistent_grid(ctx->kind, ctx->sm_count, true) : 0;
   return SEED_OK;
 }
@@ -448,6 +451,11 @@ int csr_seed_grid(const seed_ctx *ctx) {
 
 bool use_persistent_seed(seed_ctx *ctx, int nrhs) {
   const int f = ctx->prm.reorth_freq;
+  // the FP32 Wilson run works in 32-site tiles of 4 warps, one block per SM:
+  // right for latency-bound small lattices; from 65536 sites on the step
+  // kernels (one thread per site, many blocks) keep more memory traffic in
+  // flight (16^3 x 32: seed phase 55 ms from graphs, 120 ms persistent)
+  if (ctx->precision == 1 && ctx->kind == 1 && ctx->wil32.sites >= 65536) return false;
   return ctx->allow_persistent && ctx->pgrid > 0 && (f == 0 || f >= 8);
 }
 
@@ -495,11 +503,13 @@ template <class T>
 seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
   const seed_params &p = ctx->prm;
   const GridSync g = grid_sync_bufs(ctx);
+  bool launched = false;   // the error flag is this call's only after one of its persistent runs
   for (;;) {
     CU(cudaMemcpyAsync(&ctx->h_status[0], &ctx->st->i, sizeof(HostStatus), cudaMemcpyDeviceToHost, ctx->cs));
     CU(cudaMemcpyAsync(ctx->h_gerr, g.error, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->cs));
     CU(cudaStreamSynchronize(ctx->cs));
-    if (*ctx->h_gerr) return fail(ctx, SEED_ETIMEOUT, "a grid barrier of the persistent seed kernel timed out");
+    if (launched && *ctx->h_gerr)
+      return fail(ctx, SEED_ETIMEOUT, "a grid barrier of the persistent seed kernel timed out");
     const HostStatus hs = ctx->h_status[0];
     if (!hs.active) break;
     const int i = hs.i;
@@ -513,15 +523,21 @@ seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
     if (b.Wb) i_stop = std::min(i_stop, i + kSeedBlock);   // every run starts a block (blk0 = i)
     CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
     cudaError_t e;
-    if constexpr (sizeof(T) == sizeof(double2))
+    if constexpr (std::is_same_v<T, double2>)
       e = launch_seed_run_wilson(b, ctx->wil, (double2 *)ctx->T, g, ctx->partials, ctx->tpart, i_stop, ctx->pgrid,
                                  ctx->cs);
-    else
+    else if constexpr (std::is_same_v<T, double>)
       e = launch_seed_run_csr(b, ctx->csr, (double *)ctx->f2, g, ctx->partials, i_stop, csr_seed_grid(ctx), ctx->cs);
+    else if constexpr (std::is_same_v<T, float2>)
+      e = launch_seed_run_wilson32(b, ctx->wil32, (float2 *)ctx->T32, g, ctx->tpart, i_stop, ctx->pgrid, ctx->cs);
+    else
+      e = launch_seed_run_csr32(b, ctx->csr32, (float *)ctx->f2, g, ctx->partials, i_stop, csr_seed_grid(ctx),
+                                ctx->cs);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, SEED_ECUDA, std::string("persistent seed launch: ") + cudaGetErrorString(e));
     }
+    launched = true;
     ctx->stats.kernel_launches += 1 + launch_seed_flush<T>(b, ctx->blk, ctx->cs);
   }
   return SEED_OK;
@@ -1288,7 +1304,11 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   launch_seed_normalize<T32>(b, ctx->cs);
   kern += 4;
   ctx->stats.kernel_launches += kern;
-  TRY(seed_graph_runs<T32>(ctx, nrhs));
+  if (use_persistent_seed(ctx, nrhs)) {
+    TRY(seed_persistent_segments<T32>(ctx, nrhs));
+  } else {
+    TRY(seed_graph_runs<T32>(ctx, nrhs));
+  }
   CU(cudaStreamSynchronize(ctx->cs));
   if (ctx->ev_out) {
     cudaEventDestroy(ctx->ev_out);
@@ -1404,7 +1424,7 @@ seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream strea
   ctx->allow_persistent = p->kernel_path != 1;
   ctx->allow_persistent_cg = p->kernel_path == 2 && p->precision == 0;
   ctx->precision = p->precision;
-  if (p->precision == 1) ctx->allow_persistent = false;   // the persistent kernels are FP64 only
+  // mixed precision: persistent seed runs in FP32, no persistent CG
   CU(cudaGetDevice(&ctx->device));
   ctx->user_stream = (cudaStream_t)stream;
   CU(cudaStreamCreateWithFlags(&ctx->cs, cudaStreamNonBlocking));

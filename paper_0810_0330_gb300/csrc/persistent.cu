@@ -407,6 +407,166 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
   local_store(b, L);
 }
 
+// ---------------------------------------------------------------------------
+// The same two-phase Wilson run for the mixed-precision path: FP32 copy of
+// the links (structure of arrays), FP32 vectors tiled by 32 sites (component
+// k of site s at ((s/32)*12 + k)*32 + s%32, padding sites zero), FP32 sums per
+// thread, FP64 block and grid sums and scalars.  Tiles cover the padding too,
+// so every element of v_i, t, f, w_i is written (zeros in the padding).
+// ---------------------------------------------------------------------------
+template <int MU, int S>
+SEED_DEV void site_mu32(const WilsonOp32 &op, const float2 *in, int64_t s, float2 (&acc)[12]) {
+  const int32_t nf = __ldg(op.nbr + 8 * s + 2 * MU);
+  const int32_t nb = __ldg(op.nbr + 8 * s + 2 * MU + 1);
+  unsigned negf = 0u, negb = 0u;
+  if (MU == 3 && op.bc_t) {
+    const int64_t t = s / ((int64_t)op.dims[0] * op.dims[1] * op.dims[2]);
+    if (t == op.dims[3] - 1) negf = CxBits<float2>::sign;
+    if (t == 0) negb = CxBits<float2>::sign;
+  }
+  const float2 *L = op.links + (int64_t)MU * 9 * op.sites;
+  float2 pf[12], pb[12], uf[9], ub[9];
+  // spinors with ordinary loads: the run rewrites them between barriers
+  const float2 *qf = in + ((int64_t)nf >> 5) * 384 + (nf & 31), *qb = in + ((int64_t)nb >> 5) * 384 + (nb & 31);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) pf[k] = qf[32 * k];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) uf[k] = __ldg(L + (int64_t)k * op.sites + s);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) pb[k] = qb[32 * k];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ub[k] = __ldg(L + (int64_t)k * op.sites + nb);
+  hop_pair_r<MU, S>(pf, uf, negf, pb, ub, negb, acc);
+}
+
+// hopping sums of the 32-site tile starting at s0 into sacc (zeros for padding sites)
+template <int S>
+SEED_DEV void wilson_tile32(const WilsonOp32 &op, const float2 *in, int64_t s0, float (*sacc)[24][kWilsonSites + 1]) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const int64_t s = s0 + lane;
+  float2 acc[12];
+  if (s < op.sites) {
+    switch (mu) {
+      case 0: site_mu32<0, S>(op, in, s, acc); break;
+      case 1: site_mu32<1, S>(op, in, s, acc); break;
+      case 2: site_mu32<2, S>(op, in, s, acc); break;
+      default: site_mu32<3, S>(op, in, s, acc); break;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    sacc[mu][2 * k][lane] = acc[k].x;
+    sacc[mu][2 * k + 1][lane] = acc[k].y;
+  }
+  __syncthreads();
+}
+SEED_DEV float2 tile_sum32(float (*sacc)[24][kWilsonSites + 1], int cc, int sl) {
+  return make_float2(((sacc[0][2 * cc][sl] + sacc[1][2 * cc][sl]) + sacc[2][2 * cc][sl]) + sacc[3][2 * cc][sl],
+                     ((sacc[0][2 * cc + 1][sl] + sacc[1][2 * cc + 1][sl]) + sacc[2][2 * cc + 1][sl]) +
+                         sacc[3][2 * cc + 1][sl]);
+}
+
+// tpart: 3 x tiles doubles, as k_seed_run_wilson
+__global__ void __launch_bounds__(PT) k_seed_run_wilson32(SeedBufs<float2> b, WilsonOp32 op, float2 *tbuf,
+                                                           GridSync g, double *tpart, int i_stop) {
+  __shared__ float sacc[4][24][kWilsonSites + 1];
+  __shared__ double s_red[2 * (PT / 32)];
+  __shared__ LocalSeed L;
+  const int tiles = (int)(b.n / 384);
+  const float mk = (float)(-op.kappa);
+  double *part1 = tpart, *part2 = tpart + 2 * (int64_t)tiles;
+  unsigned epoch = 0;
+  local_load(b, L);
+  const SeedBufs<float2> bl = local_bufs(b, L);
+  Owners own;
+  if (!register_owner(g, epoch, own)) return;
+  float2 *const X = reinterpret_cast<float2 *>(b.call->X);
+  for (;;) {
+    const int i = L.st.i;
+    if (!L.st.active || i >= i_stop) break;
+    if (block_full(b, L, i)) break;
+    const float inv_b = (float)L.st.inv_beta;
+    const float bp = (float)((i > 1) ? L.st.beta_prev : 0.0);
+    float2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
+    const float2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+    // phase 1: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
+    if (own.rank >= 0) {
+      for (int tile = own.rank; tile < tiles; tile += own.count) {
+        wilson_tile32<+1>(op, b.f, (int64_t)tile * kWilsonSites, sacc);
+        float ptt = 0.f, pvm = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int o = threadIdx.x + PT * k, cc = o >> 5, sl = o & 31;
+          const int64_t e = (int64_t)tile * 384 + o;
+          const float2 sum = tile_sum32(sacc, cc, sl);
+          const float2 fe = b.f[e];
+          const float2 v = make_float2(inv_b * fe.x, inv_b * fe.y);
+          vi[e] = v;
+          const float2 t = make_float2(fmaf(mk, inv_b * sum.x, v.x), fmaf(mk, inv_b * sum.y, v.y));
+          tbuf[e] = t;
+          ptt = fmaf(t.y, t.y, fmaf(t.x, t.x, ptt));
+          if (i > 1) {
+            const float2 m = vm[e];
+            pvm = fmaf(v.y, m.y, fmaf(v.x, m.x, pvm));
+          }
+        }
+        double vv[2] = {(double)ptt, (double)pvm};
+        block_sum<2, PT>(vv, s_red);   // ends with a CTA barrier: sacc is free again
+        if (threadIdx.x == 0) {
+          part1[2 * tile] = vv[0];
+          part1[2 * tile + 1] = vv[1];
+        }
+      }
+    }
+    if (!seed_alpha_step<float2>(bl, part1, tiles, 2, i > 1, i, L, g, epoch)) return;
+    if (!L.st.active) break;   // delta_i <= 0
+    // phase 2: u = D^H t, f, w_i, x^1 (FP32 correction), w_i into Wb, partials of ||f||^2
+    const float a = (float)L.st.alpha, zeta = (float)L.st.zeta, inv_d = (float)(1.0 / L.st.delta);
+    float2 *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
+    if (own.rank >= 0) {
+      for (int tile = own.rank; tile < tiles; tile += own.count) {
+        wilson_tile32<-1>(op, tbuf, (int64_t)tile * kWilsonSites, sacc);
+        float pff = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int o = threadIdx.x + PT * k, cc = o >> 5, sl = o & 31;
+          const int64_t e = (int64_t)tile * 384 + o;
+          const float2 sum = tile_sum32(sacc, cc, sl);
+          const float2 tv = tbuf[e], v = vi[e];
+          float2 f = make_float2(fmaf(mk, sum.x, tv.x), fmaf(mk, sum.y, tv.y));
+          if (i > 1) {
+            const float2 m = vm[e];
+            f = make_float2(fmaf(-bp, m.x, f.x), fmaf(-bp, m.y, f.y));
+          }
+          f = make_float2(fmaf(-a, v.x, f.x), fmaf(-a, v.y, f.y));
+          float2 w;
+          if (i > 1) {
+            const float2 wp = b.w[e];
+            w = make_float2(inv_d * fmaf(-bp, wp.x, v.x), inv_d * fmaf(-bp, wp.y, v.y));
+          } else {
+            w = make_float2(inv_d * v.x, inv_d * v.y);
+          }
+          b.f[e] = f;
+          b.w[e] = w;
+          if (wcol != nullptr) wcol[e] = w;
+          const float2 x = X[e];
+          X[e] = make_float2(fmaf(zeta, w.x, x.x), fmaf(zeta, w.y, x.y));
+          pff = fmaf(f.y, f.y, fmaf(f.x, f.x, pff));
+        }
+        double vv[1] = {(double)pff};
+        block_sum<1, PT>(vv, s_red);
+        if (threadIdx.x == 0) part2[tile] = vv[0];
+      }
+    }
+    if (!seed_beta_step<float2>(bl, part2, tiles, i, L, g, epoch)) return;
+  }
+  seed_leave<float2>(b, L, b.f, i_stop);
+  local_store(b, L);
+}
+
 // Phase 3 of the CSR run: f -= alpha_i v_i, w_i (also into column i - blk0 of
 // Wb), x^1 and ||f||^2; one value per block, reduced in block order by every
 // block after the barrier, then step 9.
@@ -435,34 +595,37 @@ SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f
   return seed_beta_step<T>(bl, bpart, gridDim.x, i, L, g, epoch);
 }
 
-// real CSR operator, three barriers per step: the apply reads f_cur (two
+// real CSR operator, two barriers per step: the apply reads f_cur (two
 // buffers alternate, since a row reads other rows' entries while writing its
-// own); alpha_i from block partials; then the update.
-__global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp op, double *f2, GridSync g,
-                                                      double *bpart, int i_stop) {
+// own); alpha_i from block partials; then the update.  T = double, or float
+// for the mixed-precision path (FP32 matrix values and vectors; per-thread
+// sums in FP32, block and grid sums and every scalar in FP64).
+template <class T>
+__global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<T> b, CsrOpT<T> op, T *f2, GridSync g, double *bpart,
+                                                      int i_stop) {
   __shared__ double s_red[PT / 32];
   __shared__ LocalSeed L;
   unsigned epoch = 0;
   int par = 0;
   local_load(b, L);
-  const SeedBufs<double> bl = local_bufs(b, L);
+  const SeedBufs<T> bl = local_bufs(b, L);
   for (;;) {
     const int i = L.st.i;
     if (!L.st.active || i >= i_stop) break;
     if (block_full(b, L, i)) break;
-    const double inv_b = L.st.inv_beta;
-    const double bp = (i > 1) ? L.st.beta_prev : 0.0;
-    double *fc = par ? f2 : b.f, *fn = par ? b.f : f2;
-    double *vi = b.V + (int64_t)(i - 1) * b.ldv;
-    const double *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
-    double apart = 0.0;
+    const T inv_b = (T)L.st.inv_beta;
+    const T bp = (T)((i > 1) ? L.st.beta_prev : 0.0);
+    T *fc = par ? f2 : b.f, *fn = par ? b.f : f2;
+    T *vi = b.V + (int64_t)(i - 1) * b.ldv;
+    const T *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+    T apart = 0;
     for (int64_t r = (int64_t)blockIdx.x * PT + threadIdx.x; r < b.n; r += (int64_t)gridDim.x * PT) {
       const int32_t k0 = __ldg(op.row_ptr + r), k1 = __ldg(op.row_ptr + r + 1);
-      double sum = 0.0;
+      T sum = 0;
       for (int32_t k = k0; k < k1; ++k) sum = fma(__ldg(op.vals + k), fc[__ldg(op.col_idx + k)], sum);
-      const double v = inv_b * fc[r];
+      const T v = inv_b * fc[r];
       vi[r] = v;
-      double u = inv_b * sum;
+      T u = inv_b * sum;
       if (i > 1) u = fma(-bp, vm[r], u);
       fn[r] = u;
       apart = fma(v, u, apart);
@@ -472,16 +635,16 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<double> b, CsrOp o
     // update partial)
     double *apartials = bpart + (int64_t)gridDim.x * 32;
     {
-      double vv[1] = {apart};
+      double vv[1] = {(double)apart};
       block_sum<1, PT>(vv, s_red);
       if (threadIdx.x == 0) apartials[blockIdx.x] = vv[0];   // by blockIdx: fixed order
     }
-    if (!seed_alpha_step<double>(bl, apartials, gridDim.x, 1, false, i, L, g, epoch)) return;
+    if (!seed_alpha_step<T>(bl, apartials, gridDim.x, 1, false, i, L, g, epoch)) return;
     if (!L.st.active) break;
-    if (!seed_update_step<double>(b, bl, fn, vi, i, L, g, epoch, bpart, s_red)) return;
+    if (!seed_update_step<T>(b, bl, fn, vi, i, L, g, epoch, bpart, s_red)) return;
     par ^= 1;
   }
-  seed_leave<double>(b, L, par ? f2 : b.f, i_stop);
+  seed_leave<T>(b, L, par ? f2 : b.f, i_stop);
   local_store(b, L);
 }
 
@@ -751,20 +914,17 @@ __global__ void __launch_bounds__(PT) k_cg_run_csr(CsrOp op, const CallArgs *cal
 // ---------------------------------------------------------------------------
 // Up to 2 blocks per SM (3 for the seed runs, with the kernel bounded to fit,
 // measured no faster on the 8^4 workload); 0 when the occupancy query fails.
-int persistent_grid(int kind, int sm_count, bool cg) {
+int persistent_grid(int kind, int sm_count, bool cg, bool fp32) {
   int per_sm = 0;
-  cudaError_t e;
-  if (!cg) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kind == 0 ? (const void *)k_seed_run_csr
-                                                                               : (const void *)k_seed_run_wilson,
-                                                             PT, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kind == 0 ? (const void *)k_cg_run_csr
-                                                                           : (const void *)k_cg_run_wilson,
-                                                         PT, 0);
-  if (e != cudaSuccess) {
+  const void *k;
+  if (cg) k = kind == 0 ? (const void *)k_cg_run_csr : (const void *)k_cg_run_wilson;
+  else if (fp32) k = kind == 0 ? (const void *)k_seed_run_csr<float> : (const void *)k_seed_run_wilson32;
+  else k = kind == 0 ? (const void *)k_seed_run_csr<double> : (const void *)k_seed_run_wilson;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PT, 0) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  // the Wilson seed run works in operator tiles only (one owner block per SM):
+  // the Wilson seed runs work in operator tiles only (one owner block per SM):
   // more blocks would only add barrier arrivals
   const int cap = (!cg && kind == 1) ? 1 : 2;
   if (per_sm > cap) per_sm = cap;
@@ -783,7 +943,21 @@ cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, doub
   SeedBufs<double> bb = b;
   CsrOp o = op;
   void *args[] = {&bb, &o, &f2, &g, &bpart, &i_stop};
-  return cudaLaunchCooperativeKernel((const void *)k_seed_run_csr, dim3(grid), dim3(PT), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_csr<double>, dim3(grid), dim3(PT), args, 0, s);
+}
+cudaError_t launch_seed_run_csr32(const SeedBufs<float> &b, const CsrOp32 &op, float *f2, GridSync g, double *bpart,
+                                  int i_stop, int grid, cudaStream_t s) {
+  SeedBufs<float> bb = b;
+  CsrOp32 o = op;
+  void *args[] = {&bb, &o, &f2, &g, &bpart, &i_stop};
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_csr<float>, dim3(grid), dim3(PT), args, 0, s);
+}
+cudaError_t launch_seed_run_wilson32(const SeedBufs<float2> &b, const WilsonOp32 &op, float2 *tbuf, GridSync g,
+                                     double *tpart, int i_stop, int grid, cudaStream_t s) {
+  SeedBufs<float2> bb = b;
+  WilsonOp32 o = op;
+  void *args[] = {&bb, &o, &tbuf, &g, &tpart, &i_stop};
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson32, dim3(grid), dim3(PT), args, 0, s);
 }
 cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,
                                  double2 *tbuf, int64_t ld, const CgCols &c, GridSync g, double *bpart, int grid,

@@ -270,12 +270,17 @@ void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, c
 // cudaErrorCooperativeLaunchTooLarge and friends from the launch, and report a
 // barrier time-out through GridSync::error.  CG: nc <= 32.
 constexpr int kPersistMaxCols = 32;
-int persistent_grid(int kind, int sm_count, bool cg);
+int persistent_grid(int kind, int sm_count, bool cg, bool fp32 = false);
 // tpart: three doubles per 32-site tile
 cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, GridSync g,
                                    double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
 cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g, double *bpart,
                                 int i_stop, int grid, cudaStream_t s);
+// mixed precision (FP32 vectors and operator copy, FP64 scalars)
+cudaError_t launch_seed_run_csr32(const SeedBufs<float> &b, const CsrOp32 &op, float *f2, GridSync g, double *bpart,
+                                  int i_stop, int grid, cudaStream_t s);
+cudaError_t launch_seed_run_wilson32(const SeedBufs<float2> &b, const WilsonOp32 &op, float2 *tbuf, GridSync g,
+                                     double *tpart, int i_stop, int grid, cudaStream_t s);
 cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,
                                  double2 *tbuf, int64_t ld, const CgCols &c, GridSync g, double *bpart, int grid,
                                  cudaStream_t s);
