@@ -254,6 +254,34 @@ def test_blocked_seeding_long_run_many_rhs(seedlib, orc, kernel_path):
                  final_tol=max(REL_X, 10 * s_final), min_counted=20)
 
 
+def test_fresh_contexts_reuse_freed_memory(seedlib, orc):
+    """Contexts created right after others were destroyed get device memory
+    that held the old contexts' data; the persistent seed runs of the new ones
+    (Wilson and CSR, FP64 and mixed) must not read any of it as state.  Ten
+    create / solve / destroy rounds, each compared with the oracle's seed."""
+    dims, kappa = (3, 4, 5, 6), 0.14
+    U = I.random_su3_links(dims, 0.3, seed=7)
+    eta = I.point_sources(dims, 3, site=17)
+    B = np.stack([orc.wilson_dslash(dims, kappa, 1, -1, U, eta[:, j]) for j in range(3)], axis=1)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    ref = orc.seed_first(op, B, m_max=600, reorth_freq=10, tol=1e-10)
+    rp, ci, v = I.laplacian_2d_csr(30, 20)
+    Bc = I.gaussian_rhs(600, 3, seed=2)
+    for r in range(10):
+        prec = r % 2
+        ctx = wilson_ctx(seedlib, dims, kappa, U, bc_t=1, m_max=600, reorth_freq=10, tol_seed=1e-10,
+                         precision=prec)
+        info1, _, _, X = run_gpu(seedlib, ctx, B, rest=False)
+        assert info1[0]["converged"] == 1, r
+        if prec == 0:
+            assert info1[0]["iters"] == ref["iters"], (r, info1[0]["iters"], ref["iters"])
+        seedlib.seed_destroy(ctx)
+        cc = csr_ctx(seedlib, rp, ci, v, m_max=600, reorth_freq=10, tol_seed=1e-10, precision=prec)
+        info1, _, _, _ = run_gpu(seedlib, cc, Bc, rest=False)
+        assert info1[0]["converged"] == 1, r
+        seedlib.seed_destroy(cc)
+
+
 _WORKLOAD_REF = {}
 
 
