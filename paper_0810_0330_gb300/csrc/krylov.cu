@@ -42,10 +42,12 @@ int vec_blocks(int64_t n) {
   return (int)b;
 }
 
-// Kernels over nc lockstep columns: about 4 blocks per SM in total.
+// Kernels over nc lockstep columns: up to 8 blocks per SM in total (long
+// vectors need that many loads in flight to keep HBM busy), at least 4
+// elements per thread.
 int col_blocks(int64_t n, int nc) {
   int64_t b = (n + NT * 4 - 1) / (NT * 4);
-  int64_t cap = 608 / (nc > 0 ? nc : 1);
+  int64_t cap = kVecBlocksMax / (nc > 0 ? nc : 1);
   if (cap < 1) cap = 1;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
@@ -724,6 +726,7 @@ __global__ void __launch_bounds__(NT) k_cg_alpha(int64_t n, const T *P, const T 
   P += (int64_t)col * ld;
   Q += (int64_t)col * ld;
   typename Sc<T>::A acc = 0;
+#pragma unroll 4
   GRID_STRIDE(e, n) acc = Sc<T>::redot(P[e], Q[e], acc);
   double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
@@ -747,6 +750,7 @@ __global__ void __launch_bounds__(NT) k_cg_update(int64_t n, const CallArgs *cal
   Q += (int64_t)col * ld;
   const double a = c.alpha[col];
   typename Sc<T>::A acc = 0;
+#pragma unroll 4
   GRID_STRIDE(e, n) {
     X[e] = Sc<T>::axpy(a, P[e], X[e]);
     const T r = Sc<T>::axpy(-a, Q[e], R[e]);
@@ -773,6 +777,7 @@ __global__ void __launch_bounds__(NT) k_cg_p(int64_t n, const T *R, T *P, int64_
     GRID_STRIDE(e, n) P[e] = R[e];
   } else {
     const double be = c.beta[col];
+#pragma unroll 4
     GRID_STRIDE(e, n) P[e] = Sc<T>::axpy(be, P[e], R[e]);
   }
 }
