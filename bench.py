@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only time the dominant kernel (for profiler captures)")
+    ap.add_argument("--once", action="store_true",
+                    help="run the workload's step once and print its phase times, no bench line "
+                         "(for launch-list captures)")
     ap.add_argument("--dims", default=None, help="lattice for --kernel-only, e.g. 16,16,16,16")
     ap.add_argument("--ncols", type=int, default=None, help="columns for --kernel-only")
     ap.add_argument("--reps", type=int, default=20, help="timed launches for --kernel-only")
@@ -389,6 +392,14 @@ def run_ours(args):
         i2 = S.seed_solve_rest(ctx, B, X)
         return i1, i2
 
+    if args.once:
+        i1, i2 = step()
+        torch.cuda.synchronize()
+        st = S.seed_get_stats(ctx)
+        print(json.dumps({"once": workload_name(dims, args.sources, mixed), "seed_steps": i1[0]["iters"],
+                          "ms_seed": round(st["ms_seed"], 3), "ms_rest": round(st["ms_rest"], 3)}), flush=True)
+        S.seed_destroy(ctx)
+        return 0
     for _ in range(args.warmup):
         flush.zero_()
         i1, i2 = step()
