@@ -254,6 +254,57 @@ def test_blocked_seeding_long_run_many_rhs(seedlib, orc, kernel_path):
                  final_tol=max(REL_X, 10 * s_final), min_counted=20)
 
 
+@pytest.mark.parametrize("kernel_path", [0, 1])
+@pytest.mark.parametrize("freq", [1, 0, 10])
+def test_lucky_breakdown_diagonal(seedlib, orc, kernel_path, freq):
+    """diag(d) with 7 distinct eigenvalues (n = 100), 3 Gaussian RHS: the
+    Krylov space of b^1 is exhausted after 7 steps, so the seed run ends at a
+    lucky breakdown (beta_i ~ 0) with x^1 exact.  Step count equal to the
+    oracle's and x^1 within 1e-9, on the streaming (freq 1) and blocked
+    (freq 0, 10) seeding and both kernel paths.  The run's last step works on
+    v = f / beta with f at rounding level (beta below the breakdown threshold
+    only after it), a direction fixed by rounding; its projection moves the
+    seeded x^2, x^3 by O(1e-2), so those are held to max(1e-9, 10 x the
+    oracle's own one-ulp sensitivity)."""
+    d = np.repeat(np.array([0.5, 1.0, 2.0, 3.0, 5.0, 8.0, 13.0]), [10, 20, 15, 5, 25, 10, 15])
+    rp, ci, v = I.diagonal_csr(d)
+    B = I.gaussian_rhs(100, 3, seed=1)
+    ctx = csr_ctx(seedlib, rp, ci, v, m_max=200, reorth_freq=freq, tol_seed=1e-14, kernel_path=kernel_path)
+    info1, _, Xs, _ = run_gpu(seedlib, ctx, B, rest=False)
+    op = orc.Operator.csr(rp, ci, v)
+    ref = orc.seed_first(op, B, m_max=200, reorth_freq=freq, tol=1e-14)
+    assert info1[0]["iters"] == ref["iters"] <= 8, (info1[0]["iters"], ref["iters"])
+    assert info1[0]["converged"] == 1
+    assert info1[0]["true_relres"] < 1e-12
+    assert relerr(Xs[:, 0].real, ref["X"][:, 0].real) < REL_X
+    sens = seeded_only_sensitivity(orc, op, B, m_max=200, reorth_freq=freq, tol=1e-14)
+    assert relerr(Xs[:, 1:].real, ref["X"][:, 1:].real) < max(REL_X, 10 * sens), sens
+
+
+@pytest.mark.parametrize("kernel_path", [0, 1])
+@pytest.mark.parametrize("freq", [10, 0])
+def test_extra_iters_past_convergence(seedlib, orc, kernel_path, freq):
+    """extra_iters = 20 (the seed run continues past convergence to improve
+    the seeding): 168 + 20 = 188 steps on the 3x4x5x6 lattice as in the
+    oracle; x^1 within 1e-9 and the seeded x^2, x^3 within max(1e-9, 10 x the
+    oracle's one-ulp sensitivity)."""
+    dims, kappa = (3, 4, 5, 6), 0.14
+    U = I.random_su3_links(dims, 0.3, seed=7)
+    eta = I.point_sources(dims, 3, site=17)
+    B = np.stack([orc.wilson_dslash(dims, kappa, 1, -1, U, eta[:, j]) for j in range(3)], axis=1)
+    kw = dict(m_max=600, reorth_freq=freq, tol=1e-10, extra_iters=20)
+    ctx = wilson_ctx(seedlib, dims, kappa, U, bc_t=1, m_max=600, reorth_freq=freq, tol_seed=1e-10, extra_iters=20,
+                     kernel_path=kernel_path)
+    info1, _, Xs, _ = run_gpu(seedlib, ctx, B, rest=False)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    ref = orc.seed_first(op, B, **kw)
+    assert info1[0]["iters"] == ref["iters"], (info1[0]["iters"], ref["iters"])
+    assert ref["iters"] == ref["converged_at"] + 20
+    assert relerr(Xs[:, 0], ref["X"][:, 0]) < REL_X
+    sens = seeded_only_sensitivity(orc, op, B, **kw)
+    assert relerr(Xs[:, 1:], ref["X"][:, 1:]) < max(REL_X, 10 * sens), (relerr(Xs[:, 1:], ref["X"][:, 1:]), sens)
+
+
 def test_fresh_contexts_reuse_freed_memory(seedlib, orc):
     """Contexts created right after others were destroyed get device memory
     that held the old contexts' data; the persistent seed runs of the new ones
