@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="forward + backward of the differentiable solve: 16^4, kappa 0.150, 8 Gaussian b and t")
     ap.add_argument("--reorth-freq", type=int, default=None, help="reorthogonalization frequency for --adjoint")
+    ap.add_argument("--reliable-delta", type=float, default=0.0,
+                    help="mixed precision: reliable-update threshold (0: the library default, 0.01)")
     ap.add_argument("--sweep", action="store_true",
                     help="operator-apply bandwidth sweep (CSR Laplacian and Wilson D at growing sizes)")
     ap.add_argument("--sweep-max", type=int, default=3, help="sweep points per operator (1..4)")
@@ -378,7 +380,8 @@ def run_ours(args):
         return 0
     prm = S.seed_params_default(m_max=WL["m_max"], reorth_freq=WL["reorth_freq"],
                                 reorth_passes=WL["reorth_passes"], tol_seed=WL["tol_seed"],
-                                tol_rest=WL["tol_rest"], x0_zero=1, precision=1 if mixed else 0)
+                                tol_rest=WL["tol_rest"], x0_zero=1, precision=1 if mixed else 0,
+                                reliable_delta=args.reliable_delta)
     ctx = S.seed_create_wilson(dims, kappa, U, prm)
     eta_h = I.point_sources(dims, nrhs) if args.sources == "point" else I.z4_noise(n, nrhs, seed=0)
     ETA = torch.from_numpy(np.ascontiguousarray(eta_h.T)).to(dev).t()     # (n, nrhs) column-major
@@ -506,6 +509,7 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": workload_name(dims, args.sources, mixed), "lattice": "x".join(map(str, dims)),
                           "n": n, "nrhs": nrhs, "precision": args.precision,
+                          "reliable_delta": (args.reliable_delta or 0.01) if mixed else None,
                           "kappa": kappa, "tol_seed": WL["tol_seed"], "reorth_freq": WL["reorth_freq"],
                           "reorth_passes": WL["reorth_passes"], "tol_rest": WL["tol_rest"],
                           "parallelism": "replicas" if world > 1 else "single-gpu",
