@@ -149,6 +149,25 @@ def test_mixed_laplacian_64(seedlib, orc, nrhs, delta):
     check_solution(orc, op, B, X.real, ref, i1, i2, 1e-12, 1e-8, "lap64-mixed")
 
 
+@pytest.mark.parametrize("kernel_path", [0, 1])
+def test_mixed_csr_persistent_seed(seedlib, orc, kernel_path):
+    """Shifted 96x80 Laplacian (shift 0.05), 4 Gaussian RHS, reorthogonalization
+    every 10 steps: on path 0 the FP32 seed run is the persistent CSR kernel,
+    on path 1 the step kernels; both certified against the oracle as the
+    other solves are."""
+    rp, ci, v = I.shifted_laplacian_2d_csr(96, 80, 0.05)
+    n = 96 * 80
+    B = I.gaussian_rhs(n, 4, seed=6)
+    p = seedlib.seed_params_default(m_max=2000, reorth_freq=10, tol_seed=1e-10, tol_rest=1e-8, precision=1,
+                                    kernel_path=kernel_path)
+    ctx = seedlib.seed_create_csr(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(),
+                                  torch.from_numpy(v).cuda(), p)
+    i1, i2, X = mixed_solve(seedlib, ctx, B)
+    op = orc.Operator.csr(rp, ci, v)
+    ref = orc.seed_solve_all(op, B, m_max=2000, reorth_freq=10, tol_seed=1e-10, tol_rest=1e-8)
+    check_solution(orc, op, B, X.real, ref, i1, i2, 1e-10, 1e-8, "csr-mixed-persistent-%d" % kernel_path)
+
+
 @pytest.mark.parametrize("freq", [0, 10])
 def test_mixed_wilson_small(seedlib, orc, freq):
     """3x4x5x6 lattice, kappa 0.14, antiperiodic t, 5 RHS b = D^H eta; an
