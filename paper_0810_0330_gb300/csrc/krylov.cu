@@ -1,6 +1,8 @@
-// krylov.cu -- the Sec. 3 seed recurrence, its periodic reorthogonalization,
-// the Galerkin projection over a kept basis, and lockstep CG for the seeded
-// systems, on sm_103a in FP64.
+// krylov.cu -- the Sec. 3 seed recurrence step by step, its periodic
+// reorthogonalization, the Galerkin projection over a kept basis, and lockstep
+// CG for the seeded systems, on sm_103a.  Instantiated for FP64 (double,
+// double2) and, for the mixed-precision path, FP32 vectors (float, float2)
+// whose scalars and reductions stay FP64.
 //
 // All scalars of the recurrence (alpha_i, beta_i, delta_i, gamma_{i-1},
 // zeta_i, eta^j, the step index i and the stop flags) live in device memory

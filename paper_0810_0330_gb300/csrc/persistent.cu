@@ -1,7 +1,8 @@
 // persistent.cu -- persistent cooperative kernels for the seed solve (runs of
-// Sec. 3 Lanczos steps without reorthogonalization) and for the lockstep CG on
-// the seeded systems.  One launch runs many steps; grid-wide dependencies are
-// grid barriers instead of kernel boundaries.
+// Sec. 3 Lanczos steps without reorthogonalization; FP64, and FP32 for the
+// mixed-precision path) and for the lockstep CG on the seeded systems (FP64).
+// One launch runs many steps; grid-wide dependencies are grid barriers instead
+// of kernel boundaries.
 //
 // Why: on the benchmark's 8^4 lattice one Lanczos step is ~6 us of FP64 work
 // per SM in each operator half and a few microseconds of vector work; as a
