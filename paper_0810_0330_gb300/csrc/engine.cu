@@ -449,7 +449,7 @@ int csr_seed_grid(const seed_ctx *ctx) {
   return (int)b;
 }
 
-bool use_persistent_seed(seed_ctx *ctx, int nrhs) {
+bool use_persistent_seed(seed_ctx *ctx) {
   const int f = ctx->prm.reorth_freq;
   // the FP32 Wilson run works in 32-site tiles of 4 warps, one block per SM:
   // right for latency-bound small lattices; from 65536 sites on the step
@@ -590,7 +590,7 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   kern += 3;
   ctx->stats.kernel_launches += kern;
 
-  if (use_persistent_seed(ctx, nrhs)) {
+  if (use_persistent_seed(ctx)) {
     TRY(seed_persistent_segments<T>(ctx, nrhs));
   } else {
     TRY(seed_graph_runs<T>(ctx, nrhs));
@@ -1307,7 +1307,7 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   launch_seed_normalize<T32>(b, ctx->cs);
   kern += 4;
   ctx->stats.kernel_launches += kern;
-  if (use_persistent_seed(ctx, nrhs)) {
+  if (use_persistent_seed(ctx)) {
     TRY(seed_persistent_segments<T32>(ctx, nrhs));
   } else {
     TRY(seed_graph_runs<T32>(ctx, nrhs));
