@@ -109,11 +109,17 @@ typedef struct {
   double breakdown_rel;   /* lucky breakdown when beta_i <= breakdown_rel * max row sum of |T| */
   int32_t kernel_path;    /* How the steps are issued (same method either way):
                              0 (default): the seed's runs of Lanczos steps between
-                             reorthogonalizations in one persistent cooperative kernel (when
-                             nrhs <= 16 and the frequency is 0 or >= 8), everything else as step
-                             kernels replayed from CUDA graphs;
+                             reorthogonalizations in one persistent cooperative kernel (when the
+                             frequency is 0 or >= 8; in mixed precision for CSR and for Wilson
+                             lattices below 65536 sites), everything else as step kernels
+                             replayed from CUDA graphs, the lockstep CG in up to three concurrent
+                             column branches;
                              1: step kernels only;
-                             2: as 0, and CG in one persistent kernel as well (nrhs <= 33). */
+                             2: as 0, and FP64 CG in one persistent kernel as well (nrhs <= 33).
+                             With two or more systems and a frequency of 0 or >= 8 the seeding of
+                             systems 2..p (Sec. 3 steps 4 and 7) is folded into x^2..x^p once per
+                             block of at most 128 steps instead of every step (same vectors, other
+                             summation order). */
   int32_t precision;      /* 0 (default): FP64 throughout.
                              1: mixed.  Operator applies and Krylov vectors (V included) in FP32
                              (the context keeps an FP32 copy of the operator); every scalar of the
