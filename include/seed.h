@@ -263,8 +263,14 @@ seed_status seed_grad_kappa(seed_ctx *ctx, const void *Lambda, int64_t ldl, cons
  * op 2 = D^H (used e.g. to form normal-equation right-hand sides b = D^H eta,
  * Sec. 4).  On a mixed-precision context ops 3 = A, 4 = D, 5 = D^H apply the
  * FP32 copy of the operator to FP32 data (float, or interleaved complex float
- * for Wilson), the arithmetic of the mixed solver's iterations.  X and Y must
- * not overlap.  Not synchronising. */
+ * for Wilson), the arithmetic of the mixed solver's iterations.  On a
+ * mixed-precision Wilson context ops 6 = D and 7 = D^H take X and Y in the
+ * solver's own tiled FP32 layout, the layout and launch of its iterations and
+ * of seed_time_operator: component k = 3*spin + colour of site s at complex
+ * index ((s / 32) * 12 + k) * 32 + s % 32 of a column of length
+ * 384 * ceil(sites / 32) (ldx, ldy >= that length); the padding sites of the
+ * last tile are written as zeros.  X and Y must not overlap.  Not
+ * synchronising. */
 seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, void *Y, int64_t ldy,
                        int32_t ncols);
 

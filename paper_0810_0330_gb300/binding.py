@@ -289,9 +289,15 @@ def seed_project(ctx: Context, B: torch.Tensor, X: torch.Tensor):
     _check(lib().seed_project(ctx.handle, pb, ldb, px, ldx, nb), "seed_project", ctx.handle)
 
 
+def wilson_tiled_length(n: int) -> int:
+    """Column length of the tiled FP32 layout (seed_apply ops 6, 7) for n = 12 * sites."""
+    return 384 * ((n // 12 + 31) // 32)
+
+
 def seed_apply(ctx: Context, op: int, X: torch.Tensor, Y: torch.Tensor):
-    px, ldx, nx = _block(X, ctx.n, "X")
-    py, ldy, ny = _block(Y, ctx.n, "Y")
+    length = wilson_tiled_length(ctx.n) if op in (6, 7) else ctx.n
+    px, ldx, nx = _block(X, length, "X")
+    py, ldy, ny = _block(Y, length, "Y")
     if nx != ny:
         raise ValueError("X and Y must have the same number of columns")
     _check(lib().seed_apply(ctx.handle, int(op), px, ldx, py, ldy, nx), "seed_apply", ctx.handle)

@@ -1782,20 +1782,24 @@ seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int
 
 seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, void *Y, int64_t ldy, int32_t ncols) {
   if (!ctx) return fail(nullptr, SEED_EINVAL, "ctx is NULL");
-  if (op < 0 || op > 5 || ((op == 1 || op == 2 || op == 4 || op == 5) && ctx->kind != 1))
-    return fail(ctx, SEED_EINVAL, "op must be 0 (A), or 1 (D) / 2 (D^H) for Wilson; 3..5 in FP32");
-  if (op >= 3 && ctx->precision != 1) return fail(ctx, SEED_EINVAL, "ops 3..5 need a mixed-precision context");
+  if (op < 0 || op > 7 || ((op == 1 || op == 2 || op >= 4) && ctx->kind != 1))
+    return fail(ctx, SEED_EINVAL, "op must be 0 (A), or 1 (D) / 2 (D^H) for Wilson; 3..7 in FP32");
+  if (op >= 3 && ctx->precision != 1) return fail(ctx, SEED_EINVAL, "ops 3..7 need a mixed-precision context");
   TRY(check_block(ctx, X, ldx, ncols, "X"));
   TRY(check_block(ctx, Y, ldy, ncols, "Y"));
+  const bool tiled = op >= 6;   // the solver's tiled FP32 layout: columns of length nv
+  const int64_t len = tiled ? ctx->nv : ctx->n;
+  if (tiled && (ldx < len || ldy < len))
+    return fail(ctx, SEED_EINVAL, "leading dimension < the tiled column length 384 * ceil(sites / 32)");
   const size_t es = op >= 3 ? ctx->vsz : ctx->esz;
-  if (overlap(X, ldx, Y, ldy, ncols, ctx->n, es)) return fail(ctx, SEED_EINVAL, "X and Y overlap");
+  if (overlap(X, ldx, Y, ldy, ncols, len, es)) return fail(ctx, SEED_EINVAL, "X and Y overlap");
   TRY(ensure_cols(ctx, ncols));
   StreamScope scope(ctx);
   if (op == 3) {
     ctx->stats.kernel_launches += apply_A32(ctx, X, ldx, Y, ldy, ncols, nullptr, false);
   } else if (op >= 4) {
-    launch_wilson_dslash32(ctx->wil32, op == 4 ? +1 : -1, (const float2 *)X, ldx, (float2 *)Y, ldy, ncols, nullptr,
-                           false, ctx->cs);
+    launch_wilson_dslash32(ctx->wil32, (op == 4 || op == 6) ? +1 : -1, (const float2 *)X, ldx, (float2 *)Y, ldy,
+                           ncols, nullptr, tiled, ctx->cs);
     ctx->stats.kernel_launches += 1;
   } else if (op == 0) {
     ctx->stats.kernel_launches += apply_A(ctx, X, ldx, Y, ldy, ncols, nullptr);

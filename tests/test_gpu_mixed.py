@@ -110,6 +110,59 @@ def test_fp32_wilson_apply(seedlib, orc, dims, bc_t):
             assert np.abs(Y[:, j] - ref).max() <= bound, (op, j)
 
 
+def to_tiled(X, sites):
+    """Site-major columns (n x c, n = 12 sites) -> the solver's tiled FP32
+    layout: component k of site s at ((s // 32) * 12 + k) * 32 + s % 32."""
+    tiles, c = (sites + 31) // 32, X.shape[1]
+    P = np.zeros((tiles * 32, 12, c), dtype=X.dtype)
+    P[:sites] = X.reshape(sites, 12, c)
+    return np.ascontiguousarray(P.reshape(tiles, 32, 12, c).transpose(0, 2, 1, 3)).reshape(tiles * 384, c)
+
+
+def from_tiled(T, sites):
+    """Inverse of to_tiled: (site-major columns, the padding sites' values)."""
+    tiles, c = (sites + 31) // 32, T.shape[1]
+    P = T.reshape(tiles, 12, 32, c).transpose(0, 2, 1, 3).reshape(tiles * 32, 12, c)
+    return P[:sites].reshape(sites * 12, c), P[sites:]
+
+
+@pytest.mark.parametrize("dims,bc_t,ncols", [((16, 16, 16, 32), 0, 11), ((17, 17, 15, 16), 1, 3)])
+def test_fp32_wilson_apply_tiled(seedlib, orc, dims, bc_t, ncols):
+    """The FP32 operator in the mixed solver's own tiled layout and launch
+    (seed_apply ops 6 and 7: the kernel, layout and column count that the
+    benchmark times): the 16^3 x 32 workload lattice with the 11 columns of a
+    lockstep CG launch, and a ragged 17x17x15x16 lattice whose last tile holds
+    padding sites.  Every output against the oracle (the bound above), the
+    padding written as zeros, and the result bitwise equal to the site-major
+    launch of the same arithmetic (ops 4 and 5)."""
+    kappa = 0.155
+    U = I.random_su3_links(dims, 0.3, seed=3)
+    sites = I.lattice_sites(dims)
+    n = 12 * sites
+    p = seedlib.seed_params_default(m_max=4, precision=1)
+    ctx = seedlib.seed_create_wilson(dims, kappa, torch.from_numpy(U).cuda(), p, bc_t=bc_t)
+    X32 = I.gaussian_rhs(n, ncols, seed=6, complex_=True).astype(np.complex64)
+    Xt = dev_cols(to_tiled(X32, sites))
+    Yt = dev_cols(np.full((384 * ((sites + 31) // 32), ncols), 7.0, dtype=np.complex64))
+    Xs, Ys = dev_cols(X32), dev_cols(np.zeros_like(X32))
+    U32 = U.astype(np.complex64).astype(np.complex128)
+    for op_t, op_s, sign in ((6, 4, +1), (7, 5, -1)):
+        seedlib.seed_apply(ctx, op_t, Xt, Yt)
+        seedlib.seed_apply(ctx, op_s, Xs, Ys)
+        torch.cuda.synchronize()
+        Y, pad = from_tiled(host_cols(Yt), sites)
+        assert np.all(pad == 0), op_t
+        assert np.array_equal(Y, host_cols(Ys)), op_t
+        for j in range(ncols):
+            x = X32[:, j].astype(np.complex128)
+            ref = orc.wilson_dslash(dims, kappa, bc_t, sign, U32, x)
+            assert np.abs(Y[:, j] - ref).max() <= 1e-5 * np.abs(x).max(), (op_t, j)
+    # the tiled ops need a mixed-precision Wilson context
+    ctx64 = seedlib.seed_create_wilson(dims, kappa, torch.from_numpy(U).cuda(), seedlib.seed_params_default(m_max=4))
+    with pytest.raises(seedlib.SeedError):
+        seedlib.seed_apply(ctx64, 6, Xt, Yt)
+
+
 def test_fp32_csr_apply(seedlib, orc):
     rp, ci, v = I.laplacian_2d_csr(37, 29)
     n = 37 * 29
