@@ -44,7 +44,8 @@ typedef struct CUstream_st *seed_stream; /* a cudaStream_t; NULL = legacy defaul
 
 typedef enum {
   SEED_OK = 0,
-  SEED_EINVAL = 1,   /* bad argument (size, ld, NULL pointer, malformed operator) */
+  SEED_EINVAL = 1,   /* bad argument (size, ld, NULL pointer, malformed operator; from
+                        seed_solve_first also a NaN or infinite initial residual of system 1) */
   SEED_ENOMEM = 2,   /* device allocation failed */
   SEED_ECUDA = 3,    /* a CUDA runtime call failed (including no usable device) */
   SEED_ENOTSPD = 4,  /* the LU of the Lanczos tridiagonal met delta_i <= 0 or NaN:
@@ -273,6 +274,28 @@ seed_status seed_grad_kappa(seed_ctx *ctx, const void *Lambda, int64_t ldl, cons
  * synchronising. */
 seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, void *Y, int64_t ldy,
                        int32_t ncols);
+
+/* Failure detection, tested without a GPU fault.
+ *
+ * seed_inject_alloc_failure: host-side fault injection.  The k-th device
+ * allocation the library makes from now on (k = 1: the next one) fails as if
+ * cudaMalloc had run out of memory, without calling it; the call that needed
+ * it returns SEED_ENOMEM.  A failed seed_create_* frees what it had
+ * allocated; a failed call on a context leaves the context valid, and a later
+ * call allocates what is still missing.  k <= 0 disarms.  Process-wide (all
+ * threads and contexts).  Returns the previous countdown.
+ *
+ * seed_check_barrier_timeout: self-test of the bounded wait of the persistent
+ * kernels' grid barriers.  Launches two blocks at a barrier that can never
+ * complete (its arrival target is one epoch ahead), so that every wait runs
+ * out after its limit (2 s) and the kernel returns with the error flag set --
+ * the flag the persistent solves turn into SEED_ETIMEOUT.  On SEED_OK,
+ * *timed_out = 1 when the wait gave up as designed (0 would mean a barrier
+ * completed that cannot complete) and *ms = the kernel's device time.  Enqueued
+ * on `stream`, synchronises it; the device stays usable afterwards.
+ * SEED_ECUDA without cooperative launch support. */
+int32_t seed_inject_alloc_failure(int32_t k);
+seed_status seed_check_barrier_timeout(seed_stream stream, int32_t *timed_out, double *ms);
 
 /* Build the site -> neighbour table for a lattice on the device:
  * nbr[8*s + 2*mu] = s + mu-hat, nbr[8*s + 2*mu + 1] = s - mu-hat (periodic

@@ -32,12 +32,16 @@ EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_c
            "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
            "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related",
-           "seed_batch_solve", "seed_solve_multiple"]
+           "seed_batch_solve", "seed_solve_multiple", "seed_inject_alloc_failure", "seed_check_barrier_timeout"]
 
 
 class SeedError(RuntimeError):
+    """A status other than SEED_OK; `info` holds the per-system seed_info of a
+    failed solve call (None for other calls)."""
+
     def __init__(self, status: int, where: str, msg: str):
         self.status = status
+        self.info = None
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
         super().__init__("%s: %s (%s)" % (where, name, msg))
 
@@ -106,12 +110,15 @@ def lib():
             L.seed_solve_multiple.argtypes = [P, P, I64, P, I64, I32, P]
             L.seed_batch_solve.argtypes = [P, P, P, P, P, P, I32, I32, P]
             L.seed_grad_kappa.argtypes = [P, P, I64, P, I64, I32, C.POINTER(C.c_double)]
+            L.seed_inject_alloc_failure.argtypes = [I32]
+            L.seed_inject_alloc_failure.restype = I32
+            L.seed_check_barrier_timeout.argtypes = [P, C.POINTER(I32), C.POINTER(C.c_double)]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
             L.seed_destroy.argtypes = [P]
             L.seed_destroy.restype = None
             for name in EXPORTS:
-                if name not in ("seed_last_error", "seed_destroy", "seed_abi_version"):
+                if name not in ("seed_last_error", "seed_destroy", "seed_abi_version", "seed_inject_alloc_failure"):
                     getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -121,6 +128,14 @@ def _check(status: int, where: str, ctx=None):
     if status != SEED_OK:
         msg = lib().seed_last_error(ctx)
         raise SeedError(status, where, msg.decode() if msg else "")
+
+
+def _check_info(status: int, where: str, ctx, info):
+    try:
+        _check(status, where, ctx)
+    except SeedError as e:
+        e.info = [i.as_dict() for i in info]
+        raise
 
 
 def _stream(stream=None):
@@ -201,7 +216,7 @@ def seed_solve_first(ctx: Context, B: torch.Tensor, X: torch.Tensor):
     if nb != nx:
         raise ValueError("B and X must have the same number of columns")
     info = _infos(nb)
-    _check(lib().seed_solve_first(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_first", ctx.handle)
+    _check_info(lib().seed_solve_first(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_first", ctx.handle, info)
     return [i.as_dict() for i in info]
 
 
@@ -211,7 +226,7 @@ def seed_solve_rest(ctx: Context, B: torch.Tensor, X: torch.Tensor):
     if nb != nx:
         raise ValueError("B and X must have the same number of columns")
     info = _infos(nb)
-    _check(lib().seed_solve_rest(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_rest", ctx.handle)
+    _check_info(lib().seed_solve_rest(ctx.handle, pb, ldb, px, ldx, nb, info), "seed_solve_rest", ctx.handle, info)
     return [i.as_dict() for i in info]
 
 
@@ -301,6 +316,20 @@ def seed_apply(ctx: Context, op: int, X: torch.Tensor, Y: torch.Tensor):
     if nx != ny:
         raise ValueError("X and Y must have the same number of columns")
     _check(lib().seed_apply(ctx.handle, int(op), px, ldx, py, ldy, nx), "seed_apply", ctx.handle)
+
+
+def seed_inject_alloc_failure(k: int) -> int:
+    """Fail the k-th device allocation from now (k = 1: the next); k <= 0 disarms.
+    Returns the previous countdown."""
+    return int(lib().seed_inject_alloc_failure(int(k)))
+
+
+def seed_check_barrier_timeout(stream=None):
+    """(timed_out, ms): the persistent kernels' barrier wait run against a
+    barrier that cannot complete (about 2 s)."""
+    t, ms = C.c_int32(), C.c_double()
+    _check(lib().seed_check_barrier_timeout(_stream(stream), C.byref(t), C.byref(ms)), "seed_check_barrier_timeout")
+    return bool(t.value), ms.value
 
 
 def seed_wilson_neighbors(dims, out: torch.Tensor, stream=None):

@@ -182,8 +182,21 @@ seed_status check_params(seed_ctx *ctx, const seed_params *p) {
   return SEED_OK;
 }
 
+// Host-side fault injection (seed_inject_alloc_failure): countdown to the
+// device allocation that fails; 0 = disarmed.
+std::atomic<int> g_alloc_countdown{0};
+
+bool injected_alloc_failure() {
+  int v = g_alloc_countdown.load();
+  while (v > 0 && !g_alloc_countdown.compare_exchange_weak(v, v - 1)) {
+  }
+  return v == 1;
+}
+
 template <class Tp>
 seed_status dalloc(seed_ctx *ctx, Tp **p, size_t bytes) {
+  if (injected_alloc_failure())
+    return fail(ctx, SEED_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
   void *q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
   if (e != cudaSuccess) {
@@ -328,13 +341,18 @@ bool blocked_seeding(const seed_ctx *ctx, int nrhs) {
   return nrhs >= 2 && (f == 0 || f >= 8);
 }
 
+// (each buffer is allocated once; after a failed allocation the next call
+// allocates only what is still missing)
 seed_status ensure_block(seed_ctx *ctx) {
-  if (ctx->Wb) return SEED_OK;
-  ctx->blk = block_layout(ctx->nv);
-  TRY(dalloc(ctx, &ctx->Wb, (size_t)ctx->ldv * kSeedBlock * ctx->vsz));
-  TRY(dalloc(ctx, &ctx->blk.Hpart, sizeof(double2) * (size_t)ctx->blk.nchunk * kSeedBlock * (kMaxRhs - 1)));
-  TRY(dalloc(ctx, &ctx->blk.G, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
-  TRY(dalloc(ctx, &ctx->blk.Z, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
+  if (ctx->Wb && ctx->blk.Hpart && ctx->blk.G && ctx->blk.Z) return SEED_OK;
+  const BlockBufs lay = block_layout(ctx->nv);
+  ctx->blk.nchunk = lay.nchunk;
+  ctx->blk.rows = lay.rows;
+  if (!ctx->Wb) TRY(dalloc(ctx, &ctx->Wb, (size_t)ctx->ldv * kSeedBlock * ctx->vsz));
+  if (!ctx->blk.Hpart)
+    TRY(dalloc(ctx, &ctx->blk.Hpart, sizeof(double2) * (size_t)ctx->blk.nchunk * kSeedBlock * (kMaxRhs - 1)));
+  if (!ctx->blk.G) TRY(dalloc(ctx, &ctx->blk.G, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
+  if (!ctx->blk.Z) TRY(dalloc(ctx, &ctx->blk.Z, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
   return SEED_OK;
 }
 
@@ -605,6 +623,8 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   SeedState st;
   CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
   if (st.stop_reason == STOP_BLOCK) return fail(ctx, SEED_ECUDA, "internal: a seeding block overflowed");
+  if (st.stop_reason == STOP_NONFINITE)
+    return fail(ctx, SEED_EINVAL, "||b^1 - A x_0^1|| is not finite (NaN or Inf in B, X or the operator)");
   const int steps = st.i >= 1 ? st.i : 0;
   ctx->stats.mvps += (st.beta0 > 0.0) ? steps : 0;
   ctx->last_m = (st.beta0 > 0.0) ? steps : 0;
@@ -1321,6 +1341,8 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   SeedState st;
   CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
   if (st.stop_reason == STOP_BLOCK) return fail(ctx, SEED_ECUDA, "internal: a seeding block overflowed");
+  if (st.stop_reason == STOP_NONFINITE)
+    return fail(ctx, SEED_EINVAL, "||b^1 - A x_0^1|| is not finite (NaN or Inf in B, X or the operator)");
   const int steps = (st.beta0 > 0.0 && st.i >= 1) ? st.i : 0;
   ctx->stats.mvps += steps;
   ctx->last_m = steps;
@@ -1810,6 +1832,51 @@ seed_status seed_apply(seed_ctx *ctx, int32_t op, const void *X, int64_t ldx, vo
     ctx->stats.kernel_launches += 1;
   }
   CU(cudaGetLastError());
+  return SEED_OK;
+}
+
+int32_t seed_inject_alloc_failure(int32_t k) { return g_alloc_countdown.exchange(k > 0 ? k : 0); }
+
+seed_status seed_check_barrier_timeout(seed_stream stream, int32_t *timed_out, double *ms) {
+  seed_ctx *ctx = nullptr;   // for CU()
+  if (!timed_out || !ms) return fail(nullptr, SEED_EINVAL, "NULL argument");
+  int dev = 0, coop = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(nullptr, SEED_ECUDA, "the device has no cooperative launch");
+  const cudaStream_t s = (cudaStream_t)stream;
+  unsigned *w = nullptr;
+  if (cudaMalloc(&w, sizeof(unsigned) * kGridSyncWords) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, SEED_ENOMEM, "cudaMalloc of the barrier words failed");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  GridSync g;
+  g.count = w;
+  g.release = w + 1;
+  g.error = reinterpret_cast<int *>(w + 2);
+  g.owners = w + 3;
+  g.sm_slots = w + 4;
+  int32_t err = 0;
+  float t = 0.f;
+  cudaError_t e = cudaMemsetAsync(w, 0, sizeof(unsigned) * kGridSyncWords, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = launch_barrier_timeout_check(g, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&err, g.error, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(w);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, SEED_ECUDA, std::string("barrier self-test: ") + cudaGetErrorString(e));
+  }
+  *timed_out = err != 0;
+  *ms = t;
   return SEED_OK;
 }
 

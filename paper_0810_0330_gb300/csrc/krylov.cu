@@ -83,13 +83,13 @@ __global__ void __launch_bounds__(NT) k_seed_start(SeedBufs<T> b, const T *__res
     st->converged_at = -1;
     st->stop_at = -1;
     st->rho = b0;
-    if (b0 > 0.0) {
+    if (b0 > 0.0 && isfinite(b0)) {
       st->active = 1;
       st->stop_reason = STOP_RUNNING;
       st->inv_beta = 1.0 / b0;
-    } else {
+    } else {   // r_0 = 0: x_0 solves system 1; NaN or Inf: reported, no step runs
       st->active = 0;
-      st->stop_reason = STOP_CONVERGED;
+      st->stop_reason = b0 == 0.0 ? STOP_CONVERGED : STOP_NONFINITE;
       st->inv_beta = 0.0;
     }
   }

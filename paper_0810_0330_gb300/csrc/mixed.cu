@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_mixed_residual(int64_t n32, Layout32 L, 
       c.converged[col] = 1;
       c.reached[col] = 1;
       c.active[col] = 0;
-    } else if (c.iters[col] >= c.maxit) {
+    } else if (c.iters[col] >= c.maxit || !isfinite(s)) {   // non-finite: ends unconverged
       c.active[col] = 0;
     } else {
       c.active[col] = 1;

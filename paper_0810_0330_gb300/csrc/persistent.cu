@@ -673,7 +673,7 @@ SEED_DEV void cg_update_fin(const CgCols &c, int j, double rr) {
     c.active[j] = 0;
     c.reached[j] = 1;
     c.needs_check[j] = 1;
-  } else if (it + 1 >= c.maxit) {
+  } else if (it + 1 >= c.maxit || !isfinite(rr)) {   // non-finite: ends unconverged
     c.active[j] = 0;
     c.needs_check[j] = 1;
   } else {
@@ -968,6 +968,21 @@ cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, doubl
   void *args[] = {&o, &call, &R, &P, &Q, &tbuf, &ld, &cc, &g, &bpart};
   return cudaLaunchCooperativeKernel((const void *)k_cg_run_wilson, dim3(grid), dim3(PT), args, 0, s);
 }
+// Self-test of the bounded barrier wait: the epoch starts one ahead, so the
+// barrier's target (2 x gridDim.x arrivals) is never reached, every block's
+// wait runs out after kBarrierTimeoutNs (or ends when another block has
+// flagged the error) and the kernel returns with GridSync::error set.
+__global__ void k_barrier_timeout_check(GridSync g) {
+  unsigned epoch = 1;
+  grid_sync(g, epoch);
+}
+
+cudaError_t launch_barrier_timeout_check(GridSync g, cudaStream_t s) {
+  GridSync gg = g;
+  void *args[] = {&gg};
+  return cudaLaunchCooperativeKernel((const void *)k_barrier_timeout_check, dim3(2), dim3(PT), args, 0, s);
+}
+
 cudaError_t launch_cg_run_csr(const CsrOp &op, const CallArgs *call, double *R, double *P, double *Q, int64_t ld,
                               const CgCols &c, GridSync g, double *bpart, int grid, cudaStream_t s) {
   CsrOp o = op;

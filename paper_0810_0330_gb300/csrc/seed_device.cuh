@@ -113,7 +113,9 @@ SEED_DEV void cg_update_tail(const CgCols &c, int col, double rr) {
     c.active[col] = 0;
     c.reached[col] = 1;
     c.needs_check[col] = 1;
-  } else if (c.iters[col] >= c.maxit) {
+  } else if (c.iters[col] >= c.maxit || !isfinite(rr)) {
+    // a NaN or infinite residual (non-finite input, or p^H A p <= 0 on an
+    // operator that is not positive definite) ends the column unconverged
     c.active[col] = 0;
     c.needs_check[col] = 1;
   } else {

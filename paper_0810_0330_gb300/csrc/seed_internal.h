@@ -15,7 +15,8 @@ constexpr int kPartials = 5 * kVecBlocksMax * 32 + 5 * ((kVecBlocksMax + 31) / 3
 
 // Stop reasons of the seed recurrence (SeedState::stop_reason)
 enum { STOP_RUNNING = 0, STOP_CONVERGED = 1, STOP_BREAKDOWN = 2, STOP_MMAX = 3, STOP_NOTSPD = 4, STOP_TIMEOUT = 5,
-       STOP_BLOCK = 6 /* internal: a step found its seeding block full (never expected) */ };
+       STOP_BLOCK = 6 /* internal: a step found its seeding block full (never expected) */,
+       STOP_NONFINITE = 7 /* ||r_0^1|| is NaN or infinite */ };
 
 // Device-resident scalars of the Sec. 3 recurrence (paper notation).
 struct SeedState {
@@ -271,6 +272,8 @@ void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, c
 // barrier time-out through GridSync::error.  CG: nc <= 32.
 constexpr int kPersistMaxCols = 32;
 int persistent_grid(int kind, int sm_count, bool cg, bool fp32 = false);
+// two blocks wait at a grid barrier that can never complete; g zeroed by the caller
+cudaError_t launch_barrier_timeout_check(GridSync g, cudaStream_t s);
 // tpart: three doubles per 32-site tile
 cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &op, double2 *tbuf, GridSync g,
                                    double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
