@@ -17,7 +17,6 @@
 namespace seedk {
 
 constexpr int kAdjThreads = 128;   // 4 warps (one per mu) x 32 sites, as the operator kernel
-constexpr int kColTicketAdj = 16;  // tickets[16 + c]: per-column kernels
 
 // grid (blocks, ncols); block b of column j handles site tiles b, b + gridDim.x, ...
 __global__ void __launch_bounds__(kAdjThreads) k_dkappa_inner(WilsonOp op, const double2 *__restrict__ L, int64_t ldl,
@@ -62,7 +61,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_dkappa_inner(WilsonOp op, const
   block_sum<1, kAdjThreads>(v, sm);
   double *part = partials + (int64_t)col * gridDim.x;
   if (threadIdx.x == 0) part[blockIdx.x] = v[0];
-  if (!last_block_done(tickets + kColTicketAdj + col, gridDim.x)) return;
+  if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
   const double t = sum_partials<kAdjThreads>(part, gridDim.x, 1, 0, sm);
   if (threadIdx.x == 0) out[col] = -t;
 }

@@ -22,7 +22,6 @@ namespace seedk {
 
 constexpr int NT = kVecThreads;
 constexpr int kSeedTicket = 0;     // tickets[0..15]: seed / reorth kernels
-constexpr int kColTicket = 16;     // tickets[16 + c]: per-column kernels
 constexpr int kGroupTicket = 128;  // tickets[128 + g]: groups of 32 blocks (two-level reductions)
 constexpr int kOneLevelBlocks = 152;   // reductions over more blocks than this use two levels
 

@@ -15,7 +15,6 @@
 namespace seedk {
 
 constexpr int NT = kVecThreads;
-constexpr int kColTicket = 16;   // tickets[16 + c]: per-column kernels (shared with krylov.cu)
 
 #define GRID_STRIDE(e, n) \
   for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < (n); e += (int64_t)gridDim.x * NT)

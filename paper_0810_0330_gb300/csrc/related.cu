@@ -18,7 +18,6 @@
 namespace seedk {
 
 constexpr int NT = kVecThreads;
-constexpr int kColTicketRel = 16;   // tickets[16 + c]: per-column kernels
 
 #define GRID_STRIDE(e, n) \
   for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < (n); e += (int64_t)gridDim.x * NT)
@@ -43,7 +42,7 @@ __global__ void __launch_bounds__(NT) k_rel_dots(int64_t n, const T *__restrict_
     part[blockIdx.x * 2] = v[0];
     part[blockIdx.x * 2 + 1] = v[1];
   }
-  if (!last_block_done(tickets + kColTicketRel + col, gridDim.x)) return;
+  if (!last_block_done(tickets + kColTicket + col, gridDim.x)) return;
   const double re = sum_partials<NT>(part, gridDim.x, 2, 0, sm);
   const double im = sum_partials<NT>(part, gridDim.x, 2, 1, sm);
   if (threadIdx.x == 0) dots[col] = c2(re, im);

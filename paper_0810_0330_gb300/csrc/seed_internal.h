@@ -7,6 +7,7 @@
 namespace seedk {
 
 constexpr int kMaxRhs = 64;       // right-hand sides per call
+constexpr int kColTicket = 16;    // tickets[16 + c]: last-block tickets of per-column reductions
 constexpr int kVecThreads = 128;  // threads per block of the vector kernels
 constexpr int kVecBlocksMax = 152 * 8;   // blocks of the single-vector kernels on long vectors
 // device scratch for block partials: the seed dot kernel's 5 chunks x 32 values per block

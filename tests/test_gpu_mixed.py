@@ -240,14 +240,16 @@ def test_mixed_wilson_small(seedlib, orc, freq):
 
 
 def test_mixed_wilson_large_lattice(seedlib, orc):
-    """17x17x15x16 = 69360 sites (one thread per site in the FP32 operator,
-    and a site count that is not a multiple of 32, so the solver's tiled FP32
-    vectors carry padding), kappa 0.10, antiperiodic t, 3 Gaussian RHS.
+    """17x17x15x17 = 73695 sites (one thread per site in the FP32 operator,
+    a site count that is not a multiple of 32, so the solver's tiled FP32
+    vectors carry padding, and 2303 tiles, so the last 128-thread block of
+    the operator's launches has threads past the last tile), kappa 0.10,
+    antiperiodic t, 3 Gaussian RHS.
     Every system's FP64 true residual, recomputed by the oracle's operator,
     meets its tolerance, and the mixed solve needs at most 30 % more CG
     iterations than the FP64 solve of the same systems (a wrong FP32 operator
     would show up as slower or stalled convergence between reliable updates)."""
-    dims, kappa = (17, 17, 15, 16), 0.10
+    dims, kappa = (17, 17, 15, 17), 0.10
     U = I.random_su3_links(dims, 0.3, seed=11)
     n = 12 * I.lattice_sites(dims)
     B = I.gaussian_rhs(n, 3, seed=4, complex_=True)
