@@ -284,6 +284,40 @@ def test_mixed_wilson_8_4_workload(seedlib, orc):
     check_solution(orc, op, B, X, ref, i1, i2, 1e-12, 1e-8, "wilson-8^4-mixed")
 
 
+@pytest.mark.slow
+def test_mixed_16x3x32_workload_certified_by_oracle(seedlib, orc):
+    """The benchmark's 16^3 x 32 workload at full size, in the launch
+    configuration the benchmark times: kappa 0.155, links of spread 0.3 (seed
+    0), 12 Z4 noise sources (seed 0) with b = D^H eta formed by the oracle,
+    seed to 1e-12 with reorthogonalization every 100 steps, CG to 1e-8, mixed
+    precision.  The oracle cannot run this solve in seconds, so it certifies
+    the result instead: every system's FP64 true residual, recomputed with the
+    oracle's operator, meets its tolerance and agrees with the library's own;
+    and the mixed CG needs at most 30 % more iterations per system than the
+    FP64 solve of the same systems."""
+    dims, kappa, nrhs = (16, 16, 16, 32), 0.155, 12
+    U = I.random_su3_links(dims, 0.3, seed=0)
+    n = 12 * I.lattice_sites(dims)
+    eta = I.z4_noise(n, nrhs, seed=0)
+    B = np.stack([orc.wilson_dslash(dims, kappa, 0, -1, U, eta[:, j]) for j in range(nrhs)], axis=1)
+    prm = dict(m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
+    out = {}
+    for prec in (1, 0):
+        ctx = seedlib.seed_create_wilson(dims, kappa, torch.from_numpy(U).cuda(),
+                                         seedlib.seed_params_default(precision=prec, **prm))
+        out[prec] = mixed_solve(seedlib, ctx, B)
+        seedlib.seed_destroy(ctx)
+    i1, i2, X = out[1]
+    assert i1[0]["converged"] == 1 and all(i["converged"] for i in i2[1:])
+    op = orc.Operator.wilson(dims, kappa, U)
+    rr = true_relres(op, B, X)
+    assert rr[0] <= 1.01e-12 and np.all(rr[1:] <= 1.01e-8), rr
+    assert abs(i1[0]["true_relres"] - rr[0]) <= 1e-3 * rr[0] + 1e-16
+    for j in range(1, nrhs):
+        assert abs(i2[j]["true_relres"] - rr[j]) <= 1e-3 * rr[j] + 1e-16, j
+        assert i2[j]["iters"] <= 1.3 * out[0][1][j]["iters"] + 2, (j, i2[j]["iters"], out[0][1][j]["iters"])
+
+
 def test_mixed_rejects_fp64_basis_calls(seedlib):
     dims = (4, 4, 4, 4)
     U = I.random_su3_links(dims, 0.3, seed=2)
