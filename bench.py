@@ -45,6 +45,9 @@ except (OSError, ValueError):
 # DRAM bytes of one k_dslash launch (8^4, 11 columns) from an ncu capture of these sources of the kernel
 # (profiles/k_dslash_wilson_8x4_11cols.md); reported only while the source is unchanged.
 DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0, "6e70bd4a297626c1": 11.207424e6 + 0.0}
+# The same for k_dslash32_site<+1> (FP32, 16^3 x 32, 11 columns; profiles/k_dslash32_wilson_fp32.md)
+DSLASH32_TRAFFIC = {"7a583b64681e7245": 189.553920e6 + 104.930304e6}
+DSLASH32_TRAFFIC_DIMS = (16, 16, 16, 32)
 
 
 def cg_branch_cols(nc, branches=3):
@@ -59,18 +62,18 @@ def fp32_kernel_name(sites):
     return "k_dslash32_site" if sites >= 65536 else "k_dslash32"
 
 
-def dslash_source_hash():
+def dslash_source_hash(fp32=False):
     """Hash of the hopping kernel's sources (the .cu and its device header)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("wilson.cu", "wilson_device.cuh"):
+    for f in ("wilson32.cu" if fp32 else "wilson.cu", "wilson_device.cuh"):
         with open(os.path.join(ROOT, "paper_0810_0330_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def dslash_traffic():
-    return DSLASH_TRAFFIC.get(dslash_source_hash())
+def dslash_traffic(fp32=False):
+    return (DSLASH32_TRAFFIC if fp32 else DSLASH_TRAFFIC).get(dslash_source_hash(fp32))
 
 
 def parse():
@@ -464,7 +467,8 @@ def run_ours(args):
         achieved = b / (k_ms * 1e-3) / 1e9
         peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": dslash_traffic(fp32=True) if dims == DSLASH32_TRAFFIC_DIMS and ncols == 11 else None,
                 "kernel": "%s<+1> (Wilson D, FP32 complex), %d columns in one launch: the work of one CG "
                           "half-iteration, which the CG graphs issue as %s-column launches on concurrent streams"
                           % (fp32_kernel_name(vol), ncols, "+".join(str(x) for x in cg_branch_cols(ncols))),
