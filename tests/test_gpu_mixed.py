@@ -25,6 +25,7 @@ import numpy as np
 import pytest
 
 from paper_0810_0330_gb300 import inputs as I
+from tiled_layout import from_tiled, to_tiled
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -108,22 +109,6 @@ def test_fp32_wilson_apply(seedlib, orc, dims, bc_t):
             ref = oop.apply(x) if sign is None else orc.wilson_dslash(dims, kappa, bc_t, sign, U32, x)
             bound = (1e-4 if sign is None else 1e-5) * np.abs(x).max()
             assert np.abs(Y[:, j] - ref).max() <= bound, (op, j)
-
-
-def to_tiled(X, sites):
-    """Site-major columns (n x c, n = 12 sites) -> the solver's tiled FP32
-    layout: component k of site s at ((s // 32) * 12 + k) * 32 + s % 32."""
-    tiles, c = (sites + 31) // 32, X.shape[1]
-    P = np.zeros((tiles * 32, 12, c), dtype=X.dtype)
-    P[:sites] = X.reshape(sites, 12, c)
-    return np.ascontiguousarray(P.reshape(tiles, 32, 12, c).transpose(0, 2, 1, 3)).reshape(tiles * 384, c)
-
-
-def from_tiled(T, sites):
-    """Inverse of to_tiled: (site-major columns, the padding sites' values)."""
-    tiles, c = (sites + 31) // 32, T.shape[1]
-    P = T.reshape(tiles, 12, 32, c).transpose(0, 2, 1, 3).reshape(tiles * 32, 12, c)
-    return P[:sites].reshape(sites * 12, c), P[sites:]
 
 
 @pytest.mark.parametrize("dims,bc_t,ncols", [((16, 16, 16, 32), 0, 11), ((17, 17, 15, 16), 1, 3)])
