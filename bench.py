@@ -118,6 +118,33 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+# A replica that dies or hangs must not leave the others waiting forever: the
+# process group's timeout ends their next barrier or reduction with an error.
+# It exceeds the longest healthy gap between two collectives (set-up, warm-up
+# and the timed steps of one rank: a few minutes at most).
+REPLICA_TIMEOUT_S = 600
+
+
+def init_replicas(backend, device_id=None, timeout_s=REPLICA_TIMEOUT_S):
+    import datetime
+    import torch.distributed as dist
+    kw = dict(timeout=datetime.timedelta(seconds=timeout_s))
+    if device_id is not None:
+        kw["device_id"] = device_id
+    dist.init_process_group(backend, **kw)
+    return dist
+
+
+def replicas_barrier(dist, where):
+    """Barrier of the replicas; raises (instead of hanging) when another rank
+    has exited or stopped answering."""
+    try:
+        dist.barrier()
+    except Exception as e:
+        raise RuntimeError("replica barrier '%s' failed on rank %d: another rank has exited or stopped (%s)"
+                           % (where, dist.get_rank(), e)) from e
+
+
 def max_over_ranks(x, dist, dev):
     """The maximum of a per-rank time over all ranks (x itself without a
     process group).  Replicas run independent problems, so the job's time is
@@ -341,9 +368,8 @@ def run_ours(args):
     rank, world, local = env_rank()
     dist = None
     if world > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = init_replicas("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -421,7 +447,7 @@ def run_ours(args):
     st0 = S.seed_get_stats(ctx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
-        dist.barrier()
+        replicas_barrier(dist, "before the timed steps")
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     infos = []
@@ -433,7 +459,7 @@ def run_ours(args):
             ev[k][1].record()
         torch.cuda.synchronize()
     if dist:
-        dist.barrier()
+        replicas_barrier(dist, "after the timed steps")
     t_wall1 = time.perf_counter()
     st1 = S.seed_get_stats(ctx)
     step_ms = [a.elapsed_time(b) for a, b in ev]

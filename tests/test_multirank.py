@@ -65,6 +65,44 @@ def test_max_over_ranks_gloo_world2():
         assert hs[0] == hs[1]
 
 
+def _replica_that_may_die(rank, world, port, out_q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import time
+    import bench
+    d = bench.init_replicas("gloo", timeout_s=10)
+    if rank == 1:
+        os._exit(3)   # a replica that is gone between steps, without a word
+    t0 = time.time()
+    try:
+        bench.replicas_barrier(d, "test")
+        out_q.put((rank, "passed", time.time() - t0))
+    except RuntimeError as e:
+        out_q.put((rank, str(e), time.time() - t0))
+    out_q.close()
+    out_q.join_thread()
+    os._exit(0)
+
+
+def test_dead_replica_ends_the_next_barrier_with_an_error():
+    """Failure detection on the host: when one replica exits, the others'
+    next barrier raises (peer gone, or the process group's timeout) instead
+    of waiting forever."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_replica_that_may_die, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, msg, waited = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and msg != "passed", msg
+    assert "rank 0" in msg and "another rank" in msg, msg
+    assert waited < 60.0, waited
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+
+
 def test_max_over_ranks_single_process_is_identity():
     sys.path.insert(0, ROOT)
     import bench
