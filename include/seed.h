@@ -75,8 +75,8 @@ typedef struct {
 } seed_csr;
 
 /* Wilson-Dirac operator on a 4-d lattice; the library solves with the normal
- * operator A = D^H D (Sec. 4: "we multiply the system by the Hermitian
- * transpose of the matrix", two applications of D per iteration).
+ * operator A = D^H D (Sec. 4 turns the non-Hermitian system into a Hermitian
+ * one by multiplying it with D^H: two applications of D per iteration).
  *   (D psi)(n) = psi(n) - kappa sum_mu [ (1 - gamma_mu) U_mu(n) psi(n+mu)
  *                                       + (1 + gamma_mu) U_mu(n-mu)^H psi(n-mu) ]
  * Wilson parameter r = 1, gamma matrices in the DeGrand-Rossi (chiral) basis
@@ -94,7 +94,7 @@ typedef struct {
   const void *links;   /* device, complex double, 4*sites*9 elements */
 } seed_wilson;
 
-/* Parameters (Sec. 3 algorithm "Start": m, the frequency of
+/* Parameters (the inputs of the Sec. 3 algorithm: m, the frequency of
  * reorthogonalization; tolerances for the seed and the remaining systems). */
 typedef struct {
   int32_t m_max;          /* m: maximum Lanczos steps kept in V (>= 1) */
@@ -183,7 +183,7 @@ seed_status seed_create_csr(seed_ctx **out, const seed_csr *A, const seed_params
 seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_params *p,
                                seed_stream stream);
 
-/* Sec. 3 "Lanczos Version of Single Seed CG with Periodic Reorthogonalization",
+/* Sec. 3, the Lanczos form of single-seed CG with periodic reorthogonalization,
  * steps 1-9, on the first column of B, seeding columns 2..nrhs (steps 4, 7).
  *   B: n x nrhs (ldb), X: n x nrhs (ldx).  X in: initial guesses (ignored if
  *   x0_zero); X out: x^1 solved, x^2..x^nrhs seeded.  B and X must not overlap.
@@ -196,15 +196,15 @@ seed_status seed_solve_first(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
                              int32_t nrhs, seed_info *info);
 
 /* Galerkin projection of further right-hand sides over the kept basis of the
- * last seed_solve_first (Sec. 2.1: seeding projects "over the Krylov
- * subspace" of the first system):  x += V T^{-1} V^H (b - A x).
+ * last seed_solve_first (Sec. 2.1: seeding projects onto the Krylov subspace
+ * built for the first system):  x += V T^{-1} V^H (b - A x).
  * Requires keep_basis = 1 (else SEED_ESTATE).  Costs ncols mvps unless
  * x0_zero, in which case X is overwritten. */
 seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
                          int32_t ncols);
 
-/* Plain CG (Sec. 1, Sec. 2.2: "The other right-hand sides, after being
- * seeded, are solved with CG") on columns 2..nrhs of B from the seeded X, run
+/* Plain CG (Sec. 1, Sec. 2.2: once seeded, the remaining systems are finished
+ * by CG) on columns 2..nrhs of B from the seeded X, run
  * in lockstep with per-column scalars.  Column 1 (the seed system) is left
  * untouched.  Stops each column at ||r|| <= tol_rest ||b^j||, then checks the
  * true residual and restarts from it if it exceeds 1.5 tol_rest.
@@ -213,7 +213,7 @@ seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int
 seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
                             int32_t nrhs, seed_info *info);
 
-/* Sec. 2.3 "Single Seeding of Related Right-hand Sides", steps 3-4, after
+/* Sec. 2.3 (single seeding for related right-hand sides), steps 3-4, after
  * seed_solve_first (step 2) on the same B and X: the remaining systems are
  * projected over x^1 (x^1_bcg = 0, r^1_bcg = b^1); then for j = 2..nrhs, CG
  * runs on system j from its current approximation x^j_bcg (residual r^j_bcg)

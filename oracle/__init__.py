@@ -287,7 +287,7 @@ def seed_multiple(op: Operator, B, *, tol: float = 1e-8, maxit: int = 100000) ->
 
 def seed_solve_related(op: Operator, B, *, m_max: int, reorth_freq: int, reorth_passes: int = 2,
                        tol_seed: float = 1e-12, tol_rest: float = 1e-8, maxit_rest: int = 100000) -> dict:
-    """Sec. 2.3, "Single Seeding of Related Right-hand Sides": step 2 by the
+    """Sec. 2.3 (single seeding for related right-hand sides): step 2 by the
     Sec. 3 seed solve (no initial guesses), then steps 3-4: project the
     remaining systems over x^1 (x^1_bcg = 0, r^1_bcg = b^1); for j = 2..nrhs run
     CG on system j from its current approximation and project the later

@@ -18,14 +18,14 @@
  *   orc_wilson_dslash .... Wilson-Dirac D (sign=+1) or D^H (sign=-1); the
  *                          paper (Sec. 4) names D but does not define it, so
  *                          the textbook Wilson operator with r = 1 is used
- *   orc_op_apply ......... A = D^H D (Sec. 4: "multiply the system by the
- *                          Hermitian transpose"), or CSR, or dense
- *   orc_seed_first ....... Sec. 3, "Lanczos Version of Single Seed CG with
- *                          Periodic Reorthogonalization", steps 1-9
+ *   orc_op_apply ......... A = D^H D (Sec. 4: the system multiplied by
+ *                          D^H to make it Hermitian), or CSR, or dense
+ *   orc_seed_first ....... Sec. 3, the Lanczos form of single-seed CG with
+ *                          periodic reorthogonalization, steps 1-9
  *   orc_cg ............... plain CG (Hestenes-Stiefel) for the seeded systems
  *                          (Sec. 1, Sec. 2.2)
- *   orc_related_project .. Sec. 2.3 "Single Seeding of Related Right-hand
- *                          Sides", step 3 (projection over x_cg)
+ *   orc_related_project .. Sec. 2.3 (single seeding for related right-hand
+ *                          sides), step 3 (projection over x_cg)
  *   orc_cholesky_solve ... dense Hermitian Cholesky (pin only)
  *   orc_tridiag_eigs ..... eigenvalues of the Lanczos tridiagonal by Sturm
  *                          bisection (pin only)
@@ -55,7 +55,7 @@ static inline zc zscale(double s, zc a) { return zmk(s * a.re, s * a.im); }
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENOTSPD = 4, ORC_ENOTCONV = 5 };
 
 /* ------------------------------------------------------------------------ */
-/* length-n vector operations (the paper's "vector operations", Table 2.1)  */
+/* length-n vector operations (the vector operations Table 2.1 counts)  */
 /* ------------------------------------------------------------------------ */
 
 /* a^H b, summed in index order */
