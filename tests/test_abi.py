@@ -4,6 +4,8 @@ import ctypes as C
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -72,3 +74,15 @@ def test_argument_errors_are_status_codes(seedlib):
     assert L.seed_solve_rest(None, None, 0, None, 0, 1, None) == P.SEED_EINVAL
     assert L.seed_project(None, None, 0, None, 0, 1) == P.SEED_EINVAL
     L.seed_destroy(None)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No fallback: without libseed.so every entry point raises instead of
+    computing anything another way."""
+    from paper_0810_0330_gb300 import binding as B
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", "/nonexistent/libseed.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        B.seed_params_default()
+    with pytest.raises(RuntimeError, match="not built"):
+        B.seed_inject_alloc_failure(0)
