@@ -1,0 +1,38 @@
+"""Host arithmetic of bench.py's roofline and CG-branch bookkeeping (no GPU)."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_algorithmic_bytes_and_flops_per_unit():
+    # Wilson D per site: 4 links of 9 complex (144 B in FP64) read once, and a
+    # 12-component spinor in and out per column (192 B each in FP64)
+    assert bench.wilson_bytes(1, 1) == 4 * 9 * 16 + 2 * 12 * 16 == 960
+    assert bench.wilson_bytes(4096, 11) == 4096 * (576 + 11 * 384)
+    assert bench.wilson_bytes(131072, 11, fp32=True) == 314572800   # the 16^3 x 32 FP32 launch
+    # CSR: 8 B value + 4 B index per nonzero, row pointers, x read and y written once
+    assert bench.csr_bytes(4096, 20224) == 12 * 20224 + 4 * 4097 + 16 * 4096 == 324612
+    # 1320 hopping flops (8 hops: projection, 3x3 complex matrix times two colour vectors,
+    # accumulation) + 48 for psi - kappa * sum
+    assert bench.FLOPS_PER_SITE_D == 1368
+    assert abs(bench.FP64_PEAK_GFLOPS - 1258.56) < 1e-9
+
+
+def test_cg_branch_columns():
+    for nc in range(1, 64):
+        cols = bench.cg_branch_cols(nc)
+        assert sum(cols) == nc and 1 <= len(cols) <= 3
+        assert max(cols) - min(cols) <= 1
+        if nc >= 2:
+            assert min(cols) >= 2 or len(cols) == 1
+    assert bench.cg_branch_cols(11) == [3, 4, 4]
+
+
+def test_traffic_entries_only_for_captured_sources():
+    # a traffic figure is reported only while the kernel source matches the capture
+    assert bench.dslash_traffic() in (None, *bench.DSLASH_TRAFFIC.values())
+    assert bench.dslash_traffic(fp32=True) in (None, *bench.DSLASH32_TRAFFIC.values())
+    assert len(bench.dslash_source_hash()) == 16 and bench.dslash_source_hash() != bench.dslash_source_hash(fp32=True)
