@@ -49,18 +49,26 @@ typedef enum {
   SEED_ENOMEM = 2,   /* device allocation failed */
   SEED_ECUDA = 3,    /* a CUDA runtime call failed (including no usable device) */
   SEED_ENOTSPD = 4,  /* the LU of the Lanczos tridiagonal met delta_i <= 0 or NaN:
-                        A is not positive definite in floating point (Sec. 3,
-                        "LU factorization ... QR or LQ should be used for
-                        indefinite systems") */
+                        A is not positive definite in floating point (Sec. 3
+                        uses an LU factorization, which needs a definite T) */
   SEED_ENOTCONV = 5, /* an iteration cap was reached before the tolerance */
   SEED_ESTATE = 6,   /* call out of order (e.g. seed_project without a kept basis) */
   SEED_ETIMEOUT = 7  /* a grid barrier of a persistent kernel waited longer than its limit (2 s);
                         the kernel left without hanging, the results are not valid */
 } seed_status;
 
+/* Element types.  The caller's operator arrays, right-hand sides and
+ * solutions are always SEED_F64 (CSR) or SEED_C128 (Wilson): the paper's
+ * method is stated for one precision (Sec. 3), and the precision the solver
+ * computes in is a solver parameter (seed_params.precision), not a property
+ * of the operator.  SEED_F32 / SEED_C64 name the element type of the FP32
+ * operator copy and Krylov vectors a mixed-precision context keeps, which
+ * seed_apply ops 3-7 read and write (SEED_F32 for CSR, SEED_C64 for Wilson). */
 typedef enum {
   SEED_F64 = 0,      /* real double */
-  SEED_C128 = 1      /* complex double, interleaved */
+  SEED_C128 = 1,     /* complex double, interleaved */
+  SEED_F32 = 2,      /* real float (mixed-precision CSR vectors) */
+  SEED_C64 = 3       /* complex float, interleaved (mixed-precision Wilson vectors) */
 } seed_dtype;
 
 /* Real symmetric positive definite matrix in CSR form (device arrays).
@@ -118,14 +126,14 @@ typedef struct {
                              1: step kernels only;
                              2: as 0, and FP64 CG in one persistent kernel as well (nrhs <= 33).
                              With two or more systems and a frequency of 0 or >= 8 the seeding of
-                             systems 2..p (Sec. 3 steps 4 and 7) is folded into x^2..x^p once per
+                             systems 2..p (Sec. 3) is folded into x^2..x^p once per
                              block of at most 128 steps instead of every step (same vectors, other
                              summation order). */
   int32_t precision;      /* 0 (default): FP64 throughout.
                              1: mixed.  Operator applies and Krylov vectors (V included) in FP32
                              (the context keeps an FP32 copy of the operator); every scalar of the
                              recurrences and every reduction in FP64.  The FP32 seed Lanczos seeds
-                             all systems (Sec. 3 steps 1-9, same stopping rule), the corrections
+                             all systems (the Sec. 3 algorithm, same stopping rule), the corrections
                              are added to X in FP64, then each system is finished by CG with FP32
                              iterations and FP64 reliable updates (x += the FP32 correction,
                              r = b - A x recomputed with the FP64 operator) until the FP64 true
@@ -172,19 +180,33 @@ int32_t seed_abi_version(void);
  * reliable_delta 0.  Returns SEED_EINVAL if p is NULL. */
 seed_status seed_params_default(seed_params *p);
 
-/* Create a context for a real CSR operator (dtype SEED_F64).  Allocates the
- * Lanczos basis V (n x (m_max+1) doubles) and work space on the current
- * device.  *out is NULL on failure. */
+/* Create a context for a real CSR operator (dtype SEED_F64): the matrix A of
+ * the systems A x^j = b^j, symmetric positive definite (Sec. 1).  Allocates
+ * the Lanczos basis V (n x (m_max+1) doubles; Sec. 3 keeps the Lanczos vectors
+ * of the seed system for reorthogonalization and notes that this storage can
+ * be allocated and freed at run time) and work space on the current device.
+ *   out: receives the context (NULL on failure).  A: host struct whose arrays
+ *   are device pointers that must stay valid until seed_destroy.  p: host
+ *   struct, copied.  stream: every later call on the context is ordered on it.
+ * Returns SEED_OK, SEED_EINVAL (NULL argument, malformed CSR, bad parameter:
+ * checked on the host before any device work), SEED_ENOMEM, SEED_ECUDA. */
 seed_status seed_create_csr(seed_ctx **out, const seed_csr *A, const seed_params *p,
                             seed_stream stream);
 
-/* Create a context for the Wilson normal operator (dtype SEED_C128).  Builds
- * the site -> 8 neighbour table on the device. */
+/* Create a context for the Wilson normal operator A = D^H D (dtype SEED_C128):
+ * Sec. 4 makes the non-Hermitian lattice system Hermitian positive definite by
+ * multiplying it with D^H, so each iteration applies D twice.  Builds the
+ * site -> 8 neighbour table on the device and allocates V and the work space
+ * as seed_create_csr does (Sec. 3: basis storage allocated at run time).
+ *   out, p, stream: as for seed_create_csr.  A: host struct; A->links is a
+ *   device pointer that must stay valid until seed_destroy.
+ * Returns SEED_OK, SEED_EINVAL (dims < 2, bc_t not 0/1, kappa not finite, bad
+ * parameter), SEED_ENOMEM, SEED_ECUDA. */
 seed_status seed_create_wilson(seed_ctx **out, const seed_wilson *A, const seed_params *p,
                                seed_stream stream);
 
 /* Sec. 3, the Lanczos form of single-seed CG with periodic reorthogonalization,
- * steps 1-9, on the first column of B, seeding columns 2..nrhs (steps 4, 7).
+ * on the first column of B, seeding columns 2..nrhs as the basis grows.
  *   B: n x nrhs (ldb), X: n x nrhs (ldx).  X in: initial guesses (ignored if
  *   x0_zero); X out: x^1 solved, x^2..x^nrhs seeded.  B and X must not overlap.
  *   info: NULL or nrhs entries; entry 0 receives the seed system's results
@@ -213,8 +235,8 @@ seed_status seed_project(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int
 seed_status seed_solve_rest(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx,
                             int32_t nrhs, seed_info *info);
 
-/* Sec. 2.3 (single seeding for related right-hand sides), steps 3-4, after
- * seed_solve_first (step 2) on the same B and X: the remaining systems are
+/* Sec. 2.3 (single seeding for related right-hand sides), after
+ * seed_solve_first (which solves and seeds system 1) on the same B and X: the remaining systems are
  * projected over x^1 (x^1_bcg = 0, r^1_bcg = b^1); then for j = 2..nrhs, CG
  * runs on system j from its current approximation x^j_bcg (residual r^j_bcg)
  * to tol_rest, and every later system i receives the Galerkin projection over
@@ -303,7 +325,7 @@ seed_status seed_check_barrier_timeout(seed_stream stream, int32_t *timed_out, d
  * Synchronises the stream.  This is the table the Wilson kernels use. */
 seed_status seed_wilson_neighbors(const int32_t dims[4], int32_t *nbr, seed_stream stream);
 
-/* Tridiagonal T of the last seed solve (Sec. 3 steps 2, 5, 9):
+/* Tridiagonal T of the last seed solve (the Lanczos coefficients of Sec. 3):
  * alpha[0..m-1] = alpha_1..alpha_m, beta[0..m] = beta_0..beta_m (beta_0 =
  * ||r_0^1||), host arrays of capacity cap >= m+1; *m receives the number of
  * Lanczos steps.  With alpha and beta both NULL only *m is returned.
@@ -325,9 +347,12 @@ seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out);
  * problem (n x nrhs) first, so the launches and CUDA graphs of many small
  * problems overlap on the GPU instead of running one after another.  The
  * contexts must be distinct and must not be used by other threads meanwhile.
- * Each problem runs exactly the arithmetic of a solo solve with kernel_path
- * 1 (the persistent cooperative kernels are not used inside a batch), so its
- * results are bitwise those of that solo solve.  Returns SEED_OK, or the
+ * Each problem runs the arithmetic of a solo solve on its context: the
+ * persistent seed runs of kernel_path 0 and 2 run side by side (each waits
+ * only on its own blocks), while the persistent FP64 CG of kernel_path 2 is
+ * replaced inside a batch by the graph-replayed CG of kernel_path 0.  So each
+ * problem's results are bitwise those of a solo solve with its kernel_path (0
+ * for a kernel_path 2 context).  Returns SEED_OK, or the
  * status of the first failing problem (in problem order; the others still
  * run), with seed_last_error(NULL) naming it. */
 seed_status seed_batch_solve(seed_ctx *const *ctxs, const void *const *B, const int64_t *ldb, void *const *X,
@@ -343,6 +368,17 @@ seed_status seed_batch_solve(seed_ctx *const *ctxs, const void *const *B, const 
  * around the launches; *ms_per_apply receives the mean device time of one
  * application.  Synchronises.  reps in [1, 100000], ncols in [1, 64]. */
 seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t reps, double *ms_per_apply);
+
+/* Measurement helper (no counterpart in the paper): the FMA rate of the FP64
+ * (dtype SEED_F64) or FP32 (SEED_F32) pipe of the current device, the
+ * roofline denominator of the kernels bound by that pipe (the FP64 Wilson
+ * operator).  Every thread of a grid of 8 blocks of 256 threads per SM runs 8
+ * independent chains of 4096 fused multiply-adds; *tflops = 2 x FMAs / time
+ * of the fastest of five launches (CUDA events on `stream`, after one
+ * warm-up); *ms (may be NULL) that launch's time.  Allocates no device
+ * memory; synchronises `stream`.  SEED_EINVAL for another dtype or a NULL
+ * tflops, SEED_ECUDA without a usable device. */
+seed_status seed_time_fma(int32_t dtype, seed_stream stream, double *tflops, double *ms);
 
 /* Y = D^H D X (the Wilson normal operator, as seed_apply op 0 on a Wilson
  * context) WITHOUT allocating any device memory.  The paper has no
@@ -360,18 +396,29 @@ seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t
  * lattice allows up to 10 columns).  The array is shared by all calls and keeps
  * the last call's contents (each call overwrites what it reads, so nothing
  * needs clearing); calls whose work overlaps on the GPU (other streams, or
- * other host threads) race on it -- serialise them.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.  Never
- * calls cudaMalloc, cudaFree or any allocating routine. */
+ * other host threads) race on it -- serialise them.  The call runs in the
+ * CUDA context current on the calling thread (the device's primary context
+ * unless the caller made another one current); the first call on each device
+ * and context looks up the array's device address there
+ * (cudaGetSymbolAddress, with that device current) and keeps it, and a later
+ * call from another context (after cudaDeviceReset, or a driver context of the
+ * caller's) looks it up again.  Make that first call before any stream
+ * capture.  Never calls cudaMalloc, cudaFree or any allocating routine. */
 seed_status seed_wilson_apply_noalloc(const seed_wilson *A, const void *X, int64_t ldx, void *Y, int64_t ldy,
                                       int32_t ncols, seed_stream stream);
 
 /* One-line reason for the last failure on ctx (or of the last failed
- * seed_create_* / context-free call on this thread when ctx is NULL). */
+ * seed_create_* / context-free call on this thread when ctx is NULL).  The
+ * paper has no counterpart: this is the library's error reporting.  The
+ * string is owned by the library and valid until the next call on ctx (or,
+ * for NULL, on this thread); never NULL. */
 const char *seed_last_error(const seed_ctx *ctx);
 
-/* Free V, the work space and the context.  NULL-safe.  Synchronises. */
+/* Free V, the work space and the context (Sec. 3: the Lanczos vectors are
+ * needed only while the seed system is solved and seeds the others, and their
+ * storage can be released at run time; keep_basis = 1 keeps it until here).
+ * Never frees the caller's arrays.  NULL-safe.  Synchronises the context's
+ * stream; no status (nothing can be reported after the context is gone). */
 void seed_destroy(seed_ctx *ctx);
 
 #ifdef __cplusplus

@@ -22,20 +22,34 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "seed_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_lib = None          # the library the functions below call
+_libs = {}           # loaded builds by path
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 4: "ENOTSPD", 5: "ENOTCONV"}
 
 
-def build(force: bool = False) -> str:
-    """Compile seed_oracle.c into liboracle.so (gcc, -O2, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                        "-o", tmp, _SRC, "-lm"], check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile seed_oracle.c into liboracle.so (gcc, -O2, no FMA contraction),
+    or with omp=True into liboracle_omp.so: the same source with OpenMP on its
+    independent loops (bit-identical results; for timing on all host cores)."""
+    lib = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + ".%d.tmp" % os.getpid()
+        extra = ["-fopenmp", "-DORC_OMP"] if omp else []
+        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"] + extra +
+                       ["-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, lib)
+    return lib
+
+
+def _open(path):
+    if path not in _libs:
+        lib = C.CDLL(path)
+        _declare(lib)
+        _libs[path] = lib
+    return _libs[path]
 
 
 def _load():
@@ -43,9 +57,23 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            _lib = C.CDLL(_LIB)
-            _declare(_lib)
+            _lib = _open(_LIB)
     return _lib
+
+
+def set_threads(k: int) -> int:
+    """Run the oracle on k host threads from now on (k <= 1: the one-thread
+    build, k > 1: the OpenMP build, same results bit for bit).  Returns the
+    number of threads the active build uses."""
+    global _lib
+    with _lock:
+        if k <= 1:
+            build()
+            _lib = _open(_LIB)
+        else:
+            build(omp=True)
+            _lib = _open(_LIB_OMP)
+        return int(_lib.orc_threads(int(k)))
 
 
 class _Op(C.Structure):
@@ -73,10 +101,12 @@ class _CgOut(C.Structure):
 
 def _declare(lib):
     P = C.c_void_p
+    lib.orc_threads.argtypes = [C.c_int]
+    lib.orc_threads.restype = C.c_int
     lib.orc_csr_apply.argtypes = [C.c_int64, P, P, P, P, P]
     lib.orc_wilson_neighbors.argtypes = [P, P]
     lib.orc_wilson_dslash.argtypes = [P, C.c_double, C.c_int32, C.c_int32, P, P, P]
-    lib.orc_seed_multiple.argtypes = [C.POINTER(_Op), C.c_int32, P, P, C.c_double, C.c_int32, P, P, P]
+    lib.orc_seed_multiple.argtypes = [C.POINTER(_Op), C.c_int32, P, P, C.c_double, C.c_int32, P, P, P, P]
     lib.orc_seed_multiple.restype = C.c_int
     lib.orc_wilson_dA_dkappa.argtypes = [P, C.c_double, C.c_int32, P, P, P]
     lib.orc_wilson_dA_dkappa.restype = C.c_int
@@ -217,7 +247,8 @@ def wilson_neighbors(dims) -> np.ndarray:
 def seed_first(op: Operator, B, X0=None, *, m_max: int, reorth_freq: int = 0, reorth_passes: int = 2,
                tol: float = 1e-8, extra_iters: int = 0, breakdown_rel: float = 1e-14,
                keep_V: bool = False) -> dict:
-    """Sec. 3 algorithm (steps 1-9) on all columns of B (n x nrhs)."""
+    """The Sec. 3 seed solve (Lanczos form of CG, periodic reorthogonalization,
+    seeding of the other columns) on all columns of B (n x nrhs)."""
     B = np.asfortranarray(B, dtype=np.complex128)
     n, nrhs = B.shape
     assert n == op.n
@@ -277,18 +308,20 @@ def seed_multiple(op: Operator, B, *, tol: float = 1e-8, maxit: int = 100000) ->
     B = np.asfortranarray(B, dtype=np.complex128)
     n, p = B.shape
     X = np.zeros((n, p), dtype=np.complex128, order="F")
+    Xs = np.zeros((n, p), dtype=np.complex128, order="F")
     iters = np.zeros(p, dtype=np.int32)
     mvps = np.zeros(p, dtype=np.int32)
     relres = np.zeros(p, dtype=np.float64)
     rc = _load().orc_seed_multiple(C.byref(op.s), p, _p(B), _p(X), float(tol), int(maxit), _p(iters), _p(mvps),
-                                   _p(relres))
-    return dict(status=STATUS.get(rc, rc), X=X, iters=iters.tolist(), mvps=mvps.tolist(), relres=relres.tolist())
+                                   _p(relres), _p(Xs))
+    return dict(status=STATUS.get(rc, rc), X=X, X_seeded=Xs, iters=iters.tolist(), mvps=mvps.tolist(),
+                relres=relres.tolist())
 
 
 def seed_solve_related(op: Operator, B, *, m_max: int, reorth_freq: int, reorth_passes: int = 2,
                        tol_seed: float = 1e-12, tol_rest: float = 1e-8, maxit_rest: int = 100000) -> dict:
-    """Sec. 2.3 (single seeding for related right-hand sides): step 2 by the
-    Sec. 3 seed solve (no initial guesses), then steps 3-4: project the
+    """Sec. 2.3 (single seeding for related right-hand sides): system 1 by the
+    Sec. 3 seed solve (no initial guesses), then: project the
     remaining systems over x^1 (x^1_bcg = 0, r^1_bcg = b^1); for j = 2..nrhs run
     CG on system j from its current approximation and project the later
     systems over that CG's correction x^j - x^j_bcg (orc_related_project)."""
@@ -314,7 +347,7 @@ def seed_solve_related(op: Operator, B, *, m_max: int, reorth_freq: int, reorth_
 
 
 def related_project(x_cg, r_bcg, x_bpr, r_bpr):
-    """Sec. 2.3 step 3, in place on copies; returns (x_new, r_new)."""
+    """The Sec. 2.3 projection over one CG correction, on copies; returns (x_new, r_new)."""
     x_cg = _zvec(x_cg)
     r_bcg = _zvec(r_bcg)
     x = np.array(x_bpr, dtype=np.complex128, copy=True)

@@ -21,11 +21,11 @@
  *   orc_op_apply ......... A = D^H D (Sec. 4: the system multiplied by
  *                          D^H to make it Hermitian), or CSR, or dense
  *   orc_seed_first ....... Sec. 3, the Lanczos form of single-seed CG with
- *                          periodic reorthogonalization, steps 1-9
+ *                          periodic reorthogonalization
  *   orc_cg ............... plain CG (Hestenes-Stiefel) for the seeded systems
  *                          (Sec. 1, Sec. 2.2)
  *   orc_related_project .. Sec. 2.3 (single seeding for related right-hand
- *                          sides), step 3 (projection over x_cg)
+ *                          sides): the projection over one CG correction
  *   orc_cholesky_solve ... dense Hermitian Cholesky (pin only)
  *   orc_tridiag_eigs ..... eigenvalues of the Lanczos tridiagonal by Sturm
  *                          bisection (pin only)
@@ -41,6 +41,26 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* All-cores build (-fopenmp -DORC_OMP, used only to time the oracle on every
+ * host core): the loops whose iterations are independent -- operator applies
+ * row by row or site by site, axpys and scalings -- are split over threads;
+ * every reduction (dot product, norm) keeps its one-thread index order, so the
+ * results are bit-identical to the one-thread build. */
+#ifdef ORC_OMP
+#include <omp.h>
+#define ORC_PAR _Pragma("omp parallel for schedule(static)")
+int orc_threads(int k) {
+  if (k > 0) omp_set_num_threads(k);
+  return omp_get_max_threads();
+}
+#else
+#define ORC_PAR
+int orc_threads(int k) {
+  (void)k;
+  return 1;
+}
+#endif
 
 typedef struct { double re, im; } zc;
 
@@ -73,6 +93,7 @@ static double vnorm(int64_t n, const zc *a) {
 
 /* y += alpha x */
 static void vaxpy(int64_t n, zc alpha, const zc *x, zc *y) {
+  ORC_PAR
   for (int64_t k = 0; k < n; ++k) y[k] = zadd(y[k], zmul(alpha, x[k]));
 }
 
@@ -83,6 +104,7 @@ static void vaxpy(int64_t n, zc alpha, const zc *x, zc *y) {
 /* y = A x, A real CSR (row_ptr[n+1], col_idx[nnz], vals[nnz]) */
 void orc_csr_apply(int64_t n, const int32_t *row_ptr, const int32_t *col_idx,
                    const double *vals, const zc *x, zc *y) {
+  ORC_PAR
   for (int64_t r = 0; r < n; ++r) {
     zc s = zmk(0.0, 0.0);
     for (int32_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k)
@@ -95,6 +117,7 @@ void orc_csr_apply(int64_t n, const int32_t *row_ptr, const int32_t *col_idx,
  * nbr[8*s + 2*mu + 1] = s - mu-hat, periodic wrap in every direction. */
 void orc_wilson_neighbors(const int32_t dims[4], int32_t *nbr) {
   int64_t vol = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  ORC_PAR
   for (int64_t s = 0; s < vol; ++s) {
     int32_t c[4];
     int64_t rem = s;
@@ -147,6 +170,7 @@ void orc_wilson_dslash(const int32_t dims[4], double kappa, int32_t bc_t, int32_
   int64_t vol = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
   int32_t *nbr = (int32_t *)malloc(sizeof(int32_t) * 8 * vol);
   orc_wilson_neighbors(dims, nbr);
+  ORC_PAR
   for (int64_t s = 0; s < vol; ++s) {
     int32_t t_coord = (int32_t)(s / ((int64_t)dims[0] * dims[1] * dims[2]));
     zc acc[4][3];
@@ -201,10 +225,13 @@ int orc_wilson_dA_dkappa(const int32_t dims[4], double kappa, int32_t bc_t, cons
   if (!t1 || !t2) { free(t1); free(t2); return 2; }
   orc_wilson_dslash(dims, kappa, bc_t, +1, links, x, t1);       /* t1 = D x */
   orc_wilson_dslash(dims, 1.0, bc_t, -1, links, t1, t2);        /* t2 = D x - H^H D x */
+  ORC_PAR
   for (int64_t i = 0; i < n; ++i) y[i] = zsub(t2[i], t1[i]);    /* y = -H^H D x */
   orc_wilson_dslash(dims, 1.0, bc_t, +1, links, x, t1);         /* t1 = x - H x */
+  ORC_PAR
   for (int64_t i = 0; i < n; ++i) t1[i] = zsub(x[i], t1[i]);    /* t1 = H x */
   orc_wilson_dslash(dims, kappa, bc_t, -1, links, t1, t2);      /* t2 = D^H H x */
+  ORC_PAR
   for (int64_t i = 0; i < n; ++i) y[i] = zsub(y[i], t2[i]);
   free(t1);
   free(t2);
@@ -237,6 +264,7 @@ int orc_op_apply(const orc_op *A, const zc *x, zc *y) {
     orc_wilson_dslash(A->dims, A->kappa, A->bc_t, -1, A->links, t, y);
     free(t);
   } else {
+    ORC_PAR
     for (int64_t r = 0; r < n; ++r) {
       zc s = zmk(0.0, 0.0);
       for (int64_t c = 0; c < n; ++c) s = zadd(s, zmul(A->dense[r * n + c], x[c]));
@@ -280,17 +308,30 @@ static void cgs(int64_t n, const zc *V, int32_t k, int32_t passes, zc *x, zc *h)
 }
 
 /*
+ * The seed solve of Sec. 3, written as what it is: the Lanczos process on
+ * r_0^1 builds the orthonormal basis V and the tridiagonal T (diagonal alpha,
+ * off-diagonal beta); CG is the solution of T y = beta_0 e_1 through the LU
+ * factorisation T = L U, whose pivots delta_i and multipliers gamma_i are
+ * formed one step at a time, with W = V U^{-1} (the w_i) so that
+ * x^1 = x_0^1 + W L^{-1} beta_0 e_1 (the zeta_i) grows by one term per step.
+ * The other right-hand sides receive the same Galerkin projection over the
+ * growing space, x^j = x_0^j + V T^{-1} V^H r_0^j, also one term per step: the
+ * eta^j are the entries of L^{-1} V^H r_0^j.  Every few steps the newest
+ * basis vector and the next Lanczos direction are made orthogonal again to
+ * all stored vectors.
+ *
  * B, X: column-major n x nrhs (ld = n).  X holds the initial guesses on entry
  * (ignored when x0_zero) and on exit x^1 (solved) and x^2..x^nrhs (seeded).
  * alpha[m_max], beta[m_max+1] (beta[0] = beta_0), rho_hist[m_max] may be NULL.
  * V may be NULL or n x (m_max+1) to receive the Lanczos vectors as stored.
  * Returns ORC_OK, ORC_ENOTSPD (delta_i <= 0 or not finite), ORC_ENOMEM.
  *
- * Readings where the paper is silent: v_2 = f / beta_1 after step 2 (as in
- * step 9); step 8 first applies at i = 2 (step 2 has no reorthogonalization);
- * alpha_i is the real part of v_i^H f; the modified v_i of step 8 is what V
- * keeps and what the next step 5 uses as v_{i-1}, while alpha_i, w_i and
- * eta^j keep the values computed from v_i before step 8.
+ * Readings where the paper is silent: the second basis vector is f / beta_1,
+ * formed exactly as every later one; the first reorthogonalization can come
+ * at i = 2 (the first step has none); alpha_i is the real part of v_i^H f;
+ * after a reorthogonalization the corrected v_i is what V keeps and what the
+ * next step's three-term recurrence uses as v_{i-1}, while alpha_i, w_i and
+ * eta^j keep the values computed from v_i before the correction.
  */
 int orc_seed_first(const orc_op *A, int32_t nrhs, const zc *B, zc *X,
                    const orc_seed_params *P, orc_seed_out *out,
@@ -311,7 +352,7 @@ int orc_seed_first(const orc_op *A, int32_t nrhs, const zc *B, zc *X,
   zc *eta = (zc *)malloc(sizeof(zc) * nrhs);
   if (!V || !R0 || !f || !w || !tmp || !h || !eta) { status = ORC_ENOMEM; goto done; }
 
-  /* Step 1: x^j = initial guess, r_0^j = b^j - A x^j */
+  /* initial residuals of every system */
   for (int32_t j = 0; j < nrhs; ++j) {
     zc *xj = X + (int64_t)j * n, *rj = R0 + (int64_t)j * n;
     const zc *bj = B + (int64_t)j * n;
@@ -321,32 +362,35 @@ int orc_seed_first(const orc_op *A, int32_t nrhs, const zc *B, zc *X,
     } else {
       orc_op_apply(A, xj, tmp);
       out->mvps++;
+      ORC_PAR
       for (int64_t k = 0; k < n; ++k) rj[k] = zsub(bj[k], tmp[k]);
     }
   }
   out->bnorm1 = vnorm(n, B);
 
-  /* Step 2: beta_0 = ||r_0^1||; v_1 = r_0^1/beta_0; f = A v_1; alpha_1 = v_1^H f;
-   *         f = f - alpha_1 v_1 */
+  /* first basis vector from the seed system's residual, first diagonal entry of T */
   double beta0 = vnorm(n, R0);
   if (beta) beta[0] = beta0;
   if (beta0 == 0.0) { out->iters = 0; goto done; }
   zc *v1 = V;
+  ORC_PAR
   for (int64_t k = 0; k < n; ++k) v1[k] = zmk(R0[k].re / beta0, R0[k].im / beta0);
   orc_op_apply(A, v1, f);
   out->mvps++;
   double ai = vdot(n, v1, f).re;
+  ORC_PAR
   for (int64_t k = 0; k < n; ++k) f[k] = zsub(f[k], zscale(ai, v1[k]));
   if (alpha) alpha[0] = ai;
 
-  /* Step 3: delta_1 = alpha_1; w_1 = v_1/delta_1; zeta_1 = beta_0; x^1 += zeta_1 w_1 */
+  /* the LU factorisation starts with the pivot alpha_1; first term of x^1 */
   double delta = ai;
   if (!(delta > 0.0) || !isfinite(delta)) { status = ORC_ENOTSPD; out->iters = 1; goto done; }
+  ORC_PAR
   for (int64_t k = 0; k < n; ++k) w[k] = zmk(v1[k].re / delta, v1[k].im / delta);
   double zeta = beta0;
   vaxpy(n, zmk(zeta, 0.0), w, X);
 
-  /* Step 4: eta^j = v_1^H r_0^j; x^j += eta^j w_1 */
+  /* first projection coefficient of every other system */
   for (int32_t j = 1; j < nrhs; ++j) {
     eta[j] = vdot(n, v1, R0 + (int64_t)j * n);
     vaxpy(n, eta[j], w, X + (int64_t)j * n);
@@ -357,7 +401,7 @@ int orc_seed_first(const orc_op *A, int32_t nrhs, const zc *B, zc *X,
   double tnorm = 0.0;      /* max_k (|alpha_k| + beta_{k-1} + beta_k): row sums of |T| */
   int32_t stop_at = -1;
   for (;;) {
-    /* Step 9 (and the end of step 2): beta_i = ||f|| */
+    /* off-diagonal entry beta_i, residual estimate, stopping tests */
     double bi = vnorm(n, f);
     if (beta) beta[i] = bi;
     double row = fabs(ai) + beta_im1 + bi;
@@ -373,27 +417,30 @@ int orc_seed_first(const orc_op *A, int32_t nrhs, const zc *B, zc *X,
     if (bi <= P->breakdown_rel * tnorm) { out->breakdown = 1; break; }
     if (stop_at >= 0 && i >= stop_at) break;
     if (i >= m) break;
-    /* v_{i+1} = f / beta_i; go to the next step */
+    /* next basis vector */
     zc *vnext = V + (int64_t)i * n;
+    ORC_PAR
     for (int64_t k = 0; k < n; ++k) vnext[k] = zmk(f[k].re / bi, f[k].im / bi);
     beta_im1 = bi;
     i += 1;
     zc *vi = V + (int64_t)(i - 1) * n, *vim1 = V + (int64_t)(i - 2) * n;
 
-    /* Step 5: f = A v_i - beta_{i-1} v_{i-1}; alpha_i = v_i^H f; f = f - alpha_i v_i */
+    /* three-term recurrence: diagonal entry alpha_i and the unnormalised next direction */
     orc_op_apply(A, vi, f);
     out->mvps++;
+    ORC_PAR
     for (int64_t k = 0; k < n; ++k) f[k] = zsub(f[k], zscale(beta_im1, vim1[k]));
     ai = vdot(n, vi, f).re;
+    ORC_PAR
     for (int64_t k = 0; k < n; ++k) f[k] = zsub(f[k], zscale(ai, vi[k]));
     if (alpha) alpha[i - 1] = ai;
 
-    /* Step 6: gamma_{i-1} = beta_{i-1}/delta_{i-1}; delta_i = alpha_i - gamma_{i-1} beta_{i-1};
-     *         w_i = (v_i - beta_{i-1} w_{i-1})/delta_i; zeta_i = -gamma_{i-1} zeta_{i-1};
-     *         x^1 += zeta_i w_i */
+    /* one more row of T = L U: multiplier, pivot (positive for a definite T), the new
+     * column of W and the new term of x^1 */
     double gam = beta_im1 / delta;
     delta = ai - gam * beta_im1;
     if (!(delta > 0.0) || !isfinite(delta)) { status = ORC_ENOTSPD; out->iters = i; goto done; }
+    ORC_PAR
     for (int64_t k = 0; k < n; ++k) {
       zc t = zsub(vi[k], zscale(beta_im1, w[k]));
       w[k] = zmk(t.re / delta, t.im / delta);
@@ -401,18 +448,19 @@ int orc_seed_first(const orc_op *A, int32_t nrhs, const zc *B, zc *X,
     zeta = -gam * zeta;
     vaxpy(n, zmk(zeta, 0.0), w, X);
 
-    /* Step 7: eta^j = v_i^H r_0^j - gamma_{i-1} eta^j; x^j += eta^j w_i */
+    /* the same forward substitution for the other systems' projections */
     for (int32_t j = 1; j < nrhs; ++j) {
       zc g = vdot(n, vi, R0 + (int64_t)j * n);
       eta[j] = zsub(g, zscale(gam, eta[j]));
       vaxpy(n, eta[j], w, X + (int64_t)j * n);
     }
 
-    /* Step 8: if i is a multiple of the frequency, reorthonormalize v_i against
-     * v_1..v_{i-1}, then reorthogonalize f against v_1..v_i */
+    /* periodic reorthogonalization: the newest basis vector against the older ones
+     * (then renormalised), and the next direction against all of them */
     if (P->reorth_freq > 0 && i % P->reorth_freq == 0) {
       cgs(n, V, i - 1, P->reorth_passes, vi, h);
       double nv = vnorm(n, vi);
+      ORC_PAR
       for (int64_t k = 0; k < n; ++k) vi[k] = zmk(vi[k].re / nv, vi[k].im / nv);
       cgs(n, V, i, P->reorth_passes, f, h);
     }
@@ -453,6 +501,7 @@ int orc_cg(const orc_op *A, const zc *b, zc *x, double tol, int32_t maxit,
   int status = ORC_ENOTCONV;
   orc_op_apply(A, x, q);
   out->mvps++;
+  ORC_PAR
   for (int64_t k = 0; k < n; ++k) r[k] = zsub(b[k], q[k]);
   double rr = vnorm(n, r);
   out->true_relres = bn > 0.0 ? rr / bn : 0.0;
@@ -472,12 +521,14 @@ int orc_cg(const orc_op *A, const zc *b, zc *x, double tol, int32_t maxit,
       double rn = vnorm(n, r);
       if (rn <= tol * bn) { reached = 1; break; }
       double be = (rn * rn) / rho;
+      ORC_PAR
       for (int64_t k = 0; k < n; ++k) p[k] = zadd(r[k], zscale(be, p[k]));
       rho = rn * rn;
     }
     /* true residual */
     orc_op_apply(A, x, q);
     out->mvps++;
+    ORC_PAR
     for (int64_t k = 0; k < n; ++k) r[k] = zsub(b[k], q[k]);
     rr = vnorm(n, r);
     out->true_relres = bn > 0.0 ? rr / bn : 0.0;
@@ -501,9 +552,11 @@ done:
  *   eta = (p^H r^i) / (p^H q),  x^i += eta p,  r^i -= eta q,
  * where r^i is the tracked residual of system i (r^i = b^i at the start).
  * CG stops at ||r^j|| <= tol ||b^j||, then the true residual is computed
- * (one mvp).  iters[j], mvps[j] and relres[j] receive each system's counts. */
+ * (one mvp).  iters[j], mvps[j] and relres[j] receive each system's counts;
+ * X_seeded (NULL or n x nrhs) receives x^j as it stands when system j's own
+ * CG starts, i.e. after the projections over the earlier systems' steps. */
 int orc_seed_multiple(const orc_op *A, int32_t nrhs, const zc *B, zc *X, double tol, int32_t maxit,
-                      int32_t *iters, int32_t *mvps, double *relres) {
+                      int32_t *iters, int32_t *mvps, double *relres, zc *X_seeded) {
   int64_t n = A->n;
   zc *R = (zc *)malloc(sizeof(zc) * n * nrhs), *r = (zc *)malloc(sizeof(zc) * n),
      *p = (zc *)malloc(sizeof(zc) * n), *q = (zc *)malloc(sizeof(zc) * n);
@@ -515,9 +568,11 @@ int orc_seed_multiple(const orc_op *A, int32_t nrhs, const zc *B, zc *X, double 
     const zc *b = B + (int64_t)j * n;
     zc *x = X + (int64_t)j * n;
     double bn = vnorm(n, b);
+    if (X_seeded) memcpy(X_seeded + (int64_t)j * n, x, sizeof(zc) * n);
     iters[j] = 0;
     mvps[j] = 1;
     orc_op_apply(A, x, q);
+    ORC_PAR
     for (int64_t k = 0; k < n; ++k) r[k] = zsub(b[k], q[k]);
     double rn = vnorm(n, r);
     if (rn > tol * bn) {
@@ -542,12 +597,14 @@ int orc_seed_multiple(const orc_op *A, int32_t nrhs, const zc *B, zc *X, double 
         rn = vnorm(n, r);
         if (rn <= tol * bn) break;
         double be = (rn * rn) / rho;
+        ORC_PAR
         for (int64_t k = 0; k < n; ++k) p[k] = zadd(r[k], zscale(be, p[k]));
         rho = rn * rn;
       }
     }
     orc_op_apply(A, x, q);
     mvps[j]++;
+    ORC_PAR
     for (int64_t k = 0; k < n; ++k) r[k] = zsub(b[k], q[k]);
     relres[j] = bn > 0.0 ? vnorm(n, r) / bn : 0.0;
     if (relres[j] > 1.5 * tol) status = ORC_ENOTCONV;
@@ -557,7 +614,7 @@ int orc_seed_multiple(const orc_op *A, int32_t nrhs, const zc *B, zc *X, double 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 2.3 step 3: Galerkin projection of a later system over x_cg         */
+/* Sec. 2.3: Galerkin projection of a later system over x_cg              */
 /* ------------------------------------------------------------------------ */
 
 /* delta = x_cg^H r_bpr / x_cg^H r_bcg; x_bpr += delta x_cg; r_bpr -= delta r_bcg */

@@ -7,7 +7,13 @@ column 1, seed_solve_rest on the others), keeping the Lanczos basis.  The
 backward pass solves the adjoint systems A Lambda = G (A is Hermitian) for the
 incoming gradient G = dL/dX: their initial guesses are the Galerkin projection
 of G over the forward basis (seed_project, Sec. 2.1's projection reused for new
-right-hand sides), finished by lockstep CG (seed_solve_cg).  Then
+right-hand sides), finished by lockstep CG (seed_solve_cg) -- when
+seeded_backward is set.  It is off by default: the projection costs two FP64
+passes over the forward basis (V^H G and V c, bound by the FP64 pipe on this
+GPU) and on the 16^4 adjoint workload (kappa 0.150, 8 right-hand sides) it
+saved only 3 % of the backward CG iterations, so the seeded backward took
+longer (467 ms against 453 ms unseeded); by default the adjoint solves start
+from zero and the forward basis is not kept.  Then
 
     dL/dB     = Lambda,
     dL/dkappa = -sum_j Re <Lambda_j, (dA/dkappa) X_j>   (seed_grad_kappa),
@@ -34,9 +40,9 @@ def _colmajor(t: torch.Tensor) -> torch.Tensor:
 class WilsonSeedSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, kappa: torch.Tensor, B: torch.Tensor, links: torch.Tensor, dims, bc_t: int = 0,
-                params: dict | None = None, seeded_backward: bool = True):
+                params: dict | None = None, seeded_backward: bool = False):
         prm = dict(params or {})
-        prm["keep_basis"] = 1
+        prm["keep_basis"] = 1 if seeded_backward else 0
         p = S.seed_params_default(**prm)
         sc = S.seed_create_wilson(tuple(dims), float(kappa), links, p, bc_t=bc_t)
         Bc = _colmajor(B.detach())
@@ -63,6 +69,6 @@ class WilsonSeedSolve(torch.autograd.Function):
 
 
 def wilson_seed_solve(kappa: torch.Tensor, B: torch.Tensor, links: torch.Tensor, dims, bc_t: int = 0,
-                      params: dict | None = None, seeded_backward: bool = True) -> torch.Tensor:
+                      params: dict | None = None, seeded_backward: bool = False) -> torch.Tensor:
     """X = A(kappa)^{-1} B with gradients for kappa and B (see module docstring)."""
     return WilsonSeedSolve.apply(kappa, B, links, dims, bc_t, params, seeded_backward)

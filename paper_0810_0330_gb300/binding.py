@@ -24,6 +24,7 @@ _lib = None
 _lock = threading.Lock()
 
 SEED_OK, SEED_EINVAL, SEED_ENOMEM, SEED_ECUDA, SEED_ENOTSPD, SEED_ENOTCONV, SEED_ESTATE, SEED_ETIMEOUT = range(8)
+SEED_F64, SEED_C128, SEED_F32, SEED_C64 = range(4)
 STATUS_NAMES = ["SEED_OK", "SEED_EINVAL", "SEED_ENOMEM", "SEED_ECUDA", "SEED_ENOTSPD", "SEED_ENOTCONV",
                 "SEED_ESTATE", "SEED_ETIMEOUT"]
 
@@ -32,7 +33,8 @@ EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_c
            "seed_solve_first", "seed_project", "seed_solve_rest", "seed_apply", "seed_wilson_neighbors",
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
            "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related",
-           "seed_batch_solve", "seed_solve_multiple", "seed_inject_alloc_failure", "seed_check_barrier_timeout"]
+           "seed_batch_solve", "seed_solve_multiple", "seed_inject_alloc_failure", "seed_check_barrier_timeout",
+           "seed_time_fma"]
 
 
 class SeedError(RuntimeError):
@@ -113,6 +115,7 @@ def lib():
             L.seed_inject_alloc_failure.argtypes = [I32]
             L.seed_inject_alloc_failure.restype = I32
             L.seed_check_barrier_timeout.argtypes = [P, C.POINTER(I32), C.POINTER(C.c_double)]
+            L.seed_time_fma.argtypes = [I32, P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
             L.seed_destroy.argtypes = [P]
@@ -264,7 +267,8 @@ def seed_solve_multiple(ctx: Context, B: torch.Tensor, X: torch.Tensor):
 
 
 def seed_solve_related(ctx: Context, B: torch.Tensor, X: torch.Tensor):
-    """Sec. 2.3 steps 3-4 after seed_solve_first (systems 2.. solved one after another)."""
+    """Sec. 2.3 (related right-hand sides) after seed_solve_first: systems 2.. solved one after another,
+    each later system projected over every CG correction."""
     pb, ldb, nb = _block(B, ctx.n, "B")
     px, ldx, nx = _block(X, ctx.n, "X")
     if nb != nx:
@@ -389,6 +393,14 @@ def seed_wilson_apply_noalloc(dims, kappa: float, links: torch.Tensor, X: torch.
         a.dims[k] = int(dims[k])
     _check(lib().seed_wilson_apply_noalloc(C.byref(a), px, ldx, py, ldy, nx, _stream(stream)),
            "seed_wilson_apply_noalloc")
+
+
+def seed_time_fma(dtype: int = 0, stream=None) -> dict:
+    """Measured FMA rate of the FP64 (dtype SEED_F64) or FP32 (SEED_F32) pipe:
+    {"tflops": ..., "ms": ...} (see include/seed.h)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().seed_time_fma(int(dtype), _stream(stream), C.byref(tf), C.byref(ms)), "seed_time_fma")
+    return {"tflops": tf.value, "ms": ms.value}
 
 
 def seed_last_error(ctx: Context = None) -> str:

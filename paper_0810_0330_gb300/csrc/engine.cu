@@ -4,7 +4,7 @@
 //
 // Schedule.  The host knows the step index i of every Lanczos step it issues
 // (i advances by one per step while the device recurrence is active), so it
-// knows where Sec. 3 step 8 (reorthogonalization when i is a multiple of the
+// knows where the Sec. 3 reorthogonalization (when i is a multiple of the
 // frequency) falls and issues those kernels only there.  Runs of steps are
 // captured once into a CUDA graph per pattern and replayed; all scalars stay
 // on the device.  After each run the host copies a small status block to
@@ -56,7 +56,8 @@ struct seed_ctx {
   cudaStream_t csb[kCgBranches - 1] = {};   // further branches of the lockstep CG graphs
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kCgBranches - 1] = {};
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_in = nullptr;
+  cudaEvent_t ev_run[2] = {nullptr, nullptr};   // end of a graph run of Lanczos steps, two slots reused
   cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;
   int kind = 0;                        // 0 = CSR, 1 = Wilson
   seed_dtype dtype = SEED_F64;
@@ -332,7 +333,7 @@ int apply_A32(seed_ctx *ctx, const void *X, int64_t ldx, void *Y, int64_t ldy, i
 
 template <class T> constexpr bool kLow = std::is_same_v<T, float> || std::is_same_v<T, float2>;
 
-// Blocked seeding (Sec. 3 steps 4 and 7 folded into x^2..x^p once per block of
+// Blocked seeding (the Sec. 3 seeding of systems 2..p folded into x^2..x^p once per block of
 // steps, seedblock.cu) when there are seeded systems and blocks can be long:
 // without reorthogonalization or with reorthogonalization every 8 or more steps
 // (a block ends at every reorthogonalizing step).
@@ -407,7 +408,7 @@ ReorthBufs<T> reorth_bufs(seed_ctx *ctx) {
 
 bool reorth_at(const seed_params &p, int i) { return p.reorth_freq > 0 && i >= 2 && i % p.reorth_freq == 0; }
 
-// Issue one Lanczos step (steps 5-9 of Sec. 3; step 2-4 when i == 1).
+// Issue one Lanczos step of Sec. 3 (the first step when i == 1).
 template <class T>
 int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
   SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
@@ -417,7 +418,7 @@ int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
   launch_seed_update<T>(b, !reorth, ctx->cs);
   k += 2;
   if (reorth) {
-    k += launch_seed_flush<T>(b, ctx->blk, ctx->cs);   // step 8 rewrites v_i: fold the block first
+    k += launch_seed_flush<T>(b, ctx->blk, ctx->cs);   // reorthogonalization rewrites v_i: fold the block first
     launch_reorth<T>(b, reorth_bufs<T>(ctx), ctx->prm.reorth_passes, ctx->cs);
     k += reorth_kernel_count<T>(ctx->prm.reorth_passes);
   }
@@ -496,16 +497,12 @@ seed_status seed_graph_runs(seed_ctx *ctx, int nrhs) {
       TRY(launch_seed_run<T>(ctx, nrhs, pattern));
       i_next += len;
       CU(cudaMemcpyAsync(&ctx->h_status[slot], &ctx->st->i, sizeof(HostStatus), cudaMemcpyDeviceToHost, ctx->cs));
-      cudaEvent_t ev;
-      CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      CU(cudaEventRecord(ev, ctx->cs));
+      CU(cudaEventRecord(ctx->ev_run[slot], ctx->cs));
       if (pending >= 0) {
-        // previous run's status
-        CU(cudaEventSynchronize(ctx->ev_out));
-        cudaEventDestroy(ctx->ev_out);
+        // previous run's status (its slot is not recorded again before this wait)
+        CU(cudaEventSynchronize(ctx->ev_run[pending]));
         if (!ctx->h_status[pending].active) stopped = true;
       }
-      ctx->ev_out = ev;
       pending = slot;
       slot ^= 1;
     } else {
@@ -516,7 +513,7 @@ seed_status seed_graph_runs(seed_ctx *ctx, int nrhs) {
 }
 
 // Segments of steps in one persistent launch each, up to the next step that
-// reorthogonalizes (Sec. 3 step 8), which runs from a one-step graph.
+// reorthogonalizes (Sec. 3), which runs from a one-step graph.
 template <class T>
 seed_status seed_persistent_segments(seed_ctx *ctx, int nrhs) {
   const seed_params &p = ctx->prm;
@@ -586,7 +583,7 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   CU(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->cs));
   CU(cudaMemsetAsync(ctx->eta, 0, sizeof(double2) * kMaxRhs, ctx->cs));
 
-  // Step 1: x^j = x_0^j, r_0^j = b^j - A x_0^j (R holds r_0^2.. in columns 0..; r_0^1 in f via seed_start)
+  // start: x^j = x_0^j, r_0^j = b^j - A x_0^j (R holds r_0^2.. in columns 0..; r_0^1 in f via seed_start)
   const T *r01 = (const T *)B;
   int kern = 0;
   if (p.x0_zero) {
@@ -614,10 +611,6 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
     TRY(seed_graph_runs<T>(ctx, nrhs));
   }
   CU(cudaStreamSynchronize(ctx->cs));
-  if (ctx->ev_out) {
-    cudaEventDestroy(ctx->ev_out);
-    ctx->ev_out = nullptr;
-  }
   CU(cudaGetLastError());
 
   SeedState st;
@@ -1006,7 +999,7 @@ seed_status ensure_related(seed_ctx *ctx, int nc) {
   return SEED_OK;
 }
 
-// Steps 3-4 after the seed solve of system 1 (step 2): project the remaining
+// Sec. 2.3 after the seed solve of system 1: project the remaining
 // systems over x^1 (x^1_bcg = 0, r^1_bcg = b^1), then for j = 2, 3, ...: CG on
 // system j from its current approximation, and project the systems after it
 // over that CG's correction.
@@ -1028,13 +1021,13 @@ seed_status solve_related_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *
   int kern = apply_A(ctx, Xt + ldx, ldx, ctx->Q, ld, nc, nullptr);
   launch_sub_from<T>(Bt + ldb, ldb, (const T *)ctx->Q, ld, R, ld, n, nc, ctx->cs);
   ctx->stats.mvps += nc;
-  // step 3 for system 1: x_cg = x^1, r_bcg = b^1
+  // projection over system 1: x_cg = x^1, r_bcg = b^1
   launch_related_project<T>(n, Xt, Bt, Xt + ldx, ldx, R, ld, nc, dots, delta, ctx->partials, ctx->tickets, ctx->cs);
   ctx->stats.kernel_launches += kern + 4;
   float ms_total = 0.f;
   for (int j = 0; j < nc; ++j) {
     T *xj = Xt + (int64_t)(1 + j) * ldx;
-    // step 4: x_bcg, r_bcg of system j + 2, then CG
+    // next system: x_bcg, r_bcg of system j + 2, then CG
     launch_copy_cols<T>(xj, ldx, xb, ld, n, 1, ctx->cs);
     launch_copy_cols<T>(R + (int64_t)j * ld, ld, rb, ld, n, 1, ctx->cs);
     ctx->stats.kernel_launches += 2;
@@ -1043,7 +1036,7 @@ seed_status solve_related_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *
     cudaEventElapsedTime(&ms, ctx->t2, ctx->t3);
     ms_total += ms;
     if (j + 1 < nc) {
-      // step 3: x_cg = x^j - x^j_bcg; project the systems after j over it
+      // x_cg = x^j - x^j_bcg; project the systems after j over it
       launch_sub_from<T>(xj, ldx, xb, ld, xb, ld, n, 1, ctx->cs);
       launch_related_project<T>(n, xb, rb, xj + ldx, ldx, R + (int64_t)(j + 1) * ld, ld, nc - j - 1, dots, delta,
                                 ctx->partials, ctx->tickets, ctx->cs);
@@ -1279,7 +1272,7 @@ seed_status mixed_cg(seed_ctx *ctx, const T64 *Bc, int64_t ldb, T64 *Xc, int64_t
   return SEED_OK;
 }
 
-// Sec. 3 steps 1-9 with FP32 vectors and operator (FP64 scalars), then system
+// The Sec. 3 seed solve with FP32 vectors and operator (FP64 scalars), then system
 // 1 finished to tol_seed by mixed CG.
 template <class T64, class T32>
 seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X, int64_t ldx, int nrhs,
@@ -1306,7 +1299,7 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   CU(cudaMemcpyAsync(ctx->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, ctx->cs));
   CU(cudaMemsetAsync(ctx->eta, 0, sizeof(double2) * kMaxRhs, ctx->cs));
 
-  // Step 1 in FP64: r_0^j = b^j - A x_0^j, rounded to FP32 (column 0 starts the Lanczos run)
+  // start in FP64: r_0^j = b^j - A x_0^j, rounded to FP32 (column 0 starts the Lanczos run)
   int kern = 0;
   const int64_t nv = ctx->nv;
   if (p.x0_zero) {
@@ -1333,10 +1326,6 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
     TRY(seed_graph_runs<T32>(ctx, nrhs));
   }
   CU(cudaStreamSynchronize(ctx->cs));
-  if (ctx->ev_out) {
-    cudaEventDestroy(ctx->ev_out);
-    ctx->ev_out = nullptr;
-  }
   CU(cudaGetLastError());
   SeedState st;
   CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
@@ -1459,6 +1448,8 @@ seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream strea
   }
   CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+  CU(cudaEventCreateWithFlags(&ctx->ev_run[0], cudaEventDisableTiming));
+  CU(cudaEventCreateWithFlags(&ctx->ev_run[1], cudaEventDisableTiming));
   CU(cudaEventCreate(&ctx->t0));
   CU(cudaEventCreate(&ctx->t1));
   CU(cudaEventCreate(&ctx->t2));
@@ -1481,7 +1472,7 @@ void destroy(seed_ctx *ctx) {
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->h_gerr) cudaFreeHost(ctx->h_gerr);
-  cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3, ctx->ev_fork};
+  cudaEvent_t evs[] = {ctx->ev_in, ctx->t0, ctx->t1, ctx->t2, ctx->t3, ctx->ev_fork, ctx->ev_run[0], ctx->ev_run[1]};
   for (auto e : evs)
     if (e) cudaEventDestroy(e);
   for (int b = 0; b < kCgBranches - 1; ++b) {

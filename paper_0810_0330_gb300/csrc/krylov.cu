@@ -55,7 +55,7 @@ int col_blocks(int64_t n, int nc) {
   return (int)b;
 }
 
-// Step 2 (start): f = r_0^1, beta_0 = ||r_0^1||; v_1 follows from the normalize kernel.
+// Start of the Lanczos run: f = r_0^1, beta_0 = ||r_0^1||; v_1 follows from the normalize kernel.
 template <class T>
 __global__ void __launch_bounds__(NT) k_seed_start(SeedBufs<T> b, const T *__restrict__ r01) {
   __shared__ double sm[NT / 32];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT) k_seed_normalize(SeedBufs<T> b) {
   }
 }
 
-// Steps 5 and 7 (the dot products) and the scalar part of steps 3/4/6/7, in
+// The dot products of a Lanczos step (alpha_i, g^j) and the scalars of the LU update and seeding, in
 // one pass over the elements:  f = A v_i - beta_{i-1} v_{i-1};
 // alpha_i = Re(v_i^H f);  g^j = v_i^H r_0^j for j = 2..nrhs.
 // Values are packed 32 per chunk (alpha in slot 0 of chunk 0, then 15 complex
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
   if (threadIdx.x == 0) seed_step_scalars(b, i, s_alpha, sums);
 }
 
-// Step 5 and the scalars of steps 3/6 when no g^j is formed here (blocked
+// alpha_i and the LU-update scalars when no g^j is formed here (blocked
 // seeding, or system 1 alone): f = A v_i - beta_{i-1} v_{i-1},
 // alpha_i = Re(v_i^H f), one value per block summed in block order by the last.
 template <class T>
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NT) k_seed_alpha(SeedBufs<T> b) {
   if (threadIdx.x == 0) seed_step_scalars(b, i, a, nullptr);
 }
 
-// Steps 5 (f -= alpha_i v_i), 6 (w_i, x^1) and 7 (x^j), plus ||f||^2 when this
+// f -= alpha_i v_i, the LU update (w_i, x^1) and the seeding (x^j), plus ||f||^2 when this
 // step has no reorthogonalization.  Blocked seeding (b.Wb set): w_i also goes
 // to column i - blk0 of Wb and x^2..x^p wait for the block's flush.
 template <class T, bool NORM>
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
 }
 
 // ---------------------------------------------------------------------------
-// Sec. 3 step 8: reorthonormalize v_i against v_1..v_{i-1}, then
+// Sec. 3 reorthogonalization: reorthonormalize v_i against v_1..v_{i-1}, then
 // reorthogonalize f against v_1..v_i.  Classical Gram-Schmidt in blocked form:
 // H = V_{<i}^H [v_i f], [v_i f] -= V_{<i} H (repeated `passes` times), then
 // v_i /= ||v_i|| and f -= (v_i^H f) v_i (repeated `passes` times).
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(NT) k_reorth_scale_dot(SeedBufs<T> b) {
   if (threadIdx.x == 0) st->h = c2(re, im);
 }
 
-// f -= h v_i; then either h = v_i^H f (DOT) or ||f||^2 -> step 9 (seed_finish)
+// f -= h v_i; then either h = v_i^H f (DOT) or ||f||^2 -> end of the step (seed_finish)
 template <class T, bool DOT>
 __global__ void __launch_bounds__(NT) k_reorth_axpy(SeedBufs<T> b) {
   SeedState *st = b.st;

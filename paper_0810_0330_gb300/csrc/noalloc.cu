@@ -13,7 +13,11 @@
 // that loads this library holds until the process exits.  Host code may not
 // hand the array's name to a kernel (on the host it is only a stand-in
 // symbol), so the first call on each device looks up its device address with
-// cudaGetSymbolAddress while that device is current and keeps it.
+// cudaGetSymbolAddress while that device is current and keeps it -- keyed on
+// the CUDA context that is current, not only on the device index: a context
+// that was reset (cudaDeviceReset) or a different driver context made current
+// by the caller holds its own copy of the array at another address, and the
+// lookup is then repeated for it.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,7 +39,38 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_setup_mu;
-void *g_scratch_dev[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+// device address of g_noalloc_scratch, per device, and the id of the context it was looked up in
+void *g_scratch_dev[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// The id of the CUDA context current on this thread (unique over the process'
+// life, never reused), read through the runtime's driver entry points so the
+// library needs no link to the driver library.  0 when unavailable.
+typedef int (*PfnCtxGetCurrent)(void **);
+typedef int (*PfnCtxGetId)(void *, unsigned long long *);
+unsigned long long current_context_id() {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = (PfnCtxGetCurrent)f1;
+      get_id = (PfnCtxGetId)f2;
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || ctx == nullptr || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 seed_status na_fail(seed_status st, const std::string &msg) {
   seedk::set_last_error_message(msg);
@@ -89,11 +124,14 @@ extern "C" seed_status seed_wilson_apply_noalloc(const seed_wilson *A, const voi
   const char *y0 = (const char *)Y, *y1 = y0 + ((ncols - 1) * ldy + n) * sizeof(double2);
   if (x0 < y1 && y0 < x1) return na_fail(SEED_EINVAL, "seed_wilson_apply_noalloc: X and Y overlap");
 
-  // once per device, with that device current: the device address of the scratch array
+  // once per device and context, with that device current: the device address of the
+  // scratch array (looked up again if the current context is not the one it came from;
+  // without a context id the address is looked up on every call)
   void *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (g_scratch_dev[dev] == nullptr) {
+    const unsigned long long ctx_id = current_context_id();
+    if (g_scratch_dev[dev] == nullptr || ctx_id == 0 || g_scratch_ctx[dev] != ctx_id) {
       void *p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || p == nullptr) {
@@ -102,6 +140,7 @@ extern "C" seed_status seed_wilson_apply_noalloc(const seed_wilson *A, const voi
                                        cudaGetErrorString(e));
       }
       g_scratch_dev[dev] = p;
+      g_scratch_ctx[dev] = ctx_id;
     }
     scratch = g_scratch_dev[dev];
   }

@@ -190,7 +190,7 @@ SEED_DEV double2 tile_sum(double (*sacc)[24][kWilsonSites + 1], int cc, int sl) 
 }
 
 // ---------------------------------------------------------------------------
-// Seed runs (Sec. 3 steps 2-9 between two reorthogonalizing steps).  The
+// Seed runs (the Lanczos steps of Sec. 3 between two reorthogonalizing steps).  The
 // seeding of systems 2..p is blocked (SeedBufs::Wb, seedblock.cu): a step only
 // stores w_i, so the recurrence of system 1 is all that runs here.
 //
@@ -198,10 +198,10 @@ SEED_DEV double2 tile_sum(double (*sacc)[24][kWilsonSites + 1], int cc, int sl) 
 //   phase 1 (tiles): v_i = f / beta_{i-1} into V; t = D v_i; per tile the
 //           partial sums of ||t||^2 and Re(v_i^H v_{i-1})
 //   barrier; every block: alpha_i = ||D v_i||^2 - beta_{i-1} Re(v_i^H v_{i-1}),
-//           then gamma_{i-1}, delta_i, zeta_i (steps 3/6)
+//           then gamma_{i-1}, delta_i, zeta_i (the LU update)
 //   phase 2 (tiles): u = D^H t; f = u - beta_{i-1} v_{i-1} - alpha_i v_i (step
-//           5); w_i and x^1 += zeta_i w_i (step 6); w_i into Wb; partial ||f||^2
-//   barrier; every block: beta_i and the stopping test (step 9).
+//           5); w_i and x^1 += zeta_i w_i (LU update); w_i into Wb; partial ||f||^2
+//   barrier; every block: beta_i and the stopping test.
 // alpha_i is the paper's v_i^H (A v_i - beta_{i-1} v_{i-1}) with v_i^H A v_i
 // written as ||D v_i||^2 (A = D^H D): the same number up to rounding, available
 // one barrier earlier, so that the update runs in the D^H tiles' epilogue.
@@ -269,7 +269,7 @@ SEED_DEV bool seed_alpha_step(const SeedBufs<T> &bl, const double *parts, int np
   return true;
 }
 
-// barrier, then in every block: beta_i from the partials of ||f||^2 and step 9
+// barrier, then in every block: beta_i from the partials of ||f||^2 and the end of the step
 template <class T>
 SEED_DEV bool seed_beta_step(const SeedBufs<T> &bl, const double *parts, int nparts, int i, LocalSeed &L,
                              const GridSync &g, unsigned &epoch) {
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson32(SeedBufs<float2> b, Wi
 
 // Phase 3 of the CSR run: f -= alpha_i v_i, w_i (also into column i - blk0 of
 // Wb), x^1 and ||f||^2; one value per block, reduced in block order by every
-// block after the barrier, then step 9.
+// block after the barrier, then the end of the step.
 template <class T>
 SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i, LocalSeed &L,
                                const GridSync &g, unsigned &epoch, double *bpart, double *s_red) {

@@ -1,4 +1,4 @@
-// related.cu -- Sec. 2.3 (single seeding for related right-hand sides), step 3
+// related.cu -- Sec. 2.3 (single seeding for related right-hand sides), the projection
 // on sm_103a: after system j is solved, the remaining systems receive the
 // Galerkin projection over the correction x_cg = x^j - x^j_bcg that CG found
 // for system j:

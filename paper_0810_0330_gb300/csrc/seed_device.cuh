@@ -20,7 +20,7 @@ template <bool G, class P> SEED_DEV P sld(const P *p) {
   else return *p;
 }
 
-// Steps 3/6 (delta_i, gamma_{i-1}, zeta_i) and 4/7 (eta^j) from alpha_i and
+// The LU update (delta_i, gamma_{i-1}, zeta_i) and the seeding scalars (eta^j) from alpha_i and
 // g^j = v_i^H r_0^j (sums[j], j = 1..nrhs-1); beta_{i-1} is st->beta_prev.
 template <class T, bool G = true>
 SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const double2 *sums) {
@@ -32,18 +32,18 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
 #pragma unroll 16
   for (int j = 1; j < nr; ++j) e[j] = sld<G>(b.eta + j);
   double gam, del, zet;
-  if (i == 1) {           // step 3: delta_1 = alpha_1, zeta_1 = beta_0
+  if (i == 1) {           // first step: delta_1 = alpha_1, zeta_1 = beta_0
     gam = 0.0;
     del = a;
     zet = beta0;
-  } else {                // step 6
+  } else {                // later steps
     gam = bp / dprev;
     del = a - gam * bp;
     zet = -gam * zprev;
   }
   if (b.Wb == nullptr) {
 #pragma unroll 16
-    for (int j = 1; j < nr; ++j) {   // steps 4 / 7
+    for (int j = 1; j < nr; ++j) {   // seeding of systems 2..p
       const double2 g = sums[j];
       b.eta[j] = (i == 1) ? g : c2(g.x - gam * e[j].x, g.y - gam * e[j].y);
     }
@@ -62,7 +62,7 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
   }
 }
 
-// Sec. 3 step 9: beta_i = ||f||, residual estimate and the stopping test.
+// Sec. 3, end of a step: beta_i = ||f||, residual estimate and the stopping test.
 template <class T, bool G = true>
 SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
   SeedState *st = b.st;

@@ -24,7 +24,7 @@ struct SeedState {
   double alpha;       // alpha_i
   double beta;        // beta_i of the last finished step
   double beta_prev;   // beta_{i-1}
-  double delta;       // delta_i (delta_{i-1} until step 6 of step i runs)
+  double delta;       // delta_i (delta_{i-1} until the LU update of step i runs)
   double zeta;        // zeta_i
   double gamma;       // gamma_{i-1}
   double rho;         // beta_i |zeta_i| / delta_i
@@ -82,7 +82,7 @@ struct SeedBufs {
   double2 *eta;        // [kMaxRhs]
   double *partials;    // kPartials doubles
   unsigned *tickets;   // >= 4 counters, zero between launches
-  // Blocked seeding (Sec. 3 steps 4 and 7 deferred over a block of steps):
+  // Blocked seeding (the Sec. 3 seeding of systems 2..p deferred over a block of steps):
   // NULL = the streaming form (g^j, eta^j and x^j every step).  Otherwise each
   // step stores w_i in column i - blk0 of Wb and gamma_{i-1} in gamma_hist[i],
   // and launch_seed_flush folds the block into x^2..x^p.
@@ -103,7 +103,7 @@ struct BlockBufs {
 };
 constexpr int kBlockChunksMax = 64;
 
-// Buffers of the blocked reorthogonalization (Sec. 3 step 8).
+// Buffers of the blocked reorthogonalization (Sec. 3).
 template <class T>
 struct ReorthBufs {
   int64_t n;
@@ -237,7 +237,7 @@ struct Layout32 {
   __host__ __device__ int64_t length(int64_t n) const { return sites == 0 ? n : 384 * ((sites + 31) / 32); }
 };
 
-// Sec. 2.3 step 3 (related.cu): X[:, c] += delta_c xcg, R[:, c] -= delta_c rbcg with
+// Sec. 2.3 projection (related.cu): X[:, c] += delta_c xcg, R[:, c] -= delta_c rbcg with
 // delta_c = (xcg^H R[:, c]) / (xcg^H rbcg), c < nrem.  dots: nrem + 1, delta: nrem device scratch.
 template <class T>
 void launch_related_project(int64_t n, const T *xcg, const T *rbcg, T *X, int64_t ldx, T *R, int64_t ldr, int nrem,

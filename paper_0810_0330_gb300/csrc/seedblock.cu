@@ -1,4 +1,4 @@
-// seedblock.cu -- Sec. 3 steps 4 and 7 (the seeding of systems 2..p) in
+// seedblock.cu -- the Sec. 3 seeding of systems 2..p in
 // blocked form.
 //
 // Each Lanczos step i feeds the other right-hand sides through
@@ -12,7 +12,7 @@
 //   X_{2..p} += W Z      k_blk_x                     (Z = [eta_i^j], k x (p-1))
 // reading the block's v_i and w_i once, instead of reading and writing p-1
 // columns of X and forming p-1 dot products in every step.  Blocks end before
-// a reorthogonalizing step rewrites v_i (Sec. 3 step 8), so V_blk holds the
+// a reorthogonalizing step rewrites v_i (Sec. 3), so V_blk holds the
 // vectors the streaming form uses; the two forms differ in summation order
 // only.
 #include "seed_device.cuh"
@@ -127,7 +127,7 @@ __global__ void k_blk_reduce(const SeedState *st, int nrhs, BlockBufs k) {
   k.G[q * kLdG + j] = s;
 }
 
-// eta^j over the block, in step order (steps 4 / 7): eta_1 = g_1,
+// eta^j over the block, in step order: eta_1 = g_1,
 // eta_i = g_i - gamma_{i-1} eta_{i-1}; Z[q][j] = eta at step blk0 + q.
 // Then the next block starts after the last stored step.
 __global__ void k_blk_eta(SeedState *st, int nrhs, double2 *eta, const double *gamma_hist, BlockBufs k) {

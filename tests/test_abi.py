@@ -86,3 +86,25 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
         B.seed_params_default()
     with pytest.raises(RuntimeError, match="not built"):
         B.seed_inject_alloc_failure(0)
+
+
+def _doc_before(src, name):
+    """The comment block right before the declaration of `name` in the header."""
+    m = re.search(r"/\*((?:(?!\*/).)*?)\*/\s*(?:seed_status|void|const char \*|int32_t)\s*" + name + r"\s*\(",
+                  src, flags=re.S)
+    assert m, name
+    return " ".join(m.group(1).replace("*", " ").split())
+
+
+def test_boundary_calls_cite_their_passage():
+    """Every call of the boundary cites the passage of the paper that defines
+    its operation (Sec. 1 problem, Sec. 3 algorithm and its basis storage,
+    Sec. 4 normal equations); the error-reporting call says it has none."""
+    src = open(os.path.join(ROOT, "include", "seed.h")).read()
+    for name in ("seed_create_csr", "seed_create_wilson", "seed_solve_first", "seed_project", "seed_solve_rest",
+                 "seed_destroy", "seed_solve_related", "seed_solve_multiple", "seed_get_tridiag"):
+        assert "Sec." in _doc_before(src, name), name
+    assert "Sec. 4" in _doc_before(src, "seed_create_wilson")
+    assert "Sec. 1" in _doc_before(src, "seed_create_csr")
+    assert "no counterpart" in _doc_before(src, "seed_last_error")
+    assert "no counterpart" in _doc_before(src, "seed_wilson_apply_noalloc")

@@ -2,7 +2,7 @@
 
  * Malformed operators are rejected on the host before any launch.
  * Non-finite right-hand sides end as status codes: in the seed system the
-   initial residual norm beta_0 of Sec. 3 step 1 is not finite and no step
+   initial residual norm beta_0 of the Sec. 3 start is not finite and no step
    runs (SEED_EINVAL); in a seeded system CG stops that system at its first
    non-finite residual while the others converge (SEED_ENOTCONV).
  * Injected allocation failures (host side: the k-th device allocation

@@ -167,7 +167,7 @@ def test_tridiag_eigs_matches_scipy(orc):
 
 
 # --------------------------------------------------------------------------
-# Sec. 3 algorithm (steps 1-9)
+# Sec. 3 algorithm (the seed solve)
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("complex_", [False, True])
@@ -288,7 +288,7 @@ def test_cg_zero_iterations_when_seeded_exactly(orc):
 
 
 def test_related_projection_closed_form(orc):
-    """Sec. 2.3 step 3: after the update x_cg^H r_new = 0, and a residual that
+    """Sec. 2.3 projection over x_cg: after the update x_cg^H r_new = 0, and a residual that
     is a multiple of r_bcg is removed exactly."""
     n = 40
     rng = np.random.default_rng(0)
@@ -498,3 +498,51 @@ def test_paper_multiple_seeding_trends(orc):
         assert multiple < 0.95 * none, (seed, multiple, none)
         assert single < multiple, (seed, single, multiple)
         assert ms["iters"][2] > ms["iters"][1], (seed, ms["iters"])
+
+
+def _krylov_basis(A, b, k):
+    """Orthonormal basis of span{b, A b, ..., A^{k-1} b} by Arnoldi with two
+    Gram-Schmidt passes (numpy; independent of the oracle)."""
+    Q = np.zeros((A.shape[0], k), dtype=np.complex128)
+    q = b / np.linalg.norm(b)
+    for j in range(k):
+        Q[:, j] = q
+        w = A @ q
+        for _ in range(2):
+            w = w - Q[:, :j + 1] @ (Q[:, :j + 1].conj().T @ w)
+        q = w / np.linalg.norm(w)
+    return Q
+
+
+@pytest.mark.parametrize("k", [1, 4, 9])
+def test_multiple_seeding_is_galerkin_over_first_krylov_space_complex(orc, k):
+    """Sec. 2.1 multiple seeding: every CG step of system 1, with direction p
+    and q = A p, projects system 2 by eta = (p^H r)/(p^H q).  The directions of
+    k CG steps are A-conjugate and span the Krylov space K_k(A, b^1), so after k
+    steps x^2 is the Galerkin solution over that space,
+        x^2 = Q (Q^H A Q)^{-1} Q^H b^2,  and  Q^H (b^2 - A x^2) = 0,
+    for any orthonormal basis Q of K_k(A, b^1).  A complex Hermitian positive
+    definite matrix (random unitary eigenvectors, eigenvalues 0.1..10) and
+    complex right-hand sides make a conjugation slip anywhere in eta, the x or
+    the r update fail this; the basis comes from numpy Arnoldi, not from the
+    oracle."""
+    rng = np.random.default_rng(2024)
+    n = 40
+    M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Qm, _ = np.linalg.qr(M)
+    lam = np.geomspace(0.1, 10.0, n)
+    A = (Qm * lam) @ Qm.conj().T
+    A = 0.5 * (A + A.conj().T)
+    B = rng.standard_normal((n, 3)) + 1j * rng.standard_normal((n, 3))
+    ms = orc.seed_multiple(orc.Operator.dense(A), B, tol=1e-15, maxit=k)
+    assert ms["iters"][0] == k                      # system 1 ran exactly k CG steps
+    x2 = ms["X_seeded"][:, 1]
+    Q = _krylov_basis(A, B[:, 0], k)
+    x_gal = Q @ np.linalg.solve(Q.conj().T @ A @ Q, Q.conj().T @ B[:, 1])
+    assert np.linalg.norm(x2 - x_gal) <= 1e-11 * np.linalg.norm(x_gal)
+    assert np.linalg.norm(Q.conj().T @ (B[:, 1] - A @ x2)) <= 1e-12 * np.linalg.norm(B[:, 1])
+    # a conjugated coefficient would not give the Galerkin solution on complex data
+    assert np.linalg.norm(x_gal.conj() - x_gal) > 1e-3 * np.linalg.norm(x_gal)
+    # system 1 started from zero: its own seeded iterate is zero, x^3 was seeded too
+    assert np.abs(ms["X_seeded"][:, 0]).max() == 0.0
+    assert np.linalg.norm(ms["X_seeded"][:, 2]) > 0.0
