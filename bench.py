@@ -33,19 +33,23 @@ METRIC = "all-RHS solve time at rel. residual 1e-8; matvec HBM GB/s vs GB300 pea
 WL = dict(dims=(8, 8, 8, 8), kappa=0.155, link_eps=0.3, link_seed=0, nrhs=12, m_max=3000, reorth_freq=100,
           reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
 WORKLOAD_NAME = "wilson-dirac 8^4 kappa=0.155 A=D^H D, 12 point sources, seed tol 1e-12 reorth/100, CG tol 1e-8"
-# Wilson D per site: 1320 flops of hopping + 48 for psi - kappa*sum (FMA = 2 flops)
-FLOPS_PER_SITE_D = 1368
-# FP64 peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# Wilson D per site: 1320 flops for the eight spin-projected hops (colour matrix times two
+# half-spinors, reconstruction and accumulation; FMA = 2 flops), the usual count for this operator.
+# The epilogue psi - kappa * sum adds 48 more, which the roofline reports separately.
+FLOPS_PER_SITE_D = 1320
+FLOPS_PER_SITE_D_EPILOGUE = 48
+# FP64 peak from unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (the library's FMA-chain
+# probe, seed_time_fma, measures it live next to the roofline)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 try:
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _fh:
         MEASURED_PEAKS = json.load(_fh)
 except (OSError, ValueError):
     MEASURED_PEAKS = {}
-# DRAM bytes of one k_dslash launch (8^4, 11 columns) from an ncu capture of these sources of the kernel
-# (profiles/k_dslash_wilson_8x4_11cols.md); reported only while the source is unchanged.
+# DRAM bytes of one k_dslash launch (8^4, 11 columns) from the ncu capture of these sources of the
+# kernel; reported only while the source is unchanged.
 DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0, "6e70bd4a297626c1": 11.207424e6 + 0.0}
-# The same for k_dslash32_site<+1> (FP32, 16^3 x 32, 11 columns; profiles/k_dslash32_wilson_fp32.md)
+# The same for k_dslash32_site<+1> (FP32, 16^3 x 32, 11 columns), from the ncu capture of its sources
 DSLASH32_TRAFFIC = {"7a583b64681e7245": 189.553920e6 + 104.930304e6}
 DSLASH32_TRAFFIC_DIMS = (16, 16, 16, 32)
 
@@ -84,6 +88,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 16^3 x 32 mixed-precision and FP64 solves reported under config.secondary")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only time the dominant kernel (for profiler captures)")
     ap.add_argument("--once", action="store_true",
@@ -209,48 +215,85 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle on a bounded sample of the workload
+# CPU baseline: the oracle on the whole workload
 # ---------------------------------------------------------------------------
-def oracle_sample(rest_cols=(1, 6)):
-    """Seed solve of system 1 (complete) + CG on `rest_cols` of the 11 seeded
-    systems; the all-RHS time is extrapolated as seed + 11/len(rest_cols) * CG."""
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.machine()
+    return os.cpu_count() or 1, model
+
+
+def oracle_full(threads=1):
+    """The whole all-RHS solve by the oracle: B = D^H eta for the 12 sources, the
+    seed solve of system 1, CG on all 11 seeded systems.  threads > 1 runs the
+    oracle's OpenMP build (the same results bit for bit).  Returns
+    (seconds, detail)."""
     import oracle
     from paper_0810_0330_gb300 import inputs as I
+    used = oracle.set_threads(threads)
     dims, kappa = WL["dims"], WL["kappa"]
     U = I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])
     eta = I.point_sources(dims, WL["nrhs"])
     op = oracle.Operator.wilson(dims, kappa, U)
     t0 = time.perf_counter()
     B = np.stack([oracle.wilson_dslash(dims, kappa, 0, -1, U, eta[:, j]) for j in range(WL["nrhs"])], axis=1)
-    s = oracle.seed_first(op, B, m_max=WL["m_max"], reorth_freq=WL["reorth_freq"],
-                          reorth_passes=WL["reorth_passes"], tol=WL["tol_seed"])
+    r = oracle.seed_solve_all(op, B, m_max=WL["m_max"], reorth_freq=WL["reorth_freq"],
+                              reorth_passes=WL["reorth_passes"], tol_seed=WL["tol_seed"], tol_rest=WL["tol_rest"])
     t1 = time.perf_counter()
-    its = []
-    for j in rest_cols:
-        r = oracle.cg(op, B[:, j], s["X"][:, j], tol=WL["tol_rest"])
-        its.append(r["iters"])
-    t2 = time.perf_counter()
-    nrest = WL["nrhs"] - 1
-    total = (t1 - t0) + (t2 - t1) * nrest / len(rest_cols)
-    return total, dict(seed_s=t1 - t0, cg_s=t2 - t1, seed_iters=s["iters"], cg_iters=its)
+    oracle.set_threads(1)
+    ok = all(x["converged"] for x in r["rest"])
+    return t1 - t0, dict(threads=used, seed_iters=r["seed"]["iters"], cg_iters=[x["iters"] for x in r["rest"]],
+                         converged=ok)
 
 
-def cpu_baseline_obj(total_s, detail, rest_cols=(1, 6)):
-    return {"value": round(total_s * 1e3, 3), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": "oracle (plain C, FP64, one thread): B = D^H eta for all 12 sources, the full seed "
-                      "solve of system 1 (%d steps), CG on systems %s of the 11 seeded systems (%s iterations); "
-                      "all-RHS time = seed + B + 11/%d x CG time" % (
-                          detail["seed_iters"], [c + 1 for c in rest_cols], detail["cg_iters"], len(rest_cols))}
+def cpu_obj(total_s, d):
+    cores, model = host_cpu()
+    return {"value": round(total_s * 1e3, 3), "unit": "ms", "cores": d["threads"], "kind": "oracle",
+            "host": {"logical_cores": cores, "cpu": model},
+            "sample": "the whole workload, not a sample: the oracle (plain C, FP64, %s) forms B = D^H eta for "
+                      "the 12 sources, runs the seed solve of system 1 (%d Lanczos steps) and CG on all 11 "
+                      "seeded systems (%s iterations)" % (
+                          "one thread" if d["threads"] == 1 else
+                          "its OpenMP build on %d threads, results bit-identical to one thread" % d["threads"],
+                          d["seed_iters"], d["cg_iters"])}
+
+
+def cpu_baseline_obj():
+    """One-thread oracle (as it stands) and the same source on every host core."""
+    t1, d1 = oracle_full(1)
+    out = cpu_obj(t1, d1)
+    try:
+        tn, dn = oracle_full(os.cpu_count() or 1)
+        out["all_cores"] = cpu_obj(tn, dn)
+    except Exception as e:   # no OpenMP toolchain on this host
+        out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step is the whole all-RHS solve of the
+    workload on every host core (the OpenMP build of the oracle; results
+    bit-identical to its one-thread build)."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
+    threads = os.cpu_count() or 1
     times = []
     detail = None
     for step in range(args.warmup + args.steps):
-        t, d = oracle_sample()
+        t, d = oracle_full(threads)
         if step >= args.warmup:
             times.append(t)
             detail = d
@@ -258,9 +301,10 @@ def run_reference(args):
     out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD_NAME, "lattice": "8x8x8x8", "n": 49152, "nrhs": 12,
-                      "impl_note": "CPU oracle (the paper publishes no code)"},
-           "cpu_baseline": cpu_baseline_obj(ms / 1e3, detail),
+           "config": workload_config(WL["dims"], "point", False, world),
+           "impl_note": "the CPU oracle (the paper publishes no code), whole workload per step, all host cores",
+           "cpu_baseline": cpu_obj(ms / 1e3, detail),
+           "run": {"step_ms": [round(t * 1e3, 3) for t in times], "converged": detail["converged"]},
            "e2e": {"value": round(ms, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     out["cpu_baseline"]["value"] = out["value"]
     print(json.dumps(out), flush=True)
@@ -294,6 +338,18 @@ def workload_name(dims, sources, mixed):
     prec = ", mixed precision (FP32 iterations, FP64 reliable updates)" if mixed else ""
     return ("wilson-dirac %s kappa=0.155 A=D^H D, %s, seed tol 1e-12 reorth/100, CG tol 1e-8%s"
             % ("x".join(map(str, dims)), src, prec))
+
+
+def workload_config(dims, sources, mixed, world=1, m_max=None):
+    """The `config` object of a solve workload, the same for both arms."""
+    return {"workload": workload_name(dims, sources, mixed), "lattice": "x".join(map(str, dims)),
+            "n": 12 * int(np.prod(dims)), "nrhs": WL["nrhs"], "precision": "mixed" if mixed else "fp64",
+            "kappa": WL["kappa"], "tol_seed": WL["tol_seed"], "reorth_freq": WL["reorth_freq"],
+            "reorth_passes": WL["reorth_passes"], "tol_rest": WL["tol_rest"], "m_max": m_max or WL["m_max"],
+            "sources": "unit point sources at site 0 (every spin and colour)" if sources == "point"
+            else "Z4 noise, seed 0", "links": "exp(0.3 i H), H random Hermitian traceless, seed 0",
+            "parallelism": "replicas" if world > 1 else "single-gpu",
+            "l2": "flushed (512 MB write) before every step, outside the timed events"}
 
 
 def run_sweep(args):
@@ -362,6 +418,125 @@ def run_sweep(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def make_problem(S, I, torch, dev, dims, sources, mixed, m_max, reliable_delta=0.0):
+    """Context, sources eta (host and device), B and X blocks of one solve workload."""
+    nrhs = WL["nrhs"]
+    n = 12 * int(np.prod(dims))
+    U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
+    prm = S.seed_params_default(m_max=m_max, reorth_freq=WL["reorth_freq"], reorth_passes=WL["reorth_passes"],
+                                tol_seed=WL["tol_seed"], tol_rest=WL["tol_rest"], x0_zero=1,
+                                precision=1 if mixed else 0, reliable_delta=reliable_delta)
+    ctx = S.seed_create_wilson(dims, WL["kappa"], U, prm)
+    eta_h = I.point_sources(dims, nrhs) if sources == "point" else I.z4_noise(n, nrhs, seed=0)
+    ETA = torch.from_numpy(np.ascontiguousarray(eta_h.T)).to(dev).t()     # (n, nrhs) column-major
+    B = torch.empty((nrhs, n), dtype=torch.complex128, device=dev).t()
+    X = torch.empty((nrhs, n), dtype=torch.complex128, device=dev).t()
+    return dict(ctx=ctx, U=U, eta_h=eta_h, ETA=ETA, B=B, X=X, n=n, vol=int(np.prod(dims)))
+
+
+def solve_step(S, p):
+    """One step of the workload: B = D^H eta, seed solve of system 1, CG on the others."""
+    S.seed_apply(p["ctx"], 2, p["ETA"], p["B"])
+    i1 = S.seed_solve_first(p["ctx"], p["B"], p["X"])
+    i2 = S.seed_solve_rest(p["ctx"], p["B"], p["X"])
+    return i1, i2
+
+
+def time_steps(S, torch, p, flush, steps, warmup, clk=None):
+    """Warm-up, then `steps` steps each between CUDA events on the current stream
+    (L2 flushed before each, outside the events).  Returns per-step ms and the
+    last step's infos."""
+    for _ in range(warmup):
+        flush.zero_()
+        solve_step(S, p)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = None
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record()
+        infos = solve_step(S, p)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], infos
+
+
+def dslash_roofline(S, ctx, vol, mixed, dims, ncols_total):
+    """The dominant kernel, the Wilson hopping kernel, timed live on the
+    library's stream: one launch over all CG columns, and the launch shapes the
+    CG graphs issue (one per concurrent column branch)."""
+    shapes = cg_branch_cols(ncols_total)
+    if not mixed:
+        k_ms = S.seed_time_operator(ctx, 1, ncols_total, 200)
+        flops = FLOPS_PER_SITE_D * vol * ncols_total
+        achieved = flops / (k_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
+        probe = S.seed_time_fma(S.SEED_F64)["tflops"]
+        shape_t = {}
+        for c in sorted(set(shapes)):
+            m = S.seed_time_operator(ctx, 1, c, 200)
+            a = FLOPS_PER_SITE_D * vol * c / (m * 1e-3) / 1e12
+            shape_t[str(c)] = {"ms_per_launch": round(m, 5), "achieved": round(a, 4), "frac": round(a / peak, 4)}
+        return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": dslash_traffic() if tuple(dims) == WL["dims"] and ncols_total == 11 else None,
+                "kernel": "k_dslash<+1> (Wilson D, FP64 complex), %d columns in one launch: the work of one CG "
+                          "half-iteration" % ncols_total,
+                "ms_per_launch": round(k_ms, 5), "flops_per_launch": flops,
+                "flops_per_site": FLOPS_PER_SITE_D,
+                "epilogue_flops_per_site": FLOPS_PER_SITE_D_EPILOGUE,
+                "frac_with_epilogue": round((FLOPS_PER_SITE_D + FLOPS_PER_SITE_D_EPILOGUE) * vol * ncols_total /
+                                            (k_ms * 1e-3) / 1e12 / peak, 4),
+                "launch_shapes": {"cg_branches": shapes, "per_shape": shape_t},
+                "peak_note": "FP64 pipe from unit counts: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                "peak_measured_probe": round(probe, 4), "frac_of_probe": round(achieved / probe, 4),
+                "probe": "seed_time_fma(SEED_F64): FMA chains over the whole GPU, this run"}
+    k_ms = S.seed_time_operator(ctx, 4, ncols_total, 200)
+    b = wilson_bytes(vol, ncols_total, fp32=True)
+    achieved = b / (k_ms * 1e-3) / 1e9
+    peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
+    shape_t = {}
+    for c in sorted(set(shapes)):
+        m = S.seed_time_operator(ctx, 4, c, 200)
+        a = wilson_bytes(vol, c, fp32=True) / (m * 1e-3) / 1e9
+        shape_t[str(c)] = {"ms_per_launch": round(m, 5), "achieved": round(a, 1), "frac": round(a / peak, 4)}
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": dslash_traffic(fp32=True) if tuple(dims) == DSLASH32_TRAFFIC_DIMS and ncols_total == 11
+            else None,
+            "kernel": "%s<+1> (Wilson D, FP32 complex), %d columns in one launch: the work of one CG "
+                      "half-iteration" % (fp32_kernel_name(vol), ncols_total),
+            "ms_per_launch": round(k_ms, 5), "bytes_per_launch": b, "l2_resident": b < L2_BYTES,
+            "launch_shapes": {"cg_branches": shapes, "per_shape": shape_t},
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def run_secondary(S, I, torch, dev, flush, steps, warmup):
+    """The 16^3 x 32 lattice with 12 Z4 noise sources: mixed precision against
+    plain FP64 on the same workload, each system's FP64 true residual."""
+    dims = (16, 16, 16, 32)
+    out = {"workload": "wilson-dirac 16x16x16x32 kappa=0.155 A=D^H D, 12 Z4 noise sources (seed 0), seed tol "
+                       "1e-12 reorth/100, CG tol 1e-8; Lanczos basis up to 1000 vectors",
+           "steps": steps, "warmup": warmup}
+    for mixed in (True, False):
+        p = make_problem(S, I, torch, dev, dims, "z4", mixed, m_max=1000)
+        ms, (i1, i2) = time_steps(S, torch, p, flush, steps, warmup)
+        st = S.seed_get_stats(p["ctx"])
+        o = {"ms": round(statistics.mean(ms), 3), "step_ms": [round(x, 3) for x in ms],
+             "seed_steps": i1[0]["iters"], "cg_iters": [i["iters"] for i in i2[1:]],
+             "true_relres_fp64": [i1[0]["true_relres"]] + [i["true_relres"] for i in i2[1:]],
+             "converged": bool(i1[0]["converged"]) and all(i["converged"] for i in i2[1:]),
+             "phase_ms": {"seed_solve_first": round(st["ms_seed"], 3), "seed_solve_rest": round(st["ms_rest"], 3)}}
+        if mixed:
+            o["roofline"] = dslash_roofline(S, p["ctx"], p["vol"], True, dims, WL["nrhs"] - 1)
+        out["mixed" if mixed else "fp64"] = o
+        S.seed_destroy(p["ctx"])
+        del p
+        torch.cuda.empty_cache()
+    out["speedup_mixed_over_fp64"] = round(out["fp64"]["ms"] / out["mixed"]["ms"], 3)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -395,8 +570,8 @@ def run_ours(args):
     default_wl = dims == WL["dims"] and args.sources == "point" and not mixed
     vol = int(np.prod(dims))
     n = 12 * vol
-    U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
     if args.kernel_only:
+        U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
         prm = S.seed_params_default(m_max=4, precision=1 if mixed else 0)
         ctx = S.seed_create_wilson(dims, kappa, U, prm)
         ncols = args.ncols or nrhs - 1
@@ -407,25 +582,13 @@ def run_ours(args):
                           "tflops": flops / (ms * 1e-3) / 1e12, "gbs": b / (ms * 1e-3) / 1e9}), flush=True)
         S.seed_destroy(ctx)
         return 0
-    prm = S.seed_params_default(m_max=WL["m_max"], reorth_freq=WL["reorth_freq"],
-                                reorth_passes=WL["reorth_passes"], tol_seed=WL["tol_seed"],
-                                tol_rest=WL["tol_rest"], x0_zero=1, precision=1 if mixed else 0,
-                                reliable_delta=args.reliable_delta)
-    ctx = S.seed_create_wilson(dims, kappa, U, prm)
-    eta_h = I.point_sources(dims, nrhs) if args.sources == "point" else I.z4_noise(n, nrhs, seed=0)
-    ETA = torch.from_numpy(np.ascontiguousarray(eta_h.T)).to(dev).t()     # (n, nrhs) column-major
-    B = torch.empty((nrhs, n), dtype=torch.complex128, device=dev).t()
-    X = torch.empty((nrhs, n), dtype=torch.complex128, device=dev).t()
+    m_max = WL["m_max"] if dims == WL["dims"] else 1000
+    p = make_problem(S, I, torch, dev, dims, args.sources, mixed, m_max, args.reliable_delta)
+    ctx = p["ctx"]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
 
-    def step():
-        S.seed_apply(ctx, 2, ETA, B)
-        i1 = S.seed_solve_first(ctx, B, X)
-        i2 = S.seed_solve_rest(ctx, B, X)
-        return i1, i2
-
     if args.once:
-        i1, i2 = step()
+        i1, i2 = solve_step(S, p)
         torch.cuda.synchronize()
         st = S.seed_get_stats(ctx)
         print(json.dumps({"once": workload_name(dims, args.sources, mixed), "seed_steps": i1[0]["iters"],
@@ -434,7 +597,7 @@ def run_ours(args):
         return 0
     for _ in range(args.warmup):
         flush.zero_()
-        i1, i2 = step()
+        i1, i2 = solve_step(S, p)
     torch.cuda.synchronize()
     assert all(i["converged"] for i in i1[:1] + i2[1:]), (i1[0], i2[1:])
 
@@ -445,67 +608,27 @@ def run_ours(args):
     except Exception:
         uuid = None
     st0 = S.seed_get_stats(ctx)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         replicas_barrier(dist, "before the timed steps")
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    infos = []
     with ClockSampler(uuid) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record()
-            infos.append(step())
-            ev[k][1].record()
-        torch.cuda.synchronize()
+        step_ms, (i1, i2) = time_steps(S, torch, p, flush, args.steps, 0)
     if dist:
         replicas_barrier(dist, "after the timed steps")
     t_wall1 = time.perf_counter()
     st1 = S.seed_get_stats(ctx)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
     ms = max_over_ranks(ms, dist, dev)
-    i1, i2 = infos[-1]
     ok = all(i["converged"] for i in i1[:1] + i2[1:])
     launches = st1["kernel_launches"] - st0["kernel_launches"]
 
-    # dominant kernel: the Wilson hopping kernel over the 11 lockstep CG columns
-    ncols = nrhs - 1
-    if not mixed:
-        k_ms = S.seed_time_operator(ctx, 1, ncols, 200)
-        k_ms1 = S.seed_time_operator(ctx, 1, 1, 200)
-        flops = FLOPS_PER_SITE_D * vol * ncols
-        achieved = flops / (k_ms * 1e-3) / 1e12
-        peak = FP64_PEAK_GFLOPS / 1e3
-        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": dslash_traffic() if dims == WL["dims"] else None,
-                "kernel": "k_dslash<+1> (Wilson D, FP64 complex), %d columns in one launch: the work of one "
-                          "CG half-iteration, which the CG graphs issue as %s-column launches on concurrent "
-                          "streams" % (ncols, "+".join(str(x) for x in cg_branch_cols(ncols))),
-                "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
-                "flops_per_launch": flops,
-                "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived from unit counts and "
-                             "max clock; a probe measured 1.20 TFLOP/s)"}
-    else:
-        k_ms = S.seed_time_operator(ctx, 4, ncols, 200)
-        k_ms1 = S.seed_time_operator(ctx, 4, 1, 200)
-        b = wilson_bytes(vol, ncols, fp32=True)
-        achieved = b / (k_ms * 1e-3) / 1e9
-        peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": dslash_traffic(fp32=True) if dims == DSLASH32_TRAFFIC_DIMS and ncols == 11 else None,
-                "kernel": "%s<+1> (Wilson D, FP32 complex), %d columns in one launch: the work of one CG "
-                          "half-iteration, which the CG graphs issue as %s-column launches on concurrent streams"
-                          % (fp32_kernel_name(vol), ncols, "+".join(str(x) for x in cg_branch_cols(ncols))),
-                "ms_per_launch": round(k_ms, 5), "ms_per_launch_1col": round(k_ms1, 5),
-                "bytes_per_launch": b, "l2_resident": b < L2_BYTES,
-                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    roof = dslash_roofline(S, ctx, vol, mixed, dims, nrhs - 1)
 
     # end to end through the public API, host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        eta_pin = torch.from_numpy(np.ascontiguousarray(eta_h.T)).pin_memory()
+        eta_pin = torch.from_numpy(np.ascontiguousarray(p["eta_h"].T)).pin_memory()
         x_pin = torch.empty((nrhs, n), dtype=torch.complex128).pin_memory()
         ETA2 = torch.empty((nrhs, n), dtype=torch.complex128, device=dev)
         e2e_ms = []
@@ -515,10 +638,10 @@ def run_ours(args):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             ETA2.copy_(eta_pin, non_blocking=True)
-            S.seed_apply(ctx, 2, ETA2.t(), B)
-            S.seed_solve_first(ctx, B, X)
-            S.seed_solve_rest(ctx, B, X)
-            x_pin.copy_(X.t(), non_blocking=True)
+            S.seed_apply(ctx, 2, ETA2.t(), p["B"])
+            S.seed_solve_first(ctx, p["B"], p["X"])
+            S.seed_solve_rest(ctx, p["B"], p["X"])
+            x_pin.copy_(p["X"].t(), non_blocking=True)
             b.record()
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
@@ -526,33 +649,38 @@ def run_ours(args):
         e2e_v = max_over_ranks(e2e_v, dist, dev)
         e2e = {"value": round(e2e_v, 3), "unit": "ms", "h2d_bytes_per_step": int(eta_pin.numel() * 16),
                "d2h_bytes_per_step": int(x_pin.numel() * 16), "step_ms": [round(x, 3) for x in e2e_ms]}
+    S.seed_destroy(ctx)
+
+    secondary = None
+    if rank == 0 and world == 1 and default_wl and not args.no_secondary:
+        secondary = run_secondary(S, I, torch, dev, flush, steps=min(args.steps, 3), warmup=1)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and default_wl:
-        total_s, detail = oracle_sample()
-        cpu = cpu_baseline_obj(total_s, detail)
+        cpu = cpu_baseline_obj()
 
     if rank == 0:
+        cfg = workload_config(dims, args.sources, mixed, world, m_max)
+        if mixed:
+            cfg["reliable_delta"] = args.reliable_delta or 0.01
+        if secondary is not None:
+            cfg["secondary"] = secondary
         out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
-               "data": "synthetic",
-               "config": {"workload": workload_name(dims, args.sources, mixed), "lattice": "x".join(map(str, dims)),
-                          "n": n, "nrhs": nrhs, "precision": args.precision,
-                          "reliable_delta": (args.reliable_delta or 0.01) if mixed else None,
-                          "kappa": kappa, "tol_seed": WL["tol_seed"], "reorth_freq": WL["reorth_freq"],
-                          "reorth_passes": WL["reorth_passes"], "tol_rest": WL["tol_rest"],
-                          "parallelism": "replicas" if world > 1 else "single-gpu",
-                          "l2": "flushed (512 MB write) before every step, outside the timed events",
-                          "seed_steps": i1[0]["iters"], "cg_iters": [i["iters"] for i in i2[1:]],
-                          "last_step_phase_ms": {"seed_solve_first": round(st1["ms_seed"], 3),
-                                                 "seed_solve_rest": round(st1["ms_rest"], 3)},
-                          "wall_s_timed_region": round(t_wall1 - t_wall0, 3),
-                          "step_ms": [round(x, 3) for x in step_ms], "converged": ok},
+               "scaling": "weak", "vs_baseline": None,
+               "vs_baseline_note": "the paper prints no time for this metric and workload (its timings are "
+                                   "CPU-cluster seconds for a 20^3x32 lattice); the oracle's time is in "
+                                   "cpu_baseline",
+               "dtype": "f32+f64" if mixed else "f64", "data": "synthetic", "config": cfg,
+               "run": {"seed_steps": i1[0]["iters"], "cg_iters": [i["iters"] for i in i2[1:]],
+                       "true_relres": [i1[0]["true_relres"]] + [i["true_relres"] for i in i2[1:]],
+                       "last_step_phase_ms": {"seed_solve_first": round(st1["ms_seed"], 3),
+                                              "seed_solve_rest": round(st1["ms_rest"], 3)},
+                       "wall_s_timed_region": round(t_wall1 - t_wall0, 3),
+                       "step_ms": [round(x, 3) for x in step_ms], "converged": ok},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                "clocks": clk.summary()}
         print(json.dumps(out), flush=True)
-    S.seed_destroy(ctx)
     if dist:
         dist.destroy_process_group()
     return 0
@@ -601,14 +729,16 @@ def run_adjoint(args):
         res[seeded] = dict(fw=statistics.mean(fw), bw=statistics.mean(bw), bw_iters=its[-1], fw_iters=fits[-1],
                            grad_kappa=float(k.grad))
     s_, u_ = res.get(True, res[False]), res[False]
+    # the value is the library's default, the backward solves started from zero
     out = {"metric": "adjoint forward+backward time (loss and gradients for b and kappa)",
-           "value": round(s_["fw"] + s_["bw"], 3), "unit": "ms", "n_gpus": 1, "steps": args.steps,
+           "value": round(u_["fw"] + u_["bw"], 3), "unit": "ms", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "higher_is_better": False, "dtype": "f32+f64" if mixed else "f64",
            "data": "synthetic",
            "config": {"workload": "wilson-dirac %s kappa=%.3f A=D^H D, %d Gaussian b and t (seeds 0, 1), seed tol "
                                   "1e-10 reorth/%d, CG tol 1e-8%s" % ("x".join(map(str, dims)), kappa, nrhs, freq,
                                                                        ", mixed precision" if mixed else ""),
-                      "forward_ms": round(s_["fw"], 3), "backward_seeded_ms": round(s_["bw"], 3),
+                      "backward": "unseeded (default)",
+                      "forward_ms": round(u_["fw"], 3), "backward_seeded_ms": round(s_["bw"], 3),
                       "backward_unseeded_ms": round(u_["bw"], 3),
                       "backward_cg_iters_seeded": s_["bw_iters"], "backward_cg_iters_unseeded": u_["bw_iters"],
                       "forward_iters": s_["fw_iters"], "grad_kappa": s_["grad_kappa"],

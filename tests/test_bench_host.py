@@ -16,8 +16,13 @@ def test_algorithmic_bytes_and_flops_per_unit():
     # CSR: 8 B value + 4 B index per nonzero, row pointers, x read and y written once
     assert bench.csr_bytes(4096, 20224) == 12 * 20224 + 4 * 4097 + 16 * 4096 == 324612
     # 1320 hopping flops (8 hops: projection, 3x3 complex matrix times two colour vectors,
-    # accumulation) + 48 for psi - kappa * sum
-    assert bench.FLOPS_PER_SITE_D == 1368
+    # reconstruction, accumulation); the 48 of psi - kappa * sum are reported separately
+    assert bench.FLOPS_PER_SITE_D == 1320 and bench.FLOPS_PER_SITE_D_EPILOGUE == 48
+    # the count: each of the 8 hops projects 4 -> 2 spin components (6 complex adds, 12 flops)
+    # and multiplies the two colour vectors by a 3x3 complex matrix (2 x (9 complex multiplies
+    # of 6 flops + 6 complex adds of 2) = 132 flops); 7 of the 8 hops add 24 reals into the
+    # accumulated spinor (the first one stores); the reconstruction is sign changes only
+    assert 8 * (12 + 2 * (9 * 6 + 6 * 2)) + 7 * 24 == bench.FLOPS_PER_SITE_D
     assert abs(bench.FP64_PEAK_GFLOPS - 1258.56) < 1e-9
 
 
@@ -36,3 +41,10 @@ def test_traffic_entries_only_for_captured_sources():
     assert bench.dslash_traffic() in (None, *bench.DSLASH_TRAFFIC.values())
     assert bench.dslash_traffic(fp32=True) in (None, *bench.DSLASH32_TRAFFIC.values())
     assert len(bench.dslash_source_hash()) == 16 and bench.dslash_source_hash() != bench.dslash_source_hash(fp32=True)
+
+
+def test_workload_config_is_the_same_for_both_arms():
+    a = bench.workload_config(bench.WL["dims"], "point", False)
+    assert a["workload"] == bench.WORKLOAD_NAME and a["n"] == 49152 and a["nrhs"] == 12
+    assert a == bench.workload_config((8, 8, 8, 8), "point", False, 1)
+    assert "flushed" in a["l2"]

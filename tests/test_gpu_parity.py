@@ -129,6 +129,7 @@ def self_sensitivity(orc, op, B, ref, cols=(1,), tol_rest=1e-8, **seed_kw):
     rng = np.random.default_rng(12345)
     Bp = B * (1 + 2.2e-16 * rng.standard_normal(B.shape))
     sp = orc.seed_first(op, Bp, **seed_kw)
+    self_sensitivity.perturbed = (Bp, sp["X"])
     seeded = np.linalg.norm(sp["X"][:, 1:] - ref["X_seeded"][:, 1:]) / np.linalg.norm(ref["X_seeded"][:, 1:])
     final = 0.0
     for j in cols:
@@ -348,7 +349,13 @@ def _workload_reference(orc):
                                  tol_rest=1e-8)
         sens = self_sensitivity(orc, op, B, ref, cols=(1, 6), m_max=3000, reorth_freq=100, reorth_passes=2,
                                 tol=1e-12)
-        _WORKLOAD_REF.update(dims=dims, kappa=kappa, U=U, B=B, ref=ref, sens=sens, tridiag=self_sensitivity.tridiag)
+        # seeded residual norms and their own one-ulp sensitivity (self_sensitivity's perturbed run)
+        res = [np.linalg.norm(B[:, j] - op.apply(ref["X_seeded"][:, j])) / np.linalg.norm(B[:, j])
+               for j in range(1, 12)]
+        Bp, Xp = self_sensitivity.perturbed
+        resp = [np.linalg.norm(Bp[:, j] - op.apply(Xp[:, j])) / np.linalg.norm(Bp[:, j]) for j in range(1, 12)]
+        _WORKLOAD_REF.update(dims=dims, kappa=kappa, U=U, B=B, ref=ref, sens=sens, tridiag=self_sensitivity.tridiag,
+                             seeded_res=res, seeded_res_sens=max(abs(b / a - 1.0) for a, b in zip(res, resp)))
     return _WORKLOAD_REF
 
 
@@ -375,6 +382,53 @@ def test_seed_wilson_8_4_full_workload(seedlib, orc, kernel_path):
     assert len(a) == len(ref["seed"]["alpha"])
     assert tridiag_dev(a, b, ref["seed"]["alpha"], ref["seed"]["beta"]) <= max(1e-9, 10 * self_sensitivity.tridiag)
     assert tridiag_dev(a[:100], b[:101], ref["seed"]["alpha"][:100], ref["seed"]["beta"][:101]) < 1e-9
+    # The seeded vectors themselves depend on rounding between reorthogonalizations
+    # (Sec. 3), but what seeding achieves -- each system's seeded residual norm
+    # ||b^j - A x^j_seed|| / ||b^j||, computed here with the oracle's operator -- does
+    # not: the oracle's own values move by < 2e-4 relative under one-ulp noise on B.
+    op = orc.Operator.wilson(dims, kappa, U)
+    for j in range(1, 12):
+        r_gpu = np.linalg.norm(B[:, j] - op.apply(Xs[:, j])) / np.linalg.norm(B[:, j])
+        r_orc = w["seeded_res"][j - 1]
+        assert abs(r_gpu / r_orc - 1.0) <= max(1e-6, 10 * w["seeded_res_sens"]), (j, r_gpu, r_orc)
+
+
+_TIGHT_REF = {}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kernel_path", [0, 1])
+def test_seed_wilson_8_4_workload_tight_rest(seedlib, orc, kernel_path):
+    """The benchmark workload with the remaining systems solved to 1e-12
+    instead of 1e-8, on both sides.  Then every final solution is within
+    cond(A) x 1.5e-12 of the exact one (cond(A) = 584 from the oracle's Ritz
+    values), the oracle's own solutions move by ~4e-12 under one-ulp noise on B,
+    and the GPU's are held element-wise (per column, relative to its largest
+    entry) and column-norm-wise to the benchmark spec's 1e-9 -- the bound the 1e-8
+    run cannot carry because its solutions inherit the seeding's rounding."""
+    import os
+    w = _workload_reference(orc)
+    dims, kappa, U, B = w["dims"], w["kappa"], w["U"], w["B"]
+    if not _TIGHT_REF:
+        op = orc.Operator.wilson(dims, kappa, U)
+        orc.set_threads(os.cpu_count() or 1)      # same bits on any number of threads
+        _TIGHT_REF["ref"] = orc.seed_solve_all(op, B, m_max=3000, reorth_freq=100, reorth_passes=2,
+                                               tol_seed=1e-12, tol_rest=1e-12)
+        orc.set_threads(1)
+    ref = _TIGHT_REF["ref"]
+    prm = dict(m_max=3000, reorth_freq=100, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-12,
+               kernel_path=kernel_path)
+    ctx = wilson_ctx(seedlib, dims, kappa, U, **prm)
+    info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
+    seedlib.seed_destroy(ctx)
+    assert info1[0]["iters"] == ref["seed"]["iters"]
+    assert relerr(X[:, 0], ref["X"][:, 0]) < REL_X
+    for j, r in enumerate(ref["rest"], start=1):
+        g = info2[j]
+        assert g["converged"] == 1 and g["true_relres"] <= 1.5e-12, (j, g)
+        assert abs(g["iters"] - r["iters"]) <= max(1, 0.05 * r["iters"]), (j, g["iters"], r["iters"])
+        assert relerr(X[:, j], r["x"]) <= REL_X, (j, relerr(X[:, j], r["x"]))
+        assert np.abs(X[:, j] - r["x"]).max() <= REL_X * np.abs(r["x"]).max(), j
 
 
 # --------------------------------------------------------------------------
