@@ -380,6 +380,25 @@ seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t
  * tflops, SEED_ECUDA without a usable device. */
 seed_status seed_time_fma(int32_t dtype, seed_stream stream, double *tflops, double *ms);
 
+/* Validation and measurement helper (no counterpart in the paper as an entry
+ * point): the products of the mixed-precision seeding, G = V^H R (Sec. 3: each
+ * Lanczos vector projected onto every other right-hand side), computed the way
+ * a mixed-precision Wilson context folds a block of steps -- on the tensor cores
+ * (tcgen05, TF32 with each FP32 operand split into a rounded part and its
+ * remainder, FP32 accumulation over 2048 elements, FP64 above), operands staged
+ * by TMA, partials summed over CTAs in a fixed order.
+ *   V: device, FP32 complex (SEED_C64), n x k column-major (ldv); R: n x nr
+ *   (ldr); both 16-byte aligned, ldv and ldr even and >= n; n a positive
+ *   multiple of 64; k in [1, 128], nr in [1, 63].
+ *   G: host, k x nr complex double, row-major (G[2*(q*nr + j)] = Re g_qj).
+ *   reps: timed launches of the product kernel after one untimed one; *ms (may
+ *   be NULL): mean device time of one launch (CUDA events on `stream`).
+ * Allocates its scratch (the per-CTA partials), synchronises `stream`.
+ * SEED_EINVAL for bad sizes, SEED_ECUDA without a usable device or TMA,
+ * SEED_ETIMEOUT if a wait of the kernel ran past its 2 s limit. */
+seed_status seed_block_products(const void *V, int64_t ldv, int32_t k, const void *R, int64_t ldr, int32_t nr,
+                                int64_t n, double *G, int32_t reps, double *ms, seed_stream stream);
+
 /* Y = D^H D X (the Wilson normal operator, as seed_apply op 0 on a Wilson
  * context) WITHOUT allocating any device memory.  The paper has no
  * counterpart: this serves callers that cannot call cudaMalloc while they

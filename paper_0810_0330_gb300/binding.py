@@ -34,7 +34,7 @@ EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_c
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
            "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related",
            "seed_batch_solve", "seed_solve_multiple", "seed_inject_alloc_failure", "seed_check_barrier_timeout",
-           "seed_time_fma"]
+           "seed_time_fma", "seed_block_products"]
 
 
 class SeedError(RuntimeError):
@@ -116,6 +116,7 @@ def lib():
             L.seed_inject_alloc_failure.restype = I32
             L.seed_check_barrier_timeout.argtypes = [P, C.POINTER(I32), C.POINTER(C.c_double)]
             L.seed_time_fma.argtypes = [I32, P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.seed_block_products.argtypes = [P, I64, I32, P, I64, I32, I64, P, I32, C.POINTER(C.c_double), P]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
             L.seed_destroy.argtypes = [P]
@@ -401,6 +402,22 @@ def seed_time_fma(dtype: int = 0, stream=None) -> dict:
     tf, ms = C.c_double(), C.c_double()
     _check(lib().seed_time_fma(int(dtype), _stream(stream), C.byref(tf), C.byref(ms)), "seed_time_fma")
     return {"tflops": tf.value, "ms": ms.value}
+
+
+def seed_block_products(V: torch.Tensor, R: torch.Tensor, reps: int = 1, stream=None):
+    """G = V^H R (k x nr complex128, numpy) from FP32 complex blocks V (n x k) and
+    R (n x nr) on the tensor cores, and the mean device time of one launch in ms
+    (see include/seed.h)."""
+    import numpy as np
+    assert V.dtype == torch.complex64 and R.dtype == torch.complex64
+    n = V.shape[0]
+    pv, ldv, k = _block(V, n, "V")
+    pr, ldr, nr = _block(R, n, "R")
+    G = np.zeros((k, nr), dtype=np.complex128)
+    ms = C.c_double()
+    _check(lib().seed_block_products(pv, ldv, k, pr, ldr, nr, n, G.ctypes.data_as(C.c_void_p), int(reps),
+                                     C.byref(ms), _stream(stream)), "seed_block_products")
+    return G, ms.value
 
 
 def seed_last_error(ctx: Context = None) -> str:

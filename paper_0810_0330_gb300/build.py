@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libseed.so")
-SOURCES = ["wilson.cu", "wilson32.cu", "csr.cu", "krylov.cu", "mixed.cu", "adjoint.cu", "related.cu", "persistent.cu", "engine.cu", "noalloc.cu", "seedblock.cu", "probe.cu"]
+SOURCES = ["wilson.cu", "wilson32.cu", "csr.cu", "krylov.cu", "mixed.cu", "adjoint.cu", "related.cu", "persistent.cu", "engine.cu", "noalloc.cu", "seedblock.cu", "probe.cu", "tc_dots.cu"]
 HEADERS = ["device_common.cuh", "seed_internal.h", "wilson_device.cuh", "seed_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -127,6 +127,8 @@ struct seed_ctx {
   void *Wb = nullptr;
   double *gamma_hist = nullptr;
   BlockBufs blk{};
+  TcFlush tcf{};                       // tensor-core flush products (mixed-precision Wilson)
+  int *tc_err = nullptr;               // its device error flag
 
   std::map<std::string, GraphEntry> graphs;
   std::string err;
@@ -344,14 +346,27 @@ bool blocked_seeding(const seed_ctx *ctx, int nrhs) {
 
 // (each buffer is allocated once; after a failed allocation the next call
 // allocates only what is still missing)
+// The tensor-core flush serves FP32 complex vectors whose length is a multiple of its 64-element chunk.
+bool tc_flush_eligible(const seed_ctx *ctx) {
+  return ctx->precision == 1 && ctx->kind == 1 && ctx->nv >= 64 && ctx->nv % 64 == 0;
+}
+
 seed_status ensure_block(seed_ctx *ctx) {
-  if (ctx->Wb && ctx->blk.Hpart && ctx->blk.G && ctx->blk.Z) return SEED_OK;
+  if (ctx->Wb && ctx->blk.Hpart && ctx->blk.G && ctx->blk.Z && (!tc_flush_eligible(ctx) || ctx->tc_err))
+    return SEED_OK;
   const BlockBufs lay = block_layout(ctx->nv);
   ctx->blk.nchunk = lay.nchunk;
   ctx->blk.rows = lay.rows;
+  ctx->blk.tc = nullptr;
+  int chunks = lay.nchunk;
+  if (tc_flush_eligible(ctx)) chunks = std::max(chunks, tc_grid(ctx->nv));
   if (!ctx->Wb) TRY(dalloc(ctx, &ctx->Wb, (size_t)ctx->ldv * kSeedBlock * ctx->vsz));
   if (!ctx->blk.Hpart)
-    TRY(dalloc(ctx, &ctx->blk.Hpart, sizeof(double2) * (size_t)ctx->blk.nchunk * kSeedBlock * (kMaxRhs - 1)));
+    TRY(dalloc(ctx, &ctx->blk.Hpart, sizeof(double2) * (size_t)chunks * kSeedBlock * (kMaxRhs - 1)));
+  if (tc_flush_eligible(ctx) && !ctx->tc_err) {
+    TRY(dalloc(ctx, (void **)&ctx->tc_err, sizeof(int)));
+    CU(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), ctx->cs));
+  }
   if (!ctx->blk.G) TRY(dalloc(ctx, &ctx->blk.G, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
   if (!ctx->blk.Z) TRY(dalloc(ctx, &ctx->blk.Z, sizeof(double2) * (size_t)kSeedBlock * (kMaxRhs - 1)));
   return SEED_OK;
@@ -1283,6 +1298,18 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   if (blocked_seeding(ctx, nrhs)) TRY(ensure_block(ctx));
   ctx->basis_valid = false;
   ctx->seeded = false;
+  // TMA maps of the tensor-core flush over this call's buffers (V, r_0^2.. in FP32)
+  ctx->blk.tc = nullptr;
+  if (blocked_seeding(ctx, nrhs) && tc_flush_eligible(ctx) && ctx->tc_err) {
+    TcFlush &t = ctx->tcf;
+    t.err = ctx->tc_err;
+    t.grid = tc_grid(ctx->nv);
+    t.ok = t.grid >= 1 &&
+           tc_make_map(&t.vmap, ctx->V, ctx->nv, ctx->ldv, (int64_t)ctx->prm.m_max + 1) &&
+           tc_make_map(&t.rmap, (const char *)ctx->R32 + ctx->ldv * ctx->vsz, ctx->nv, ctx->ldv,
+                       std::max(ctx->cap_cols - 1, 1));
+    if (t.ok) ctx->blk.tc = &ctx->tcf;
+  }
   CU(cudaEventRecord(ctx->t0, ctx->cs));
   T32 *E = E_cols<T32>(ctx);
   const CallArgs ca{(void *)E, ld, 0};
@@ -1327,6 +1354,14 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   }
   CU(cudaStreamSynchronize(ctx->cs));
   CU(cudaGetLastError());
+  if (ctx->blk.tc) {
+    int terr = 0;
+    CU(cudaMemcpy(&terr, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (terr) {
+      CU(cudaMemset(ctx->tc_err, 0, sizeof(int)));
+      return fail(ctx, SEED_ETIMEOUT, "a wait of the tensor-core seeding kernel timed out");
+    }
+  }
   SeedState st;
   CU(cudaMemcpy(&st, ctx->st, sizeof(st), cudaMemcpyDeviceToHost));
   if (st.stop_reason == STOP_BLOCK) return fail(ctx, SEED_ECUDA, "internal: a seeding block overflowed");
@@ -1466,7 +1501,8 @@ void destroy(seed_ctx *ctx) {
                   ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
                   ctx->gsync, ctx->f2, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
                   ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots,
-                  ctx->msX, ctx->msR, ctx->Wb, ctx->gamma_hist, ctx->blk.Hpart, ctx->blk.G, ctx->blk.Z};
+                  ctx->msX, ctx->msR, ctx->Wb, ctx->gamma_hist, ctx->blk.Hpart, ctx->blk.G, ctx->blk.Z,
+                  ctx->tc_err};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);

@@ -1,6 +1,7 @@
 // seed_internal.h -- declarations shared by the kernel translation units and
 // the engine (host).  Not part of the public ABI.
 #pragma once
+#include <cuda.h>   // CUtensorMap (type only)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -93,15 +94,33 @@ struct SeedBufs {
 // Steps per block of the blocked seeding (columns of SeedBufs::Wb).
 constexpr int kSeedBlock = 128;
 
+// Tensor-core form of the FP32 complex flush products (tc_dots.cu): TMA maps
+// over V and R_0 and the CTA count of its grid; a host-side descriptor.
+struct TcFlush {
+  CUtensorMap vmap;   // V: columns of the FP32 basis (len nv, leading dimension ldv)
+  CUtensorMap rmap;   // R_0: r_0^2.. in FP32
+  int *err;           // device flag: a wait of the kernel ran out (reported as SEED_ETIMEOUT)
+  int grid;           // CTAs along the vector (<= SMs, <= nv / 64); also the partials' chunk count
+  bool ok;            // maps valid for the current buffers
+};
+
 // Workspace of the block flush (seedblock.cu).
 struct BlockBufs {
-  double2 *Hpart;   // [nchunk][kSeedBlock][kMaxRhs - 1] partial products v_i^H r_0^j
+  double2 *Hpart;   // [max(nchunk, tc grid)][kSeedBlock][kMaxRhs - 1] partial products v_i^H r_0^j
   double2 *G;       // [kSeedBlock][kMaxRhs - 1]   g_i^j
   double2 *Z;       // [kSeedBlock][kMaxRhs - 1]   eta_i^j
   int32_t nchunk;   // row chunks of the partial products
   int64_t rows;     // rows per chunk
+  const TcFlush *tc;   // host pointer, NULL or !ok: CUDA-core products (only read by the launcher)
 };
 constexpr int kBlockChunksMax = 64;
+
+// tc_dots.cu
+bool tc_make_map(CUtensorMap *map, const void *base, int64_t len, int64_t ld, int64_t ncols);
+int tc_grid(int64_t len);
+cudaError_t launch_blk_dots_tc(const CUtensorMap &vmap, const CUtensorMap &rmap, const SeedState *st, int len_host,
+                               int vcol_host, int nj, int64_t len, double2 *Hpart, int grid, int *err,
+                               cudaStream_t s);
 
 // Buffers of the blocked reorthogonalization (Sec. 3).
 template <class T>

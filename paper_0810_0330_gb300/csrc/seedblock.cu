@@ -15,6 +15,8 @@
 // a reorthogonalizing step rewrites v_i (Sec. 3), so V_blk holds the
 // vectors the streaming form uses; the two forms differ in summation order
 // only.
+#include <type_traits>
+
 #include "seed_device.cuh"
 
 namespace seedk {
@@ -201,11 +203,19 @@ template <class T>
 int launch_seed_flush(const SeedBufs<T> &b, const BlockBufs &k, cudaStream_t s) {
   if (b.Wb == nullptr || b.nrhs < 2) return 0;
   const int nj = b.nrhs - 1;
-  const int64_t tiles = (int64_t)((kSeedBlock + kBQ - 1) / kBQ) * ((nj + kBJ - 1) / kBJ);
-  int64_t grid = (int64_t)k.nchunk * tiles;   // items of a full block; shorter blocks leave blocks idle
-  if (grid > 152 * 16) grid = 152 * 16;
-  k_blk_dots<T><<<(unsigned)grid, NT, 0, s>>>(b, k);
-  k_blk_reduce<<<(kSeedBlock * kLdG + NT - 1) / NT, NT, 0, s>>>(b.st, b.nrhs, k);
+  if (std::is_same<T, float2>::value && k.tc && k.tc->ok) {
+    // FP32 complex: G = V_blk^H R_0 on the tensor cores (3xTF32), then the same reduction
+    launch_blk_dots_tc(k.tc->vmap, k.tc->rmap, b.st, 0, 0, nj, b.n, k.Hpart, k.tc->grid, k.tc->err, s);
+    BlockBufs kr = k;
+    kr.nchunk = k.tc->grid;
+    k_blk_reduce<<<(kSeedBlock * kLdG + NT - 1) / NT, NT, 0, s>>>(b.st, b.nrhs, kr);
+  } else {
+    const int64_t tiles = (int64_t)((kSeedBlock + kBQ - 1) / kBQ) * ((nj + kBJ - 1) / kBJ);
+    int64_t grid = (int64_t)k.nchunk * tiles;   // items of a full block; shorter blocks leave blocks idle
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_blk_dots<T><<<(unsigned)grid, NT, 0, s>>>(b, k);
+    k_blk_reduce<<<(kSeedBlock * kLdG + NT - 1) / NT, NT, 0, s>>>(b.st, b.nrhs, k);
+  }
   k_blk_eta<<<1, kMaxRhs, 0, s>>>(b.st, b.nrhs, b.eta, b.gamma_hist, k);
   int64_t bx = (b.n + NT - 1) / NT;
   if (bx > 152 * 16) bx = 152 * 16;
