@@ -385,11 +385,11 @@ seed_status seed_time_fma(int32_t dtype, seed_stream stream, double *tflops, dou
  * Lanczos vector projected onto every other right-hand side), computed the way
  * a mixed-precision Wilson context folds a block of steps -- on the tensor cores
  * (tcgen05, TF32 with each FP32 operand split into a rounded part and its
- * remainder, FP32 accumulation over 2048 elements, FP64 above), operands staged
+ * remainder, FP32 accumulation over 512 elements, FP64 above), operands staged
  * by TMA, partials summed over CTAs in a fixed order.
  *   V: device, FP32 complex (SEED_C64), n x k column-major (ldv); R: n x nr
  *   (ldr); both 16-byte aligned, ldv and ldr even and >= n; n a positive
- *   multiple of 64; k in [1, 128], nr in [1, 63].
+ *   multiple of 128; k in [1, 128], nr in [1, 63].
  *   G: host, k x nr complex double, row-major (G[2*(q*nr + j)] = Re g_qj).
  *   reps: timed launches of the product kernel after one untimed one; *ms (may
  *   be NULL): mean device time of one launch (CUDA events on `stream`).

@@ -346,9 +346,9 @@ bool blocked_seeding(const seed_ctx *ctx, int nrhs) {
 
 // (each buffer is allocated once; after a failed allocation the next call
 // allocates only what is still missing)
-// The tensor-core flush serves FP32 complex vectors whose length is a multiple of its 64-element chunk.
+// The tensor-core flush serves FP32 complex vectors whose length is a multiple of its 128-element chunk.
 bool tc_flush_eligible(const seed_ctx *ctx) {
-  return ctx->precision == 1 && ctx->kind == 1 && ctx->nv >= 64 && ctx->nv % 64 == 0;
+  return ctx->precision == 1 && ctx->kind == 1 && ctx->nv >= 128 && ctx->nv % 128 == 0;
 }
 
 seed_status ensure_block(seed_ctx *ctx) {
@@ -1305,9 +1305,9 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
     t.err = ctx->tc_err;
     t.grid = tc_grid(ctx->nv);
     t.ok = t.grid >= 1 &&
-           tc_make_map(&t.vmap, ctx->V, ctx->nv, ctx->ldv, (int64_t)ctx->prm.m_max + 1) &&
-           tc_make_map(&t.rmap, (const char *)ctx->R32 + ctx->ldv * ctx->vsz, ctx->nv, ctx->ldv,
-                       std::max(ctx->cap_cols - 1, 1));
+           tc_make_maps(t.maps.v, ctx->V, ctx->nv, ctx->ldv, (int64_t)ctx->prm.m_max + 1) &&
+           tc_make_maps(t.maps.r, (const char *)ctx->R32 + ctx->ldv * ctx->vsz, ctx->nv, ctx->ldv,
+                        std::max(ctx->cap_cols - 1, 1));
     if (t.ok) ctx->blk.tc = &ctx->tcf;
   }
   CU(cudaEventRecord(ctx->t0, ctx->cs));

@@ -96,11 +96,16 @@ constexpr int kSeedBlock = 128;
 
 // Tensor-core form of the FP32 complex flush products (tc_dots.cu): TMA maps
 // over V and R_0 and the CTA count of its grid; a host-side descriptor.
+// TMA maps of one FP32 complex block, one per box height: v[h] loads 16 >> h columns
+// (16, 8, 4, 2, 1) of 128 complex each; a height above the block's column count is never used.
+struct TcMaps {
+  CUtensorMap v[5];   // V: columns of the FP32 basis (len nv, leading dimension ldv)
+  CUtensorMap r[5];   // R_0: r_0^2.. in FP32
+};
 struct TcFlush {
-  CUtensorMap vmap;   // V: columns of the FP32 basis (len nv, leading dimension ldv)
-  CUtensorMap rmap;   // R_0: r_0^2.. in FP32
+  TcMaps maps;
   int *err;           // device flag: a wait of the kernel ran out (reported as SEED_ETIMEOUT)
-  int grid;           // CTAs along the vector (<= SMs, <= nv / 64); also the partials' chunk count
+  int grid;           // CTAs along the vector (<= SMs, <= nv / 128); also the partials' chunk count
   bool ok;            // maps valid for the current buffers
 };
 
@@ -116,11 +121,10 @@ struct BlockBufs {
 constexpr int kBlockChunksMax = 64;
 
 // tc_dots.cu
-bool tc_make_map(CUtensorMap *map, const void *base, int64_t len, int64_t ld, int64_t ncols);
+bool tc_make_maps(CUtensorMap maps[5], const void *base, int64_t len, int64_t ld, int64_t ncols);
 int tc_grid(int64_t len);
-cudaError_t launch_blk_dots_tc(const CUtensorMap &vmap, const CUtensorMap &rmap, const SeedState *st, int len_host,
-                               int vcol_host, int nj, int64_t len, double2 *Hpart, int grid, int *err,
-                               cudaStream_t s);
+cudaError_t launch_blk_dots_tc(const TcMaps &maps, const SeedState *st, int len_host, int vcol_host, int nj,
+                               int64_t len, double2 *Hpart, int grid, int *err, cudaStream_t s);
 
 // Buffers of the blocked reorthogonalization (Sec. 3).
 template <class T>

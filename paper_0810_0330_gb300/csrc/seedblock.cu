@@ -205,7 +205,7 @@ int launch_seed_flush(const SeedBufs<T> &b, const BlockBufs &k, cudaStream_t s) 
   const int nj = b.nrhs - 1;
   if (std::is_same<T, float2>::value && k.tc && k.tc->ok) {
     // FP32 complex: G = V_blk^H R_0 on the tensor cores (3xTF32), then the same reduction
-    launch_blk_dots_tc(k.tc->vmap, k.tc->rmap, b.st, 0, 0, nj, b.n, k.Hpart, k.tc->grid, k.tc->err, s);
+    launch_blk_dots_tc(k.tc->maps, b.st, 0, 0, nj, b.n, k.Hpart, k.tc->grid, k.tc->err, s);
     BlockBufs kr = k;
     kr.nchunk = k.tc->grid;
     k_blk_reduce<<<(kSeedBlock * kLdG + NT - 1) / NT, NT, 0, s>>>(b.st, b.nrhs, kr);

@@ -14,7 +14,7 @@
 // products hi*hi + hi*lo + lo*hi ("3xTF32") reproduce the FP32 product to
 // about 2^-21 -- the FP32 accuracy of the CUDA-core version -- where plain TF32
 // would leave ~2e-4 relative error in G.  The tensor cores accumulate in FP32
-// over at most 2048 elements (one "item"); each item is then drained from
+// over at most 512 elements (one "item"); each item is then drained from
 // tensor memory and added in FP64, and the per-CTA partials are summed over
 // CTAs in a fixed order by k_blk_reduce (deterministic).
 //
@@ -28,15 +28,20 @@
 // and more systems run as more CTAs (grid.y: 32-step tiles, grid.z: 16-system
 // tiles).
 //
-// Warp roles (10 warps, one CTA per SM):
-//   warp 0      TMA producer: one thread issues a 2-d cp.async.bulk.tensor per
-//               column and stage (64 complex = 512 B of a V or R_0 column)
-//               into a 4-stage raw ring
+// Warp roles (12 warps, one CTA per SM):
+//   warp 0      TMA producer: one thread issues 2-d cp.async.bulk.tensor loads of
+//               128-element chunks (1 KB rows) of 16, 8, 4, 2 or 1 consecutive
+//               columns into a raw ring of as many stages as fit 120 KB (3 for
+//               the 36 columns of a 25-step, 11-system block).  Few large
+//               requests: measured on this GPU, streaming 36 such columns with
+//               one request per 512 B row reaches 1.5 TB/s, with one per 6 KB
+//               6.5 TB/s (each request costs the TMA unit ~50 ns)
 //   warp 1      tensor memory allocation, the MMA issuer (one thread), and
 //               deallocation
-//   warps 2,3,8,9  converters: raw FP32 (re, im interleaved) -> TF32 hi/lo,
+//   warps 2,3,8-11  converters: raw FP32 (re, im interleaved) -> TF32 hi/lo,
 //               deinterleaved, into the UMMA K-major core-matrix layout of a
-//               2-stage operand ring
+//               4-stage operand ring of 32 elements per stage (the round trip
+//               from MMA issue to the stage's release is ~0.6 us)
 //   warps 4-7   epilogue: warp 4 + q reads tensor-memory lanes 32q..32q+31
 //               (rows of A part q), accumulates FP64
 // Every wait on an mbarrier gives up after kTcWaitNs, sets *err and lets all
@@ -45,6 +50,7 @@
 #include <cuda.h>   // CUtensorMap (the type only; the encode call is found through the runtime)
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <string>
 
 #include "seed.h"
@@ -54,36 +60,43 @@ namespace seedk {
 
 namespace tc {
 
-constexpr int kThreads = 320;                 // 10 warps
-constexpr int kChunk = 64;                    // complex elements of a column per stage
+constexpr int kThreads = 384;                 // 12 warps
+constexpr int kConvWarps = 6;
+constexpr int kChunk = 128;                   // complex elements of a column per raw (TMA) stage
+constexpr int kOpChunk = 32;                  // complex elements per operand stage (four per raw stage)
+constexpr int kOpPerRaw = kChunk / kOpChunk;
+constexpr int kBoxes = 5;                     // TMA box heights 16, 8, 4, 2, 1 columns
 constexpr int kSteps = 32;                    // Lanczos steps per M tile
 constexpr int kCols = 16;                     // right-hand sides per N tile
-constexpr int kRawStages = 4;
-constexpr int kOpStages = 2;
-constexpr int kItemChunks = 32;               // stages accumulated in FP32 before a drain
-constexpr int kSlot = kChunk * 8;             // 512 B: one column's chunk (64 float2)
-constexpr int kRawStage = (kSteps + kCols) * kSlot;   // 24576 B
-constexpr int kKGroups = kChunk / 4;          // 16 core-matrix columns of 4 TF32 per stage
+constexpr int kConvThreads = kConvWarps * 32;
+constexpr int kConvUnits = (kSteps + kCols) * (kOpChunk / 2);   // 16-byte pieces of an operand stage, at most
+constexpr int kConvPerThread = (kConvUnits + kConvThreads - 1) / kConvThreads;   // 4
+constexpr int kOpStages = 4;
+constexpr int kRawMaxStages = 12;
+constexpr int kItemOps = 16;                  // operand stages (512 elements) accumulated in FP32 per drain
+constexpr int kSlot = kChunk * 8;             // 1 KB: one column's chunk (128 float2)
+constexpr int kKGroups = kOpChunk / 4;        // 8 core-matrix columns of 4 TF32 per operand stage
 constexpr int kM = 128, kN = 64;
 // K-major, no swizzle: a core matrix is 8 rows x 16 B; SBO (next 8 rows) = 128 B; LBO
-// (next 4 elements of K) = all row groups + 16 B of padding, so that the 8 lanes of a
-// shared-memory phase writing one row at 8 consecutive K groups hit 8 different banks.
+// (next 4 elements of K) = all row groups + 16 B of padding, so that the lanes of a
+// shared-memory phase writing one row at consecutive K groups hit different banks.
 constexpr int kSBO = 128;
 constexpr int kLboA = (kM / 8) * 128 + 16;    // 2064
 constexpr int kLboB = (kN / 8) * 128 + 16;    // 1040
-constexpr int kOpA = kKGroups * kLboA;        // 33024
-constexpr int kOpB = kKGroups * kLboB;        // 16640
-constexpr int kOpStage = kOpA + kOpB;         // 49664
-constexpr int kRawBytes = kRawStages * kRawStage;   // 98304
+constexpr int kOpA = kKGroups * kLboA;        // 16512
+constexpr int kOpB = kKGroups * kLboB;        // 8320
+constexpr int kOpStage = kOpA + kOpB;         // 24832
+constexpr int kRawBytes = 120 * 1024;         // raw ring: floor(kRawBytes / stage) stages, <= kRawMaxStages
 constexpr int kOpBytes = kOpStages * kOpStage;      // 99328
-constexpr int kBarBytes = 256;
-constexpr int kSmemBytes = 1024 + kRawBytes + kOpBytes + kBarBytes;   // + alignment slack
+constexpr int kBarBytes = 512;
+constexpr int kSmemBytes = 1024 + kRawBytes + kOpBytes + kBarBytes;   // + alignment slack: 223744
 constexpr int kTmemCols = 128;                // two accumulators of N = 64 FP32 columns
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
 // epilogue combine buffer (aliases the raw ring once every stage is consumed)
-constexpr int kCombBytes = 4 * 32 * 2 * kCols * 8;  // 32768
+constexpr int kCombBytes = 4 * 2 * kCols * 32 * 8;  // 32768
 static_assert(kCombBytes <= kRawBytes, "combine buffer must fit in the raw ring");
-static_assert(kOpA % 16 == 0 && kOpB % 16 == 0 && kRawStage % 1024 == 0, "alignment");
+static_assert(kOpA % 16 == 0 && kOpB % 16 == 0 && kOpStage % 16 == 0 && kRawBytes % 1024 == 0, "alignment");
+static_assert(kSmemBytes <= 232448, "shared memory per block");
 
 // instruction descriptor of tcgen05.mma kind::tf32: D FP32, A and B TF32, both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24
@@ -91,8 +104,8 @@ constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN 
                             ((uint32_t)(kM >> 4) << 24);
 
 struct Bars {
-  uint64_t raw_full[kRawStages];
-  uint64_t raw_empty[kRawStages];
+  uint64_t raw_full[kRawMaxStages];
+  uint64_t raw_empty[kRawMaxStages];
   uint64_t op_full[kOpStages];
   uint64_t op_empty[kOpStages];
   uint64_t acc_full[2];
@@ -161,7 +174,7 @@ __device__ void bar_drain(uint64_t *b, uint32_t parity, int *err) {
   }
 }
 
-// 2-d TMA load of one box (128 floats x 1 column) into shared memory, completion on `bar`
+// 2-d TMA load of one box (128 floats x 8, 4, 2 or 1 columns) into shared memory, completion on `bar`
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
@@ -209,11 +222,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
+// x rounded to TF32 (10 explicit mantissa bits, to nearest, ties away from zero) by
+// integer operations on its bits: add half a TF32 unit in the last place, clear the
+// 13 dropped bits (a carry into the exponent is the correct rounding)
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
 
 // byte offset of (row, K group) in an operand tile (K-major, no swizzle)
 __device__ __forceinline__ uint32_t op_off(int row, int kg, int lbo) {
@@ -228,9 +240,8 @@ __device__ __forceinline__ uint32_t op_off(int row, int kg, int lbo) {
 // len_host columns from column vcol_host.  Hpart[(cta * kSeedBlock + q) * kLdG + j]
 // receives the CTA's FP64 partial of G[q][j].
 __global__ void __launch_bounds__(tc::kThreads, 1)
-    k_blk_dots_tc(const __grid_constant__ CUtensorMap vmap, const __grid_constant__ CUtensorMap rmap,
-                  const SeedState *st, int len_host, int vcol_host, int nj, int64_t nchunks, double2 *Hpart,
-                  int *err) {
+    k_blk_dots_tc(const __grid_constant__ TcMaps maps, const SeedState *st, int len_host, int vcol_host, int nj,
+                  int64_t nchunks, double2 *Hpart, int *err) {
   using namespace tc;
   constexpr int kLdG = kMaxRhs - 1;
   int len, vcol0;
@@ -248,8 +259,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   vcol0 += mt * kSteps;
   const int rcol0 = nt * kCols;
   const int64_t c0 = nchunks * blockIdx.x / gridDim.x, c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
-  const int nst = (int)(c1 - c0);                       // >= 1: the host keeps gridDim.x <= nchunks
-  const int nitems = (nst + kItemChunks - 1) / kItemChunks;
+  const int nst = (int)(c1 - c0);                       // raw stages, >= 1: the host keeps gridDim.x <= nchunks
+  const int nop = kOpPerRaw * nst;                      // operand stages (quarters of each raw stage)
+  const int nitems = (nop + kItemOps - 1) / kItemOps;
+  const int ns = len_t + nr_t;                          // column slots of a raw stage: V, then R_0
+  const int raw_stage = ns * kSlot;
+  const int nraw = min(kRawMaxStages, kRawBytes / raw_stage);   // >= 2 (ns <= 48)
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -259,12 +274,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kRawStages; ++s) {
+    for (int s = 0; s < kRawMaxStages; ++s) {
       tc::bar_init(&bars->raw_full[s], 1);
-      tc::bar_init(&bars->raw_empty[s], 4);
+      tc::bar_init(&bars->raw_empty[s], kConvWarps);
     }
     for (int s = 0; s < kOpStages; ++s) {
-      tc::bar_init(&bars->op_full[s], 4);
+      tc::bar_init(&bars->op_full[s], kConvWarps);
       tc::bar_init(&bars->op_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -291,31 +306,34 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     if (lane == 0) {
       int issued = 0;
       for (int g = 0; g < nst; ++g) {
-        const int r = g % kRawStages;
-        if (g >= kRawStages && !tc::bar_wait(&bars->raw_empty[r], ((g / kRawStages) + 1) & 1, err)) break;
-        unsigned char *dst = raw + r * kRawStage;
+        const int r = g % nraw;
+        if (g >= nraw && !tc::bar_wait(&bars->raw_empty[r], ((g / nraw) + 1) & 1, err)) break;
+        unsigned char *dst = raw + r * raw_stage;
         const int x = (int)((c0 + g) * (kChunk * 2));   // float index of the chunk
-        tc::bar_expect_tx(&bars->raw_full[r], (uint32_t)((len_t + nr_t) * kSlot));
-        for (int s = 0; s < len_t; ++s) tc::tma_load_2d(dst + s * kSlot, &vmap, x, vcol0 + s, &bars->raw_full[r]);
-        for (int c = 0; c < nr_t; ++c)
-          tc::tma_load_2d(dst + (kSteps + c) * kSlot, &rmap, x, rcol0 + c, &bars->raw_full[r]);
+        tc::bar_expect_tx(&bars->raw_full[r], (uint32_t)raw_stage);
+        // columns in boxes of 16, 8, 4, 2, 1 (box h holds 16 >> h columns, slot after slot)
+        for (int h = 0, c = 0; h < kBoxes; ++h)
+          for (const int w = 16 >> h; len_t - c >= w; c += w)
+            tc::tma_load_2d(dst + c * kSlot, &maps.v[h], x, vcol0 + c, &bars->raw_full[r]);
+        for (int h = 0, c = 0; h < kBoxes; ++h)
+          for (const int w = 16 >> h; nr_t - c >= w; c += w)
+            tc::tma_load_2d(dst + (len_t + c) * kSlot, &maps.r[h], x, rcol0 + c, &bars->raw_full[r]);
         issued = g + 1;
       }
       // copies still in flight land before the CTA may leave (their phases are the last ones)
-      for (int g = issued - kRawStages > 0 ? issued - kRawStages : 0; g < issued; ++g)
-        tc::bar_drain(&bars->raw_full[g % kRawStages], (g / kRawStages) & 1, err);
+      for (int g = issued - nraw > 0 ? issued - nraw : 0; g < issued; ++g)
+        tc::bar_drain(&bars->raw_full[g % nraw], (g / nraw) & 1, err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      bool ok = true;
-      for (int g = 0; g < nst && ok; ++g) {
-        const int s = g % kOpStages;
-        const int t = g / kItemChunks;
-        const bool first = (g % kItemChunks) == 0;
-        const bool last = (g % kItemChunks) == kItemChunks - 1 || g == nst - 1;
+      for (int j = 0; j < nop; ++j) {
+        const int s = j % kOpStages;
+        const int t = j / kItemOps;
+        const bool first = (j % kItemOps) == 0;
+        const bool last = (j % kItemOps) == kItemOps - 1 || j == nop - 1;
         if (first && t >= 2 && !tc::bar_wait(&bars->acc_empty[t & 1], ((t >> 1) + 1) & 1, err)) break;
-        if (!tc::bar_wait(&bars->op_full[s], (g / kOpStages) & 1, err)) break;
+        if (!tc::bar_wait(&bars->op_full[s], (j / kOpStages) & 1, err)) break;
         tc::tc_fence_after();
         const uint32_t a0 = tc::saddr(ops + s * kOpStage), b0 = a0 + kOpA;
         const uint32_t d = tmem + (uint32_t)((t & 1) * kN);
@@ -334,6 +352,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     }
   } else if (warp >= 4 && warp < 8) {
     // ---------------- epilogue: drain the accumulators into FP64 ----------------
+    // D columns: [re: R hi 0..15, R lo 16..31][im: R hi 32..47, R lo 48..63]
     const int q = warp - 4;                  // A part: 0 hi re, 1 hi im, 2 lo re, 3 lo im
     const bool vim = (q & 1) != 0, vlo = (q >> 1) != 0;
     double gre[kCols], gim[kCols];
@@ -342,98 +361,116 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     for (int t = 0; t < nitems; ++t) {
       if (!tc::bar_wait(&bars->acc_full[t & 1], (t >> 1) & 1, err)) break;
       tc::tc_fence_after();
-      float v[64];
+      // keep hi*hi, hi*lo, lo*hi: a hi row takes both R parts (added in FP32 first), a lo row
+      // the hi part only; re columns, then im columns, to keep few registers live
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((t & 1) * kN);
+      float v[32], pre[kCols];
       tc::tmem_ld32(ta, v);
-      tc::tmem_ld32(ta + 32, v + 32);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) pre[c] = vlo ? v[c] : v[c] + v[kCols + c];
+      tc::tmem_ld32(ta + 32, v);
       tc::tmem_wait_ld();
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::bar_arrive(&bars->acc_empty[t & 1]);
-      // columns: [R part hi/lo][re/im][system]; keep hi*hi, hi*lo, lo*hi
 #pragma unroll
       for (int c = 0; c < kCols; ++c) {
-        double pre = (double)v[c], pim = (double)v[kCols + c];
-        if (!vlo) {
-          pre += (double)v[2 * kCols + c];
-          pim += (double)v[3 * kCols + c];
-        }
+        const double dre = (double)pre[c], dim = (double)(vlo ? v[c] : v[c] + v[kCols + c]);
         if (!vim) {
-          gre[c] += pre;
-          gim[c] += pim;
+          gre[c] += dre;
+          gim[c] += dim;
         } else {
-          gre[c] += pim;
-          gim[c] -= pre;
+          gre[c] += dim;
+          gim[c] -= dre;
         }
       }
     }
     // the four A parts of each step meet in shared memory (the raw ring is idle by now:
-    // every stage was consumed before the last accumulator completed)
+    // every stage was consumed before the last accumulator completed); [q][re/im][c][step]
     double *comb = reinterpret_cast<double *>(raw);
 #pragma unroll
     for (int c = 0; c < kCols; ++c) {
-      comb[((q * 32 + lane) * 2) * kCols + c] = gre[c];
-      comb[((q * 32 + lane) * 2 + 1) * kCols + c] = gim[c];
+      comb[((q * 2 + 0) * kCols + c) * 32 + lane] = gre[c];
+      comb[((q * 2 + 1) * kCols + c) * 32 + lane] = gim[c];
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const int te = threadIdx.x - 128;         // 0..127
     for (int e = te; e < kSteps * kCols; e += 128) {
-      const int sq = e / kCols, c = e % kCols;
+      const int sq = e & 31, c = e >> 5;
       if (sq < len_t && c < nr_t) {
         double re = 0.0, im = 0.0;
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) {
-          re += comb[((qq * 32 + sq) * 2) * kCols + c];
-          im += comb[((qq * 32 + sq) * 2 + 1) * kCols + c];
+          re += comb[((qq * 2 + 0) * kCols + c) * 32 + sq];
+          im += comb[((qq * 2 + 1) * kCols + c) * 32 + sq];
         }
         Hpart[((int64_t)blockIdx.x * kSeedBlock + mt * kSteps + sq) * kLdG + rcol0 + c] = make_double2(re, im);
       }
     }
   } else {
-    // ---------------- converters (warps 2, 3, 8, 9) ----------------
-    const int cw = warp < 4 ? warp - 2 : warp - 6;      // 0..3
-    const int tid = cw * 32 + lane;                      // 0..127
-    for (int g = 0; g < nst; ++g) {
-      const int r = g % kRawStages, s = g % kOpStages;
-      if (!tc::bar_wait(&bars->raw_full[r], (g / kRawStages) & 1, err)) break;
-      if (g >= kOpStages && !tc::bar_wait(&bars->op_empty[s], ((g / kOpStages) + 1) & 1, err)) break;
-      const unsigned char *src = raw + r * kRawStage;
-      unsigned char *opa = ops + s * kOpStage, *opb = opa + kOpA;
-      // units (column slot, K group of 4 elements): 16 K groups per slot, 48 slots
-#pragma unroll 2
-      for (int u = tid; u < (kSteps + kCols) * kKGroups; u += 128) {
-        const int slot = u >> 4, kg = u & 15;
-        const bool isv = slot < kSteps;
-        const int col = isv ? slot : slot - kSteps;
-        if (col >= (isv ? len_t : nr_t)) continue;
-        const float4 a = *reinterpret_cast<const float4 *>(src + slot * kSlot + kg * 32);
-        const float4 b = *reinterpret_cast<const float4 *>(src + slot * kSlot + kg * 32 + 16);
-        const float re[4] = {a.x, a.z, b.x, b.z}, im[4] = {a.y, a.w, b.y, b.w};
-        float rh[4], rl[4], ih[4], il[4];
+    // ---------------- converters (warps 2, 3, 8..11) ----------------
+    // unit = one 16-byte piece (2 complex elements) of one column slot in the
+    // stage's quarter: 16 lanes read 256 contiguous bytes of a slot (conflict-free)
+    // and write 8 bytes into each of its 4 rows, at 8 consecutive K groups
+    // (LBO = 16 mod 128: conflict-free)
+    const int cw = warp < 4 ? warp - 2 : warp - 6;      // 0..5
+    const int tid = cw * 32 + lane;                      // 0..191
+    const int nunits = ns * (kOpChunk / 2);
+    // The same units every stage: source offset in a raw stage's quarter and the four
+    // destination offsets (hi re, hi im, lo re, lo im rows) in an operand stage, once.
+    uint32_t roff[kConvPerThread], d0[kConvPerThread], d1[kConvPerThread], d2[kConvPerThread],
+        d3[kConvPerThread];
+    bool valid[kConvPerThread];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          rh[k] = tc::tf32_round(re[k]);
-          rl[k] = tc::tf32_round(re[k] - rh[k]);
-          ih[k] = tc::tf32_round(im[k]);
-          il[k] = tc::tf32_round(im[k] - ih[k]);
+    for (int i = 0; i < kConvPerThread; ++i) {
+      const int u = tid + kConvThreads * i;
+      valid[i] = u < nunits;
+      const int slot = valid[i] ? u >> 4 : 0, ch = u & 15;
+      const int kg = ch >> 1;
+      const uint32_t koff = (uint32_t)((ch & 1) * 8);   // second pair of the K group
+      roff[i] = (uint32_t)(slot * kSlot + ch * 16);
+      if (slot < len_t) {   // V column: rows col, 32 + col, 64 + col, 96 + col of A
+        d0[i] = tc::op_off(slot, kg, kLboA) + koff;
+        d1[i] = tc::op_off(kSteps + slot, kg, kLboA) + koff;
+        d2[i] = tc::op_off(2 * kSteps + slot, kg, kLboA) + koff;
+        d3[i] = tc::op_off(3 * kSteps + slot, kg, kLboA) + koff;
+      } else {              // R_0 column c: rows c (hi re), 32 + c (hi im), 16 + c (lo re), 48 + c (lo im) of B
+        const int c = slot - len_t;
+        d0[i] = kOpA + tc::op_off(c, kg, kLboB) + koff;
+        d1[i] = kOpA + tc::op_off(2 * kCols + c, kg, kLboB) + koff;
+        d2[i] = kOpA + tc::op_off(kCols + c, kg, kLboB) + koff;
+        d3[i] = kOpA + tc::op_off(3 * kCols + c, kg, kLboB) + koff;
+      }
+    }
+    for (int j = 0; j < nop; ++j) {
+      const int g = j / kOpPerRaw, part = j % kOpPerRaw;
+      const int r = g % nraw, s = j % kOpStages;
+      if (part == 0 && !tc::bar_wait(&bars->raw_full[r], (g / nraw) & 1, err)) break;
+      if (j >= kOpStages && !tc::bar_wait(&bars->op_empty[s], ((j / kOpStages) + 1) & 1, err)) break;
+      const unsigned char *src = raw + r * raw_stage + part * (kOpChunk * 8);
+      unsigned char *op = ops + s * kOpStage;
+      float4 in[kConvPerThread];
+#pragma unroll
+      for (int i = 0; i < kConvPerThread; ++i)
+        if (valid[i]) in[i] = *reinterpret_cast<const float4 *>(src + roff[i]);
+#pragma unroll
+      for (int i = 0; i < kConvPerThread; ++i) {
+        if (valid[i]) {
+          const float re0 = in[i].x, im0 = in[i].y, re1 = in[i].z, im1 = in[i].w;
+          const float rh0 = tc::tf32_hi(re0), rh1 = tc::tf32_hi(re1), ih0 = tc::tf32_hi(im0), ih1 = tc::tf32_hi(im1);
+          *reinterpret_cast<float2 *>(op + d0[i]) = make_float2(rh0, rh1);
+          *reinterpret_cast<float2 *>(op + d1[i]) = make_float2(ih0, ih1);
+          *reinterpret_cast<float2 *>(op + d2[i]) = make_float2(re0 - rh0, re1 - rh1);
+          *reinterpret_cast<float2 *>(op + d3[i]) = make_float2(im0 - ih0, im1 - ih1);
         }
-        unsigned char *base = isv ? opa : opb;
-        const int lbo = isv ? kLboA : kLboB;
-        const int stride = isv ? kSteps : kCols;     // rows per (hi/lo, re/im) block
-        *reinterpret_cast<float4 *>(base + tc::op_off(col, kg, lbo)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
-        *reinterpret_cast<float4 *>(base + tc::op_off(stride + col, kg, lbo)) =
-            make_float4(ih[0], ih[1], ih[2], ih[3]);
-        *reinterpret_cast<float4 *>(base + tc::op_off(2 * stride + col, kg, lbo)) =
-            make_float4(rl[0], rl[1], rl[2], rl[3]);
-        *reinterpret_cast<float4 *>(base + tc::op_off(3 * stride + col, kg, lbo)) =
-            make_float4(il[0], il[1], il[2], il[3]);
       }
       // generic-proxy writes become visible to the tensor cores (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
         tc::bar_arrive(&bars->op_full[s]);
-        tc::bar_arrive(&bars->raw_empty[r]);
+        if (part == kOpPerRaw - 1) tc::bar_arrive(&bars->raw_empty[r]);
       }
     }
   }
@@ -470,20 +507,29 @@ PfnEncodeTiled encode_fn() {
 }
 }  // namespace
 
-// A 2-d map over ncols FP32-complex columns of `len` elements (leading dimension ld
-// elements), boxes of 64 complex x 1 column.  False if the map cannot be made.
-bool tc_make_map(CUtensorMap *map, const void *base, int64_t len, int64_t ld, int64_t ncols) {
+// 2-d maps over ncols FP32-complex columns of `len` elements (leading dimension ld
+// elements), boxes of 128 complex x (16, 8, 4, 2, 1) columns.  A box taller than ncols
+// is left zeroed: the kernel never takes more columns than the block has.  False if a
+// needed map cannot be made.
+bool tc_make_maps(CUtensorMap maps[tc::kBoxes], const void *base, int64_t len, int64_t ld, int64_t ncols) {
   PfnEncodeTiled enc = encode_fn();
   if (!enc || !base || ncols < 1 || len < tc::kChunk || len % tc::kChunk || ld % 2 ||
       ((uintptr_t)base & 15) || (ld * 8) % 16)
     return false;
   const cuuint64_t dims[2] = {(cuuint64_t)(2 * len), (cuuint64_t)ncols};
   const cuuint64_t strides[1] = {(cuuint64_t)(ld * 8)};
-  const cuuint32_t box[2] = {(cuuint32_t)(2 * tc::kChunk), 1u};
   const cuuint32_t estr[2] = {1u, 1u};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  for (int h = 0; h < tc::kBoxes; ++h) {
+    memset(&maps[h], 0, sizeof(CUtensorMap));
+    const int w = 16 >> h;
+    if (w > ncols) continue;
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * tc::kChunk), (cuuint32_t)w};
+    if (enc(&maps[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 int tc_grid(int64_t len) {
@@ -499,19 +545,18 @@ int tc_grid(int64_t len) {
   return (int)(chunks < sms ? chunks : sms);
 }
 
-cudaError_t launch_blk_dots_tc(const CUtensorMap &vmap, const CUtensorMap &rmap, const SeedState *st, int len_host,
-                               int vcol_host, int nj, int64_t len, double2 *Hpart, int grid, int *err,
-                               cudaStream_t s) {
+cudaError_t launch_blk_dots_tc(const TcMaps &maps, const SeedState *st, int len_host, int vcol_host, int nj,
+                               int64_t len, double2 *Hpart, int grid, int *err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_blk_dots_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int ytiles = (kSeedBlock + tc::kSteps - 1) / tc::kSteps;
+  const int ytiles = (kSeedBlock + tc::kSteps - 1) / tc::kSteps;   // idle tiles leave at once
   const int ztiles = (nj + tc::kCols - 1) / tc::kCols;
   k_blk_dots_tc<<<dim3((unsigned)grid, (unsigned)ytiles, (unsigned)ztiles), tc::kThreads, tc::kSmemBytes, s>>>(
-      vmap, rmap, st, len_host, vcol_host, nj, len / tc::kChunk, Hpart, err);
+      maps, st, len_host, vcol_host, nj, len / tc::kChunk, Hpart, err);
   return cudaGetLastError();
 }
 
@@ -544,12 +589,12 @@ extern "C" seed_status seed_block_products(const void *V, int64_t ldv, int32_t k
   if (!V || !R || !G) return bad("NULL argument");
   if (k < 1 || k > kSeedBlock) return bad("k must be in [1, 128]");
   if (nr < 1 || nr > kMaxRhs - 1) return bad("nr must be in [1, 63]");
-  if (n < 64 || n % 64) return bad("n must be a positive multiple of 64");
+  if (n < 128 || n % 128) return bad("n must be a positive multiple of 128");
   if (ldv < n || ldr < n || ldv % 2 || ldr % 2) return bad("ldv and ldr must be even and >= n");
   if (((uintptr_t)V & 15) || ((uintptr_t)R & 15)) return bad("V and R must be 16-byte aligned");
   if (reps < 1 || reps > 100000) return bad("reps must be in [1, 100000]");
-  CUtensorMap vmap, rmap;
-  if (!tc_make_map(&vmap, V, n, ldv, k) || !tc_make_map(&rmap, R, n, ldr, nr)) {
+  TcMaps maps;
+  if (!tc_make_maps(maps.v, V, n, ldv, k) || !tc_make_maps(maps.r, R, n, ldr, nr)) {
     set_last_error_message("seed_block_products: the TMA maps could not be made (no driver entry point?)");
     return SEED_ECUDA;
   }
@@ -572,10 +617,10 @@ extern "C" seed_status seed_block_products(const void *V, int64_t ldv, int32_t k
       cudaEventCreate(&e1) != cudaSuccess)
     goto cuda_fail;
   // one untimed launch, then reps timed launches of the product kernel alone
-  if (launch_blk_dots_tc(vmap, rmap, nullptr, k, 0, nr, n, Hpart, grid, err, s) != cudaSuccess) goto cuda_fail;
+  if (launch_blk_dots_tc(maps, nullptr, k, 0, nr, n, Hpart, grid, err, s) != cudaSuccess) goto cuda_fail;
   cudaEventRecord(e0, s);
   for (int r = 0; r < reps; ++r)
-    if (launch_blk_dots_tc(vmap, rmap, nullptr, k, 0, nr, n, Hpart, grid, err, s) != cudaSuccess) goto cuda_fail;
+    if (launch_blk_dots_tc(maps, nullptr, k, 0, nr, n, Hpart, grid, err, s) != cudaSuccess) goto cuda_fail;
   cudaEventRecord(e1, s);
   k_tc_reduce<<<(k * nr + 127) / 128, 128, 0, s>>>(Hpart, grid, k, nr, Gd);
   if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess ||
