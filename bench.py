@@ -511,6 +511,24 @@ def dslash_roofline(S, ctx, vol, mixed, dims, ncols_total):
             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
 
+def flush_roofline(S, torch, dev, n, steps, nsys):
+    """The seeding products of one block flush in mixed precision, G = V_blk^H R_0
+    (steps x nsys, FP32 complex vectors of length n) on the tensor cores
+    (k_blk_dots_tc through seed_block_products): algorithmic bytes = every
+    column read once, against the measured HBM copy peak."""
+    g = torch.Generator(device=dev).manual_seed(0)
+    V = torch.randn((steps, n), dtype=torch.complex64, device=dev, generator=g).t()
+    R = torch.randn((nsys, n), dtype=torch.complex64, device=dev, generator=g).t()
+    _, ms = S.seed_block_products(V, R, reps=50)
+    b = (steps + nsys) * n * 8
+    peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
+    del V, R
+    return {"bound": "hbm", "kernel": "k_blk_dots_tc (tcgen05 kind::tf32, 3xTF32, TMA-staged)",
+            "shape": "%d steps x %d systems, n = %d" % (steps, nsys, n), "ms_per_launch": round(ms, 5),
+            "bytes_per_launch": b, "achieved": round(b / (ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(b / (ms * 1e-3) / 1e9 / peak, 4)}
+
+
 def run_secondary(S, I, torch, dev, flush, steps, warmup):
     """The 16^3 x 32 lattice with 12 Z4 noise sources: mixed precision against
     plain FP64 on the same workload, each system's FP64 true residual."""
@@ -529,6 +547,7 @@ def run_secondary(S, I, torch, dev, flush, steps, warmup):
              "phase_ms": {"seed_solve_first": round(st["ms_seed"], 3), "seed_solve_rest": round(st["ms_rest"], 3)}}
         if mixed:
             o["roofline"] = dslash_roofline(S, p["ctx"], p["vol"], True, dims, WL["nrhs"] - 1)
+            o["flush_roofline"] = flush_roofline(S, torch, dev, p["n"], steps=25, nsys=WL["nrhs"] - 1)
         out["mixed" if mixed else "fp64"] = o
         S.seed_destroy(p["ctx"])
         del p

@@ -122,6 +122,8 @@ def test_bench_json_contract_keys():
     """The JSON line's reference-arm fields are complete (the line is built from a tiny fake timing)."""
     sys.path.insert(0, ROOT)
     import bench
-    obj = bench.cpu_baseline_obj(1.234, dict(seed_iters=10, cg_iters=[3, 4]))
-    assert obj["kind"] == "oracle" and obj["unit"] == "ms" and obj["cores"] >= 1
+    obj = bench.cpu_obj(1.234, dict(threads=4, seed_iters=10, cg_iters=[3, 4]))
+    assert obj["kind"] == "oracle" and obj["unit"] == "ms" and obj["cores"] == 4
+    assert "not a sample" in obj["sample"] and "4 threads" in obj["sample"]
+    assert obj["host"]["logical_cores"] >= 1
     assert json.loads(json.dumps(obj))["value"] == 1234.0
