@@ -300,24 +300,110 @@ SEED_DEV void seed_leave(const SeedBufs<T> &b, const LocalSeed &L, const T *f, i
   }
 }
 
+// FP64 Wilson run: five warps per block.  Warps 0-3 are the tile warps of the
+// operator (one direction each, as everywhere); warp 4 is a scalar warp.  After
+// each grid barrier the stencil of the next phase does not depend on the
+// scalars the barrier made available (D f and D^H t need only f and t; v_i =
+// f / beta_{i-1} is applied to D f in the epilogue, D being linear), so the
+// scalar warp reduces the tiles' partials and runs the recurrence's scalar
+// code while the tile warps compute the stencil of the block's first tile;
+// one CTA barrier joins them before the epilogue.  On the 8^4 lattice this
+// hides the two scalar phases of a step (about 5 of its 29.5 us) behind the
+// stencils.  Same arithmetic and summation order as before.
+constexpr int PTW = PT + 32;
+
+// named barrier of the four tile warps
+SEED_DEV void tile_warps_sync() { asm volatile("bar.sync 1, %0;" ::"n"(PT) : "memory"); }
+
+// wilson_tile for the tile warps alone (ends with their named barrier)
+template <int S>
+SEED_DEV void wilson_tile4(const WilsonOp &op, const double2 *in, int64_t s0, double (*sacc)[24][kWilsonSites + 1]) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const int64_t s = s0 + lane;
+  double2 acc[12];
+  if (s < op.sites) {
+    switch (mu) {
+      case 0: site_mu<0, S, false>(op, in, s, acc); break;
+      case 1: site_mu<1, S, false>(op, in, s, acc); break;
+      case 2: site_mu<2, S, false>(op, in, s, acc); break;
+      default: site_mu<3, S, false>(op, in, s, acc); break;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = c2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    sacc[mu][2 * k][lane] = acc[k].x;
+    sacc[mu][2 * k + 1][lane] = acc[k].y;
+  }
+  tile_warps_sync();
+}
+
+// One warp: the sums over b < nb of the pairs (partial[2b], partial[2b + 1]) in
+// warp_sum_partials' order, both in one pass over the partials.
+SEED_DEV double2 warp_sum_partial_pairs(const double *partial, int nb) {
+  const int lane = threadIdx.x & 31;
+  double sx[8], sy[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) sx[u] = sy[u] = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < nb ? __ldcg(reinterpret_cast<const double2 *>(partial) + b) : c2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      sx[u] += v[u].x;
+      sy[u] += v[u].y;
+    }
+  }
+  const double tx = ((sx[0] + sx[1]) + (sx[2] + sx[3])) + ((sx[4] + sx[5]) + (sx[6] + sx[7]));
+  const double ty = ((sy[0] + sy[1]) + (sy[2] + sy[3])) + ((sy[4] + sy[5]) + (sy[6] + sy[7]));
+  return c2(warp_sum(tx), warp_sum(ty));
+}
+
 // tpart: 3 x tiles doubles (phase-1 pairs, then the phase-2 norms)
-__global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, WilsonOp op, double2 *tbuf,
-                                                         GridSync g, double *bpart, double *tpart, int i_stop) {
+__global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, WilsonOp op, double2 *tbuf,
+                                                          GridSync g, double *bpart, double *tpart, int i_stop) {
   __shared__ double sacc[4][24][kWilsonSites + 1];
-  __shared__ double s_red[2 * (PT / 32)];
+  __shared__ double s_red[2 * (PTW / 32)];
   __shared__ LocalSeed L;
   (void)bpart;
   const int64_t sites = op.sites;
   const int tiles = (int)((sites + kWilsonSites - 1) / kWilsonSites);
   const double kappa = op.kappa;
   double *part1 = tpart, *part2 = tpart + 2 * (int64_t)tiles;
+  const int warp = threadIdx.x >> 5;
+  const bool tw = warp < 4;            // tile warp; warp 4 is the scalar warp
   unsigned epoch = 0;
   local_load(b, L);
   const SeedBufs<double2> bl = local_bufs(b, L);
   Owners own;
   if (!register_owner(g, epoch, own)) return;
   double2 *const X = reinterpret_cast<double2 *>(b.call->X);
+  const int first_tile = own.rank >= 0 && own.rank < tiles ? own.rank : -1;
+  bool pending_beta = false;           // the end of the previous step (beta_{i-1}) is still to run
   for (;;) {
+    // ---- phase 1 of step i, overlapped with the end of step i-1 ----
+    {
+      // the stencil D f of the step that may follow (discarded if the end of step i-1 stops the run)
+      const int ip = L.st.i + (pending_beta ? 1 : 0);
+      const bool go = L.st.active && ip < i_stop && (b.Wb == nullptr || ip - L.st.blk0 < kSeedBlock);
+      __syncthreads();                 // everyone has read L.st before the scalar warp updates it
+      if (tw && go && first_tile >= 0) wilson_tile4<+1>(op, b.f, (int64_t)first_tile * kWilsonSites, sacc);
+      if (!tw && pending_beta) {
+        const double ss = warp_sum_partials(part2, tiles, 1, 0);
+        if (threadIdx.x == PT) {
+          if (bl.Wb != nullptr) L.st.w_last = L.st.i;
+          seed_finish<double2, false>(bl, ss);
+        }
+      }
+      __syncthreads();
+      pending_beta = false;
+    }
     const int i = L.st.i;
     if (!L.st.active || i >= i_stop) break;
     if (block_full(b, L, i)) break;
@@ -325,86 +411,98 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson(SeedBufs<double2> b, Wil
     const double bp = (i > 1) ? L.st.beta_prev : 0.0;
     double2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
     const double2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
-    // phase 1: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
-    if (own.rank >= 0) {
-      for (int tile = own.rank; tile < tiles; tile += own.count) {
+    // phase 1 epilogue: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
+    if (first_tile >= 0) {
+      for (int tile = first_tile; tile < tiles; tile += own.count) {
         const int64_t s0 = (int64_t)tile * kWilsonSites;
-        wilson_tile<+1>(op, b.f, s0, sacc);
+        if (tile != first_tile && tw) wilson_tile4<+1>(op, b.f, s0, sacc);
         double ptt = 0.0, pvm = 0.0;
+        if (tw) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
-          const int64_t ss = s0 + sl;
-          if (ss < sites) {
-            const double2 sum = tile_sum(sacc, cc, sl);
-            const int64_t e = 12 * ss + cc;
-            const double2 fe = b.f[e];
-            const double2 v = c2(inv_b * fe.x, inv_b * fe.y);
-            vi[e] = v;
-            const double2 t = c2(fma(-kappa, inv_b * sum.x, v.x), fma(-kappa, inv_b * sum.y, v.y));
-            tbuf[e] = t;
-            ptt = fma(t.y, t.y, fma(t.x, t.x, ptt));
-            if (i > 1) {
-              const double2 m = vm[e];
-              pvm = fma(v.y, m.y, fma(v.x, m.x, pvm));
+          for (int k = 0; k < 3; ++k) {
+            const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
+            const int64_t ss = s0 + sl;
+            if (ss < sites) {
+              const double2 sum = tile_sum(sacc, cc, sl);
+              const int64_t e = 12 * ss + cc;
+              const double2 fe = b.f[e];
+              const double2 v = c2(inv_b * fe.x, inv_b * fe.y);
+              vi[e] = v;
+              const double2 t = c2(fma(-kappa, inv_b * sum.x, v.x), fma(-kappa, inv_b * sum.y, v.y));
+              tbuf[e] = t;
+              ptt = fma(t.y, t.y, fma(t.x, t.x, ptt));
+              if (i > 1) {
+                const double2 m = vm[e];
+                pvm = fma(v.y, m.y, fma(v.x, m.x, pvm));
+              }
             }
           }
         }
         double vv[2] = {ptt, pvm};
-        block_sum<2, PT>(vv, s_red);   // ends with a CTA barrier: sacc is free again
+        block_sum<2, PTW>(vv, s_red);   // ends with a CTA barrier: sacc is free again
         if (threadIdx.x == 0) {
           part1[2 * tile] = vv[0];
           part1[2 * tile + 1] = vv[1];
         }
       }
     }
-    if (!seed_alpha_step<double2>(bl, part1, tiles, 2, i > 1, i, L, g, epoch)) return;
+    if (!grid_sync(g, epoch)) return;
+    // ---- phase 2: u = D^H t overlapped with alpha_i and the LU update's scalars ----
+    if (tw && first_tile >= 0) wilson_tile4<-1>(op, tbuf, (int64_t)first_tile * kWilsonSites, sacc);
+    if (!tw) {
+      const double2 s2 = warp_sum_partial_pairs(part1, tiles);
+      const double a = i > 1 ? s2.x - L.st.beta_prev * s2.y : s2.x;
+      if (threadIdx.x == PT) seed_step_scalars<double2, false>(bl, i, a, nullptr);
+    }
+    __syncthreads();
     if (!L.st.active) break;   // delta_i <= 0
-    // phase 2: u = D^H t, f, w_i, x^1, w_i into Wb, partials of ||f||^2
     const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
     double2 *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
-    if (own.rank >= 0) {
-      for (int tile = own.rank; tile < tiles; tile += own.count) {
+    if (first_tile >= 0) {
+      for (int tile = first_tile; tile < tiles; tile += own.count) {
         const int64_t s0 = (int64_t)tile * kWilsonSites;
-        wilson_tile<-1>(op, tbuf, s0, sacc);
+        if (tile != first_tile && tw) wilson_tile4<-1>(op, tbuf, s0, sacc);
         double pff = 0.0;
+        if (tw) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
-          const int64_t ss = s0 + sl;
-          if (ss < sites) {
-            const double2 sum = tile_sum(sacc, cc, sl);
-            const int64_t e = 12 * ss + cc;
-            const double2 tv = tbuf[e], v = vi[e];
-            double2 f = c2(fma(-kappa, sum.x, tv.x), fma(-kappa, sum.y, tv.y));
-            if (i > 1) {
-              const double2 m = vm[e];
-              f = c2(fma(-bp, m.x, f.x), fma(-bp, m.y, f.y));
+          for (int k = 0; k < 3; ++k) {
+            const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
+            const int64_t ss = s0 + sl;
+            if (ss < sites) {
+              const double2 sum = tile_sum(sacc, cc, sl);
+              const int64_t e = 12 * ss + cc;
+              const double2 tv = tbuf[e], v = vi[e];
+              double2 f = c2(fma(-kappa, sum.x, tv.x), fma(-kappa, sum.y, tv.y));
+              if (i > 1) {
+                const double2 m = vm[e];
+                f = c2(fma(-bp, m.x, f.x), fma(-bp, m.y, f.y));
+              }
+              f = c2(fma(-a, v.x, f.x), fma(-a, v.y, f.y));
+              double2 w;
+              if (i > 1) {
+                const double2 wp = b.w[e];
+                w = c2(inv_d * fma(-bp, wp.x, v.x), inv_d * fma(-bp, wp.y, v.y));
+              } else {
+                w = c2(inv_d * v.x, inv_d * v.y);
+              }
+              b.f[e] = f;
+              b.w[e] = w;
+              if (wcol != nullptr) wcol[e] = w;
+              const double2 x = X[e];
+              X[e] = c2(fma(zeta, w.x, x.x), fma(zeta, w.y, x.y));
+              pff = fma(f.y, f.y, fma(f.x, f.x, pff));
             }
-            f = c2(fma(-a, v.x, f.x), fma(-a, v.y, f.y));
-            double2 w;
-            if (i > 1) {
-              const double2 wp = b.w[e];
-              w = c2(inv_d * fma(-bp, wp.x, v.x), inv_d * fma(-bp, wp.y, v.y));
-            } else {
-              w = c2(inv_d * v.x, inv_d * v.y);
-            }
-            b.f[e] = f;
-            b.w[e] = w;
-            if (wcol != nullptr) wcol[e] = w;
-            const double2 x = X[e];
-            X[e] = c2(fma(zeta, w.x, x.x), fma(zeta, w.y, x.y));
-            pff = fma(f.y, f.y, fma(f.x, f.x, pff));
           }
         }
         double vv[1] = {pff};
-        block_sum<1, PT>(vv, s_red);
+        block_sum<1, PTW>(vv, s_red);
         if (threadIdx.x == 0) part2[tile] = vv[0];
       }
     }
-    if (!seed_beta_step<double2>(bl, part2, tiles, i, L, g, epoch)) return;
+    if (!grid_sync(g, epoch)) return;
+    pending_beta = true;               // beta_i and the stopping test run with the next stencil
   }
-  seed_leave<double2>(b, L, b.f, i_stop);
+  if (tw) seed_leave<double2>(b, L, b.f, i_stop);
   local_store(b, L);
 }
 
@@ -921,7 +1019,8 @@ int persistent_grid(int kind, int sm_count, bool cg, bool fp32) {
   if (cg) k = kind == 0 ? (const void *)k_cg_run_csr : (const void *)k_cg_run_wilson;
   else if (fp32) k = kind == 0 ? (const void *)k_seed_run_csr<float> : (const void *)k_seed_run_wilson32;
   else k = kind == 0 ? (const void *)k_seed_run_csr<double> : (const void *)k_seed_run_wilson;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PT, 0) != cudaSuccess) {
+  const int threads = (!cg && !fp32 && kind == 1) ? PTW : PT;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -937,7 +1036,7 @@ cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &o
   SeedBufs<double2> bb = b;
   WilsonOp o = op;
   void *args[] = {&bb, &o, &tbuf, &g, &bpart, &tpart, &i_stop};
-  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson, dim3(grid), dim3(PT), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson, dim3(grid), dim3(PTW), args, 0, s);
 }
 cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g, double *bpart,
                                 int i_stop, int grid, cudaStream_t s) {
