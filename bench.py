@@ -217,18 +217,28 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle on the whole workload
 # ---------------------------------------------------------------------------
+ARM_PARTS = {("0x41", "0xd4f"): "Arm Neoverse-V2", ("0x41", "0xd40"): "Arm Neoverse-V1",
+             ("0x41", "0xd0c"): "Arm Neoverse-N1"}
+
+
 def host_cpu():
-    """(logical cores, CPU model) of this host."""
-    model = None
+    """(logical cores, CPU model) of this host (x86 'model name'; Arm implementer and part)."""
+    model, impl, part = None, None, None
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
                 k = line.split(":")[0].strip().lower()
-                if k in ("model name", "cpu model", "hardware"):
-                    model = line.split(":", 1)[1].strip()
-                    break
+                val = line.split(":", 1)[1].strip() if ":" in line else ""
+                if k in ("model name", "cpu model") and model is None:
+                    model = val
+                elif k == "cpu implementer" and impl is None:
+                    impl = val
+                elif k == "cpu part" and part is None:
+                    part = val
     except OSError:
         pass
+    if model is None and impl is not None:
+        model = ARM_PARTS.get((impl.lower(), (part or "").lower()), "Arm implementer %s part %s" % (impl, part))
     if model is None:
         import platform
         model = platform.machine()
@@ -556,6 +566,54 @@ def run_secondary(S, I, torch, dev, flush, steps, warmup):
     return out
 
 
+LAP = dict(side=64, nrhs=4, m_max=4096, reorth_freq=1, tol_seed=1e-12, tol_rest=1e-8)
+
+
+def run_laplacian_line(S, I, torch, dev, flush, steps, warmup, with_oracle=True):
+    """The 64x64 Dirichlet Laplacian (n = 4096, real FP64 CSR), 4 Gaussian right-hand
+    sides from seed 0: seed solve of system 1 to 1e-12 with full reorthogonalization,
+    CG on the other three to 1e-8; GPU time per all-RHS solve (CUDA events), and the
+    oracle on the same solve (one thread and all host cores)."""
+    rp, ci, v = I.laplacian_2d_csr(LAP["side"], LAP["side"])
+    n = LAP["side"] ** 2
+    Bh = I.gaussian_rhs(n, LAP["nrhs"], seed=0)
+    prm = S.seed_params_default(m_max=LAP["m_max"], reorth_freq=LAP["reorth_freq"], tol_seed=LAP["tol_seed"],
+                                tol_rest=LAP["tol_rest"])
+    ctx = S.seed_create_csr(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(v).to(dev),
+                            prm)
+    B = torch.from_numpy(np.ascontiguousarray(Bh.T)).to(dev).t()
+    X = torch.empty((LAP["nrhs"], n), dtype=torch.float64, device=dev).t()
+    ms = []
+    for k in range(warmup + steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        i1 = S.seed_solve_first(ctx, B, X)
+        i2 = S.seed_solve_rest(ctx, B, X)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    S.seed_destroy(ctx)
+    out = {"workload": "2-d 5-point Dirichlet Laplacian 64x64 (n = 4096, CSR FP64), 4 Gaussian RHS (seed 0); seed "
+                       "tol 1e-12 with reorthogonalization every step, CG tol 1e-8",
+           "ms": round(statistics.mean(ms), 3), "step_ms": [round(x, 3) for x in ms], "seed_steps": i1[0]["iters"],
+           "cg_iters": [i["iters"] for i in i2[1:]],
+           "converged": bool(i1[0]["converged"]) and all(i["converged"] for i in i2[1:])}
+    if with_oracle:
+        import oracle
+        op = oracle.Operator.csr(rp, ci, v)
+        for threads, key in ((1, "oracle_ms_1_thread"), (os.cpu_count() or 1, "oracle_ms_all_cores")):
+            used = oracle.set_threads(threads)
+            t0 = time.perf_counter()
+            oracle.seed_solve_all(op, Bh, m_max=LAP["m_max"], reorth_freq=LAP["reorth_freq"], tol_seed=LAP["tol_seed"],
+                                  tol_rest=LAP["tol_rest"])
+            out[key] = round((time.perf_counter() - t0) * 1e3, 1)
+            out[key.replace("ms", "threads")] = used
+        oracle.set_threads(1)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -670,9 +728,11 @@ def run_ours(args):
                "d2h_bytes_per_step": int(x_pin.numel() * 16), "step_ms": [round(x, 3) for x in e2e_ms]}
     S.seed_destroy(ctx)
 
-    secondary = None
+    secondary = lap = None
     if rank == 0 and world == 1 and default_wl and not args.no_secondary:
         secondary = run_secondary(S, I, torch, dev, flush, steps=min(args.steps, 3), warmup=1)
+        lap = run_laplacian_line(S, I, torch, dev, flush, steps=min(args.steps, 5), warmup=1,
+                                 with_oracle=not args.no_cpu_baseline)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and default_wl:
@@ -684,6 +744,8 @@ def run_ours(args):
             cfg["reliable_delta"] = args.reliable_delta or 0.01
         if secondary is not None:
             cfg["secondary"] = secondary
+        if lap is not None:
+            cfg["laplacian_64"] = lap
         out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
                "scaling": "weak", "vs_baseline": None,
