@@ -614,6 +614,37 @@ def run_laplacian_line(S, I, torch, dev, flush, steps, warmup, with_oracle=True)
     return out
 
 
+def matvec_hbm(S, I, torch, dev):
+    """The metric's second half, operator-apply bandwidth against the HBM peak,
+    where the apply is bound by memory: the CSR SpMV of the 2-d Laplacian
+    beyond L2 (2048^2 rows) and the FP32 Wilson D of the mixed path on
+    16^3 x 32 (11 columns, the CG launch).  CUDA events, library stream."""
+    peak = MEASURED_PEAKS.get("hbm_gbs", 6663.9)
+    out = {"peak": peak, "unit": "GB/s", "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    rp, ci, v = I.laplacian_2d_csr(2048, 2048)
+    ctx = S.seed_create_csr(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), torch.from_numpy(v).to(dev),
+                            S.seed_params_default(m_max=4))
+    ms = S.seed_time_operator(ctx, 0, 1, 200)
+    b = csr_bytes(2048 * 2048, int(ci.shape[0]))
+    out["csr_spmv_laplacian_2048sq"] = {"kernel": "k_csr_spmv (FP64)", "ms_per_launch": round(ms, 5), "bytes": b,
+                                        "achieved": round(b / (ms * 1e-3) / 1e9, 1),
+                                        "frac": round(b / (ms * 1e-3) / 1e9 / peak, 4)}
+    S.seed_destroy(ctx)
+    del rp, ci, v
+    dims = (16, 16, 16, 32)
+    U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
+    ctx = S.seed_create_wilson(dims, WL["kappa"], U, S.seed_params_default(m_max=4, precision=1))
+    ms = S.seed_time_operator(ctx, 4, WL["nrhs"] - 1, 200)
+    b = wilson_bytes(int(np.prod(dims)), WL["nrhs"] - 1, fp32=True)
+    out["wilson_d_fp32_16x16x16x32_11cols"] = {"kernel": "k_dslash32_site (FP32)", "ms_per_launch": round(ms, 5),
+                                               "bytes": b, "achieved": round(b / (ms * 1e-3) / 1e9, 1),
+                                               "frac": round(b / (ms * 1e-3) / 1e9 / peak, 4)}
+    S.seed_destroy(ctx)
+    del U
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -728,11 +759,22 @@ def run_ours(args):
                "d2h_bytes_per_step": int(x_pin.numel() * 16), "step_ms": [round(x, 3) for x in e2e_ms]}
     S.seed_destroy(ctx)
 
-    secondary = lap = None
+    secondary = lap = mv = bat = adj = None
     if rank == 0 and world == 1 and default_wl and not args.no_secondary:
         secondary = run_secondary(S, I, torch, dev, flush, steps=min(args.steps, 3), warmup=1)
         lap = run_laplacian_line(S, I, torch, dev, flush, steps=min(args.steps, 5), warmup=1,
                                  with_oracle=not args.no_cpu_baseline)
+        mv = matvec_hbm(S, I, torch, dev)
+        del flush
+        torch.cuda.empty_cache()
+        bat = batched_core(steps=2, warmup=1)
+        torch.cuda.empty_cache()
+        adj = adjoint_core((16, 16, 16, 16), False, steps=2, warmup=1)
+        adj_mixed = adjoint_core((16, 16, 16, 16), True, steps=2, warmup=1)
+        adj["mixed_precision_ms"] = adj_mixed["ms"]
+        adj["mixed_precision_grad_kappa"] = adj_mixed["grad_kappa"]
+        adj["speedup_mixed_over_fp64"] = round(adj["ms"] / adj_mixed["ms"], 3)
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and default_wl:
@@ -746,6 +788,10 @@ def run_ours(args):
             cfg["secondary"] = secondary
         if lap is not None:
             cfg["laplacian_64"] = lap
+        if bat is not None:
+            cfg["batched"] = bat
+        if adj is not None:
+            cfg["adjoint"] = adj
         out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
                "scaling": "weak", "vs_baseline": None,
@@ -759,7 +805,7 @@ def run_ours(args):
                                               "seed_solve_rest": round(st1["ms_rest"], 3)},
                        "wall_s_timed_region": round(t_wall1 - t_wall0, 3),
                        "step_ms": [round(x, 3) for x in step_ms], "converged": ok},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+               "roofline": roof, "matvec_hbm": mv, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                "clocks": clk.summary()}
         print(json.dumps(out), flush=True)
     if dist:
@@ -767,30 +813,27 @@ def run_ours(args):
     return 0
 
 
-def run_adjoint(args):
+def adjoint_core(dims, mixed, steps, warmup, reorth_freq=None):
     """Loss sum_j ||x_j - t_j||^2, x = A(kappa)^{-1} b through the autograd
     Function: forward (context, seed solve, CG) and backward (adjoint solves
-    seeded from the forward basis, or from zero for comparison, and the kappa
-    gradient), each timed with CUDA events."""
+    from zero, the default, and seeded from the forward basis for comparison,
+    and the kappa gradient), each timed with CUDA events.  Returns a dict."""
     import torch
     from paper_0810_0330_gb300 import inputs as I
     from paper_0810_0330_gb300.adjoint import WilsonSeedSolve
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    dims = tuple(int(x) for x in args.lattice.split(",")) if args.lattice else (16, 16, 16, 16)
+    dev = torch.device("cuda", torch.cuda.current_device())
     kappa, nrhs = 0.150, 8
     n = 12 * int(np.prod(dims))
     U = torch.from_numpy(I.random_su3_links(dims, WL["link_eps"], seed=WL["link_seed"])).to(dev)
     B = torch.from_numpy(np.ascontiguousarray(I.gaussian_rhs(n, nrhs, seed=0, complex_=True).T)).to(dev).t()
     T = torch.from_numpy(np.ascontiguousarray(I.gaussian_rhs(n, nrhs, seed=1, complex_=True).T)).to(dev).t()
-    freq = args.reorth_freq if args.reorth_freq is not None else 100
-    mixed = args.precision == "mixed"
+    freq = reorth_freq if reorth_freq is not None else 100
     prm = dict(m_max=1000, reorth_freq=freq, reorth_passes=2, tol_seed=1e-10, tol_rest=1e-8,
                precision=1 if mixed else 0)
     res = {}
     for seeded in ((False,) if mixed else (True, False)):
         fw, bw, its, fits = [], [], [], []
-        for step in range(args.warmup + args.steps):
+        for step in range(warmup + steps):
             k = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             torch.cuda.synchronize()
@@ -801,7 +844,7 @@ def run_adjoint(args):
             loss.backward()
             e[2].record()
             torch.cuda.synchronize()
-            if step >= args.warmup:
+            if step >= warmup:
                 fw.append(e[0].elapsed_time(e[1]))
                 bw.append(e[1].elapsed_time(e[2]))
                 its.append(sum(i["iters"] for i in X.grad_fn.info_backward))
@@ -811,24 +854,30 @@ def run_adjoint(args):
                            grad_kappa=float(k.grad))
     s_, u_ = res.get(True, res[False]), res[False]
     # the value is the library's default, the backward solves started from zero
-    out = {"metric": "adjoint forward+backward time (loss and gradients for b and kappa)",
-           "value": round(u_["fw"] + u_["bw"], 3), "unit": "ms", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "higher_is_better": False, "dtype": "f32+f64" if mixed else "f64",
-           "data": "synthetic",
-           "config": {"workload": "wilson-dirac %s kappa=%.3f A=D^H D, %d Gaussian b and t (seeds 0, 1), seed tol "
-                                  "1e-10 reorth/%d, CG tol 1e-8%s" % ("x".join(map(str, dims)), kappa, nrhs, freq,
-                                                                       ", mixed precision" if mixed else ""),
-                      "backward": "unseeded (default)",
-                      "forward_ms": round(u_["fw"], 3), "backward_seeded_ms": round(s_["bw"], 3),
-                      "backward_unseeded_ms": round(u_["bw"], 3),
-                      "backward_cg_iters_seeded": s_["bw_iters"], "backward_cg_iters_unseeded": u_["bw_iters"],
-                      "forward_iters": s_["fw_iters"], "grad_kappa": s_["grad_kappa"],
-                      "grad_kappa_unseeded": u_["grad_kappa"]}}
+    return {"ms": round(u_["fw"] + u_["bw"], 3),
+            "workload": "wilson-dirac %s kappa=%.3f A=D^H D, %d Gaussian b and t (seeds 0, 1), seed tol 1e-10 "
+                        "reorth/%d, CG tol 1e-8%s" % ("x".join(map(str, dims)), kappa, nrhs, freq,
+                                                      ", mixed precision" if mixed else ""),
+            "backward": "unseeded (default)", "forward_ms": round(u_["fw"], 3),
+            "backward_unseeded_ms": round(u_["bw"], 3), "backward_seeded_ms": round(s_["bw"], 3),
+            "backward_cg_iters_seeded": s_["bw_iters"], "backward_cg_iters_unseeded": u_["bw_iters"],
+            "forward_iters": s_["fw_iters"], "grad_kappa": u_["grad_kappa"],
+            "grad_kappa_seeded": s_["grad_kappa"], "steps": steps, "warmup": warmup}
+
+
+def run_adjoint(args):
+    import torch
+    torch.cuda.set_device(0)
+    dims = tuple(int(x) for x in args.lattice.split(",")) if args.lattice else (16, 16, 16, 16)
+    r = adjoint_core(dims, args.precision == "mixed", args.steps, args.warmup, args.reorth_freq)
+    out = {"metric": "adjoint forward+backward time (loss and gradients for b and kappa)", "value": r["ms"],
+           "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+           "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic", "config": r}
     print(json.dumps(out), flush=True)
     return 0
 
 
-def run_batched(args):
+def batched_core(steps, warmup):
     """All right-hand sides of 32 independent problems: one after another
     through seed_solve_first / seed_solve_rest, against seed_batch_solve (all
     problems concurrently), FP64 and mixed precision; CUDA events around each
@@ -836,8 +885,7 @@ def run_batched(args):
     import torch
     from paper_0810_0330_gb300 import binding as S
     from paper_0810_0330_gb300 import inputs as I
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     probs = I.batch_problems(count=32, n_min=1e4, n_max=1e6, seed=0)
     prm = dict(m_max=500, reorth_freq=100, reorth_passes=2, tol_seed=1e-10, tol_rest=1e-8)
     arrays = []
@@ -852,14 +900,14 @@ def run_batched(args):
 
     def timed(fn):
         ms = []
-        for step in range(args.warmup + args.steps):
+        for step in range(warmup + steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record()
             out = fn()
             e1.record()
             torch.cuda.synchronize()
-            if step >= args.warmup:
+            if step >= warmup:
                 ms.append(e0.elapsed_time(e1))
         return statistics.mean(ms), out
 
@@ -882,17 +930,23 @@ def run_batched(args):
     for c in ctx32:
         S.seed_destroy(c)
     ok = all(all(i["converged"] for i in inf[1:]) for inf in bat_info + mix_info)
-    out = {"metric": "batched uneven problems: all right-hand sides of 32 problems", "value": round(bat_ms, 3),
+    return {"ms": round(bat_ms, 3),
+            "workload": "32 shifted 2-d/3-d Dirichlet Laplacians (shift U(0.01,1)), n log-uniform 1e4..1e6, 4..16 "
+                        "Gaussian RHS each (seed 0); seed tol 1e-10 reorth/100, CG tol 1e-8",
+            "total_n": int(sum(a[0].shape[0] - 1 for a in arrays)), "total_rhs": int(sum(p["nrhs"] for p in probs)),
+            "sequential_ms": round(seq_ms, 3), "batched_fp64_ms": round(bat_ms, 3),
+            "batched_mixed_ms": round(mix_ms, 3), "speedup_batched_fp64": round(seq_ms / bat_ms, 3),
+            "speedup_batched_mixed": round(seq_ms / mix_ms, 3), "converged": ok,
+            "seed_steps": [i[0] for i in seq_its], "steps": steps, "warmup": warmup}
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = batched_core(args.steps, args.warmup)
+    out = {"metric": "batched uneven problems: all right-hand sides of 32 problems", "value": r["ms"],
            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
-           "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "32 shifted 2-d/3-d Dirichlet Laplacians (shift U(0.01,1)), n log-uniform "
-                                  "1e4..1e6, 4..16 Gaussian RHS each (seed 0); seed tol 1e-10 reorth/100, "
-                                  "CG tol 1e-8",
-                      "total_n": int(sum(a[0].shape[0] - 1 for a in arrays)),
-                      "total_rhs": int(sum(p["nrhs"] for p in probs)),
-                      "sequential_ms": round(seq_ms, 3), "batched_fp64_ms": round(bat_ms, 3),
-                      "batched_mixed_ms": round(mix_ms, 3), "converged": ok,
-                      "seed_steps": [i[0] for i in seq_its]}}
+           "dtype": "f64", "data": "synthetic", "config": r}
     print(json.dumps(out), flush=True)
     return 0
 
