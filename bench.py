@@ -500,7 +500,8 @@ def dslash_roofline(S, ctx, vol, mixed, dims, ncols_total):
                 "launch_shapes": {"cg_branches": shapes, "per_shape": shape_t},
                 "peak_note": "FP64 pipe from unit counts: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                 "peak_measured_probe": round(probe, 4), "frac_of_probe": round(achieved / probe, 4),
-                "probe": "seed_time_fma(SEED_F64): FMA chains over the whole GPU, this run"}
+                "probe": "seed_time_fma(SEED_F64): FMA chains over the whole GPU, this run",
+                "fp64_matrix_probe": {k: round(v, 4) for k, v in S.seed_time_fp64_paths().items()}}
     k_ms = S.seed_time_operator(ctx, 4, ncols_total, 200)
     b = wilson_bytes(vol, ncols_total, fp32=True)
     achieved = b / (k_ms * 1e-3) / 1e9

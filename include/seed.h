@@ -380,6 +380,20 @@ seed_status seed_time_operator(seed_ctx *ctx, int32_t op, int32_t ncols, int32_t
  * tflops, SEED_ECUDA without a usable device. */
 seed_status seed_time_fma(int32_t dtype, seed_stream stream, double *tflops, double *ms);
 
+/* Measurement helper (no counterpart in the paper): whether the FP64 matrix
+ * instructions (mma.sync f64, "DMMA") offer FP64 throughput beyond the FMA pipe
+ * that bounds the FP64 Wilson operator (Sec. 4) and the FP64 contractions of
+ * Sec. 3.  Fills out[7] (host):
+ *   out[0] FP64 FMA chains, TFLOP/s; out[1] DMMA m8n8k4, TFLOP/s;
+ *   out[2] DMMA m16n8k16, TFLOP/s (all warps of a full grid in one role);
+ *   out[3] t_mix / (t_fma + t_mma): the launch with half the warps on FMA
+ *     chains and half on m8n8k4 against the two halves launched alone --
+ *     about 0.5 if the two run on separate units, about 1 if they share one;
+ *   out[4..6] t_fma, t_mma, t_mix in ms (fastest of five after a warm-up).
+ * Allocates no device memory; synchronises `stream`.  SEED_EINVAL for a NULL
+ * out, SEED_ECUDA without a usable device. */
+seed_status seed_time_fp64_paths(seed_stream stream, double *out);
+
 /* Validation and measurement helper (no counterpart in the paper as an entry
  * point): the products of the mixed-precision seeding, G = V^H R (Sec. 3: each
  * Lanczos vector projected onto every other right-hand side), computed the way

@@ -34,7 +34,7 @@ EXPORTS = ["seed_abi_version", "seed_params_default", "seed_create_csr", "seed_c
            "seed_get_tridiag", "seed_get_basis", "seed_get_stats", "seed_time_operator", "seed_last_error",
            "seed_destroy", "seed_wilson_apply_noalloc", "seed_solve_cg", "seed_grad_kappa", "seed_solve_related",
            "seed_batch_solve", "seed_solve_multiple", "seed_inject_alloc_failure", "seed_check_barrier_timeout",
-           "seed_time_fma", "seed_block_products"]
+           "seed_time_fma", "seed_block_products", "seed_time_fp64_paths"]
 
 
 class SeedError(RuntimeError):
@@ -117,6 +117,7 @@ def lib():
             L.seed_check_barrier_timeout.argtypes = [P, C.POINTER(I32), C.POINTER(C.c_double)]
             L.seed_time_fma.argtypes = [I32, P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.seed_block_products.argtypes = [P, I64, I32, P, I64, I32, I64, P, I32, C.POINTER(C.c_double), P]
+            L.seed_time_fp64_paths.argtypes = [P, C.POINTER(C.c_double)]
             L.seed_last_error.argtypes = [P]
             L.seed_last_error.restype = C.c_char_p
             L.seed_destroy.argtypes = [P]
@@ -402,6 +403,16 @@ def seed_time_fma(dtype: int = 0, stream=None) -> dict:
     tf, ms = C.c_double(), C.c_double()
     _check(lib().seed_time_fma(int(dtype), _stream(stream), C.byref(tf), C.byref(ms)), "seed_time_fma")
     return {"tflops": tf.value, "ms": ms.value}
+
+
+def seed_time_fp64_paths(stream=None) -> dict:
+    """FP64 FMA chains against the FP64 matrix instructions (see include/seed.h):
+    rates in TFLOP/s, and the mixed launch's time over the two halves' sum
+    (~0.5: separate units, ~1: one shared unit)."""
+    out = (C.c_double * 7)()
+    _check(lib().seed_time_fp64_paths(_stream(stream), out), "seed_time_fp64_paths")
+    return {"fma_tflops": out[0], "dmma_m8n8k4_tflops": out[1], "dmma_m16n8k16_tflops": out[2],
+            "mix_over_sum": out[3], "ms_fma_half": out[4], "ms_dmma_half": out[5], "ms_mix": out[6]}
 
 
 def seed_block_products(V: torch.Tensor, R: torch.Tensor, reps: int = 1, stream=None):
