@@ -95,6 +95,9 @@ def parse():
     ap.add_argument("--once", action="store_true",
                     help="run the workload's step once and print its phase times, no bench line "
                          "(for launch-list captures)")
+    ap.add_argument("--laplacian-once", action="store_true",
+                    help="run the 64x64 Laplacian all-RHS solve once and print its phase times (for "
+                         "launch-list captures)")
     ap.add_argument("--dims", default=None, help="lattice for --kernel-only, e.g. 16,16,16,16")
     ap.add_argument("--ncols", type=int, default=None, help="columns for --kernel-only")
     ap.add_argument("--reps", type=int, default=20, help="timed launches for --kernel-only")
@@ -595,11 +598,13 @@ def run_laplacian_line(S, I, torch, dev, flush, steps, warmup, with_oracle=True)
         torch.cuda.synchronize()
         if k >= warmup:
             ms.append(e0.elapsed_time(e1))
+    st = S.seed_get_stats(ctx)
     S.seed_destroy(ctx)
     out = {"workload": "2-d 5-point Dirichlet Laplacian 64x64 (n = 4096, CSR FP64), 4 Gaussian RHS (seed 0); seed "
                        "tol 1e-12 with reorthogonalization every step, CG tol 1e-8",
            "ms": round(statistics.mean(ms), 3), "step_ms": [round(x, 3) for x in ms], "seed_steps": i1[0]["iters"],
            "cg_iters": [i["iters"] for i in i2[1:]],
+           "ms_seed": round(st["ms_seed"], 3), "ms_rest": round(st["ms_rest"], 3),
            "converged": bool(i1[0]["converged"]) and all(i["converged"] for i in i2[1:])}
     if with_oracle:
         import oracle
@@ -669,6 +674,13 @@ def run_ours(args):
         print(json.dumps({"kernel": "k_csr_spmv", "n": args.csr_side ** 2, "nnz": int(ci.shape[0]), "ms": ms,
                           "bytes": b, "gbs": b / (ms * 1e-3) / 1e9}), flush=True)
         S.seed_destroy(ctx)
+        return 0
+    if args.laplacian_once:
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        r = run_laplacian_line(S, I, torch, dev, flush, 1, 0, with_oracle=False)
+        print(json.dumps({"laplacian_once": r["workload"], "ms": r["ms"], "ms_seed": r["ms_seed"],
+                          "ms_rest": r["ms_rest"], "seed_steps": r["seed_steps"], "cg_iters": r["cg_iters"]}),
+              flush=True)
         return 0
     dims, kappa, nrhs = WL["dims"], WL["kappa"], WL["nrhs"]
     if args.kernel_only and args.dims:

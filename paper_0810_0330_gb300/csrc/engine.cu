@@ -100,6 +100,9 @@ struct seed_ctx {
   int32_t *h_gerr = nullptr;           // pinned copy of the error flag
   void *f2 = nullptr;                  // second Lanczos-vector buffer (CSR persistent run)
   double *tpart = nullptr;             // per-tile partial sums (persistent Wilson seed run)
+  int rgrid_cap[2] = {0, 0};           // most blocks of a reorthogonalizing CSR run, 16 / 32 rows per block
+  double *rhpart = nullptr;            // its partial products, 2 x (m_max + 1) x grid doubles
+  int64_t rhpart_grid = 0;             // the grid rhpart was sized for
   bool allow_persistent = true;        // persistent seed runs
   bool allow_persistent_cg = false;    // persistent CG
 
@@ -266,6 +269,8 @@ seed_status alloc_common(seed_ctx *ctx) {
   CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
   ctx->pgrid = coop ? persistent_grid(ctx->kind, ctx->sm_count, false, ctx->precision == 1) : 0;
   ctx->pgrid_cg = coop ? persistent_grid(ctx->kind, ctx->sm_count, true) : 0;
+  if (coop && ctx->kind == 0 && ctx->precision == 0)
+    for (int q = 0; q < 2; ++q) ctx->rgrid_cap[q] = reorth_run_grid_cap(ctx->sm_count, 16 << q);
   return SEED_OK;
 }
 
@@ -493,6 +498,54 @@ bool use_persistent_seed(seed_ctx *ctx) {
   return ctx->allow_persistent && ctx->pgrid > 0 && (f == 0 || f >= 8);
 }
 
+// The one-launch seed run of small real CSR problems that reorthogonalize every
+// 1 to 7 steps (the streaming form of the seeding): rows per block (16, or 32
+// when 16 would need more blocks than can be resident) and the grid; grid 0
+// when the problem does not qualify.
+struct ReorthRun {
+  int rb = 0, grid = 0;
+};
+ReorthRun reorth_run_shape(const seed_ctx *ctx, int nrhs) {
+  const int f = ctx->prm.reorth_freq;
+  ReorthRun r;
+  if (!ctx->allow_persistent || ctx->kind != 0 || ctx->precision != 0 || f < 1 || f >= 8) return r;
+  if (nrhs > kReorthRunMaxRhs || ctx->n > kReorthRunMaxN || ctx->n < 1) return r;
+  for (int q = 0; q < 2; ++q) {
+    const int rb = 16 << q;
+    const int64_t grid = (ctx->n + rb - 1) / rb;
+    if (grid <= ctx->rgrid_cap[q]) {
+      r.rb = rb;
+      r.grid = (int)grid;
+      return r;
+    }
+  }
+  return r;
+}
+
+seed_status seed_reorth_run(seed_ctx *ctx, int nrhs, ReorthRun shape) {
+  const seed_params &p = ctx->prm;
+  if (!ctx->rhpart) {
+    TRY(dalloc(ctx, &ctx->rhpart, sizeof(double) * 2 * (size_t)(p.m_max + 1) * shape.grid));
+    ctx->rhpart_grid = shape.grid;
+  }
+  if (shape.grid > ctx->rhpart_grid) return fail(ctx, SEED_ECUDA, "internal: reorthogonalizing run grid grew");
+  const GridSync g = grid_sync_bufs(ctx);
+  SeedBufs<double> b = seed_bufs<double>(ctx, nrhs);
+  CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
+  cudaError_t e = launch_seed_run_csr_reorth(b, ctx->csr, (double *)ctx->f2, g, ctx->partials, ctx->rhpart,
+                                             reinterpret_cast<double *>(ctx->H), p.reorth_freq, p.reorth_passes,
+                                             p.m_max + 1, shape.rb, shape.grid, ctx->cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SEED_ECUDA, std::string("persistent seed launch: ") + cudaGetErrorString(e));
+  }
+  ctx->stats.kernel_launches += 1;
+  CU(cudaMemcpyAsync(ctx->h_gerr, g.error, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->cs));
+  CU(cudaStreamSynchronize(ctx->cs));
+  if (*ctx->h_gerr) return fail(ctx, SEED_ETIMEOUT, "a grid barrier of the persistent seed kernel timed out");
+  return SEED_OK;
+}
+
 // Runs of Lanczos steps from CUDA graphs, status polled one run behind.
 template <class T>
 seed_status seed_graph_runs(seed_ctx *ctx, int nrhs) {
@@ -620,7 +673,11 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   kern += 3;
   ctx->stats.kernel_launches += kern;
 
-  if (use_persistent_seed(ctx)) {
+  ReorthRun rr;
+  if constexpr (std::is_same_v<T, double>) rr = reorth_run_shape(ctx, nrhs);
+  if (rr.grid > 0) {
+    TRY(seed_reorth_run(ctx, nrhs, rr));
+  } else if (use_persistent_seed(ctx)) {
     TRY(seed_persistent_segments<T>(ctx, nrhs));
   } else {
     TRY(seed_graph_runs<T>(ctx, nrhs));
@@ -1502,7 +1559,7 @@ void destroy(seed_ctx *ctx) {
                   ctx->gsync, ctx->f2, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
                   ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots,
                   ctx->msX, ctx->msR, ctx->Wb, ctx->gamma_hist, ctx->blk.Hpart, ctx->blk.G, ctx->blk.Z,
-                  ctx->tc_err};
+                  ctx->tc_err, ctx->rhpart};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);

@@ -389,12 +389,19 @@ __global__ void __launch_bounds__(NT) k_reorth_reduce(SeedBufs<T> b, ReorthBufs<
   gram_reduce(r.Hpart, r.H, st->i - 1, r.nrb, r.kcap);
 }
 
-// F_v += sgn * V[:, 0:k] H[:, v] for the two vectors (one thread per row).
+// F_v += sgn * V[:, 0:k] H[:, v] for the two vectors.  A block covers NT / S
+// rows; its S thread groups (S = 1, 2 or 4: one warp each when S = 4) take
+// consecutive slices of every 256-column chunk of H, and the S partial sums of
+// a row are added in group order (fixed, so the result does not depend on the
+// timing).  Short vectors use S = 4 so that a 4096-row vector still spreads
+// over 128 blocks instead of 32 serial ones.
 template <class T>
 SEED_DEV void gram_update(const T *__restrict__ V, int64_t ldv, int64_t n, int k, const double2 *__restrict__ H,
-                          T *F0, T *F1, double sgn) {
+                          T *F0, T *F1, double sgn, int S) {
   __shared__ typename Sc<T>::A2 sH[256][2];
-  const int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x;
+  __shared__ T spart[2][NT];
+  const int rb = NT / S, sub = threadIdx.x / rb, rl = threadIdx.x - sub * rb;
+  const int64_t row = (int64_t)blockIdx.x * rb + rl;
   const bool valid = row < n;
   T a0 = Sc<T>::zero(), a1 = Sc<T>::zero();
   for (int c0 = 0; c0 < k; c0 += 256) {
@@ -404,12 +411,24 @@ SEED_DEV void gram_update(const T *__restrict__ V, int64_t ldv, int64_t n, int k
       sH[q >> 1][q & 1] = Sc<T>::from2(H[(int64_t)(c0 + (q >> 1)) * 2 + (q & 1)]);
     __syncthreads();
     if (valid) {
+      const int ca = cn * sub / S, cb = cn * (sub + 1) / S;
       const T *vr = V + row + (int64_t)c0 * ldv;
-      for (int c = 0; c < cn; ++c) {
+#pragma unroll 4
+      for (int c = ca; c < cb; ++c) {
         const T v = vr[(int64_t)c * ldv];
         a0 = Sc<T>::caxpy2(sH[c][0], v, a0);
         a1 = Sc<T>::caxpy2(sH[c][1], v, a1);
       }
+    }
+  }
+  if (S > 1) {
+    spart[0][threadIdx.x] = a0;
+    spart[1][threadIdx.x] = a1;
+    __syncthreads();
+    if (sub != 0) return;
+    for (int q = 1; q < S; ++q) {
+      a0 = Sc<T>::add(a0, spart[0][q * rb + rl]);
+      a1 = Sc<T>::add(a1, spart[1][q * rb + rl]);
     }
   }
   if (valid) {
@@ -418,12 +437,17 @@ SEED_DEV void gram_update(const T *__restrict__ V, int64_t ldv, int64_t n, int k
   }
 }
 
+// column slices per row block of gram_update: 4 below 304 blocks of NT rows
+// (two per SM), else 1
+inline int gram_splits(int64_t n) { return n < (int64_t)NT * 304 ? 4 : 1; }
+inline int gram_blocks(int64_t n) { return (int)((n + NT / gram_splits(n) - 1) / (NT / gram_splits(n))); }
+
 template <class T>
-__global__ void __launch_bounds__(NT) k_reorth_sub(SeedBufs<T> b, ReorthBufs<T> r) {
+__global__ void __launch_bounds__(NT) k_reorth_sub(SeedBufs<T> b, ReorthBufs<T> r, int S) {
   const SeedState *st = b.st;
   if (!st->active) return;
   const int i = st->i;
-  gram_update<T>(r.V, r.ldv, r.n, i - 1, r.H, b.V + (int64_t)(i - 1) * b.ldv, b.f, -1.0);
+  gram_update<T>(r.V, r.ldv, r.n, i - 1, r.H, b.V + (int64_t)(i - 1) * b.ldv, b.f, -1.0, S);
 }
 
 // scratch = 1 / ||v_i||
@@ -521,11 +545,10 @@ void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s) {
 }
 template <class T>
 void launch_reorth(const SeedBufs<T> &b, const ReorthBufs<T> &r, int passes, cudaStream_t s) {
-  const int rows_blocks = (int)((r.n + NT - 1) / NT);
   for (int p = 0; p < passes; ++p) {
     k_reorth_tiles<T><<<r.nitems_grid, NT, 0, s>>>(b, r);
     k_reorth_reduce<T><<<64, NT, 0, s>>>(b, r);
-    k_reorth_sub<T><<<rows_blocks, NT, 0, s>>>(b, r);
+    k_reorth_sub<T><<<gram_blocks(r.n), NT, 0, s>>>(b, r, gram_splits(r.n));
   }
   k_reorth_norm_vi<T><<<b.nblocks, NT, 0, s>>>(b);
   k_reorth_scale_dot<T><<<b.nblocks, NT, 0, s>>>(b);
@@ -583,15 +606,14 @@ __global__ void k_tridiag_solve(const double *alpha, const double *beta, int m, 
 }
 template <class T>
 __global__ void __launch_bounds__(NT) k_gram_add(const T *V, int64_t ldv, int64_t n, int k, const double2 *H, T *F0,
-                                                 T *F1) {
-  gram_update<T>(V, ldv, n, k, H, F0, F1, 1.0);
+                                                 T *F1, int S) {
+  gram_update<T>(V, ldv, n, k, H, F0, F1, 1.0, S);
 }
 
 template <class T>
 void launch_project(int64_t n, const T *V, int64_t ldv, int m, const double *alpha, const double *beta, const T *R,
                     int64_t ldr, T *X, int64_t ldx, int ncols, double2 *G, double2 *Gpart, int nrb,
                     int rows_per_item, cudaStream_t s) {
-  const int rows_blocks = (int)((n + NT - 1) / NT);
   for (int j = 0; j < ncols; j += 2) {
     const bool two = j + 1 < ncols;
     const T *F0 = R + (int64_t)j * ldr;
@@ -600,8 +622,8 @@ void launch_project(int64_t n, const T *V, int64_t ldv, int m, const double *alp
     k_gram_reduce<<<64, NT, 0, s>>>(Gpart, G, m, nrb, m + 1);
     // the Thomas scratch reuses the (now reduced) partial buffer
     k_tridiag_solve<<<1, 32, 0, s>>>(alpha, beta, m, G, reinterpret_cast<double *>(Gpart));
-    k_gram_add<T><<<rows_blocks, NT, 0, s>>>(V, ldv, n, m, G, X + (int64_t)j * ldx,
-                                             two ? X + (int64_t)(j + 1) * ldx : nullptr);
+    k_gram_add<T><<<gram_blocks(n), NT, 0, s>>>(V, ldv, n, m, G, X + (int64_t)j * ldx,
+                                                two ? X + (int64_t)(j + 1) * ldx : nullptr, gram_splits(n));
   }
 }
 

@@ -748,6 +748,282 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr(SeedBufs<T> b, CsrOpT<T> op
 }
 
 // ---------------------------------------------------------------------------
+// Small real CSR problems that reorthogonalize every few steps (Sec. 3 with a
+// reorthogonalization frequency of 1 to 7, where the seeding of systems 2..p
+// runs in its streaming form): every step -- the apply, alpha_i and
+// g^j = v_i^H r_0^j, the LU update with x^1 += zeta_i w_i and
+// x^j += eta^j w_i, and on reorthogonalizing steps the classical Gram-Schmidt
+// passes over V_{<i}, the renormalization of v_i and the projections of f on
+// it -- in one cooperative launch, instead of 10 to 14 kernels per step.
+//
+// Block b owns rows [b RB, (b + 1) RB) (RB = 16 or 32, so that the grid spans
+// most SMs even for n = 4096); thread t < RB holds row b RB + t in every row
+// phase.  The products with V_{<i} run with one thread per basis column
+// (columns t, t + PT, ...): a thread loads its column's RB rows (one or two
+// 128-byte lines), so the whole grid streams V with many loads in flight.
+//   H = V_{<i}^H [v_i f]: per block and column the dot products over the
+//   block's rows, written to hpart[(2 c + v) G + b]; after a barrier block b
+//   sums the values [2 k b / G, 2 k (b + 1) / G) over the blocks in block order
+//   into H; after a second barrier each thread adds x_rc H_c of its columns
+//   into 2 RB row sums, the block combines them (warp reduce-scatter, then the
+//   warps in order), and the rows subtract them.  When a second pass follows,
+//   its dot products use the same lines again (from L1) in the same phase.
+// Scalar sums (alpha_i with the g^j, ||v_i||^2, v_i^H f, ||f||^2): one row of
+// block partials per block in one of two alternating regions -- a block that
+// has run ahead writes the other region while slower blocks still read this
+// one -- reduced by every block in block order, so the blocks' shared-memory
+// copies of the recurrence's scalars stay identical.
+// ---------------------------------------------------------------------------
+constexpr int kRunRegion = 32;                 // doubles per block in a scalar partial region
+constexpr int kRunMaxRhs = kReorthRunMaxRhs;   // alpha_i and g^2..g^16 in one region row
+
+// block sums of v[0..nv) into row[0..nv) (warp sums, then the four warps in order)
+template <int NV>
+SEED_DEV void block_row(const double (&v)[NV], int nv, double *row, double (*s)[kRunRegion]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    if (q < nv) {
+      const double t = warp_sum(v[q]);
+      if (lane == 0) s[warp][q] = t;
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nv)
+    row[threadIdx.x] = ((s[0][threadIdx.x] + s[1][threadIdx.x]) + s[2][threadIdx.x]) + s[3][threadIdx.x];
+}
+
+// after the barrier: S[q] = sum over blocks (in block order) of region[b * kRunRegion + q], q < nv
+SEED_DEV void reduce_region(const double *region, int nv, double *S) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = warp; q < nv; q += PT / 32) {
+    const double t = warp_sum_partials(region, gridDim.x, kRunRegion, q);
+    if (lane == 0) S[q] = t;
+  }
+  __syncthreads();
+}
+
+// hpart[(2 c + v) G + b] = sum over the block's rows r of V[c][row0 + r] y_v[r], c < k
+template <int RB>
+SEED_DEV void col_dots(const double *V, int64_t ldv, int64_t row0, int rows, int k, const double (*y)[RB],
+                       double *hpart) {
+  const int G = gridDim.x;
+  for (int c = threadIdx.x; c < k; c += PT) {
+    const double *vc = V + (int64_t)c * ldv + row0;
+    double x[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) x[r] = r < rows ? vc[r] : 0.0;
+    double hv = 0.0, hf = 0.0;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      hv = fma(x[r], y[0][r], hv);
+      hf = fma(x[r], y[1][r], hf);
+    }
+    hpart[(int64_t)(2 * c) * G + blockIdx.x] = hv;
+    hpart[(int64_t)(2 * c + 1) * G + blockIdx.x] = hf;
+  }
+}
+
+// H[q] = sum over blocks (block order) of hpart[q G + b], for this block's slice of q < 2k
+SEED_DEV void slice_reduce(const double *hpart, int k, double *H) {
+  const int G = gridDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q0 = (int)((int64_t)2 * k * blockIdx.x / G), q1 = (int)((int64_t)2 * k * (blockIdx.x + 1) / G);
+  for (int q = q0 + warp; q < q1; q += PT / 32) {
+    const double t = warp_sum_partials(hpart + (int64_t)q * G, G, 1, 0);
+    if (lane == 0) H[q] = t;
+  }
+}
+
+// sub[v][r] = sum over c < k of V[c][row0 + r] H[2 c + v] (threads over columns, then the block)
+template <int RB>
+SEED_DEV void rows_times_h(const double *V, int64_t ldv, int64_t row0, int rows, int k, const double *H,
+                           double (*sub)[RB], double (*sred)[2 * RB]) {
+  double p[2 * RB];
+#pragma unroll
+  for (int q = 0; q < 2 * RB; ++q) p[q] = 0.0;
+  for (int c = threadIdx.x; c < k; c += PT) {
+    const double *vc = V + (int64_t)c * ldv + row0;
+    const double hv = __ldcg(H + 2 * c), hf = __ldcg(H + 2 * c + 1);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const double x = r < rows ? vc[r] : 0.0;
+      p[r] = fma(x, hv, p[r]);
+      p[RB + r] = fma(x, hf, p[RB + r]);
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int h = 0; h < 2 * RB; h += 32) {
+    double v32[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v32[q] = p[h + q];
+    sred[warp][h + lane] = warp_reduce_scatter32(v32);
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < 2 * RB) {
+    const int q = threadIdx.x;
+    sub[q / RB][q % RB] = ((sred[0][q] + sred[1][q]) + sred[2][q]) + sred[3][q];
+  }
+  __syncthreads();
+}
+
+template <int RB>
+__global__ void __launch_bounds__(PT) k_seed_run_csr_reorth(SeedBufs<double> b, CsrOp op, double *f2, GridSync g,
+                                                            double *bpart, double *hpart, double *H, int freq,
+                                                            int passes, int i_stop) {
+  static_assert(2 * RB % 32 == 0 && 2 * RB <= PT, "rows per block");
+  __shared__ double s_w[PT / 32][kRunRegion];
+  __shared__ double s_sum[kRunRegion];
+  __shared__ double2 s_g[kRunMaxRhs];
+  __shared__ double2 s_eta[kRunMaxRhs];
+  __shared__ double s_y[2][RB];
+  __shared__ double s_sub[2][RB];
+  __shared__ double s_red[PT / 32][2 * RB];
+  __shared__ LocalSeed L;
+  unsigned epoch = 0;
+  int par = 0, reg = 0;
+  local_load(b, L);
+  const int nr = b.nrhs;   // <= kRunMaxRhs (checked by the host)
+  for (int j = threadIdx.x; j < nr; j += PT) s_eta[j] = b.eta[j];
+  __syncthreads();
+  SeedBufs<double> bl = local_bufs(b, L);
+  bl.eta = s_eta;
+  const int G = gridDim.x;
+  const int64_t n = b.n, ldv = b.ldv;
+  const int64_t row0 = (int64_t)blockIdx.x * RB;
+  const int rows = (int)(n - row0 < RB ? n - row0 : RB);   // >= 1: the grid is ceil(n / RB)
+  const int64_t e = row0 + threadIdx.x;                     // this thread's row in the row phases
+  const bool own = (int)threadIdx.x < rows;
+  double *const X = reinterpret_cast<double *>(b.call->X);
+  const int64_t ldx = b.call->ldx;
+  auto region = [&]() {   // the next scalar partial region (alternating)
+    double *r = bpart + (int64_t)reg * G * kRunRegion;
+    reg ^= 1;
+    return r;
+  };
+  for (;;) {
+    const int i = L.st.i;
+    if (!L.st.active || i >= i_stop) break;
+    const double inv_b = L.st.inv_beta;
+    const double bp = (i > 1) ? L.st.beta_prev : 0.0;
+    const double *fc = par ? f2 : b.f;
+    double *fn = par ? b.f : f2;
+    double *vi = b.V + (int64_t)(i - 1) * ldv;
+    const double *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * ldv;
+    // ---- v_i = f / beta_{i-1}; f = A v_i - beta_{i-1} v_{i-1}; alpha_i and g^j ----
+    double acc[kRunMaxRhs];
+#pragma unroll
+    for (int q = 0; q < kRunMaxRhs; ++q) acc[q] = 0.0;
+    double v = 0.0, fe = 0.0;
+    if (own) {
+      const int32_t k0 = __ldg(op.row_ptr + e), k1 = __ldg(op.row_ptr + e + 1);
+      double sum = 0.0;
+      for (int32_t q = k0; q < k1; ++q) sum = fma(__ldg(op.vals + q), __ldcg(fc + __ldg(op.col_idx + q)), sum);
+      v = inv_b * __ldcg(fc + e);
+      vi[e] = v;
+      double u = inv_b * sum;
+      if (i > 1) u = fma(-bp, vm[e], u);
+      fe = u;
+      acc[0] = v * u;
+#pragma unroll
+      for (int q = 1; q < kRunMaxRhs; ++q)
+        if (q < nr) acc[q] = v * b.R0[(int64_t)(q - 1) * b.ldr + e];
+    }
+    {
+      double *r = region();
+      block_row<kRunMaxRhs>(acc, nr, r + (int64_t)blockIdx.x * kRunRegion, s_w);
+      if (!grid_sync(g, epoch)) return;
+      reduce_region(r, nr, s_sum);
+    }
+    if (threadIdx.x == 0) {
+      for (int j = 1; j < nr; ++j) s_g[j] = c2(s_sum[j], 0.0);
+      seed_step_scalars<double, false>(bl, i, s_sum[0], s_g);
+    }
+    __syncthreads();
+    if (!L.st.active) break;   // delta_i <= 0
+    // ---- f -= alpha_i v_i; w_i; x^1 += zeta_i w_i; x^j += eta^j w_i ----
+    const bool ro = freq > 0 && i >= 2 && i % freq == 0;
+    {
+      const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+      double nf = 0.0;
+      if (own) {
+        fe = fma(-a, v, fe);
+        const double we = (i > 1) ? inv_d * fma(-bp, b.w[e], v) : inv_d * v;
+        b.w[e] = we;
+        X[e] = fma(zeta, we, X[e]);
+        for (int j = 1; j < nr; ++j) X[e + j * ldx] = fma(s_eta[j].x, we, X[e + j * ldx]);
+        nf = fe * fe;
+        if (!ro) fn[e] = fe;
+      }
+      if (!ro) {
+        double vv[1] = {nf};
+        double *r = region();
+        block_row<1>(vv, 1, r + (int64_t)blockIdx.x * kRunRegion, s_w);
+        if (!grid_sync(g, epoch)) return;
+        reduce_region(r, 1, s_sum);
+        if (threadIdx.x == 0) seed_finish<double, false>(bl, s_sum[0]);
+        __syncthreads();
+        par ^= 1;
+        continue;
+      }
+    }
+    // ---- reorthogonalization of v_i and f against V_{<i} (classical Gram-Schmidt, `passes` times) ----
+    const int k = i - 1;
+    if ((int)threadIdx.x < RB) {
+      s_y[0][threadIdx.x] = own ? v : 0.0;
+      s_y[1][threadIdx.x] = own ? fe : 0.0;
+    }
+    __syncthreads();
+    col_dots<RB>(b.V, ldv, row0, rows, k, s_y, hpart);
+    for (int pass = 0; pass < passes; ++pass) {
+      if (!grid_sync(g, epoch)) return;
+      slice_reduce(hpart, k, H);
+      if (!grid_sync(g, epoch)) return;
+      rows_times_h<RB>(b.V, ldv, row0, rows, k, H, s_sub, s_red);
+      if ((int)threadIdx.x < RB) {
+        s_y[0][threadIdx.x] = fma(-1.0, s_sub[0][threadIdx.x], s_y[0][threadIdx.x]);
+        s_y[1][threadIdx.x] = fma(-1.0, s_sub[1][threadIdx.x], s_y[1][threadIdx.x]);
+      }
+      __syncthreads();
+      if (pass + 1 < passes) col_dots<RB>(b.V, ldv, row0, rows, k, s_y, hpart);
+    }
+    v = own ? s_y[0][threadIdx.x] : 0.0;
+    fe = own ? s_y[1][threadIdx.x] : 0.0;
+    // ---- v_i /= ||v_i||, then f -= (v_i^H f) v_i, `passes` times; ||f||^2 ends the step ----
+    {
+      double vv[1] = {v * v};
+      double *r = region();
+      block_row<1>(vv, 1, r + (int64_t)blockIdx.x * kRunRegion, s_w);
+      if (!grid_sync(g, epoch)) return;
+      reduce_region(r, 1, s_sum);
+    }
+    v = (1.0 / sqrt(s_sum[0])) * v;
+    if (own) vi[e] = v;
+    for (int pass = 0; pass <= passes; ++pass) {
+      // pass < passes: h = v_i^H f, then f -= h v_i; pass == passes: ||f||^2 (f final: stored first)
+      if (pass == passes && own) fn[e] = fe;
+      double vv[1] = {pass < passes ? v * fe : fe * fe};
+      double *r = region();
+      block_row<1>(vv, 1, r + (int64_t)blockIdx.x * kRunRegion, s_w);
+      if (!grid_sync(g, epoch)) return;
+      reduce_region(r, 1, s_sum);
+      if (pass < passes) {
+        fe = fma(-s_sum[0], v, fe);
+      } else {
+        if (threadIdx.x == 0) seed_finish<double, false>(bl, s_sum[0]);
+        __syncthreads();
+      }
+    }
+    par ^= 1;
+  }
+  seed_leave<double>(b, L, par ? f2 : b.f, i_stop);
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < nr; j += PT) b.eta[j] = s_eta[j];
+  local_store(b, L);
+}
+
+// ---------------------------------------------------------------------------
 // lockstep CG (Hestenes-Stiefel) on nc columns, per-column scalars in CgCols:
 //   phase 1: t = D p;  phase 2: q = D^H t, p^H q;  alpha = rho / Re(p^H q)
 //   phase 3: x += alpha p, r -= alpha q, ||r||^2;  convergence, beta
@@ -1080,6 +1356,27 @@ cudaError_t launch_barrier_timeout_check(GridSync g, cudaStream_t s) {
   GridSync gg = g;
   void *args[] = {&gg};
   return cudaLaunchCooperativeKernel((const void *)k_barrier_timeout_check, dim3(2), dim3(PT), args, 0, s);
+}
+
+int reorth_run_grid_cap(int sm_count, int rb) {
+  int per_sm = 0;
+  const void *k = rb == 16 ? (const void *)k_seed_run_csr_reorth<16> : (const void *)k_seed_run_csr_reorth<32>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PT, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (per_sm > 2) per_sm = 2;
+  return per_sm * sm_count;
+}
+
+cudaError_t launch_seed_run_csr_reorth(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g,
+                                       double *bpart, double *hpart, double *H, int freq, int passes, int i_stop,
+                                       int rb, int grid, cudaStream_t s) {
+  SeedBufs<double> bb = b;
+  CsrOp o = op;
+  void *args[] = {&bb, &o, &f2, &g, &bpart, &hpart, &H, &freq, &passes, &i_stop};
+  const void *k = rb == 16 ? (const void *)k_seed_run_csr_reorth<16> : (const void *)k_seed_run_csr_reorth<32>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(PT), args, 0, s);
 }
 
 cudaError_t launch_cg_run_csr(const CsrOp &op, const CallArgs *call, double *R, double *P, double *Q, int64_t ld,

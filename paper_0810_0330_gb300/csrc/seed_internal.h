@@ -303,6 +303,16 @@ cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &o
                                    double *bpart, double *tpart, int i_stop, int grid, cudaStream_t s);
 cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g, double *bpart,
                                 int i_stop, int grid, cudaStream_t s);
+// Small real CSR problems reorthogonalizing every freq (1..7) steps, streaming
+// seeding, nrhs <= 16: the whole seed run in one launch of ceil(n / rb) blocks
+// (rb = 16 or 32 rows per block).  bpart: 2 x grid x 32 doubles; hpart:
+// 2 x (m_max + 1) x grid doubles; H: 2 x (m_max + 1) doubles.
+constexpr int64_t kReorthRunMaxN = 32 * 304;
+constexpr int kReorthRunMaxRhs = 16;
+int reorth_run_grid_cap(int sm_count, int rb);
+cudaError_t launch_seed_run_csr_reorth(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g,
+                                       double *bpart, double *hpart, double *H, int freq, int passes, int i_stop,
+                                       int rb, int grid, cudaStream_t s);
 // mixed precision (FP32 vectors and operator copy, FP64 scalars)
 cudaError_t launch_seed_run_csr32(const SeedBufs<float> &b, const CsrOp32 &op, float *f2, GridSync g, double *bpart,
                                   int i_stop, int grid, cudaStream_t s);
