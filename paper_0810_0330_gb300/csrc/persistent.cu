@@ -896,6 +896,22 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr_reorth(SeedBufs<double> b, 
   const bool own = (int)threadIdx.x < rows;
   double *const X = reinterpret_cast<double *>(b.call->X);
   const int64_t ldx = b.call->ldx;
+  // this thread's matrix row, held in registers for the whole run when it has
+  // at most kRowCache entries (every step's apply then waits on one round trip)
+  constexpr int kRowCache = 8;
+  int32_t k0 = 0, k1 = 0, rc_col[kRowCache];
+  double rc_val[kRowCache];
+  if (own) {
+    k0 = __ldg(op.row_ptr + e);
+    k1 = __ldg(op.row_ptr + e + 1);
+  }
+  const bool cached = k1 - k0 <= kRowCache;
+#pragma unroll
+  for (int q = 0; q < kRowCache; ++q) {
+    const bool in = cached && q < k1 - k0;
+    rc_col[q] = in ? __ldg(op.col_idx + k0 + q) : (int32_t)e;
+    rc_val[q] = in ? __ldg(op.vals + k0 + q) : 0.0;
+  }
   auto region = [&]() {   // the next scalar partial region (alternating)
     double *r = bpart + (int64_t)reg * G * kRunRegion;
     reg ^= 1;
@@ -916,9 +932,17 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr_reorth(SeedBufs<double> b, 
     for (int q = 0; q < kRunMaxRhs; ++q) acc[q] = 0.0;
     double v = 0.0, fe = 0.0;
     if (own) {
-      const int32_t k0 = __ldg(op.row_ptr + e), k1 = __ldg(op.row_ptr + e + 1);
       double sum = 0.0;
-      for (int32_t q = k0; q < k1; ++q) sum = fma(__ldg(op.vals + q), __ldcg(fc + __ldg(op.col_idx + q)), sum);
+      if (cached) {
+        double xv[kRowCache];
+#pragma unroll
+        for (int q = 0; q < kRowCache; ++q) xv[q] = q < k1 - k0 ? __ldcg(fc + rc_col[q]) : 0.0;
+#pragma unroll
+        for (int q = 0; q < kRowCache; ++q)
+          if (q < k1 - k0) sum = fma(rc_val[q], xv[q], sum);
+      } else {
+        for (int32_t q = k0; q < k1; ++q) sum = fma(__ldg(op.vals + q), __ldcg(fc + __ldg(op.col_idx + q)), sum);
+      }
       v = inv_b * __ldcg(fc + e);
       vi[e] = v;
       double u = inv_b * sum;
