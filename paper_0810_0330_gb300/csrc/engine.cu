@@ -498,6 +498,14 @@ bool use_persistent_seed(seed_ctx *ctx) {
   return ctx->allow_persistent && ctx->pgrid > 0 && (f == 0 || f >= 8);
 }
 
+// Blocks of the persistent CSR CG: one per work item (1024 rows of one column)
+// up to the resident limit -- small problems get small grids, whose barriers
+// cost less than those of a full grid with idle blocks.
+int cg_csr_grid(const seed_ctx *ctx, int nc) {
+  const int64_t items = (ctx->n + 1023) / 1024 * nc;
+  return (int)std::min<int64_t>(ctx->pgrid_cg, std::max<int64_t>(1, items));
+}
+
 // The one-launch seed run of small real CSR problems that reorthogonalize every
 // 1 to 7 steps (the streaming form of the seeding): rows per block (16, or 32
 // when 16 would need more blocks than can be resident) and the grid; grid 0
@@ -905,7 +913,7 @@ seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx,
                                  (double2 *)ctx->T, ld, c, g, ctx->partials, ctx->pgrid_cg, ctx->cs);
       else
         e = launch_cg_run_csr(ctx->csr, ctx->call, (double *)ctx->R, (double *)ctx->P, (double *)ctx->Q, ld, c, g,
-                              ctx->partials, ctx->pgrid_cg, ctx->cs);
+                              ctx->partials, cg_csr_grid(ctx, nc), ctx->cs);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, SEED_ECUDA, std::string("persistent CG launch: ") + cudaGetErrorString(e));
