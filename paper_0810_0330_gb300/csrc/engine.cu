@@ -102,6 +102,7 @@ struct seed_ctx {
   double *tpart = nullptr;             // per-tile partial sums (persistent Wilson seed run)
   int rgrid_cap[2] = {0, 0};           // most blocks of a reorthogonalizing CSR run, 16 / 32 rows per block
   double *rhpart = nullptr;            // its partial products, 2 x (m_max + 1) x grid doubles
+  double2 *Hrows = nullptr;            // FP32 reorthogonalization partials by 4096-row chunks (long vectors)
   int64_t rhpart_grid = 0;             // the grid rhpart was sized for
   bool allow_persistent = true;        // persistent seed runs
   bool allow_persistent_cg = false;    // persistent CG
@@ -249,6 +250,9 @@ seed_status alloc_common(seed_ctx *ctx) {
   ctx->nrb = (int)((n + rows - 1) / rows);
   TRY(dalloc(ctx, &ctx->Hpart, sizeof(double2) * (size_t)ctx->nrb * (m + 1) * 2 + 64));
   TRY(dalloc(ctx, &ctx->H, sizeof(double2) * (size_t)(m + 1) * 2));
+  // long FP32 vectors: reorthogonalization partials by 4096-row chunks (krylov.cu)
+  if (ctx->precision == 1 && n >= 65536)
+    TRY(dalloc(ctx, &ctx->Hrows, sizeof(double2) * (size_t)((n + 4095) / 4096) * (m + 1) * 2));
   TRY(dalloc(ctx, &ctx->cg_d, sizeof(double) * kCgDoubles * kMaxRhs));
   TRY(dalloc(ctx, &ctx->cg_i, sizeof(int32_t) * kCgInts * kMaxRhs));
   // call32: [0] seed run (X = E), [1 + b] branch b of the mixed CG graphs
@@ -423,6 +427,11 @@ ReorthBufs<T> reorth_bufs(seed_ctx *ctx) {
   r.ldv = ctx->ldv;
   r.Hpart = ctx->Hpart;
   r.H = ctx->H;
+  r.Hrows = kLow<T> ? ctx->Hrows : nullptr;
+  // about two chunks per SM (one wave), within what one SM's L1 holds of v_i and f
+  int64_t rc = (r.n + 2 * ctx->sm_count - 1) / (2 * ctx->sm_count);
+  rc = (rc + 255) / 256 * 256;
+  r.row_chunk = (int32_t)std::min<int64_t>(8192, std::max<int64_t>(4096, rc));
   return r;
 }
 
@@ -1567,7 +1576,7 @@ void destroy(seed_ctx *ctx) {
                   ctx->gsync, ctx->f2, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,
                   ctx->T32, ctx->E32, ctx->call32, ctx->Rrel, ctx->xrel, ctx->rrel, ctx->reldots,
                   ctx->msX, ctx->msR, ctx->Wb, ctx->gamma_hist, ctx->blk.Hpart, ctx->blk.G, ctx->blk.Z,
-                  ctx->tc_err, ctx->rhpart};
+                  ctx->tc_err, ctx->rhpart, ctx->Hrows};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);

@@ -16,6 +16,8 @@
 // block order by the last block (see device_common.cuh).
 #include <math.h>
 
+#include <type_traits>
+
 #include "seed_device.cuh"
 
 namespace seedk {
@@ -372,6 +374,95 @@ __global__ void __launch_bounds__(NT) k_reorth_tiles(SeedBufs<T> b, ReorthBufs<T
   }
 }
 
+// Long low-precision vectors: the partial products by row chunks.  Block b
+// takes rows [b R, (b + 1) R) (R = r.row_chunk, 4096 to 8192, about two chunks
+// per SM) against every column of V_{<i} in tiles of 8; the chunk's v_i and f
+// (64 to 128 KB in FP32) are staged in shared memory once for all the block's
+// tiles (with one block per (row block, tile) pair they were re-read for every
+// tile, and V streamed at a fifth of the HBM rate).
+// Hrows[(b kcap + c) 2 + v].
+template <class T> constexpr bool kLowT = std::is_same_v<T, float> || std::is_same_v<T, float2>;
+constexpr int kRowThreads = 256;
+
+template <class T>
+__global__ void __launch_bounds__(kRowThreads) k_reorth_rows(SeedBufs<T> b, ReorthBufs<T> r, double2 *Hrows) {
+  const SeedState *st = b.st;
+  if (!st->active) return;
+  __shared__ double sred[kRowThreads / 32][32];
+  extern __shared__ unsigned char s_dyn[];
+  T *sF = reinterpret_cast<T *>(s_dyn);   // [2][row_chunk]: this chunk of v_i and f
+  const int i = st->i, k = i - 1;
+  const int64_t r0 = (int64_t)blockIdx.x * r.row_chunk;
+  const int64_t r1 = (r0 + r.row_chunk < r.n) ? r0 + r.row_chunk : r.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += kRowThreads) {
+      sF[row - r0] = vi[row];
+      sF[r.row_chunk + row - r0] = b.f[row];
+    }
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    const int nc = (k - c0 < 8) ? k - c0 : 8;
+    typename Sc<T>::A2 acc[8][2];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c][0] = acc[c][1] = Sc<T>::zero2();
+    const T *Vc = r.V + (int64_t)c0 * r.ldv;
+#pragma unroll 2
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += kRowThreads) {
+      const T f0 = sF[row - r0], f1 = sF[r.row_chunk + row - r0];
+      T v[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] = c < nc ? Vc[row + (int64_t)c * r.ldv] : Sc<T>::zero();
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        acc[c][0] = Sc<T>::dotc(v[c], f0, acc[c][0]);
+        acc[c][1] = Sc<T>::dotc(v[c], f1, acc[c][1]);
+      }
+    }
+    double vals[32];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      vals[4 * c + 0] = acc[c][0].x;
+      vals[4 * c + 1] = acc[c][0].y;
+      vals[4 * c + 2] = acc[c][1].x;
+      vals[4 * c + 3] = acc[c][1].y;
+    }
+    sred[warp][lane] = warp_reduce_scatter32(vals);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kRowThreads / 32; ++w) t += sred[w][lane];
+      const int c = lane >> 2, vv = (lane >> 1) & 1, ri = lane & 1;
+      if (c < nc) reinterpret_cast<double *>(Hrows)[(((int64_t)blockIdx.x * r.kcap + c0 + c) * 2 + vv) * 2 + ri] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// H[c][v] = sum over the row chunks (in order) of Hrows: one warp per value,
+// lane l taking chunks l, l + 32, ... in order, then a fixed shuffle tree.
+template <class T>
+__global__ void __launch_bounds__(NT) k_reorth_rows_reduce(SeedBufs<T> b, ReorthBufs<T> r, const double2 *Hrows,
+                                                           int nchunks) {
+  const SeedState *st = b.st;
+  if (!st->active) return;
+  const int k = st->i - 1, lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);   // value: column q / 2, vector q % 2
+  if (q >= 2 * (int64_t)k) return;
+  double sx = 0.0, sy = 0.0;
+  for (int ch = lane; ch < nchunks; ch += 32) {
+    const double2 h = __ldcg(Hrows + (int64_t)ch * r.kcap * 2 + q);
+    sx += h.x;
+    sy += h.y;
+  }
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  if (lane == 0) r.H[q] = c2(sx, sy);
+}
+
 // H[c][v] = sum over row blocks (in order) of Hpart
 SEED_DEV void gram_reduce(const double2 *Hpart, double2 *H, int k, int nrb, int kcap) {
   for (int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x; q < 2 * (int64_t)k; q += (int64_t)gridDim.x * NT) {
@@ -545,9 +636,22 @@ void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s) {
 }
 template <class T>
 void launch_reorth(const SeedBufs<T> &b, const ReorthBufs<T> &r, int passes, cudaStream_t s) {
+  const bool rows = kLowT<T> && r.Hrows != nullptr;
+  const int nchunks = rows ? (int)((r.n + r.row_chunk - 1) / r.row_chunk) : 0;
   for (int p = 0; p < passes; ++p) {
-    k_reorth_tiles<T><<<r.nitems_grid, NT, 0, s>>>(b, r);
-    k_reorth_reduce<T><<<64, NT, 0, s>>>(b, r);
+    if (rows) {
+      const size_t smem = 2 * sizeof(T) * (size_t)r.row_chunk;
+      static bool attr = false;   // per instantiation: allow up to 2 x 8192 FP32 complex rows
+      if (!attr) {
+        cudaFuncSetAttribute(k_reorth_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(T) * 8192);
+        attr = true;
+      }
+      k_reorth_rows<T><<<nchunks, kRowThreads, smem, s>>>(b, r, r.Hrows);
+      k_reorth_rows_reduce<T><<<(2 * r.kcap + NT / 32 - 1) / (NT / 32), NT, 0, s>>>(b, r, r.Hrows, nchunks);
+    } else {
+      k_reorth_tiles<T><<<r.nitems_grid, NT, 0, s>>>(b, r);
+      k_reorth_reduce<T><<<64, NT, 0, s>>>(b, r);
+    }
     k_reorth_sub<T><<<gram_blocks(r.n), NT, 0, s>>>(b, r, gram_splits(r.n));
   }
   k_reorth_norm_vi<T><<<b.nblocks, NT, 0, s>>>(b);

@@ -138,6 +138,8 @@ struct ReorthBufs {
   int64_t ldv;
   double2 *Hpart;          // [nrb][m_max+1][2]
   double2 *H;              // [m_max+1][2]
+  double2 *Hrows;          // long FP32 vectors: [ceil(n / 4096)][m_max+1][2] partials by row chunks, else NULL
+  int32_t row_chunk;       // rows per chunk of Hrows: 4096..8192, a multiple of 256
 };
 
 // Per-column CG state (lockstep CG over nc columns).  rupd, upd and delta are
