@@ -1013,17 +1013,23 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr_reorth(SeedBufs<double> b, 
     }
     v = own ? s_y[0][threadIdx.x] : 0.0;
     fe = own ? s_y[1][threadIdx.x] : 0.0;
-    // ---- v_i /= ||v_i||, then f -= (v_i^H f) v_i, `passes` times; ||f||^2 ends the step ----
+    // ---- v_i /= ||v_i||, then f -= (v_i^H f) v_i, `passes` times; ||f||^2 ends the step.
+    // ||v_i||^2 and v_i^H f come from one reduction (h = (v_i^H f) / ||v_i|| before
+    // the scaling: the first projection's coefficient, rounded in another order) ----
     {
-      double vv[1] = {v * v};
+      double vv[2] = {v * v, v * fe};
       double *r = region();
-      block_row<1>(vv, 1, r + (int64_t)blockIdx.x * kRunRegion, s_w);
+      block_row<2>(vv, 2, r + (int64_t)blockIdx.x * kRunRegion, s_w);
       if (!grid_sync(g, epoch)) return;
-      reduce_region(r, 1, s_sum);
+      reduce_region(r, 2, s_sum);
     }
-    v = (1.0 / sqrt(s_sum[0])) * v;
+    {
+      const double inv = 1.0 / sqrt(s_sum[0]);
+      v = inv * v;
+      fe = fma(-(s_sum[1] * inv), v, fe);
+    }
     if (own) vi[e] = v;
-    for (int pass = 0; pass <= passes; ++pass) {
+    for (int pass = 1; pass <= passes; ++pass) {
       // pass < passes: h = v_i^H f, then f -= h v_i; pass == passes: ||f||^2 (f final: stored first)
       if (pass == passes && own) fn[e] = fe;
       double vv[1] = {pass < passes ? v * fe : fe * fe};

@@ -67,6 +67,36 @@ def test_batch_equals_solo_solves_and_oracle(seedlib, orc, kernel_path):
             assert np.linalg.norm(B[:, j] - op.apply(X[:, j]).real) <= 1.5e-8 * np.linalg.norm(B[:, j])
 
 
+def test_batch_one_launch_reorthogonalizing_runs_side_by_side(seedlib, orc):
+    """Small problems that reorthogonalize every 3 steps run their whole seed
+    run as one cooperative launch each (up to 4 at a time from the batch's
+    workers): bitwise the solo results, and one problem against the oracle."""
+    probs = I.batch_problems(count=6, n_min=300, n_max=9000, seed=11)
+    prm = dict(m_max=600, reorth_freq=3, tol_seed=1e-10, tol_rest=1e-8, kernel_path=0)
+    ctxs, ops, Bs, Xs = [], [], [], []
+    for p in probs:
+        c, op, B = make(seedlib, p, **prm)
+        ctxs.append(c), ops.append(op), Bs.append(dev(B))
+        Xs.append(torch.zeros_like(Bs[-1].t()).t())
+    infos = seedlib.seed_batch_solve(ctxs, Bs, Xs, workers=4)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        c, _, _ = make(seedlib, p, **prm)
+        X = torch.zeros_like(Bs[i].t()).t()
+        a = seedlib.seed_solve_first(c, Bs[i], X)
+        seedlib.seed_solve_rest(c, Bs[i], X)
+        torch.cuda.synchronize()
+        assert torch.equal(X, Xs[i]), i
+        assert infos[i][0]["iters"] == a[0]["iters"]
+    B = host(Bs[0])
+    op = orc.Operator.csr(*ops[0])
+    ref = orc.seed_solve_all(op, B, m_max=600, reorth_freq=3, tol_seed=1e-10, tol_rest=1e-8)
+    assert infos[0][0]["iters"] == ref["seed"]["iters"]
+    X = host(Xs[0]).real
+    for j in range(1, B.shape[1]):
+        assert np.linalg.norm(B[:, j] - op.apply(X[:, j]).real) <= 1.5e-8 * np.linalg.norm(B[:, j])
+
+
 def test_batch_reports_failing_problem(seedlib):
     probs = I.batch_problems(count=3, n_min=300, n_max=3000, seed=5)
     ctxs, Bs, Xs = [], [], []

@@ -5,7 +5,7 @@ the most right-hand sides the run takes (16), 32 rows per block (more than
 304 blocks of 16 would be needed) with a ragged last block and one
 Gram-Schmidt pass, the largest size the run takes, and the first size past it
 (the step kernels run instead).  Reorthogonalization every 3 and 7 steps
-mixes reorthogonalizing steps (nine grid barriers) with plain ones (two).
+mixes reorthogonalizing steps (eight grid barriers) with plain ones (two).
 
 Checks: the seed run's step count equals the oracle's, x^1 within 1e-9, the
 seeded x^2.. within max(1e-9, 10 x the oracle's one-ulp sensitivity), the
