@@ -101,6 +101,8 @@ struct seed_ctx {
   void *f2 = nullptr;                  // second Lanczos-vector buffer (CSR persistent run)
   double *tpart = nullptr;             // per-tile partial sums (persistent Wilson seed run)
   int rgrid_cap[2] = {0, 0};           // most blocks of a reorthogonalizing CSR run, 16 / 32 rows per block
+  int scg_cap[2] = {0, 0};             // most blocks of the small-problem CSR CG, 16 / 32 rows per block
+  bool allow_small_cg = true;          // the small-problem CSR CG (not on kernel_path 1)
   double *rhpart = nullptr;            // its partial products, 2 x (m_max + 1) x grid doubles
   double2 *Hrows = nullptr;            // FP32 reorthogonalization partials by 4096-row chunks (long vectors)
   int64_t rhpart_grid = 0;             // the grid rhpart was sized for
@@ -274,7 +276,10 @@ seed_status alloc_common(seed_ctx *ctx) {
   ctx->pgrid = coop ? persistent_grid(ctx->kind, ctx->sm_count, false, ctx->precision == 1) : 0;
   ctx->pgrid_cg = coop ? persistent_grid(ctx->kind, ctx->sm_count, true) : 0;
   if (coop && ctx->kind == 0 && ctx->precision == 0)
-    for (int q = 0; q < 2; ++q) ctx->rgrid_cap[q] = reorth_run_grid_cap(ctx->sm_count, 16 << q);
+    for (int q = 0; q < 2; ++q) {
+      ctx->rgrid_cap[q] = reorth_run_grid_cap(ctx->sm_count, 16 << q);
+      ctx->scg_cap[q] = small_cg_grid_cap(ctx->sm_count, 16 << q);
+    }
   return SEED_OK;
 }
 
@@ -531,6 +536,24 @@ ReorthRun reorth_run_shape(const seed_ctx *ctx, int nrhs) {
     const int rb = 16 << q;
     const int64_t grid = (ctx->n + rb - 1) / rb;
     if (grid <= ctx->rgrid_cap[q]) {
+      r.rb = rb;
+      r.grid = (int)grid;
+      return r;
+    }
+  }
+  return r;
+}
+
+// The one-launch lockstep CG of small real CSR problems: rows per block and
+// grid, as for the reorthogonalizing seed run; grid 0 when it does not apply.
+ReorthRun small_cg_shape(const seed_ctx *ctx, int nc) {
+  ReorthRun r;
+  if (!ctx->allow_small_cg || ctx->kind != 0 || ctx->precision != 0 || nc > 16 || nc < 1) return r;
+  if (ctx->n > kReorthRunMaxN || ctx->n < 1) return r;
+  for (int q = 0; q < 2; ++q) {
+    const int rb = 16 << q;
+    const int64_t grid = (ctx->n + rb - 1) / rb;
+    if (grid <= ctx->scg_cap[q]) {
       r.rb = rb;
       r.grid = (int)grid;
       return r;
@@ -909,7 +932,9 @@ seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx,
   ctx->stats.kernel_launches += kern + 1;
   ctx->stats.mvps += nc;
 
-  const bool persist = ctx->allow_persistent_cg && ctx->pgrid_cg > 0 && nc <= kPersistMaxCols;
+  ReorthRun scg;   // small real CSR problems: the one-launch CG with two barriers per iteration
+  if constexpr (std::is_same_v<T, double>) scg = small_cg_shape(ctx, nc);
+  const bool persist = scg.grid > 0 || (ctx->allow_persistent_cg && ctx->pgrid_cg > 0 && nc <= kPersistMaxCols);
   const GridSync g = grid_sync_bufs(ctx);
   const int L = 16;
   for (int round = 0;; ++round) {
@@ -920,6 +945,9 @@ seed_status cg_impl(seed_ctx *ctx, const T *Bc, int64_t ldb, T *Xc, int64_t ldx,
       if constexpr (sizeof(T) == sizeof(double2))
         e = launch_cg_run_wilson(ctx->wil, ctx->call, (double2 *)ctx->R, (double2 *)ctx->P, (double2 *)ctx->Q,
                                  (double2 *)ctx->T, ld, c, g, ctx->partials, ctx->pgrid_cg, ctx->cs);
+      else if (scg.grid > 0)
+        e = launch_cg_run_csr_small(ctx->csr, ctx->call, (double *)ctx->R, (double *)ctx->P, (double *)ctx->T,
+                                    (double *)ctx->Q, ld, c, g, ctx->partials, scg.rb, scg.grid, ctx->cs);
       else
         e = launch_cg_run_csr(ctx->csr, ctx->call, (double *)ctx->R, (double *)ctx->P, (double *)ctx->Q, ld, c, g,
                               ctx->partials, cg_csr_grid(ctx, nc), ctx->cs);
@@ -1546,6 +1574,7 @@ seed_status create_common(seed_ctx *ctx, const seed_params *p, seed_stream strea
   ctx->prm = *p;
   ctx->allow_persistent = p->kernel_path != 1;
   ctx->allow_persistent_cg = p->kernel_path == 2 && p->precision == 0;
+  ctx->allow_small_cg = p->kernel_path != 1;
   ctx->precision = p->precision;
   // mixed precision: persistent seed runs in FP32, no persistent CG
   CU(cudaGetDevice(&ctx->device));
@@ -2094,15 +2123,17 @@ seed_status seed_batch_solve(seed_ctx *const *ctxs, const void *const *B, const 
         st[i] = fail(c, SEED_ECUDA, "cudaSetDevice failed in a batch worker");
         continue;
       }
-      // persistent seed runs of different problems may run side by side (each
-      // waits only on its own blocks); the persistent CG stays off in a batch
-      const bool p0 = c->allow_persistent, p1 = c->allow_persistent_cg;
+      // persistent seed runs and small-problem CG runs of different problems may
+      // run side by side (each waits only on its own blocks, every wait is
+      // time-bounded); the full-grid persistent CG stays off in a batch
+      const bool p0 = c->allow_persistent, p1 = c->allow_persistent_cg, p2 = c->allow_small_cg;
       c->allow_persistent_cg = false;
       seed_info *inf = info ? info[i] : nullptr;
       st[i] = seed_solve_first(c, B[i], ldb[i], X[i], ldx[i], nrhs[i], inf);
       if (st[i] == SEED_OK) st[i] = seed_solve_rest(c, B[i], ldb[i], X[i], ldx[i], nrhs[i], inf);
       c->allow_persistent = p0;
       c->allow_persistent_cg = p1;
+      c->allow_small_cg = p2;
     }
   };
   std::vector<std::thread> pool;

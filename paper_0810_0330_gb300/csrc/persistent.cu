@@ -1315,6 +1315,215 @@ __global__ void __launch_bounds__(PT) k_cg_run_csr(CsrOp op, const CallArgs *cal
 }
 
 // ---------------------------------------------------------------------------
+// Lockstep CG on small real CSR problems (n <= kReorthRunMaxN, at most
+// kSmallCgCols columns): the row layout of k_seed_run_csr_reorth (block b owns
+// RB rows; here thread t of a block holds row t % RB of column slot t / RB),
+// each thread's matrix row kept in registers, and two grid barriers per
+// iteration instead of three: the direction update p = r + beta p of the
+// previous iteration is formed inside the apply, for the block's own rows
+// (written to the other of two p buffers) and, redundantly and with the same
+// arithmetic, for the neighbour rows the row reads -- so no barrier is needed
+// between the p update and the apply.  The first iteration of a launch takes
+// beta = 0 (p = r after the initialisation or a restart).
+//   apply: p = r + beta p (own rows), q = A p, partial p^H q
+//   barrier; every block: alpha_j = rho_j / (p^H q)_j
+//   update: x += alpha p, r -= alpha q, partial ||r||^2
+//   barrier; every block: the column's count, relres, stop test, beta, rho
+// Every block keeps its own shared-memory copy of the per-column scalars and
+// computes them from the same partials in the same order; block 0 writes them
+// to the CgCols arrays.  Arithmetic as in the step kernels (the same fma for p,
+// x and r; dot products in a different order).
+// ---------------------------------------------------------------------------
+constexpr int kSmallCgCols = 16;
+
+template <int RB>
+__global__ void __launch_bounds__(PT) k_cg_run_csr_small(CsrOp op, const CallArgs *call, double *R, double *P,
+                                                         double *P2, double *Q, int64_t ld, CgCols c, GridSync g,
+                                                         double *bpart) {
+  constexpr int kSlots = PT / RB;   // column slots per block
+  __shared__ double s_w[PT / 32][kRunRegion];
+  __shared__ double s_sum[kRunRegion];
+  __shared__ double s_part[kSmallCgCols][RB];
+  __shared__ double s_rho[kSmallCgCols], s_alpha[kSmallCgCols], s_beta[kSmallCgCols], s_bn[kSmallCgCols];
+  __shared__ int s_act[kSmallCgCols], s_it[kSmallCgCols], s_mv[kSmallCgCols];
+  __shared__ int s_any;
+  unsigned epoch = 0;
+  int reg = 0, par = 0;
+  const int nc = c.nc;   // <= kSmallCgCols (checked by the host)
+  const int G = gridDim.x;
+  const int64_t n = op.n;
+  const int rl = threadIdx.x % RB, slot = threadIdx.x / RB;
+  const int64_t row0 = (int64_t)blockIdx.x * RB;
+  const int rows = (int)(n - row0 < RB ? n - row0 : RB);
+  const int64_t e = row0 + rl;
+  const bool own = rl < rows;
+  double *const X = reinterpret_cast<double *>(call->X) + call->col0 * call->ldx;
+  const int64_t ldx = call->ldx;
+  constexpr int kRowCache = 8;
+  int32_t k0 = 0, k1 = 0, rc_col[kRowCache];
+  double rc_val[kRowCache];
+  if (own) {
+    k0 = __ldg(op.row_ptr + e);
+    k1 = __ldg(op.row_ptr + e + 1);
+  }
+  const bool cached = k1 - k0 <= kRowCache;
+#pragma unroll
+  for (int q = 0; q < kRowCache; ++q) {
+    const bool in = cached && q < k1 - k0;
+    rc_col[q] = in ? __ldg(op.col_idx + k0 + q) : 0;
+    rc_val[q] = in ? __ldg(op.vals + k0 + q) : 0.0;
+  }
+  for (int j = threadIdx.x; j < nc; j += PT) {
+    s_act[j] = __ldcg(c.active + j);
+    s_rho[j] = __ldcg(c.rho + j);
+    s_bn[j] = __ldcg(c.bnorm + j);
+    s_it[j] = __ldcg(c.iters + j);
+    s_mv[j] = __ldcg(c.mvps + j);
+    s_beta[j] = 0.0;
+  }
+  auto region = [&]() {
+    double *r = bpart + (int64_t)reg * G * kRunRegion;
+    reg ^= 1;
+    return r;
+  };
+  // per-column block sums of the threads' values (s_part[j][rl]) into a region row, then the grid sums
+  auto column_sums = [&](double *r) -> bool {
+    __syncthreads();
+    if ((int)threadIdx.x < nc) {
+      double t = 0.0;
+      for (int q = 0; q < RB; ++q) t += s_part[threadIdx.x][q];
+      r[(int64_t)blockIdx.x * kRunRegion + threadIdx.x] = t;
+    }
+    if (!grid_sync(g, epoch)) return false;
+    reduce_region(r, nc, s_sum);
+    return true;
+  };
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int j = 0; j < nc; ++j) any |= s_act[j];
+      s_any = any;
+    }
+    __syncthreads();
+    if (!s_any) break;
+    const double *Po = par ? P2 : P;
+    double *Pn = par ? P : P2;
+    // ---- p = r + beta p; q = A p; partial p^H q ----
+    for (int j0 = 0; j0 < nc; j0 += kSlots) {
+      const int j = j0 + slot;
+      if (j < nc) {
+        double pq = 0.0;
+        if (own && s_act[j]) {
+          const double be = s_beta[j];
+          const double *rj = R + j * ld, *pj = Po + j * ld;
+          double sum = 0.0;
+          if (cached) {
+            double xr[kRowCache], xp[kRowCache];
+#pragma unroll
+            for (int q = 0; q < kRowCache; ++q) {
+              xr[q] = q < k1 - k0 ? __ldcg(rj + rc_col[q]) : 0.0;
+              xp[q] = q < k1 - k0 ? __ldcg(pj + rc_col[q]) : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kRowCache; ++q)
+              if (q < k1 - k0) sum = fma(rc_val[q], fma(be, xp[q], xr[q]), sum);
+          } else {
+            for (int32_t q = k0; q < k1; ++q) {
+              const int32_t col = __ldg(op.col_idx + q);
+              sum = fma(__ldg(op.vals + q), fma(be, __ldcg(pj + col), __ldcg(rj + col)), sum);
+            }
+          }
+          const double pe = fma(be, __ldcg(pj + e), __ldcg(rj + e));
+          Pn[j * ld + e] = pe;
+          Q[j * ld + e] = sum;
+          pq = pe * sum;
+        }
+        s_part[j][rl] = pq;
+      }
+    }
+    if (!column_sums(region())) return;
+    if ((int)threadIdx.x < nc && s_act[threadIdx.x]) {
+      const int j = threadIdx.x;
+      s_alpha[j] = s_rho[j] / s_sum[j];
+      if (blockIdx.x == 0) c.alpha[j] = s_alpha[j];
+    }
+    __syncthreads();
+    // ---- x += alpha p; r -= alpha q; partial ||r||^2 ----
+    for (int j0 = 0; j0 < nc; j0 += kSlots) {
+      const int j = j0 + slot;
+      if (j < nc) {
+        double rr = 0.0;
+        if (own && s_act[j]) {
+          const double a = s_alpha[j];
+          const double pe = Pn[j * ld + e], qe = Q[j * ld + e];
+          X[j * ldx + e] = fma(a, pe, X[j * ldx + e]);
+          const double rn = fma(-a, qe, R[j * ld + e]);
+          R[j * ld + e] = rn;
+          rr = rn * rn;
+        }
+        s_part[j][rl] = rr;
+      }
+    }
+    if (!column_sums(region())) return;
+    if ((int)threadIdx.x < nc && s_act[threadIdx.x]) {
+      const int j = threadIdx.x;
+      const double rr = s_sum[j], rn = sqrt(rr), bn = s_bn[j];
+      const int it = s_it[j] + 1;
+      s_it[j] = it;
+      s_mv[j] += 1;
+      int act = 1, reached = 0, check = 0;
+      if (rn <= c.tol * bn) {
+        act = 0;
+        reached = 1;
+        check = 1;
+      } else if (it >= c.maxit || !isfinite(rr)) {   // non-finite: ends unconverged
+        act = 0;
+        check = 1;
+      } else {
+        s_beta[j] = rr / s_rho[j];
+        s_rho[j] = rr;
+      }
+      s_act[j] = act;
+      if (blockIdx.x == 0) {
+        c.iters[j] = it;
+        c.mvps[j] = s_mv[j];
+        c.relres[j] = bn > 0.0 ? rn / bn : 0.0;
+        c.beta[j] = s_beta[j];
+        c.rho[j] = s_rho[j];
+        if (!act) {
+          c.active[j] = 0;
+          if (reached) c.reached[j] = 1;
+          c.needs_check[j] = check;
+        }
+      }
+    }
+    par ^= 1;
+  }
+}
+
+int small_cg_grid_cap(int sm_count, int rb) {
+  int per_sm = 0;
+  const void *k = rb == 16 ? (const void *)k_cg_run_csr_small<16> : (const void *)k_cg_run_csr_small<32>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PT, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (per_sm > 2) per_sm = 2;
+  return per_sm * sm_count;
+}
+
+cudaError_t launch_cg_run_csr_small(const CsrOp &op, const CallArgs *call, double *R, double *P, double *P2,
+                                    double *Q, int64_t ld, const CgCols &c, GridSync g, double *bpart, int rb,
+                                    int grid, cudaStream_t s) {
+  CsrOp o = op;
+  CgCols cc = c;
+  void *args[] = {&o, &call, &R, &P, &P2, &Q, &ld, &cc, &g, &bpart};
+  const void *k = rb == 16 ? (const void *)k_cg_run_csr_small<16> : (const void *)k_cg_run_csr_small<32>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(PT), args, 0, s);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 // Up to 2 blocks per SM (3 for the seed runs, with the kernel bounded to fit,

@@ -323,6 +323,13 @@ cudaError_t launch_seed_run_wilson32(const SeedBufs<float2> &b, const WilsonOp32
 cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,
                                  double2 *tbuf, int64_t ld, const CgCols &c, GridSync g, double *bpart, int grid,
                                  cudaStream_t s);
+// Lockstep CG on small real CSR problems (n <= kReorthRunMaxN, nc <= 16): one
+// launch of ceil(n / rb) blocks, two grid barriers per iteration; P2 is a
+// second n x nc p buffer (ld).
+int small_cg_grid_cap(int sm_count, int rb);
+cudaError_t launch_cg_run_csr_small(const CsrOp &op, const CallArgs *call, double *R, double *P, double *P2,
+                                    double *Q, int64_t ld, const CgCols &c, GridSync g, double *bpart, int rb,
+                                    int grid, cudaStream_t s);
 cudaError_t launch_cg_run_csr(const CsrOp &op, const CallArgs *call, double *R, double *P, double *Q, int64_t ld,
                               const CgCols &c, GridSync g, double *bpart, int grid, cudaStream_t s);
 
