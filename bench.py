@@ -48,7 +48,8 @@ except (OSError, ValueError):
     MEASURED_PEAKS = {}
 # DRAM bytes of one k_dslash launch (8^4, 11 columns) from the ncu capture of these sources of the
 # kernel; reported only while the source is unchanged.
-DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0, "6e70bd4a297626c1": 11.207424e6 + 0.0}
+DSLASH_TRAFFIC = {"fa1e067f137fcf97": 11.207168e6 + 0.0, "6e70bd4a297626c1": 11.207424e6 + 0.0,
+                 "ea8d71246ee34395": 11.207424e6 + 0.0}
 # The same for k_dslash32_site<+1> (FP32, 16^3 x 32, 11 columns), from the ncu capture of its sources
 DSLASH32_TRAFFIC = {"7a583b64681e7245": 189.553920e6 + 104.930304e6}
 DSLASH32_TRAFFIC_DIMS = (16, 16, 16, 32)

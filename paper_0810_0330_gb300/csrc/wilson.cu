@@ -55,17 +55,18 @@ void launch_wilson_neighbors(const int32_t dims[4], int32_t *nbr, cudaStream_t s
 }
 
 
-// Grid: one block per (32-site tile, column), the column fastest, so that the
-// columns of one tile run together and its links are read from DRAM once per
-// launch even when the links do not fit in L2 (with the column slowest every
-// column re-read them: 2.3x the algorithmic DRAM bytes at 24^4 x 11 columns).
-template <int S, class C>
+// Grid: one block per (32-site tile, column), the column fastest (blockIdx.x,
+// tiles on blockIdx.y) while the tiles fit in gridDim.y, so that the columns of
+// one tile run together and its links are read from DRAM once per launch even
+// when the links do not fit in L2 (with the column slowest every column re-read
+// them: 2.3x the algorithmic DRAM bytes at 24^4 x 11 columns).
+template <int S, bool COLX, class C>
 __global__ void __launch_bounds__(128) k_dslash(WilsonOpT<C> op, const C *__restrict__ in, int64_t ldi,
                                                 C *__restrict__ out, int64_t ldo,
-                                                const int32_t *__restrict__ col_active, int ncols) {
+                                                const int32_t *__restrict__ col_active) {
   using R = typename CxBits<C>::R;
-  const int64_t tile = (int64_t)blockIdx.x / ncols;
-  const int col = (int)(blockIdx.x - tile * ncols);
+  const int64_t tile = COLX ? blockIdx.y : blockIdx.x;
+  const int col = COLX ? blockIdx.x : blockIdx.y;
   if (col_active != nullptr && col_active[col] == 0) return;
   in += (int64_t)col * ldi;
   out += (int64_t)col * ldo;
@@ -87,9 +88,16 @@ __global__ void __launch_bounds__(128) k_dslash(WilsonOpT<C> op, const C *__rest
 void launch_wilson_dslash(const WilsonOp &op, int sign, const double2 *in, int64_t ldi, double2 *out, int64_t ldo,
                           int ncols, const int32_t *col_active, cudaStream_t s) {
   if (ncols < 1) return;
-  const unsigned grid = (unsigned)((op.sites + kWilsonSites - 1) / kWilsonSites * ncols);
-  if (sign > 0) k_dslash<+1><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
-  else k_dslash<-1><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active, ncols);
+  const int64_t tiles = (op.sites + kWilsonSites - 1) / kWilsonSites;
+  if (tiles <= 65535) {
+    const dim3 grid((unsigned)ncols, (unsigned)tiles);
+    if (sign > 0) k_dslash<+1, true><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);
+    else k_dslash<-1, true><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);
+  } else {
+    const dim3 grid((unsigned)tiles, (unsigned)ncols);
+    if (sign > 0) k_dslash<+1, false><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);
+    else k_dslash<-1, false><<<grid, 128, 0, s>>>(op, in, ldi, out, ldo, col_active);
+  }
 }
 
 }  // namespace seedk
