@@ -86,6 +86,29 @@ def test_wilson_apply_matches_oracle(seedlib, orc, dims, bc_t):
             assert err < 1e-13, (op, j, err)
 
 
+def test_wilson_apply_past_grid_y_limit(seedlib, orc):
+    """8x8x8x4096 = 2^21 sites = 65536 tiles of 32, one more than a grid's y
+    extent: the hopping kernel runs its (tile, column) grid with the tile on x
+    (the other order); D and D^H on two columns against the oracle.  The links
+    are 64 random t-slices repeated (the kernel's indexing does not care)."""
+    dims, kappa = (8, 8, 8, 4096), 0.155
+    U = np.ascontiguousarray(np.tile(I.random_su3_links((8, 8, 8, 64), 0.3, seed=2), (1, 64, 1, 1)))
+    n = 12 * I.lattice_sites(dims)
+    ctx = wilson_ctx(seedlib, dims, kappa, U, bc_t=1, m_max=4)
+    X = I.gaussian_rhs(n, 2, seed=6, complex_=True)
+    Xd = dev_cols(X)
+    Yd = dev_cols(np.zeros_like(X))
+    for op, sign, cols in ((1, +1, (0, 1)), (2, -1, (1,))):
+        seedlib.seed_apply(ctx, op, Xd, Yd)
+        torch.cuda.synchronize()
+        Y = host_cols(Yd)
+        for j in cols:
+            ref = orc.wilson_dslash(dims, kappa, 1, sign, U, X[:, j])
+            err = np.abs(Y[:, j] - ref).max() / np.abs(ref).max()
+            assert err < 1e-13, (op, j, err)
+    seedlib.seed_destroy(ctx)
+
+
 def test_csr_apply_matches_oracle(seedlib, orc):
     rp, ci, v = I.laplacian_2d_csr(37, 29)
     n = 37 * 29
