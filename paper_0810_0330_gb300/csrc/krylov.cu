@@ -641,11 +641,11 @@ void launch_reorth(const SeedBufs<T> &b, const ReorthBufs<T> &r, int passes, cud
   for (int p = 0; p < passes; ++p) {
     if (rows) {
       const size_t smem = 2 * sizeof(T) * (size_t)r.row_chunk;
-      static bool attr = false;   // per instantiation: allow up to 2 x 8192 FP32 complex rows
-      if (!attr) {
-        cudaFuncSetAttribute(k_reorth_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(T) * 8192);
-        attr = true;
-      }
+      // once per instantiation (thread-safe static initialisation: batch workers launch concurrently):
+      // allow up to 2 x 8192 rows of shared memory
+      static const cudaError_t attr =
+          cudaFuncSetAttribute(k_reorth_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (int)sizeof(T) * 8192);
+      (void)attr;   // a failure shows as the launch's error
       k_reorth_rows<T><<<nchunks, kRowThreads, smem, s>>>(b, r, r.Hrows);
       k_reorth_rows_reduce<T><<<(2 * r.kcap + NT / 32 - 1) / (NT / 32), NT, 0, s>>>(b, r, r.Hrows, nchunks);
     } else {

@@ -48,23 +48,27 @@ unsigned long long g_scratch_ctx[kMaxDevices] = {};
 // library needs no link to the driver library.  0 when unavailable.
 typedef int (*PfnCtxGetCurrent)(void **);
 typedef int (*PfnCtxGetId)(void *, unsigned long long *);
+struct CtxFns {
+  PfnCtxGetCurrent get_current = nullptr;
+  PfnCtxGetId get_id = nullptr;
+};
 unsigned long long current_context_id() {
-  static PfnCtxGetCurrent get_current = nullptr;
-  static PfnCtxGetId get_id = nullptr;
-  static bool looked_up = false;
-  if (!looked_up) {
+  static const CtxFns fns = [] {   // looked up once (thread-safe static initialisation)
+    CtxFns r;
     cudaDriverEntryPointQueryResult q1, q2;
     void *f1 = nullptr, *f2 = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
         q1 == cudaDriverEntryPointSuccess &&
         cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
         q2 == cudaDriverEntryPointSuccess) {
-      get_current = (PfnCtxGetCurrent)f1;
-      get_id = (PfnCtxGetId)f2;
+      r.get_current = (PfnCtxGetCurrent)f1;
+      r.get_id = (PfnCtxGetId)f2;
     }
     cudaGetLastError();
-    looked_up = true;
-  }
+    return r;
+  }();
+  const PfnCtxGetCurrent get_current = fns.get_current;
+  const PfnCtxGetId get_id = fns.get_id;
   if (!get_current || !get_id) return 0;
   void *ctx = nullptr;
   unsigned long long id = 0;

@@ -492,17 +492,16 @@ typedef CUresult (*PfnEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 PfnEncodeTiled encode_fn() {
-  static PfnEncodeTiled fn = nullptr;
-  static bool looked = false;
-  if (!looked) {
+  static const PfnEncodeTiled fn = [] {   // looked up once (thread-safe static initialisation)
     void *p = nullptr;
+    PfnEncodeTiled f = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PfnEncodeTiled)p;
+      f = (PfnEncodeTiled)p;
     cudaGetLastError();
-    looked = true;
-  }
+    return f;
+  }();
   return fn;
 }
 }  // namespace
@@ -533,26 +532,24 @@ bool tc_make_maps(CUtensorMap maps[tc::kBoxes], const void *base, int64_t len, i
 }
 
 int tc_grid(int64_t len) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess || sms < 1)
-      sms = 148;
+  static const int sms = [] {   // thread-safe static initialisation
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || v < 1)
+      v = 148;
     cudaGetLastError();
-  }
+    return v;
+  }();
   const int64_t chunks = len / tc::kChunk;
   return (int)(chunks < sms ? chunks : sms);
 }
 
 cudaError_t launch_blk_dots_tc(const TcMaps &maps, const SeedState *st, int len_host, int vcol_host, int nj,
                                int64_t len, double2 *Hpart, int grid, int *err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_blk_dots_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // once (thread-safe static initialisation: batch workers launch concurrently)
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_blk_dots_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+  if (attr != cudaSuccess) return attr;
   const int ytiles = (kSeedBlock + tc::kSteps - 1) / tc::kSteps;   // idle tiles leave at once
   const int ztiles = (nj + tc::kCols - 1) / tc::kCols;
   k_blk_dots_tc<<<dim3((unsigned)grid, (unsigned)ytiles, (unsigned)ztiles), tc::kThreads, tc::kSmemBytes, s>>>(
