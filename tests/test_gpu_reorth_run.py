@@ -64,3 +64,33 @@ def test_reorth_run_agrees_with_step_kernels(seedlib):
     x0, x1 = out[0][1], out[1][1]
     assert np.linalg.norm(x0[:, 0] - x1[:, 0]) <= 1e-10 * np.linalg.norm(x1[:, 0])
     assert np.linalg.norm(x0[:, 1:] - x1[:, 1:]) <= 1e-8 * np.linalg.norm(x1[:, 1:])
+
+
+def test_reorth_run_stops_at_mmax_and_on_indefinite(seedlib, orc):
+    """The one-launch run's other stops: m_max reached (20 steps of a 300-entry
+    diagonal, reorthogonalization every 2 steps, one right-hand side and two),
+    x^1 as the oracle's after the same 20 steps; an indefinite matrix makes
+    delta_i <= 0 inside the launch: SEED_ENOTSPD, not a fault."""
+    from test_gpu_parity import dev_cols, seeded_only_sensitivity, relerr
+    d = np.linspace(0.01, 1.0, 300)
+    rp, ci, v = I.diagonal_csr(d)
+    op = orc.Operator.csr(rp, ci, v)
+    for nrhs in (1, 2):
+        B = I.gaussian_rhs(300, nrhs, seed=1)
+        ctx = csr_ctx(seedlib, rp, ci, v, m_max=20, reorth_freq=2, tol_seed=1e-12)
+        info1, _, _, X = run_gpu(seedlib, ctx, B, rest=False)
+        assert info1[0]["iters"] == 20 and info1[0]["converged"] == 0
+        ref = orc.seed_first(op, B, m_max=20, reorth_freq=2, tol=1e-12)
+        assert relerr(X[:, 0].real, ref["X"][:, 0].real) < REL_X
+        if nrhs > 1:
+            sens = seeded_only_sensitivity(orc, op, B, m_max=20, reorth_freq=2, tol=1e-12)
+            assert relerr(X[:, 1:].real, ref["X"][:, 1:].real) < max(REL_X, 10 * sens)
+        seedlib.seed_destroy(ctx)
+    dn = d.copy()
+    dn[:150] *= -1.0
+    ctx2 = csr_ctx(seedlib, *I.diagonal_csr(dn), m_max=300, reorth_freq=1)
+    B = I.gaussian_rhs(300, 2, seed=1)
+    with pytest.raises(seedlib.SeedError) as e:
+        seedlib.seed_solve_first(ctx2, dev_cols(B), dev_cols(np.zeros_like(B)))
+    assert e.value.status == seedlib.SEED_ENOTSPD
+    seedlib.seed_destroy(ctx2)
