@@ -122,7 +122,10 @@ typedef struct {
                              frequency is 0 or >= 8; in mixed precision for CSR and for Wilson
                              lattices below 65536 sites), everything else as step kernels
                              replayed from CUDA graphs, the lockstep CG in up to three concurrent
-                             column branches;
+                             column branches; small real CSR problems in FP64 (n <= 9728) run
+                             the whole seed run as one cooperative kernel when the frequency is
+                             1 to 7 and nrhs <= 16, and their lockstep CG as one cooperative
+                             kernel when at most 16 systems remain;
                              1: step kernels only;
                              2: as 0, and FP64 CG in one persistent kernel as well (nrhs <= 33).
                              With two or more systems and a frequency of 0 or >= 8 the seeding of
@@ -348,11 +351,11 @@ seed_status seed_get_stats(const seed_ctx *ctx, seed_stats *out);
  * problems overlap on the GPU instead of running one after another.  The
  * contexts must be distinct and must not be used by other threads meanwhile.
  * Each problem runs the arithmetic of a solo solve on its context: the
- * persistent seed runs of kernel_path 0 and 2 run side by side (each waits
- * only on its own blocks), while the persistent FP64 CG of kernel_path 2 is
- * replaced inside a batch by the graph-replayed CG of kernel_path 0.  So each
- * problem's results are bitwise those of a solo solve with its kernel_path (0
- * for a kernel_path 2 context).  Returns SEED_OK, or the
+ * persistent seed runs of kernel_path 0 and 2 and the one-launch CG of small
+ * CSR problems run side by side (each waits only on its own blocks), while
+ * the persistent FP64 CG of kernel_path 2 is replaced inside a batch by the
+ * CG of kernel_path 0.  So each problem's results are bitwise those of a solo
+ * solve with its kernel_path (0 for a kernel_path 2 context).  Returns SEED_OK, or the
  * status of the first failing problem (in problem order; the others still
  * run), with seed_last_error(NULL) naming it. */
 seed_status seed_batch_solve(seed_ctx *const *ctxs, const void *const *B, const int64_t *ldb, void *const *X,
