@@ -834,35 +834,35 @@ SEED_DEV void slice_reduce(const double *hpart, int k, double *H) {
   }
 }
 
-// sub[v][r] = sum over c < k of V[c][row0 + r] H[2 c + v] (threads over columns, then the block)
+// sub[v][r] = sum over c < k of V[c][row0 + r] H[2 c + v]: thread (r, g) of the
+// block (r = t mod RB, g = t / RB) sums the columns c = g, g + G, ... (G = PT /
+// RB groups) of row r, then each output adds its G group sums in group order --
+// G - 1 FP64 adds per output instead of a 31-add warp reduce-scatter per lane
+// (FP64 adds run at 2 per clock per SM on this part).
 template <int RB>
 SEED_DEV void rows_times_h(const double *V, int64_t ldv, int64_t row0, int rows, int k, const double *H,
                            double (*sub)[RB], double (*sred)[2 * RB]) {
-  double p[2 * RB];
-#pragma unroll
-  for (int q = 0; q < 2 * RB; ++q) p[q] = 0.0;
-  for (int c = threadIdx.x; c < k; c += PT) {
-    const double *vc = V + (int64_t)c * ldv + row0;
-    const double hv = __ldcg(H + 2 * c), hf = __ldcg(H + 2 * c + 1);
-#pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const double x = r < rows ? vc[r] : 0.0;
-      p[r] = fma(x, hv, p[r]);
-      p[RB + r] = fma(x, hf, p[RB + r]);
+  constexpr int kGroups = PT / RB;
+  const int r = threadIdx.x % RB, grp = threadIdx.x / RB;
+  double pv = 0.0, pf = 0.0;
+  if (r < rows) {
+    const double *vr = V + row0 + r;
+#pragma unroll 4
+    for (int c = grp; c < k; c += kGroups) {
+      const double x = vr[(int64_t)c * ldv];
+      pv = fma(x, __ldcg(H + 2 * c), pv);
+      pf = fma(x, __ldcg(H + 2 * c + 1), pf);
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int h = 0; h < 2 * RB; h += 32) {
-    double v32[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v32[q] = p[h + q];
-    sred[warp][h + lane] = warp_reduce_scatter32(v32);
-  }
+  sred[grp][r] = pv;
+  sred[grp][RB + r] = pf;
   __syncthreads();
   if ((int)threadIdx.x < 2 * RB) {
     const int q = threadIdx.x;
-    sub[q / RB][q % RB] = ((sred[0][q] + sred[1][q]) + sred[2][q]) + sred[3][q];
+    double t = sred[0][q];
+#pragma unroll
+    for (int g2 = 1; g2 < kGroups; ++g2) t += sred[g2][q];
+    sub[q / RB][q % RB] = t;
   }
   __syncthreads();
 }
@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr_reorth(SeedBufs<double> b, 
   __shared__ double2 s_eta[kRunMaxRhs];
   __shared__ double s_y[2][RB];
   __shared__ double s_sub[2][RB];
-  __shared__ double s_red[PT / 32][2 * RB];
+  __shared__ double s_red[PT / RB][2 * RB];
   __shared__ LocalSeed L;
   unsigned epoch = 0;
   int par = 0, reg = 0;
