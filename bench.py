@@ -116,7 +116,7 @@ def parse():
                     help="forward + backward of the differentiable solve: 16^4, kappa 0.150, 8 Gaussian b and t")
     ap.add_argument("--reorth-freq", type=int, default=None, help="reorthogonalization frequency for --adjoint")
     ap.add_argument("--reliable-delta", type=float, default=0.0,
-                    help="mixed precision: reliable-update threshold (0: the library default, 0.01)")
+                    help="mixed precision: reliable-update threshold (0: the library default, 0.001)")
     ap.add_argument("--sweep", action="store_true",
                     help="operator-apply bandwidth sweep (CSR Laplacian and Wilson D at growing sizes)")
     ap.add_argument("--sweep-max", type=int, default=3, help="sweep points per operator (1..4)")
@@ -797,7 +797,7 @@ def run_ours(args):
     if rank == 0:
         cfg = workload_config(dims, args.sources, mixed, world, m_max)
         if mixed:
-            cfg["reliable_delta"] = args.reliable_delta or 0.01
+            cfg["reliable_delta"] = args.reliable_delta or 0.001
         if secondary is not None:
             cfg["secondary"] = secondary
         if lap is not None:

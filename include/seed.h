@@ -151,7 +151,7 @@ typedef struct {
   double reliable_delta;  /* mixed only: a reliable update is made when the FP32 recursive residual
                              has fallen below reliable_delta times its value at the last update
                              (checked every 16 iterations), and whenever it meets the tolerance;
-                             0 selects 0.01.  Range [0, 1). */
+                             0 selects 0.001.  Range [0, 1). */
 } seed_params;
 
 /* Per right-hand side results. */

@@ -863,7 +863,7 @@ CgCols cg_cols(seed_ctx *ctx, int nc) {
   // default: a reliable update every two decades of the FP32 recursive residual
   // (16^3 x 32 mixed workload: 171 CG iterations per system at 0.1, 0.03 and
   // 0.01 alike, and 164 -> 155 ms as the FP64 operator runs less often)
-  c.delta = ctx->prm.reliable_delta > 0.0 ? ctx->prm.reliable_delta : 0.01;
+  c.delta = ctx->prm.reliable_delta > 0.0 ? ctx->prm.reliable_delta : 0.001;
   return c;
 }
 

@@ -170,7 +170,7 @@ def test_fp32_csr_apply(seedlib, orc):
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("nrhs", [2, 4])
-@pytest.mark.parametrize("delta", [0.0, 0.1])   # 0: the default, 0.01
+@pytest.mark.parametrize("delta", [0.0, 0.1])   # 0: the default, 0.001
 def test_mixed_laplacian_64(seedlib, orc, nrhs, delta):
     """64x64 Laplacian, Gaussian RHS (seed 0), seed to 1e-12 with full
     reorthogonalization; nrhs = 2 makes system 1's refinement and the rest
