@@ -1,5 +1,5 @@
-"""The paper's Table 3.1 experiment (Sec. 3, Examples 4 and 5) run through the
-library on the GPU, against the oracle on the same draw: the Example 1
+"""The paper's experiments with printed numbers, run through the library on the
+GPU.  Table 3.1 (Sec. 3, Examples 4 and 5) against the oracle on the same draw: the Example 1
 diagonal matrix (n = 5000, entries U[0,1] sorted; the paper's draw is not
 given, seed 0 here), two N(0,1) right-hand sides; the first system is run for
 exactly m Lanczos steps (tolerance 0, m_max = m) with a reorthogonalization
@@ -48,3 +48,35 @@ def test_table3_1_second_system_counts(seedlib, orc):
     for m, got in zip((1000, 1500), counts[1:]):
         paper = g["second_reorth_freq50"][g["first_mvps"].index(m)]
         assert paper / 2 <= got <= 2 * paper, (m, got, paper)
+
+
+def test_table2_1_single_seeding_saves_mvps(seedlib, orc):
+    """Table 2.1 (Sec. 2.2, Example 2): with single seeding the 8 right-hand
+    sides of Example 1 need far fewer matrix-vector products than CG on each
+    (the paper: 2439 against 4935).  On the GPU, same draw as the oracle (seed
+    0 matrix, seed 100 right-hand sides), tolerance 1e-8 for all systems, no
+    reorthogonalization: the seed system takes the oracle's step count, the
+    plain-CG counts match the oracle's within 5 %, and the single-seeding total
+    is below 0.85 of the no-seeding total (the oracle's pin over 4 draws)."""
+    n = 5000
+    rp, ci, v = I.diagonal_csr(I.paper_diagonal(n, seed=0))
+    B = I.gaussian_rhs(n, 8, seed=100)
+    op = orc.Operator.csr(rp, ci, v)
+    ctx = csr_ctx(seedlib, rp, ci, v, m_max=5000, reorth_freq=0, tol_seed=1e-8, tol_rest=1e-8)
+    info1, info2, _, _ = run_gpu(seedlib, ctx, B)
+    ref = orc.seed_solve_all(op, B, m_max=5000, reorth_freq=0, tol_seed=1e-8, tol_rest=1e-8)
+    assert info1[0]["iters"] == ref["seed"]["iters"]
+    single = info1[0]["iters"] + sum(i["iters"] for i in info2[1:])
+    assert all(i["converged"] for i in info2[1:])
+    # no seeding: CG on every system from zero
+    from test_gpu_parity import dev_cols, host_cols
+    import torch
+    Bd, Xd = dev_cols(B), dev_cols(np.zeros_like(B))
+    cg = seedlib.seed_solve_cg(ctx, Bd, Xd)
+    torch.cuda.synchronize()
+    none = sum(i["iters"] for i in cg)
+    for j in range(8):
+        r = orc.cg(op, B[:, j], np.zeros(n), tol=1e-8)
+        assert abs(cg[j]["iters"] - r["iters"]) <= max(2, 0.05 * r["iters"]), (j, cg[j]["iters"], r["iters"])
+    assert single < 0.85 * none, (single, none)
+    seedlib.seed_destroy(ctx)
