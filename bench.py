@@ -38,6 +38,11 @@ WORKLOAD_NAME = "wilson-dirac 8^4 kappa=0.155 A=D^H D, 12 point sources, seed to
 # The epilogue psi - kappa * sum adds 48 more, which the roofline reports separately.
 FLOPS_PER_SITE_D = 1320
 FLOPS_PER_SITE_D_EPILOGUE = 48
+# FP64 instructions the kernel issues per site (each a full FMA slot whether it is an FMA, a multiply
+# or an add): 4 directions x (84 + 96) for the fused hop pairs, 72 adds combining the four direction
+# partials, 24 FMAs of psi - kappa * sum.  1320 counted flops over 2 x 816 slots: the kernel cannot
+# exceed 0.809 of the unit-count peak.
+FP64_INSTR_PER_SITE_D = 816
 # FP64 peak from unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (the library's FMA-chain
 # probe, seed_time_fma, measures it live next to the roofline)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
@@ -503,6 +508,10 @@ def dslash_roofline(S, ctx, vol, mixed, dims, ncols_total):
                                             (k_ms * 1e-3) / 1e12 / peak, 4),
                 "launch_shapes": {"cg_branches": shapes, "per_shape": shape_t},
                 "peak_note": "FP64 pipe from unit counts: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                "fp64_instructions_per_site": FP64_INSTR_PER_SITE_D,
+                "instruction_mix_ceiling": round(FLOPS_PER_SITE_D / (2.0 * FP64_INSTR_PER_SITE_D), 4),
+                "frac_of_instruction_mix_ceiling": round(achieved / peak / (FLOPS_PER_SITE_D /
+                                                                             (2.0 * FP64_INSTR_PER_SITE_D)), 4),
                 "peak_measured_probe": round(probe, 4), "frac_of_probe": round(achieved / probe, 4),
                 "probe": "seed_time_fma(SEED_F64): FMA chains over the whole GPU, this run",
                 "fp64_matrix_probe": {k: round(v, 4) for k, v in S.seed_time_fp64_paths().items()}}

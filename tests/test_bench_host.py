@@ -24,6 +24,14 @@ def test_algorithmic_bytes_and_flops_per_unit():
     # accumulated spinor (the first one stores); the reconstruction is sign changes only
     assert 8 * (12 + 2 * (9 * 6 + 6 * 2)) + 7 * 24 == bench.FLOPS_PER_SITE_D
     assert abs(bench.FP64_PEAK_GFLOPS - 1258.56) < 1e-9
+    # the FP64 instructions the kernel issues per site: per direction the forward hop (12 adds of
+    # the projection, 3 rows x 2 spins of one complex multiply (4 instructions) and two complex
+    # FMAs (8) = 72) and the backward hop chained onto it (12 adds, 18 complex FMAs = 72, and the
+    # lower half as 12 FMAs of 2 x forward - phase(upper)); 3 adds per real component to combine
+    # the four direction partials (72) and 24 FMAs of psi - kappa * sum
+    fwd = 12 + 3 * 2 * (4 + 2 * 4)
+    bwd = 12 + 18 * 4 + 12
+    assert 4 * (fwd + bwd) + 3 * 24 + 24 == bench.FP64_INSTR_PER_SITE_D == 816
 
 
 def test_cg_branch_columns():
