@@ -268,7 +268,7 @@ seed_status alloc_common(seed_ctx *ctx) {
   // cudaMalloc memory may hold an earlier allocation's bytes
   CU(cudaMemsetAsync(ctx->gsync, 0, sizeof(unsigned) * kGridSyncWords, ctx->cs));
   TRY(dalloc(ctx, &ctx->f2, n * es));
-  TRY(dalloc(ctx, &ctx->tpart, sizeof(double) * (size_t)(3 * ((n / 12 + 31) / 32) + 3)));
+  TRY(dalloc(ctx, &ctx->tpart, sizeof(double) * (size_t)(12 * ((n / 12 + 31) / 32) + 3)));
   CU(cudaMallocHost(&ctx->h_gerr, sizeof(int32_t) * 2));
   CU(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
   int coop = 0;

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NT) k_seed_update(SeedBufs<T> b) {
   }
   for (int j = threadIdx.x; j < nx; j += NT) s_eta[j] = Sc<T>::from2(b.eta[j]);
   __syncthreads();
-  const double a = st->alpha, zeta = st->zeta, inv_d = 1.0 / st->delta, bp = st->beta_prev;
+  const double a = st->alpha, zeta = st->zeta, inv_d = st->inv_delta, bp = st->beta_prev;
   const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
   const int64_t ldx = b.call->ldx;
   T *const X = reinterpret_cast<T *>(b.call->X);

@@ -365,18 +365,91 @@ SEED_DEV double2 warp_sum_partial_pairs(const double *partial, int nb) {
   return c2(warp_sum(tx), warp_sum(ty));
 }
 
-// tpart: 3 x tiles doubles (phase-1 pairs, then the phase-2 norms)
+// The two values of every lane summed over the warp, both returned to every
+// lane: the first level trades halves (lanes < 16 keep x, the others y), so
+// each lane adds 5 times instead of 10.  Fixed order, deterministic.
+SEED_DEV double2 warp_sum_pair(double x, double y) {
+  const bool hi = (threadIdx.x & 16) != 0;
+  double keep = hi ? y : x;
+  keep += __shfl_xor_sync(0xffffffffu, hi ? x : y, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  return c2(__shfl_sync(0xffffffffu, keep, 0), __shfl_sync(0xffffffffu, keep, 16));
+}
+
+// Resident form of the run, used when every owner block holds at most one tile
+// (lattices with no more 32-site tiles than SMs, e.g. 8^4 with 128 tiles): the
+// tile's links (both hops of each direction) stay in shared memory and its
+// neighbour indices and boundary signs in registers for the whole run, and the
+// tile's own elements of f, t, w_i, x^1, v_i and v_{i-1} are kept in shared
+// memory, so that after each grid barrier only the neighbours' spinors come
+// from L2.  f, t and v_i still go to global memory every step (other blocks'
+// stencils read f and t, V keeps the basis); x^1 and w_i are written back when
+// the run ends.  Links: s_lnk[(mu * 18 + k) * 32 + lane], k < 9 the forward
+// link U_mu(s), k >= 9 the backward link U_mu(s - mu); vectors:
+// s_vec[slot * 384 + o] with o = 12 * (site in tile) + component.
+constexpr int kResLinks = 4 * 18 * kWilsonSites;
+constexpr int kResTile = 12 * kWilsonSites;
+enum { kResF = 0, kResT = 1, kResW = 2, kResX = 3, kResV = 4 };   // kResV + (i & 1): v_i
+constexpr size_t kResSmemBytes = (size_t)(kResLinks + 6 * kResTile) * sizeof(double2);
+
+template <int MU, int S>
+SEED_DEV void site_mu_res(const double2 *in, int32_t nf, int32_t nb, unsigned long long negf,
+                          unsigned long long negb, const double2 *su, double2 (&acc)[12]) {
+  double2 pf[12], pb[12], uf[9], ub[9];
+  const double2 *psf = in + 12 * (int64_t)nf, *psb = in + 12 * (int64_t)nb;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) pf[k] = psf[k];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) pb[k] = psb[k];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) uf[k] = su[k * 32];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ub[k] = su[(9 + k) * 32];
+  hop_pair_r<MU, S>(pf, uf, negf, pb, ub, negb, acc);
+}
+
+// wilson_tile4 with the links, indices and signs resident (live: the site exists)
+template <int S>
+SEED_DEV void wilson_tile4_res(const double2 *in, int32_t nf, int32_t nb, unsigned long long negf,
+                               unsigned long long negb, bool live, const double2 *s_lnk,
+                               double (*sacc)[24][kWilsonSites + 1]) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const double2 *su = s_lnk + mu * 18 * 32 + lane;
+  double2 acc[12];
+  if (live) {
+    switch (mu) {
+      case 0: site_mu_res<0, S>(in, nf, nb, negf, negb, su, acc); break;
+      case 1: site_mu_res<1, S>(in, nf, nb, negf, negb, su, acc); break;
+      case 2: site_mu_res<2, S>(in, nf, nb, negf, negb, su, acc); break;
+      default: site_mu_res<3, S>(in, nf, nb, negf, negb, su, acc); break;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = c2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    sacc[mu][2 * k][lane] = acc[k].x;
+    sacc[mu][2 * k + 1][lane] = acc[k].y;
+  }
+  tile_warps_sync();
+}
+
+// tpart: 12 x tiles doubles -- per tile warp (4 per tile) the phase-1 pairs,
+// then the phase-2 norms; each tile warp sums its lanes and lane 0 stores, and
+// the scalar warp of every block sums all of them in (tile, warp) order.
 __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, WilsonOp op, double2 *tbuf,
                                                           GridSync g, double *bpart, double *tpart, int i_stop) {
   __shared__ double sacc[4][24][kWilsonSites + 1];
-  __shared__ double s_red[2 * (PTW / 32)];
   __shared__ LocalSeed L;
+  extern __shared__ double2 s_dyn[];
   (void)bpart;
   const int64_t sites = op.sites;
   const int tiles = (int)((sites + kWilsonSites - 1) / kWilsonSites);
   const double kappa = op.kappa;
-  double *part1 = tpart, *part2 = tpart + 2 * (int64_t)tiles;
-  const int warp = threadIdx.x >> 5;
+  double *part1 = tpart, *part2 = tpart + 8 * (int64_t)tiles;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool tw = warp < 4;            // tile warp; warp 4 is the scalar warp
   unsigned epoch = 0;
   local_load(b, L);
@@ -385,6 +458,46 @@ __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, Wi
   if (!register_owner(g, epoch, own)) return;
   double2 *const X = reinterpret_cast<double2 *>(b.call->X);
   const int first_tile = own.rank >= 0 && own.rank < tiles ? own.rank : -1;
+  // resident form: one tile per owner block
+  const bool res = tiles <= own.count && first_tile >= 0;
+  double2 *const s_lnk = s_dyn;
+  double2 *const s_vec = s_dyn + kResLinks;
+  int32_t r_nf = 0, r_nb = 0;
+  unsigned long long r_negf = 0, r_negb = 0;
+  const int64_t r_site = (int64_t)(first_tile >= 0 ? first_tile : 0) * kWilsonSites + lane;
+  const bool r_live = r_site < sites;
+  if (res) {
+    const int64_t e0 = (int64_t)first_tile * kResTile;
+    const int i0 = L.st.i;
+    if (tw && r_live) {
+      const int mu = warp;
+      r_nf = __ldg(op.nbr + 8 * r_site + 2 * mu);
+      r_nb = __ldg(op.nbr + 8 * r_site + 2 * mu + 1);
+      if (mu == 3 && op.bc_t) {
+        const int64_t t = r_site / ((int64_t)op.dims[0] * op.dims[1] * op.dims[2]);
+        if (t == op.dims[3] - 1) r_negf = CxBits<double2>::sign;
+        if (t == 0) r_negb = CxBits<double2>::sign;
+      }
+      const double2 *Uf = op.links + ((int64_t)mu * sites + r_site) * 9;
+      const double2 *Ub = op.links + ((int64_t)mu * sites + r_nb) * 9;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        s_lnk[(mu * 18 + k) * 32 + lane] = __ldg(Uf + k);
+        s_lnk[(mu * 18 + 9 + k) * 32 + lane] = __ldg(Ub + k);
+      }
+    }
+    const double2 *vprev = b.V + (int64_t)(i0 > 1 ? i0 - 2 : 0) * b.ldv;
+    for (int o = threadIdx.x; o < kResTile; o += PTW) {
+      const int64_t e = e0 + o;
+      if (e < b.n) {
+        s_vec[kResF * kResTile + o] = b.f[e];
+        s_vec[kResW * kResTile + o] = i0 > 1 ? b.w[e] : c2(0.0, 0.0);
+        s_vec[kResX * kResTile + o] = X[e];
+        s_vec[(kResV + ((i0 - 1) & 1)) * kResTile + o] = i0 > 1 ? vprev[e] : c2(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+  }
   bool pending_beta = false;           // the end of the previous step (beta_{i-1}) is still to run
   for (;;) {
     // ---- phase 1 of step i, overlapped with the end of step i-1 ----
@@ -393,9 +506,12 @@ __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, Wi
       const int ip = L.st.i + (pending_beta ? 1 : 0);
       const bool go = L.st.active && ip < i_stop && (b.Wb == nullptr || ip - L.st.blk0 < kSeedBlock);
       __syncthreads();                 // everyone has read L.st before the scalar warp updates it
-      if (tw && go && first_tile >= 0) wilson_tile4<+1>(op, b.f, (int64_t)first_tile * kWilsonSites, sacc);
+      if (tw && go && first_tile >= 0) {
+        if (res) wilson_tile4_res<+1>(b.f, r_nf, r_nb, r_negf, r_negb, r_live, s_lnk, sacc);
+        else wilson_tile4<+1>(op, b.f, (int64_t)first_tile * kWilsonSites, sacc);
+      }
       if (!tw && pending_beta) {
-        const double ss = warp_sum_partials(part2, tiles, 1, 0);
+        const double ss = warp_sum_partials(part2, 4 * tiles, 1, 0);
         if (threadIdx.x == PT) {
           if (bl.Wb != nullptr) L.st.w_last = L.st.i;
           seed_finish<double2, false>(bl, ss);
@@ -411,13 +527,15 @@ __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, Wi
     const double bp = (i > 1) ? L.st.beta_prev : 0.0;
     double2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
     const double2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
+    double2 *const s_vi = s_vec + (kResV + (i & 1)) * kResTile;
+    double2 *const s_vm = s_vec + (kResV + ((i - 1) & 1)) * kResTile;
     // phase 1 epilogue: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
     if (first_tile >= 0) {
       for (int tile = first_tile; tile < tiles; tile += own.count) {
         const int64_t s0 = (int64_t)tile * kWilsonSites;
         if (tile != first_tile && tw) wilson_tile4<+1>(op, b.f, s0, sacc);
-        double ptt = 0.0, pvm = 0.0;
         if (tw) {
+          double ptt = 0.0, pvm = 0.0;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
@@ -425,45 +543,52 @@ __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, Wi
             if (ss < sites) {
               const double2 sum = tile_sum(sacc, cc, sl);
               const int64_t e = 12 * ss + cc;
-              const double2 fe = b.f[e];
+              const double2 fe = res ? s_vec[kResF * kResTile + o] : b.f[e];
               const double2 v = c2(inv_b * fe.x, inv_b * fe.y);
               vi[e] = v;
               const double2 t = c2(fma(-kappa, inv_b * sum.x, v.x), fma(-kappa, inv_b * sum.y, v.y));
               tbuf[e] = t;
+              if (res) {
+                s_vi[o] = v;
+                s_vec[kResT * kResTile + o] = t;
+              }
               ptt = fma(t.y, t.y, fma(t.x, t.x, ptt));
               if (i > 1) {
-                const double2 m = vm[e];
+                const double2 m = res ? s_vm[o] : vm[e];
                 pvm = fma(v.y, m.y, fma(v.x, m.x, pvm));
               }
             }
           }
+          const double2 ws = warp_sum_pair(ptt, pvm);
+          if (lane == 0) {
+            part1[2 * (4 * tile + warp)] = ws.x;
+            part1[2 * (4 * tile + warp) + 1] = ws.y;
+          }
         }
-        double vv[2] = {ptt, pvm};
-        block_sum<2, PTW>(vv, s_red);   // ends with a CTA barrier: sacc is free again
-        if (threadIdx.x == 0) {
-          part1[2 * tile] = vv[0];
-          part1[2 * tile + 1] = vv[1];
-        }
+        if (tile + own.count < tiles) __syncthreads();   // sacc is reused by the next tile
       }
     }
     if (!grid_sync(g, epoch)) return;
     // ---- phase 2: u = D^H t overlapped with alpha_i and the LU update's scalars ----
-    if (tw && first_tile >= 0) wilson_tile4<-1>(op, tbuf, (int64_t)first_tile * kWilsonSites, sacc);
+    if (tw && first_tile >= 0) {
+      if (res) wilson_tile4_res<-1>(tbuf, r_nf, r_nb, r_negf, r_negb, r_live, s_lnk, sacc);
+      else wilson_tile4<-1>(op, tbuf, (int64_t)first_tile * kWilsonSites, sacc);
+    }
     if (!tw) {
-      const double2 s2 = warp_sum_partial_pairs(part1, tiles);
+      const double2 s2 = warp_sum_partial_pairs(part1, 4 * tiles);
       const double a = i > 1 ? s2.x - L.st.beta_prev * s2.y : s2.x;
       if (threadIdx.x == PT) seed_step_scalars<double2, false>(bl, i, a, nullptr);
     }
     __syncthreads();
     if (!L.st.active) break;   // delta_i <= 0
-    const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+    const double a = L.st.alpha, zeta = L.st.zeta, inv_d = L.st.inv_delta;
     double2 *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
     if (first_tile >= 0) {
       for (int tile = first_tile; tile < tiles; tile += own.count) {
         const int64_t s0 = (int64_t)tile * kWilsonSites;
         if (tile != first_tile && tw) wilson_tile4<-1>(op, tbuf, s0, sacc);
-        double pff = 0.0;
         if (tw) {
+          double pff = 0.0;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             const int o = threadIdx.x + PT * k, sl = o / 12, cc = o - 12 * (o / 12);
@@ -471,36 +596,55 @@ __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, Wi
             if (ss < sites) {
               const double2 sum = tile_sum(sacc, cc, sl);
               const int64_t e = 12 * ss + cc;
-              const double2 tv = tbuf[e], v = vi[e];
+              const double2 tv = res ? s_vec[kResT * kResTile + o] : tbuf[e];
+              const double2 v = res ? s_vi[o] : vi[e];
               double2 f = c2(fma(-kappa, sum.x, tv.x), fma(-kappa, sum.y, tv.y));
               if (i > 1) {
-                const double2 m = vm[e];
+                const double2 m = res ? s_vm[o] : vm[e];
                 f = c2(fma(-bp, m.x, f.x), fma(-bp, m.y, f.y));
               }
               f = c2(fma(-a, v.x, f.x), fma(-a, v.y, f.y));
               double2 w;
               if (i > 1) {
-                const double2 wp = b.w[e];
+                const double2 wp = res ? s_vec[kResW * kResTile + o] : b.w[e];
                 w = c2(inv_d * fma(-bp, wp.x, v.x), inv_d * fma(-bp, wp.y, v.y));
               } else {
                 w = c2(inv_d * v.x, inv_d * v.y);
               }
               b.f[e] = f;
-              b.w[e] = w;
               if (wcol != nullptr) wcol[e] = w;
-              const double2 x = X[e];
-              X[e] = c2(fma(zeta, w.x, x.x), fma(zeta, w.y, x.y));
+              const double2 x = res ? s_vec[kResX * kResTile + o] : X[e];
+              const double2 xn = c2(fma(zeta, w.x, x.x), fma(zeta, w.y, x.y));
+              if (res) {
+                s_vec[kResF * kResTile + o] = f;
+                s_vec[kResW * kResTile + o] = w;
+                s_vec[kResX * kResTile + o] = xn;
+              } else {
+                b.w[e] = w;
+                X[e] = xn;
+              }
               pff = fma(f.y, f.y, fma(f.x, f.x, pff));
             }
           }
+          const double ws = warp_sum(pff);
+          if (lane == 0) part2[4 * tile + warp] = ws;
         }
-        double vv[1] = {pff};
-        block_sum<1, PTW>(vv, s_red);
-        if (threadIdx.x == 0) part2[tile] = vv[0];
+        if (tile + own.count < tiles) __syncthreads();
       }
     }
     if (!grid_sync(g, epoch)) return;
     pending_beta = true;               // beta_i and the stopping test run with the next stencil
+  }
+  if (res) {   // x^1 and w_i back to global memory
+    __syncthreads();
+    const int64_t e0 = (int64_t)first_tile * kResTile;
+    for (int o = threadIdx.x; o < kResTile; o += PTW) {
+      const int64_t e = e0 + o;
+      if (e < b.n) {
+        X[e] = s_vec[kResX * kResTile + o];
+        b.w[e] = s_vec[kResW * kResTile + o];
+      }
+    }
   }
   if (tw) seed_leave<double2>(b, L, b.f, i_stop);
   local_store(b, L);
@@ -623,7 +767,7 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson32(SeedBufs<float2> b, Wi
     if (!seed_alpha_step<float2>(bl, part1, tiles, 2, i > 1, i, L, g, epoch)) return;
     if (!L.st.active) break;   // delta_i <= 0
     // phase 2: u = D^H t, f, w_i, x^1 (FP32 correction), w_i into Wb, partials of ||f||^2
-    const float a = (float)L.st.alpha, zeta = (float)L.st.zeta, inv_d = (float)(1.0 / L.st.delta);
+    const float a = (float)L.st.alpha, zeta = (float)L.st.zeta, inv_d = (float)L.st.inv_delta;
     float2 *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
     if (own.rank >= 0) {
       for (int tile = own.rank; tile < tiles; tile += own.count) {
@@ -672,7 +816,7 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson32(SeedBufs<float2> b, Wi
 template <class T>
 SEED_DEV bool seed_update_step(const SeedBufs<T> &b, const SeedBufs<T> &bl, T *f, const T *vi, int i, LocalSeed &L,
                                const GridSync &g, unsigned &epoch, double *bpart, double *s_red) {
-  const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+  const double a = L.st.alpha, zeta = L.st.zeta, inv_d = L.st.inv_delta;
   const double bp = (i > 1) ? L.st.beta_prev : 0.0;
   T *const X = reinterpret_cast<T *>(b.call->X);
   T *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
@@ -968,7 +1112,7 @@ __global__ void __launch_bounds__(PT) k_seed_run_csr_reorth(SeedBufs<double> b, 
     // ---- f -= alpha_i v_i; w_i; x^1 += zeta_i w_i; x^j += eta^j w_i ----
     const bool ro = freq > 0 && i >= 2 && i % freq == 0;
     {
-      const double a = L.st.alpha, zeta = L.st.zeta, inv_d = 1.0 / L.st.delta;
+      const double a = L.st.alpha, zeta = L.st.zeta, inv_d = L.st.inv_delta;
       double nf = 0.0;
       if (own) {
         fe = fma(-a, v, fe);
@@ -1341,7 +1485,6 @@ __global__ void __launch_bounds__(PT) k_cg_run_csr_small(CsrOp op, const CallArg
                                                          double *P2, double *Q, int64_t ld, CgCols c, GridSync g,
                                                          double *bpart) {
   constexpr int kSlots = PT / RB;   // column slots per block
-  __shared__ double s_w[PT / 32][kRunRegion];
   __shared__ double s_sum[kRunRegion];
   __shared__ double s_part[kSmallCgCols][RB];
   __shared__ double s_rho[kSmallCgCols], s_alpha[kSmallCgCols], s_beta[kSmallCgCols], s_bn[kSmallCgCols];
@@ -1526,6 +1669,14 @@ cudaError_t launch_cg_run_csr_small(const CsrOp &op, const CallArgs *call, doubl
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// The FP64 Wilson run's dynamic shared memory (resident links and tile
+// vectors) is above the default 48 KB limit: raise it once per process.
+cudaError_t seed_run_wilson_smem_attr() {
+  static const cudaError_t attr = cudaFuncSetAttribute((const void *)k_seed_run_wilson,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmemBytes);
+  return attr;
+}
+
 // Up to 2 blocks per SM (3 for the seed runs, with the kernel bounded to fit,
 // measured no faster on the 8^4 workload); 0 when the occupancy query fails.
 int persistent_grid(int kind, int sm_count, bool cg, bool fp32) {
@@ -1534,8 +1685,13 @@ int persistent_grid(int kind, int sm_count, bool cg, bool fp32) {
   if (cg) k = kind == 0 ? (const void *)k_cg_run_csr : (const void *)k_cg_run_wilson;
   else if (fp32) k = kind == 0 ? (const void *)k_seed_run_csr<float> : (const void *)k_seed_run_wilson32;
   else k = kind == 0 ? (const void *)k_seed_run_csr<double> : (const void *)k_seed_run_wilson;
-  const int threads = (!cg && !fp32 && kind == 1) ? PTW : PT;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess) {
+  const bool wil64 = !cg && !fp32 && kind == 1;
+  const int threads = wil64 ? PTW : PT;
+  if (wil64 && seed_run_wilson_smem_attr() != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, wil64 ? kResSmemBytes : 0) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1551,7 +1707,9 @@ cudaError_t launch_seed_run_wilson(const SeedBufs<double2> &b, const WilsonOp &o
   SeedBufs<double2> bb = b;
   WilsonOp o = op;
   void *args[] = {&bb, &o, &tbuf, &g, &bpart, &tpart, &i_stop};
-  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson, dim3(grid), dim3(PTW), args, 0, s);
+  const cudaError_t attr = seed_run_wilson_smem_attr();
+  if (attr != cudaSuccess) return attr;
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson, dim3(grid), dim3(PTW), args, kResSmemBytes, s);
 }
 cudaError_t launch_seed_run_csr(const SeedBufs<double> &b, const CsrOp &op, double *f2, GridSync g, double *bpart,
                                 int i_stop, int grid, cudaStream_t s) {

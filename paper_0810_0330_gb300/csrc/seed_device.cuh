@@ -53,6 +53,7 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
   st->alpha = a;
   st->gamma = gam;
   st->delta = del;
+  st->inv_delta = 1.0 / del;
   st->zeta = zet;
   if (b.alpha_hist) b.alpha_hist[i] = a;
   if (b.delta_hist) b.delta_hist[i] = del;

@@ -26,6 +26,7 @@ struct SeedState {
   double beta;        // beta_i of the last finished step
   double beta_prev;   // beta_{i-1}
   double delta;       // delta_i (delta_{i-1} until the LU update of step i runs)
+  double inv_delta;   // 1 / delta_i, formed once by the LU update's scalar code
   double zeta;        // zeta_i
   double gamma;       // gamma_{i-1}
   double rho;         // beta_i |zeta_i| / delta_i

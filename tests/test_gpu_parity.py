@@ -253,6 +253,29 @@ def test_seed_wilson_small(seedlib, orc, freq, passes, kernel_path):
 
 
 @pytest.mark.parametrize("kernel_path", [0, 1])
+def test_seed_wilson_more_tiles_than_sms(seedlib, orc, kernel_path):
+    """5x6x7x24 lattice (5040 sites: 158 tiles of 32 sites, the last one
+    ragged), kappa 0.12, antiperiodic t, 3 RHS, reorthogonalization every 25
+    steps (152 seed steps): more tiles than the GB300's 152 SMs, so the
+    persistent FP64 run (path 0) takes its general form, with several tiles
+    per block and the links, indices and tile vectors read from global memory;
+    smaller lattices (every other Wilson test here) take the resident form."""
+    dims, kappa = (5, 6, 7, 24), 0.12
+    U = I.random_su3_links(dims, 0.3, seed=11)
+    eta = I.point_sources(dims, 3, site=101)
+    B = np.stack([orc.wilson_dslash(dims, kappa, 1, -1, U, eta[:, j]) for j in range(3)], axis=1)
+    ctx = wilson_ctx(seedlib, dims, kappa, U, bc_t=1, m_max=800, reorth_freq=25, reorth_passes=2,
+                     tol_seed=1e-12, tol_rest=1e-8, kernel_path=kernel_path)
+    info1, info2, Xs, X = run_gpu(seedlib, ctx, B)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    ref = orc.seed_solve_all(op, B, m_max=800, reorth_freq=25, reorth_passes=2, tol_seed=1e-12, tol_rest=1e-8)
+    s_seed, s_final = self_sensitivity(orc, op, B, ref, cols=(1, 2), m_max=800, reorth_freq=25,
+                                       reorth_passes=2, tol=1e-12)
+    compare_full(ref, info1, info2, Xs, X, "wilson-158-tiles-%d" % kernel_path, seeded_tol=max(REL_X, 10 * s_seed),
+                 final_tol=max(REL_X, 10 * s_final))
+
+
+@pytest.mark.parametrize("kernel_path", [0, 1])
 def test_blocked_seeding_long_run_many_rhs(seedlib, orc, kernel_path):
     """Without reorthogonalization the 3x4x5x6 lattice at kappa 0.15 needs 219
     seed steps: on path 0 the persistent run is cut into segments of at most
