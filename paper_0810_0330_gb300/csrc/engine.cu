@@ -71,7 +71,7 @@ struct seed_ctx {
   // seed recurrence
   void *V = nullptr;
   int64_t ldv = 0;
-  void *vcur = nullptr, *u = nullptr, *f = nullptr, *w = nullptr;
+  void *u = nullptr, *f = nullptr, *w = nullptr;
   SeedState *st = nullptr;
   double *alpha_hist = nullptr, *beta_hist = nullptr, *delta_hist = nullptr;
   double2 *eta = nullptr;
@@ -109,7 +109,7 @@ struct seed_ctx {
   bool allow_persistent = true;        // persistent seed runs
   bool allow_persistent_cg = false;    // persistent CG
 
-  // mixed precision: V, vcur, u, f, w hold FP32 vectors (vsz bytes per element)
+  // mixed precision: V, u, f, w hold FP32 vectors (vsz bytes per element)
   int precision = 0;
   size_t vsz = 8;
   int64_t nv = 0;                      // length of the Krylov vectors (n, or the tiled FP32 length)
@@ -229,7 +229,6 @@ seed_status alloc_common(seed_ctx *ctx) {
   const int m = ctx->prm.m_max;
   ctx->ldv = (n + 31) / 32 * 32;   // 256-byte aligned columns for complex, 256 B for real
   TRY(dalloc(ctx, &ctx->V, (size_t)ctx->ldv * (m + 1) * es));
-  TRY(dalloc(ctx, &ctx->vcur, n * es));
   TRY(dalloc(ctx, &ctx->u, n * es));
   TRY(dalloc(ctx, &ctx->f, n * es));
   TRY(dalloc(ctx, &ctx->w, n * es));
@@ -397,7 +396,6 @@ SeedBufs<T> seed_bufs(seed_ctx *ctx, int nrhs) {
   b.nblocks = vec_blocks(ctx->n);
   b.V = (T *)ctx->V;
   b.ldv = ctx->ldv;
-  b.vcur = (T *)ctx->vcur;
   b.u = (T *)ctx->u;
   b.f = (T *)ctx->f;
   b.w = (T *)ctx->w;
@@ -446,8 +444,9 @@ bool reorth_at(const seed_params &p, int i) { return p.reorth_freq > 0 && i >= 2
 template <class T>
 int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
   SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
-  int k = kLow<T> ? apply_A32(ctx, ctx->vcur, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr)
-                  : apply_A(ctx, ctx->vcur, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr);
+  // u = A f with f = beta_{i-1} v_i not yet normalized: the dots kernel forms v_i and scales u
+  int k = kLow<T> ? apply_A32(ctx, ctx->f, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr)
+                  : apply_A(ctx, ctx->f, ctx->ldv, ctx->u, ctx->ldv, 1, nullptr);
   launch_seed_dots<T>(b, ctx->cs);
   launch_seed_update<T>(b, !reorth, ctx->cs);
   k += 2;
@@ -456,8 +455,7 @@ int issue_seed_step(seed_ctx *ctx, int nrhs, bool reorth) {
     launch_reorth<T>(b, reorth_bufs<T>(ctx), ctx->prm.reorth_passes, ctx->cs);
     k += reorth_kernel_count<T>(ctx->prm.reorth_passes);
   }
-  launch_seed_normalize<T>(b, ctx->cs);
-  return k + 1;
+  return k;
 }
 
 // Capture (once) and launch a graph for the given pattern of steps.
@@ -709,8 +707,7 @@ seed_status solve_first_impl(seed_ctx *ctx, const void *B, int64_t ldb, void *X,
   launch_colnorms<T>(n, (const T *)B, ldb, 1, &ctx->st->bnorm1, ctx->partials, ctx->tickets, ctx->cs);
   SeedBufs<T> b = seed_bufs<T>(ctx, nrhs);
   launch_seed_start<T>(b, r01, ctx->cs);
-  launch_seed_normalize<T>(b, ctx->cs);
-  kern += 3;
+  kern += 2;
   ctx->stats.kernel_launches += kern;
 
   ReorthRun rr;
@@ -1446,8 +1443,7 @@ seed_status solve_first_mixed(seed_ctx *ctx, const void *B, int64_t ldb, void *X
   launch_colnorms<T64>(n, (const T64 *)B, ldb, 1, &ctx->st->bnorm1, ctx->partials, ctx->tickets, ctx->cs);
   SeedBufs<T32> b = seed_bufs<T32>(ctx, nrhs);
   launch_seed_start<T32>(b, (const T32 *)ctx->R32, ctx->cs);
-  launch_seed_normalize<T32>(b, ctx->cs);
-  kern += 4;
+  kern += 3;
   ctx->stats.kernel_launches += kern;
   if (use_persistent_seed(ctx)) {
     TRY(seed_persistent_segments<T32>(ctx, nrhs));
@@ -1599,7 +1595,7 @@ void destroy(seed_ctx *ctx) {
   if (!ctx) return;
   if (ctx->cs) cudaStreamSynchronize(ctx->cs);
   for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
-  void *ptrs[] = {ctx->V, ctx->vcur, ctx->u, ctx->f, ctx->w, ctx->st, ctx->alpha_hist, ctx->beta_hist,
+  void *ptrs[] = {ctx->V, ctx->u, ctx->f, ctx->w, ctx->st, ctx->alpha_hist, ctx->beta_hist,
                   ctx->delta_hist, ctx->eta, ctx->partials, ctx->tickets, ctx->Hpart, ctx->H, ctx->call,
                   ctx->colnorm, ctx->R, ctx->P, ctx->Q, ctx->T, ctx->cg_d, ctx->cg_i, ctx->nbr,
                   ctx->gsync, ctx->f2, ctx->tpart, ctx->op32, ctx->R32, ctx->P32, ctx->Q32,

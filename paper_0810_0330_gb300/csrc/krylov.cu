@@ -57,7 +57,7 @@ int col_blocks(int64_t n, int nc) {
   return (int)b;
 }
 
-// Start of the Lanczos run: f = r_0^1, beta_0 = ||r_0^1||; v_1 follows from the normalize kernel.
+// Start of the Lanczos run: f = r_0^1, beta_0 = ||r_0^1||; the first step forms v_1 = f / beta_0.
 template <class T>
 __global__ void __launch_bounds__(NT) k_seed_start(SeedBufs<T> b, const T *__restrict__ r01) {
   __shared__ double sm[NT / 32];
@@ -96,22 +96,10 @@ __global__ void __launch_bounds__(NT) k_seed_start(SeedBufs<T> b, const T *__res
   }
 }
 
-// v_i = f / beta_{i-1} into column i-1 of V and into vcur (the operator input).
-template <class T>
-__global__ void __launch_bounds__(NT) k_seed_normalize(SeedBufs<T> b) {
-  const SeedState *st = b.st;
-  if (!st->active) return;
-  const double inv = st->inv_beta;
-  T *vi = b.V + (int64_t)(st->i - 1) * b.ldv;
-  GRID_STRIDE(e, b.n) {
-    const T v = Sc<T>::scale(inv, b.f[e]);
-    vi[e] = v;
-    b.vcur[e] = v;
-  }
-}
-
 // The dot products of a Lanczos step (alpha_i, g^j) and the scalars of the LU update and seeding, in
-// one pass over the elements:  f = A v_i - beta_{i-1} v_{i-1};
+// one pass over the elements.  The step's operator was applied to f (not yet
+// normalized: beta_{i-1} v_i), so with u = A f:  v_i = f / beta_{i-1} into
+// column i-1 of V;  f = u / beta_{i-1} - beta_{i-1} v_{i-1} (A is linear);
 // alpha_i = Re(v_i^H f);  g^j = v_i^H r_0^j for j = 2..nrhs.
 // Values are packed 32 per chunk (alpha in slot 0 of chunk 0, then 15 complex
 // g^j per chunk), reduced per block with a warp reduce-scatter, and the last
@@ -130,9 +118,9 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
   const int i = st->i;
   const int nr = b.Wb == nullptr ? b.nrhs : 1;   // blocked seeding: g^j at the flush
   const int nch = nr > 1 ? (nr - 1 + kDotsPerChunk - 1) / kDotsPerChunk : 1;
-  const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
+  T *vi = b.V + (int64_t)(i - 1) * b.ldv;
   const T *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
-  const double bp = (i > 1) ? st->beta_prev : 0.0;
+  const double bp = (i > 1) ? st->beta_prev : 0.0, inv_b = st->inv_beta;
   for (int ch = 0; ch < nch; ++ch) {
     const int j0 = 1 + kDotsPerChunk * ch;
     const int jn = nr - j0 < kDotsPerChunk ? nr - j0 : kDotsPerChunk;   // may be <= 0
@@ -140,11 +128,16 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc[q] = 0;
     GRID_STRIDE(e, b.n) {
-      const T v = vi[e];
-      if (ch == 0) {
-        const T fe = (i > 1) ? Sc<T>::axpy(-bp, vm[e], b.u[e]) : b.u[e];
+      T v;
+      if (ch == 0) {   // the same thread reads v_i back in the later chunks
+        v = Sc<T>::scale(inv_b, b.f[e]);
+        vi[e] = v;
+        const T ue = Sc<T>::scale(inv_b, b.u[e]);
+        const T fe = (i > 1) ? Sc<T>::axpy(-bp, vm[e], ue) : ue;
         b.f[e] = fe;
         acc[0] = Sc<T>::redot(v, fe, acc[0]);
+      } else {
+        v = vi[e];
       }
 #pragma unroll
       for (int q = 0; q < kDotsPerChunk; ++q) {
@@ -221,7 +214,8 @@ __global__ void __launch_bounds__(NT) k_seed_dots(SeedBufs<T> b) {
 }
 
 // alpha_i and the LU-update scalars when no g^j is formed here (blocked
-// seeding, or system 1 alone): f = A v_i - beta_{i-1} v_{i-1},
+// seeding, or system 1 alone): with u = A f as in k_seed_dots, v_i = f /
+// beta_{i-1} into V, f = u / beta_{i-1} - beta_{i-1} v_{i-1},
 // alpha_i = Re(v_i^H f), one value per block summed in block order by the last.
 template <class T>
 __global__ void __launch_bounds__(NT) k_seed_alpha(SeedBufs<T> b) {
@@ -229,14 +223,17 @@ __global__ void __launch_bounds__(NT) k_seed_alpha(SeedBufs<T> b) {
   if (!st->active) return;
   __shared__ double sm[NT / 32];
   const int i = st->i;
-  const T *vi = b.V + (int64_t)(i - 1) * b.ldv;
+  T *vi = b.V + (int64_t)(i - 1) * b.ldv;
   const T *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
-  const double bp = (i > 1) ? st->beta_prev : 0.0;
+  const double bp = (i > 1) ? st->beta_prev : 0.0, inv_b = st->inv_beta;
   typename Sc<T>::A acc = 0;
   GRID_STRIDE(e, b.n) {
-    const T fe = (i > 1) ? Sc<T>::axpy(-bp, vm[e], b.u[e]) : b.u[e];
+    const T v = Sc<T>::scale(inv_b, b.f[e]);
+    vi[e] = v;
+    const T ue = Sc<T>::scale(inv_b, b.u[e]);
+    const T fe = (i > 1) ? Sc<T>::axpy(-bp, vm[e], ue) : ue;
     b.f[e] = fe;
-    acc = Sc<T>::redot(vi[e], fe, acc);
+    acc = Sc<T>::redot(v, fe, acc);
   }
   double v[1] = {(double)acc};
   block_sum<1, NT>(v, sm);
@@ -621,10 +618,6 @@ void launch_seed_start(const SeedBufs<T> &b, const T *r01, cudaStream_t s) {
   k_seed_start<T><<<b.nblocks, NT, 0, s>>>(b, r01);
 }
 template <class T>
-void launch_seed_normalize(const SeedBufs<T> &b, cudaStream_t s) {
-  k_seed_normalize<T><<<b.nblocks, NT, 0, s>>>(b);
-}
-template <class T>
 void launch_seed_dots(const SeedBufs<T> &b, cudaStream_t s) {
   if (b.Wb != nullptr || b.nrhs <= 1) k_seed_alpha<T><<<b.nblocks, NT, 0, s>>>(b);
   else k_seed_dots<T><<<b.nblocks, NT, 0, s>>>(b);
@@ -981,7 +974,6 @@ void launch_cg_check(int64_t n, const T *B, int64_t ldb, const T *Q, int64_t ldq
 
 #define SEED_INSTANTIATE(T)                                                                                        \
   template void launch_seed_start<T>(const SeedBufs<T> &, const T *, cudaStream_t);                              \
-  template void launch_seed_normalize<T>(const SeedBufs<T> &, cudaStream_t);                                     \
   template void launch_seed_dots<T>(const SeedBufs<T> &, cudaStream_t);                                          \
   template void launch_seed_update<T>(const SeedBufs<T> &, bool, cudaStream_t);                                  \
   template void launch_reorth<T>(const SeedBufs<T> &, const ReorthBufs<T> &, int, cudaStream_t);                 \

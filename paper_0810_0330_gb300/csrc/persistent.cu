@@ -285,19 +285,14 @@ SEED_DEV bool seed_beta_step(const SeedBufs<T> &bl, const double *parts, int npa
   return true;
 }
 
-// On leaving at a reorthogonalization step: v_i = f / beta_{i-1} into V and vcur.
+// On leaving with i == i_stop (a reorthogonalization step or the end of a
+// seeding block follows): the next step starts from f = beta_{i-1} v_i in b.f
+// (its first kernel forms v_i), so a run that alternates two f buffers copies
+// the current one there.
 template <class T>
 SEED_DEV void seed_leave(const SeedBufs<T> &b, const LocalSeed &L, const T *f, int i_stop) {
-  if (!L.st.active || L.st.i != i_stop) return;
-  const double inv_b = L.st.inv_beta;
-  T *vi = b.V + (int64_t)(i_stop - 1) * b.ldv;
-  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) {
-    const T fe = __ldcg(f + e);
-    const T v = Sc<T>::scale(inv_b, fe);
-    vi[e] = v;
-    b.vcur[e] = v;
-    if (f != b.f) b.f[e] = fe;
-  }
+  if (!L.st.active || L.st.i != i_stop || f == b.f) return;
+  for (int64_t e = (int64_t)blockIdx.x * PT + threadIdx.x; e < b.n; e += (int64_t)gridDim.x * PT) b.f[e] = __ldcg(f + e);
 }
 
 // FP64 Wilson run: five warps per block.  Warps 0-3 are the tile warps of the

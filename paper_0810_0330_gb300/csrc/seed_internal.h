@@ -70,7 +70,6 @@ struct SeedBufs {
   int32_t nblocks;     // blocks of the vector kernels (fixed for n)
   T *V;                // n x (m_max+1), column c holds v_{c+1}
   int64_t ldv;
-  T *vcur;             // copy of v_i, the operator's input
   T *u;                // A v_i
   T *f;                // the Lanczos residual vector
   T *w;                // w_i
@@ -214,7 +213,6 @@ extern const int32_t kCsrShape[kCsrShapes][2];
 // Seed recurrence, reorthogonalization, CG (krylov.cu)
 int vec_blocks(int64_t n);
 template <class T> void launch_seed_start(const SeedBufs<T> &b, const T *r01, cudaStream_t s);
-template <class T> void launch_seed_normalize(const SeedBufs<T> &b, cudaStream_t s);
 template <class T> void launch_seed_dots(const SeedBufs<T> &b, cudaStream_t s);
 template <class T> void launch_seed_update(const SeedBufs<T> &b, bool with_norm, cudaStream_t s);
 template <class T> void launch_reorth(const SeedBufs<T> &b, const ReorthBufs<T> &r, int passes, cudaStream_t s);
@@ -293,8 +291,8 @@ void launch_mixed_residual(int64_t n32, Layout32 L, const T64 *B, int64_t ldb, c
 
 // Persistent cooperative kernels (persistent.cu).  Seed: runs Lanczos steps
 // i < i_stop (none of which reorthogonalizes) while the recurrence is active;
-// on leaving with i == i_stop it forms v_i in V and vcur for the step-by-step
-// path.  CG: runs lockstep iterations until no column is active.  Both return
+// on leaving with i == i_stop it leaves f = beta_{i-1} v_i in SeedBufs::f, from
+// which the step-by-step path continues.  CG: runs lockstep iterations until no column is active.  Both return
 // cudaErrorCooperativeLaunchTooLarge and friends from the launch, and report a
 // barrier time-out through GridSync::error.  CG: nc <= 32.
 constexpr int kPersistMaxCols = 32;
