@@ -335,31 +335,6 @@ SEED_DEV void wilson_tile4(const WilsonOp &op, const double2 *in, int64_t s0, do
   tile_warps_sync();
 }
 
-// One warp: the sums over b < nb of the pairs (partial[2b], partial[2b + 1]) in
-// warp_sum_partials' order, both in one pass over the partials.
-SEED_DEV double2 warp_sum_partial_pairs(const double *partial, int nb) {
-  const int lane = threadIdx.x & 31;
-  double sx[8], sy[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) sx[u] = sy[u] = 0.0;
-  for (int b0 = 0; b0 < nb; b0 += 256) {
-    double2 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int b = b0 + u * 32 + lane;
-      v[u] = b < nb ? __ldcg(reinterpret_cast<const double2 *>(partial) + b) : c2(0.0, 0.0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      sx[u] += v[u].x;
-      sy[u] += v[u].y;
-    }
-  }
-  const double tx = ((sx[0] + sx[1]) + (sx[2] + sx[3])) + ((sx[4] + sx[5]) + (sx[6] + sx[7]));
-  const double ty = ((sy[0] + sy[1]) + (sy[2] + sy[3])) + ((sy[4] + sy[5]) + (sy[6] + sy[7]));
-  return c2(warp_sum(tx), warp_sum(ty));
-}
-
 // The two values of every lane summed over the warp, both returned to every
 // lane: the first level trades halves (lanes < 16 keep x, the others y), so
 // each lane adds 5 times instead of 10.  Fixed order, deterministic.
@@ -371,6 +346,49 @@ SEED_DEV double2 warp_sum_pair(double x, double y) {
   for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
   return c2(__shfl_sync(0xffffffffu, keep, 0), __shfl_sync(0xffffffffu, keep, 16));
 }
+
+// One warp: the sum of nb partials with up to 32 PER of them loaded at once
+// (lane l adds partial[l], partial[l + 32], ... in order), then the warp tree:
+// one FP64 add per value and one round trip to L2 for the short lists of the
+// persistent runs, where the scalar warp's FP64 instructions are on the
+// critical path.  Longer lists run in chunks.
+template <int PER>
+SEED_DEV double warp_sum_short(const double *p, int nb) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32 * PER) {
+    double v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < nb ? __ldcg(p + b) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) s += v[u];
+  }
+  return warp_sum(s);
+}
+// The same for nb pairs (p[2b], p[2b + 1]); both sums returned to every lane.
+template <int PER>
+SEED_DEV double2 warp_sum_short_pairs(const double *p, int nb) {
+  const int lane = threadIdx.x & 31;
+  double sx = 0.0, sy = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32 * PER) {
+    double2 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int b = b0 + u * 32 + lane;
+      v[u] = b < nb ? __ldcg(reinterpret_cast<const double2 *>(p) + b) : c2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      sx += v[u].x;
+      sy += v[u].y;
+    }
+  }
+  return warp_sum_pair(sx, sy);
+}
+constexpr int kScalarSumPer = 16;   // 512 partials (128 tiles x 4 warps, the 8^4 lattice) in one round
 
 // Resident form of the run, used when every owner block holds at most one tile
 // (lattices with no more 32-site tiles than SMs, e.g. 8^4 with 128 tiles): the
@@ -506,7 +524,7 @@ __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, Wi
         else wilson_tile4<+1>(op, b.f, (int64_t)first_tile * kWilsonSites, sacc);
       }
       if (!tw && pending_beta) {
-        const double ss = warp_sum_partials(part2, 4 * tiles, 1, 0);
+        const double ss = warp_sum_short<kScalarSumPer>(part2, 4 * tiles);
         if (threadIdx.x == PT) {
           if (bl.Wb != nullptr) L.st.w_last = L.st.i;
           seed_finish<double2, false>(bl, ss);
@@ -570,7 +588,7 @@ __global__ void __launch_bounds__(PTW) k_seed_run_wilson(SeedBufs<double2> b, Wi
       else wilson_tile4<-1>(op, tbuf, (int64_t)first_tile * kWilsonSites, sacc);
     }
     if (!tw) {
-      const double2 s2 = warp_sum_partial_pairs(part1, 4 * tiles);
+      const double2 s2 = warp_sum_short_pairs<kScalarSumPer>(part1, 4 * tiles);
       const double a = i > 1 ? s2.x - L.st.beta_prev * s2.y : s2.x;
       if (threadIdx.x == PT) seed_step_scalars<double2, false>(bl, i, a, nullptr);
     }
@@ -677,7 +695,8 @@ SEED_DEV void site_mu32(const WilsonOp32 &op, const float2 *in, int64_t s, float
   hop_pair_r<MU, S>(pf, uf, negf, pb, ub, negb, acc);
 }
 
-// hopping sums of the 32-site tile starting at s0 into sacc (zeros for padding sites)
+// hopping sums of the 32-site tile starting at s0 into sacc (zeros for padding
+// sites), by the four tile warps (ends with their named barrier)
 template <int S>
 SEED_DEV void wilson_tile32(const WilsonOp32 &op, const float2 *in, int64_t s0, float (*sacc)[24][kWilsonSites + 1]) {
   const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
@@ -699,7 +718,7 @@ SEED_DEV void wilson_tile32(const WilsonOp32 &op, const float2 *in, int64_t s0, 
     sacc[mu][2 * k][lane] = acc[k].x;
     sacc[mu][2 * k + 1][lane] = acc[k].y;
   }
-  __syncthreads();
+  tile_warps_sync();
 }
 SEED_DEV float2 tile_sum32(float (*sacc)[24][kWilsonSites + 1], int cc, int sl) {
   return make_float2(((sacc[0][2 * cc][sl] + sacc[1][2 * cc][sl]) + sacc[2][2 * cc][sl]) + sacc[3][2 * cc][sl],
@@ -707,22 +726,131 @@ SEED_DEV float2 tile_sum32(float (*sacc)[24][kWilsonSites + 1], int cc, int sl) 
                          sacc[3][2 * cc + 1][sl]);
 }
 
-// tpart: 3 x tiles doubles, as k_seed_run_wilson
-__global__ void __launch_bounds__(PT) k_seed_run_wilson32(SeedBufs<float2> b, WilsonOp32 op, float2 *tbuf,
-                                                           GridSync g, double *tpart, int i_stop) {
+// Resident form, as in the FP64 run: s_lnk32[(mu * 18 + k) * 32 + lane] holds
+// the tile's links, s_vec32[slot * 384 + o] its elements of f, t, w_i, x^1
+// (the FP32 correction), v_i and v_{i-1} (o = the element's offset in the
+// tile, the same as in the tiled vectors).
+constexpr size_t kResSmemBytes32 = (size_t)(kResLinks + 6 * kResTile) * sizeof(float2);
+
+template <int MU, int S>
+SEED_DEV void site_mu32_res(const float2 *in, int32_t nf, int32_t nb, unsigned negf, unsigned negb,
+                            const float2 *su, float2 (&acc)[12]) {
+  float2 pf[12], pb[12], uf[9], ub[9];
+  const float2 *qf = in + ((int64_t)nf >> 5) * 384 + (nf & 31), *qb = in + ((int64_t)nb >> 5) * 384 + (nb & 31);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) pf[k] = qf[32 * k];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) pb[k] = qb[32 * k];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) uf[k] = su[k * 32];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ub[k] = su[(9 + k) * 32];
+  hop_pair_r<MU, S>(pf, uf, negf, pb, ub, negb, acc);
+}
+
+template <int S>
+SEED_DEV void wilson_tile32_res(const float2 *in, int32_t nf, int32_t nb, unsigned negf, unsigned negb, bool live,
+                                const float2 *s_lnk, float (*sacc)[24][kWilsonSites + 1]) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const float2 *su = s_lnk + mu * 18 * 32 + lane;
+  float2 acc[12];
+  if (live) {
+    switch (mu) {
+      case 0: site_mu32_res<0, S>(in, nf, nb, negf, negb, su, acc); break;
+      case 1: site_mu32_res<1, S>(in, nf, nb, negf, negb, su, acc); break;
+      case 2: site_mu32_res<2, S>(in, nf, nb, negf, negb, su, acc); break;
+      default: site_mu32_res<3, S>(in, nf, nb, negf, negb, su, acc); break;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    sacc[mu][2 * k][lane] = acc[k].x;
+    sacc[mu][2 * k + 1][lane] = acc[k].y;
+  }
+  tile_warps_sync();
+}
+
+// tpart: 12 x tiles doubles, per tile warp as in k_seed_run_wilson.  Five
+// warps: four tile warps and the scalar warp, which reduces the partials and
+// runs the recurrence's scalar code while the tile warps compute the next
+// stencil (the same overlap as the FP64 run).
+__global__ void __launch_bounds__(PTW, 1) k_seed_run_wilson32(SeedBufs<float2> b, WilsonOp32 op, float2 *tbuf,
+                                                            GridSync g, double *tpart, int i_stop) {
   __shared__ float sacc[4][24][kWilsonSites + 1];
-  __shared__ double s_red[2 * (PT / 32)];
   __shared__ LocalSeed L;
+  extern __shared__ float2 s_dyn32[];
   const int tiles = (int)(b.n / 384);
   const float mk = (float)(-op.kappa);
-  double *part1 = tpart, *part2 = tpart + 2 * (int64_t)tiles;
+  double *part1 = tpart, *part2 = tpart + 8 * (int64_t)tiles;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool tw = warp < 4;
   unsigned epoch = 0;
   local_load(b, L);
   const SeedBufs<float2> bl = local_bufs(b, L);
   Owners own;
   if (!register_owner(g, epoch, own)) return;
   float2 *const X = reinterpret_cast<float2 *>(b.call->X);
+  const int first_tile = own.rank >= 0 && own.rank < tiles ? own.rank : -1;
+  const bool res = tiles <= own.count && first_tile >= 0;
+  float2 *const s_lnk = s_dyn32;
+  float2 *const s_vec = s_dyn32 + kResLinks;
+  int32_t r_nf = 0, r_nb = 0;
+  unsigned r_negf = 0u, r_negb = 0u;
+  const int64_t r_site = (int64_t)(first_tile >= 0 ? first_tile : 0) * kWilsonSites + lane;
+  const bool r_live = r_site < op.sites;
+  if (res) {
+    const int64_t e0 = (int64_t)first_tile * kResTile;
+    const int i0 = L.st.i;
+    if (tw && r_live) {
+      const int mu = warp;
+      r_nf = __ldg(op.nbr + 8 * r_site + 2 * mu);
+      r_nb = __ldg(op.nbr + 8 * r_site + 2 * mu + 1);
+      if (mu == 3 && op.bc_t) {
+        const int64_t t = r_site / ((int64_t)op.dims[0] * op.dims[1] * op.dims[2]);
+        if (t == op.dims[3] - 1) r_negf = CxBits<float2>::sign;
+        if (t == 0) r_negb = CxBits<float2>::sign;
+      }
+      const float2 *Lk = op.links + (int64_t)mu * 9 * op.sites;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        s_lnk[(mu * 18 + k) * 32 + lane] = __ldg(Lk + (int64_t)k * op.sites + r_site);
+        s_lnk[(mu * 18 + 9 + k) * 32 + lane] = __ldg(Lk + (int64_t)k * op.sites + r_nb);
+      }
+    }
+    const float2 *vprev = b.V + (int64_t)(i0 > 1 ? i0 - 2 : 0) * b.ldv;
+    for (int o = threadIdx.x; o < kResTile; o += PTW) {
+      const int64_t e = e0 + o;
+      s_vec[kResF * kResTile + o] = b.f[e];
+      s_vec[kResW * kResTile + o] = i0 > 1 ? b.w[e] : make_float2(0.f, 0.f);
+      s_vec[kResX * kResTile + o] = X[e];
+      s_vec[(kResV + ((i0 - 1) & 1)) * kResTile + o] = i0 > 1 ? vprev[e] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+  }
+  bool pending_beta = false;
   for (;;) {
+    // ---- phase 1 of step i, overlapped with the end of step i-1 ----
+    {
+      const int ip = L.st.i + (pending_beta ? 1 : 0);
+      const bool go = L.st.active && ip < i_stop && (b.Wb == nullptr || ip - L.st.blk0 < kSeedBlock);
+      __syncthreads();                 // everyone has read L.st before the scalar warp updates it
+      if (tw && go && first_tile >= 0) {
+        if (res) wilson_tile32_res<+1>(b.f, r_nf, r_nb, r_negf, r_negb, r_live, s_lnk, sacc);
+        else wilson_tile32<+1>(op, b.f, (int64_t)first_tile * kWilsonSites, sacc);
+      }
+      if (!tw && pending_beta) {
+        const double ss = warp_sum_short<kScalarSumPer>(part2, 4 * tiles);
+        if (threadIdx.x == PT) {
+          if (bl.Wb != nullptr) L.st.w_last = L.st.i;
+          seed_finish<float2, false>(bl, ss);
+        }
+      }
+      __syncthreads();
+      pending_beta = false;
+    }
     const int i = L.st.i;
     if (!L.st.active || i >= i_stop) break;
     if (block_full(b, L, i)) break;
@@ -730,78 +858,115 @@ __global__ void __launch_bounds__(PT) k_seed_run_wilson32(SeedBufs<float2> b, Wi
     const float bp = (float)((i > 1) ? L.st.beta_prev : 0.0);
     float2 *vi = b.V + (int64_t)(i - 1) * b.ldv;
     const float2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
-    // phase 1: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
-    if (own.rank >= 0) {
-      for (int tile = own.rank; tile < tiles; tile += own.count) {
-        wilson_tile32<+1>(op, b.f, (int64_t)tile * kWilsonSites, sacc);
-        float ptt = 0.f, pvm = 0.f;
+    float2 *const s_vi = s_vec + (kResV + (i & 1)) * kResTile;
+    float2 *const s_vm = s_vec + (kResV + ((i - 1) & 1)) * kResTile;
+    // phase 1 epilogue: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
+    if (first_tile >= 0) {
+      for (int tile = first_tile; tile < tiles; tile += own.count) {
+        if (tile != first_tile && tw) wilson_tile32<+1>(op, b.f, (int64_t)tile * kWilsonSites, sacc);
+        if (tw) {
+          float ptt = 0.f, pvm = 0.f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int o = threadIdx.x + PT * k, cc = o >> 5, sl = o & 31;
-          const int64_t e = (int64_t)tile * 384 + o;
-          const float2 sum = tile_sum32(sacc, cc, sl);
-          const float2 fe = b.f[e];
-          const float2 v = make_float2(inv_b * fe.x, inv_b * fe.y);
-          vi[e] = v;
-          const float2 t = make_float2(fmaf(mk, inv_b * sum.x, v.x), fmaf(mk, inv_b * sum.y, v.y));
-          tbuf[e] = t;
-          ptt = fmaf(t.y, t.y, fmaf(t.x, t.x, ptt));
-          if (i > 1) {
-            const float2 m = vm[e];
-            pvm = fmaf(v.y, m.y, fmaf(v.x, m.x, pvm));
+          for (int k = 0; k < 3; ++k) {
+            const int o = threadIdx.x + PT * k, cc = o >> 5, sl = o & 31;
+            const int64_t e = (int64_t)tile * 384 + o;
+            const float2 sum = tile_sum32(sacc, cc, sl);
+            const float2 fe = res ? s_vec[kResF * kResTile + o] : b.f[e];
+            const float2 v = make_float2(inv_b * fe.x, inv_b * fe.y);
+            vi[e] = v;
+            const float2 t = make_float2(fmaf(mk, inv_b * sum.x, v.x), fmaf(mk, inv_b * sum.y, v.y));
+            tbuf[e] = t;
+            if (res) {
+              s_vi[o] = v;
+              s_vec[kResT * kResTile + o] = t;
+            }
+            ptt = fmaf(t.y, t.y, fmaf(t.x, t.x, ptt));
+            if (i > 1) {
+              const float2 m = res ? s_vm[o] : vm[e];
+              pvm = fmaf(v.y, m.y, fmaf(v.x, m.x, pvm));
+            }
+          }
+          const double2 ws = warp_sum_pair((double)ptt, (double)pvm);
+          if (lane == 0) {
+            part1[2 * (4 * tile + warp)] = ws.x;
+            part1[2 * (4 * tile + warp) + 1] = ws.y;
           }
         }
-        double vv[2] = {(double)ptt, (double)pvm};
-        block_sum<2, PT>(vv, s_red);   // ends with a CTA barrier: sacc is free again
-        if (threadIdx.x == 0) {
-          part1[2 * tile] = vv[0];
-          part1[2 * tile + 1] = vv[1];
-        }
+        if (tile + own.count < tiles) __syncthreads();   // sacc is reused by the next tile
       }
     }
-    if (!seed_alpha_step<float2>(bl, part1, tiles, 2, i > 1, i, L, g, epoch)) return;
+    if (!grid_sync(g, epoch)) return;
+    // ---- phase 2: u = D^H t overlapped with alpha_i and the LU update's scalars ----
+    if (tw && first_tile >= 0) {
+      if (res) wilson_tile32_res<-1>(tbuf, r_nf, r_nb, r_negf, r_negb, r_live, s_lnk, sacc);
+      else wilson_tile32<-1>(op, tbuf, (int64_t)first_tile * kWilsonSites, sacc);
+    }
+    if (!tw) {
+      const double2 s2 = warp_sum_short_pairs<kScalarSumPer>(part1, 4 * tiles);
+      const double a = i > 1 ? s2.x - L.st.beta_prev * s2.y : s2.x;
+      if (threadIdx.x == PT) seed_step_scalars<float2, false>(bl, i, a, nullptr);
+    }
+    __syncthreads();
     if (!L.st.active) break;   // delta_i <= 0
-    // phase 2: u = D^H t, f, w_i, x^1 (FP32 correction), w_i into Wb, partials of ||f||^2
     const float a = (float)L.st.alpha, zeta = (float)L.st.zeta, inv_d = (float)L.st.inv_delta;
     float2 *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
-    if (own.rank >= 0) {
-      for (int tile = own.rank; tile < tiles; tile += own.count) {
-        wilson_tile32<-1>(op, tbuf, (int64_t)tile * kWilsonSites, sacc);
-        float pff = 0.f;
+    if (first_tile >= 0) {
+      for (int tile = first_tile; tile < tiles; tile += own.count) {
+        if (tile != first_tile && tw) wilson_tile32<-1>(op, tbuf, (int64_t)tile * kWilsonSites, sacc);
+        if (tw) {
+          float pff = 0.f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int o = threadIdx.x + PT * k, cc = o >> 5, sl = o & 31;
-          const int64_t e = (int64_t)tile * 384 + o;
-          const float2 sum = tile_sum32(sacc, cc, sl);
-          const float2 tv = tbuf[e], v = vi[e];
-          float2 f = make_float2(fmaf(mk, sum.x, tv.x), fmaf(mk, sum.y, tv.y));
-          if (i > 1) {
-            const float2 m = vm[e];
-            f = make_float2(fmaf(-bp, m.x, f.x), fmaf(-bp, m.y, f.y));
+          for (int k = 0; k < 3; ++k) {
+            const int o = threadIdx.x + PT * k, cc = o >> 5, sl = o & 31;
+            const int64_t e = (int64_t)tile * 384 + o;
+            const float2 sum = tile_sum32(sacc, cc, sl);
+            const float2 tv = res ? s_vec[kResT * kResTile + o] : tbuf[e];
+            const float2 v = res ? s_vi[o] : vi[e];
+            float2 f = make_float2(fmaf(mk, sum.x, tv.x), fmaf(mk, sum.y, tv.y));
+            if (i > 1) {
+              const float2 m = res ? s_vm[o] : vm[e];
+              f = make_float2(fmaf(-bp, m.x, f.x), fmaf(-bp, m.y, f.y));
+            }
+            f = make_float2(fmaf(-a, v.x, f.x), fmaf(-a, v.y, f.y));
+            float2 w;
+            if (i > 1) {
+              const float2 wp = res ? s_vec[kResW * kResTile + o] : b.w[e];
+              w = make_float2(inv_d * fmaf(-bp, wp.x, v.x), inv_d * fmaf(-bp, wp.y, v.y));
+            } else {
+              w = make_float2(inv_d * v.x, inv_d * v.y);
+            }
+            b.f[e] = f;
+            if (wcol != nullptr) wcol[e] = w;
+            const float2 x = res ? s_vec[kResX * kResTile + o] : X[e];
+            const float2 xn = make_float2(fmaf(zeta, w.x, x.x), fmaf(zeta, w.y, x.y));
+            if (res) {
+              s_vec[kResF * kResTile + o] = f;
+              s_vec[kResW * kResTile + o] = w;
+              s_vec[kResX * kResTile + o] = xn;
+            } else {
+              b.w[e] = w;
+              X[e] = xn;
+            }
+            pff = fmaf(f.y, f.y, fmaf(f.x, f.x, pff));
           }
-          f = make_float2(fmaf(-a, v.x, f.x), fmaf(-a, v.y, f.y));
-          float2 w;
-          if (i > 1) {
-            const float2 wp = b.w[e];
-            w = make_float2(inv_d * fmaf(-bp, wp.x, v.x), inv_d * fmaf(-bp, wp.y, v.y));
-          } else {
-            w = make_float2(inv_d * v.x, inv_d * v.y);
-          }
-          b.f[e] = f;
-          b.w[e] = w;
-          if (wcol != nullptr) wcol[e] = w;
-          const float2 x = X[e];
-          X[e] = make_float2(fmaf(zeta, w.x, x.x), fmaf(zeta, w.y, x.y));
-          pff = fmaf(f.y, f.y, fmaf(f.x, f.x, pff));
+          const double ws = warp_sum((double)pff);
+          if (lane == 0) part2[4 * tile + warp] = ws;
         }
-        double vv[1] = {(double)pff};
-        block_sum<1, PT>(vv, s_red);
-        if (threadIdx.x == 0) part2[tile] = vv[0];
+        if (tile + own.count < tiles) __syncthreads();
       }
     }
-    if (!seed_beta_step<float2>(bl, part2, tiles, i, L, g, epoch)) return;
+    if (!grid_sync(g, epoch)) return;
+    pending_beta = true;               // beta_i and the stopping test run with the next stencil
   }
-  seed_leave<float2>(b, L, b.f, i_stop);
+  if (res) {   // x^1 (FP32 correction) and w_i back to global memory
+    __syncthreads();
+    const int64_t e0 = (int64_t)first_tile * kResTile;
+    for (int o = threadIdx.x; o < kResTile; o += PTW) {
+      X[e0 + o] = s_vec[kResX * kResTile + o];
+      b.w[e0 + o] = s_vec[kResW * kResTile + o];
+    }
+  }
+  if (tw) seed_leave<float2>(b, L, b.f, i_stop);
   local_store(b, L);
 }
 
@@ -1664,11 +1829,16 @@ cudaError_t launch_cg_run_csr_small(const CsrOp &op, const CallArgs *call, doubl
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// The FP64 Wilson run's dynamic shared memory (resident links and tile
-// vectors) is above the default 48 KB limit: raise it once per process.
+// The Wilson runs' dynamic shared memory (resident links and tile vectors)
+// is above the default 48 KB limit: raise it once per process.
 cudaError_t seed_run_wilson_smem_attr() {
-  static const cudaError_t attr = cudaFuncSetAttribute((const void *)k_seed_run_wilson,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmemBytes);
+  static const cudaError_t attr = [] {
+    const cudaError_t e = cudaFuncSetAttribute((const void *)k_seed_run_wilson,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)k_seed_run_wilson32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kResSmemBytes32);
+  }();
   return attr;
 }
 
@@ -1680,13 +1850,14 @@ int persistent_grid(int kind, int sm_count, bool cg, bool fp32) {
   if (cg) k = kind == 0 ? (const void *)k_cg_run_csr : (const void *)k_cg_run_wilson;
   else if (fp32) k = kind == 0 ? (const void *)k_seed_run_csr<float> : (const void *)k_seed_run_wilson32;
   else k = kind == 0 ? (const void *)k_seed_run_csr<double> : (const void *)k_seed_run_wilson;
-  const bool wil64 = !cg && !fp32 && kind == 1;
-  const int threads = wil64 ? PTW : PT;
-  if (wil64 && seed_run_wilson_smem_attr() != cudaSuccess) {
+  const bool wil = !cg && kind == 1;   // the Wilson seed runs: five warps, resident tiles
+  const int threads = wil ? PTW : PT;
+  if (wil && seed_run_wilson_smem_attr() != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, wil64 ? kResSmemBytes : 0) != cudaSuccess) {
+  const size_t dyn = !wil ? 0 : fp32 ? kResSmemBytes32 : kResSmemBytes;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, dyn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1725,7 +1896,10 @@ cudaError_t launch_seed_run_wilson32(const SeedBufs<float2> &b, const WilsonOp32
   SeedBufs<float2> bb = b;
   WilsonOp32 o = op;
   void *args[] = {&bb, &o, &tbuf, &g, &tpart, &i_stop};
-  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson32, dim3(grid), dim3(PT), args, 0, s);
+  const cudaError_t attr = seed_run_wilson_smem_attr();
+  if (attr != cudaSuccess) return attr;
+  return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson32, dim3(grid), dim3(PTW), args, kResSmemBytes32,
+                                     s);
 }
 cudaError_t launch_cg_run_wilson(const WilsonOp &op, const CallArgs *call, double2 *R, double2 *P, double2 *Q,
                                  double2 *tbuf, int64_t ld, const CgCols &c, GridSync g, double *bpart, int grid,

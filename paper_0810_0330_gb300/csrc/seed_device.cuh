@@ -25,7 +25,7 @@ template <bool G, class P> SEED_DEV P sld(const P *p) {
 template <class T, bool G = true>
 SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const double2 *sums) {
   SeedState *st = b.st;
-  const double bp = sld<G>(&st->beta_prev), dprev = sld<G>(&st->delta), zprev = sld<G>(&st->zeta),
+  const double bp = sld<G>(&st->beta_prev), inv_dprev = sld<G>(&st->inv_delta), zprev = sld<G>(&st->zeta),
                beta0 = sld<G>(&st->beta0);
   const int nr = b.Wb == nullptr ? b.nrhs : 1;
   double2 e[kMaxRhs];
@@ -36,8 +36,9 @@ SEED_DEV void seed_step_scalars(const SeedBufs<T> &b, int i, double a, const dou
     gam = 0.0;
     del = a;
     zet = beta0;
-  } else {                // later steps
-    gam = bp / dprev;
+  } else {                // later steps (gamma_{i-1} = beta_{i-1} / delta_{i-1}, by the stored reciprocal:
+                          // a division costs this part's FP64 pipe about as much as 20 multiplies)
+    gam = bp * inv_dprev;
     del = a - gam * bp;
     zet = -gam * zprev;
   }
@@ -69,7 +70,7 @@ SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
   SeedState *st = b.st;
   const int i = sld<G>(&st->i);
   const double alpha = sld<G>(&st->alpha), bp = sld<G>(&st->beta_prev), tnorm = sld<G>(&st->tnorm),
-               zeta = sld<G>(&st->zeta), delta = sld<G>(&st->delta), tol_abs = sld<G>(&st->tol_abs),
+               zeta = sld<G>(&st->zeta), inv_delta = sld<G>(&st->inv_delta), tol_abs = sld<G>(&st->tol_abs),
                brel = sld<G>(&st->breakdown_rel);
   int converged_at = sld<G>(&st->converged_at), stop_at = sld<G>(&st->stop_at);
   const int extra = sld<G>(&st->extra_iters), m_max = sld<G>(&st->m_max);
@@ -77,7 +78,7 @@ SEED_DEV void seed_finish(const SeedBufs<T> &b, double sumsq) {
   if (b.beta_hist) b.beta_hist[i] = beta;
   const double row = fabs(alpha) + (i > 1 ? bp : 0.0) + beta;
   const double tn = row > tnorm ? row : tnorm;
-  const double rho = beta * fabs(zeta) / delta;
+  const double rho = beta * fabs(zeta) * inv_delta;
   if (converged_at < 0 && rho <= tol_abs) {
     converged_at = i;
     stop_at = i + extra;

@@ -224,6 +224,25 @@ def test_mixed_wilson_small(seedlib, orc, freq):
     check_solution(orc, op, B, X, ref, i1, i2, 1e-12, 1e-8, "wilson-small-mixed")
 
 
+def test_mixed_wilson_more_tiles_than_sms(seedlib, orc):
+    """5x6x7x24 lattice (5040 sites, 158 tiles of 32: more than the GB300's 152
+    SMs, below the 65536 sites from which the FP32 seed runs from step
+    kernels), kappa 0.12, antiperiodic t, 3 RHS, reorthogonalization every 25
+    steps: the persistent FP32 seed run takes its general form, several tiles
+    per block, links and tile vectors from global memory (smaller lattices
+    take the resident form)."""
+    dims, kappa = (5, 6, 7, 24), 0.12
+    U = I.random_su3_links(dims, 0.3, seed=11)
+    eta = I.point_sources(dims, 3, site=101)
+    B = np.stack([orc.wilson_dslash(dims, kappa, 1, -1, U, eta[:, j]) for j in range(3)], axis=1)
+    p = seedlib.seed_params_default(m_max=800, reorth_freq=25, tol_seed=1e-12, tol_rest=1e-8, precision=1)
+    ctx = seedlib.seed_create_wilson(dims, kappa, torch.from_numpy(U).cuda(), p, bc_t=1)
+    i1, i2, X = mixed_solve(seedlib, ctx, B)
+    op = orc.Operator.wilson(dims, kappa, U, bc_t=1)
+    ref = orc.seed_solve_all(op, B, m_max=800, reorth_freq=25, tol_seed=1e-12, tol_rest=1e-8)
+    check_solution(orc, op, B, X, ref, i1, i2, 1e-12, 1e-8, "wilson-158-tiles-mixed")
+
+
 def test_mixed_wilson_large_lattice(seedlib, orc):
     """17x17x15x17 = 73695 sites (one thread per site in the FP32 operator,
     a site count that is not a multiple of 32, so the solver's tiled FP32
