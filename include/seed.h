@@ -119,8 +119,7 @@ typedef struct {
   int32_t kernel_path;    /* How the steps are issued (same method either way):
                              0 (default): the seed's runs of Lanczos steps between
                              reorthogonalizations in one persistent cooperative kernel (when the
-                             frequency is 0 or >= 8; in mixed precision for CSR and for Wilson
-                             lattices below 65536 sites), everything else as step kernels
+                             frequency is 0 or >= 8), everything else as step kernels
                              replayed from CUDA graphs, the lockstep CG in up to three concurrent
                              column branches; small real CSR problems in FP64 (n <= 9728) run
                              the whole seed run as one cooperative kernel when the frequency is

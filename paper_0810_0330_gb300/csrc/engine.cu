@@ -500,13 +500,13 @@ int csr_seed_grid(const seed_ctx *ctx) {
   return (int)b;
 }
 
+// Runs of steps between reorthogonalizations as one cooperative launch each.
+// The Wilson runs take their resident form when the lattice has no more
+// 32-site tiles than blocks, else the general one (FP32: the grouped form,
+// four tile groups per SM; 16^3 x 32 mixed seed phase 40.1 ms from graphs of
+// step kernels, 38.9 ms grouped).
 bool use_persistent_seed(seed_ctx *ctx) {
   const int f = ctx->prm.reorth_freq;
-  // the FP32 Wilson run works in 32-site tiles of 4 warps, one block per SM:
-  // right for latency-bound small lattices; from 65536 sites on the step
-  // kernels (one thread per site, many blocks) keep more memory traffic in
-  // flight (16^3 x 32: seed phase 55 ms from graphs, 120 ms persistent)
-  if (ctx->precision == 1 && ctx->kind == 1 && ctx->wil32.sites >= 65536) return false;
   return ctx->allow_persistent && ctx->pgrid > 0 && (f == 0 || f >= 8);
 }
 
