@@ -502,9 +502,9 @@ int csr_seed_grid(const seed_ctx *ctx) {
 
 // Runs of steps between reorthogonalizations as one cooperative launch each.
 // The Wilson runs take their resident form when the lattice has no more
-// 32-site tiles than blocks, else the general one (FP32: the grouped form,
-// four tile groups per SM; 16^3 x 32 mixed seed phase 40.1 ms from graphs of
-// step kernels, 38.9 ms grouped).
+// 32-site tiles than blocks, else the general one (FP32: the site form, one
+// thread per site; 16^3 x 32 mixed seed phase 40.1 ms from graphs of step
+// kernels, 37.1 ms in the site form).
 bool use_persistent_seed(seed_ctx *ctx) {
   const int f = ctx->prm.reorth_freq;
   return ctx->allow_persistent && ctx->pgrid > 0 && (f == 0 || f >= 8);

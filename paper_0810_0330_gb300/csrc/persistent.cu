@@ -971,85 +971,97 @@ __global__ void __launch_bounds__(PTW, 1) k_seed_run_wilson32(SeedBufs<float2> b
 }
 
 // ---------------------------------------------------------------------------
-// Grouped form of the FP32 run for lattices with many more tiles than SMs
-// (16^3 x 32: 4096 tiles): G groups of four tile warps per block, each group
-// working through its own tiles with its own partial-sum buffer and named
-// barrier, so that G tiles' loads are in flight on every SM; the links and
-// the vectors come from global memory (L2); warp 4 G is the scalar warp, as
-// in the other forms.  Group q of block r takes tiles r G + q, r G + q + G
-// blocks, ... (by block index, so the grouping of the sums is fixed).  With
-// thousands of tiles per-tile partials would cost every block's scalar warp
-// thousands of FP64 adds, so each thread accumulates its tiles in FP64, and
-// the block's warp totals are added in warp order into one partial per
-// block (fixed order: the results are reproducible).
+// Site form of the FP32 run for lattices with many more sites than threads
+// of one wave (from 65536 sites): every thread takes whole sites (all eight
+// hops of a site, as the FP32 operator kernel does there), so that each link
+// is read once per site and phase and no partial sums cross shared memory;
+// sites blockIdx.x * 448 + t, then every 448 * gridDim.x (tiled vectors:
+// component k of site s at ((s / 32) 12 + k) 32 + s mod 32); thread 448
+// starts the scalar warp.  Each thread accumulates its sites' partial sums in FP64, the
+// block adds its warp totals in warp order into one partial per block
+// (reproducible grouping).  The first site's stencil of each phase runs
+// while the scalar warp works.
 // ---------------------------------------------------------------------------
-constexpr int kGroups32 = 4;
+constexpr int kBlockSumPer = 8;     // one partial per block: 256 blocks in one round
+constexpr int kSiteThreads32 = 448;   // 14 site warps + the scalar warp: 15 warps, at most 4 per sub-partition, 128 registers
 
-template <int S>
-SEED_DEV void wilson_tile32_grp(const WilsonOp32 &op, const float2 *in, int64_t s0,
-                                float (*sacc)[24][kWilsonSites + 1], int mu, int bar) {
-  const int lane = threadIdx.x & 31;
-  const int64_t s = s0 + lane;
-  float2 acc[12];
-  if (s < op.sites) {
-    switch (mu) {
-      case 0: site_mu32<0, S>(op, in, s, acc); break;
-      case 1: site_mu32<1, S>(op, in, s, acc); break;
-      case 2: site_mu32<2, S>(op, in, s, acc); break;
-      default: site_mu32<3, S>(op, in, s, acc); break;
-    }
-  } else {
+template <int MU, int S>
+SEED_DEV void site32_dir(const WilsonOp32 &op, const float2 *in, int64_t s, int32_t nf, int32_t nb, unsigned negf,
+                         unsigned negb, float2 (&acc)[12]) {
+  const float2 *L = op.links + (int64_t)MU * 9 * op.sites;
+  {
+    float2 u[9], p[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = make_float2(0.f, 0.f);
-  }
+    for (int k = 0; k < 9; ++k) u[k] = __ldcg(L + (int64_t)k * op.sites + s);
+    const float2 *q = in + ((int64_t)nf >> 5) * 384 + (nf & 31);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    sacc[mu][2 * k][lane] = acc[k].x;
-    sacc[mu][2 * k + 1][lane] = acc[k].y;
+    for (int k = 0; k < 12; ++k) p[k] = q[32 * k];
+    hop_r<MU, S, true, MU == 0>(p, u, negf, acc);
   }
-  asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(PT) : "memory");
+  {
+    float2 u[9], p[12];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = __ldcg(L + (int64_t)k * op.sites + nb);
+    const float2 *q = in + ((int64_t)nb >> 5) * 384 + (nb & 31);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k] = q[32 * k];
+    hop_r<MU, -S, false, false>(p, u, negb, acc);
+  }
 }
 
-constexpr size_t kGrpSaccBytes = (size_t)4 * 24 * (kWilsonSites + 1) * sizeof(float);
+// the eight hops of site s (zero for padding sites)
+template <int S>
+SEED_DEV void site32_hops(const WilsonOp32 &op, const float2 *in, int64_t s, float2 (&acc)[12]) {
+  if (s >= op.sites) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = make_float2(0.f, 0.f);
+    return;
+  }
+  const int4 *q = reinterpret_cast<const int4 *>(op.nbr + 8 * s);
+  const int4 a = __ldg(q), c = __ldg(q + 1);
+  unsigned negf = 0u, negb = 0u;
+  if (op.bc_t) {
+    const int64_t t = s / ((int64_t)op.dims[0] * op.dims[1] * op.dims[2]);
+    if (t == op.dims[3] - 1) negf = CxBits<float2>::sign;
+    if (t == 0) negb = CxBits<float2>::sign;
+  }
+  site32_dir<0, S>(op, in, s, a.x, a.y, 0u, 0u, acc);
+  site32_dir<1, S>(op, in, s, a.z, a.w, 0u, 0u, acc);
+  site32_dir<2, S>(op, in, s, c.x, c.y, 0u, 0u, acc);
+  site32_dir<3, S>(op, in, s, c.z, c.w, negf, negb, acc);
+}
 
 // tpart: 3 x blocks doubles (per block: the phase-1 pair, then the phase-2 norm)
-template <int G>
-__global__ void __launch_bounds__(G * PT + 32, 1) k_seed_run_wilson32g(SeedBufs<float2> b, WilsonOp32 op,
-                                                                         float2 *tbuf, GridSync g, double *tpart,
-                                                                         int i_stop) {
-  constexpr int kScalar = G * PT;      // first thread of the scalar warp
-  extern __shared__ float s_grp32[];
+__global__ void __launch_bounds__(kSiteThreads32 + 32, 1) k_seed_run_wilson32s(SeedBufs<float2> b, WilsonOp32 op,
+                                                                                float2 *tbuf, GridSync g,
+                                                                                double *tpart, int i_stop) {
+  constexpr int kW = kSiteThreads32 / 32;   // site warps
   __shared__ LocalSeed L;
-  __shared__ double s_wp[4 * G][2];
-  const int tiles = (int)(b.n / 384);
+  __shared__ double s_wp[kW][2];
+  const int64_t padded = b.n / 12;          // sites including the padding of the last tile
   const float mk = (float)(-op.kappa);
   const int nb = gridDim.x;
   double *part1 = tpart, *part2 = tpart + 2 * (int64_t)nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool tw = warp < 4 * G;
-  const int grp = tw ? warp >> 2 : 0, mu = warp & 3;
-  const int gt = threadIdx.x - grp * PT;   // thread of the group (tile warps)
-  const int bar = 1 + grp;
-  float (*sacc)[24][kWilsonSites + 1] =
-      reinterpret_cast<float (*)[24][kWilsonSites + 1]>(s_grp32 + (size_t)grp * (kGrpSaccBytes / sizeof(float)));
+  const bool sw = warp < kW;                // site warp; warp kW is the scalar warp
+  const int64_t stride = (int64_t)nb * kSiteThreads32;
+  const int64_t first = sw ? (int64_t)blockIdx.x * kSiteThreads32 + threadIdx.x : padded;
   unsigned epoch = 0;
   local_load(b, L);
   const SeedBufs<float2> bl = local_bufs(b, L);
   float2 *const X = reinterpret_cast<float2 *>(b.call->X);
-  const int nslots = nb * G;
-  const int slot = blockIdx.x * G + grp;
-  const int first_tile = (tw && slot < tiles) ? slot : -1;   // uniform over a group
   bool pending_beta = false;
   for (;;) {
+    float2 acc[12];
     // ---- phase 1 of step i, overlapped with the end of step i-1 ----
     {
       const int ip = L.st.i + (pending_beta ? 1 : 0);
       const bool go = L.st.active && ip < i_stop && (b.Wb == nullptr || ip - L.st.blk0 < kSeedBlock);
       __syncthreads();                 // everyone has read L.st before the scalar warp updates it
-      if (go && first_tile >= 0) wilson_tile32_grp<+1>(op, b.f, (int64_t)first_tile * kWilsonSites, sacc, mu, bar);
-      if (!tw && pending_beta) {
-        const double ss = warp_sum_short<kScalarSumPer>(part2, nb);
-        if (threadIdx.x == kScalar) {
+      if (go && first < padded) site32_hops<+1>(op, b.f, first, acc);
+      if (!sw && pending_beta) {
+        const double ss = warp_sum_short<kBlockSumPer>(part2, nb);
+        if (threadIdx.x == kSiteThreads32) {
           if (bl.Wb != nullptr) L.st.w_last = L.st.i;
           seed_finish<float2, false>(bl, ss);
         }
@@ -1066,18 +1078,17 @@ __global__ void __launch_bounds__(G * PT + 32, 1) k_seed_run_wilson32g(SeedBufs<
     const float2 *vm = b.V + (int64_t)(i > 1 ? i - 2 : 0) * b.ldv;
     // phase 1 epilogue: v_i, t = D v_i, partials of ||t||^2 and Re(v_i^H v_{i-1})
     double att = 0.0, avm = 0.0;
-    for (int tile = first_tile; tile >= 0 && tile < tiles; tile += nslots) {
-      if (tile != first_tile) wilson_tile32_grp<+1>(op, b.f, (int64_t)tile * kWilsonSites, sacc, mu, bar);
+    for (int64_t s = first; s < padded; s += stride) {
+      if (s != first) site32_hops<+1>(op, b.f, s, acc);
+      const int64_t e0 = (s >> 5) * 384 + (s & 31);
       float ptt = 0.f, pvm = 0.f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int o = gt + PT * k, cc = o >> 5, sl = o & 31;
-        const int64_t e = (int64_t)tile * 384 + o;
-        const float2 sum = tile_sum32(sacc, cc, sl);
+      for (int k = 0; k < 12; ++k) {
+        const int64_t e = e0 + 32 * k;
         const float2 fe = b.f[e];
         const float2 v = make_float2(inv_b * fe.x, inv_b * fe.y);
         vi[e] = v;
-        const float2 t = make_float2(fmaf(mk, inv_b * sum.x, v.x), fmaf(mk, inv_b * sum.y, v.y));
+        const float2 t = make_float2(fmaf(mk, inv_b * acc[k].x, v.x), fmaf(mk, inv_b * acc[k].y, v.y));
         tbuf[e] = t;
         ptt = fmaf(t.y, t.y, fmaf(t.x, t.x, ptt));
         if (i > 1) {
@@ -1087,9 +1098,8 @@ __global__ void __launch_bounds__(G * PT + 32, 1) k_seed_run_wilson32g(SeedBufs<
       }
       att += (double)ptt;
       avm += (double)pvm;
-      if (tile + nslots < tiles) asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(PT) : "memory");
     }
-    if (tw) {
+    if (sw) {
       const double2 ws = warp_sum_pair(att, avm);
       if (lane == 0) {
         s_wp[warp][0] = ws.x;
@@ -1099,7 +1109,7 @@ __global__ void __launch_bounds__(G * PT + 32, 1) k_seed_run_wilson32g(SeedBufs<
     __syncthreads();
     if (threadIdx.x == 0) {
       double s0 = 0.0, s1 = 0.0;
-      for (int w = 0; w < 4 * G; ++w) {
+      for (int w = 0; w < kW; ++w) {
         s0 += s_wp[w][0];
         s1 += s_wp[w][1];
       }
@@ -1108,27 +1118,26 @@ __global__ void __launch_bounds__(G * PT + 32, 1) k_seed_run_wilson32g(SeedBufs<
     }
     if (!grid_sync(g, epoch)) return;
     // ---- phase 2: u = D^H t overlapped with alpha_i and the LU update's scalars ----
-    if (first_tile >= 0) wilson_tile32_grp<-1>(op, tbuf, (int64_t)first_tile * kWilsonSites, sacc, mu, bar);
-    if (!tw) {
-      const double2 s2 = warp_sum_short_pairs<kScalarSumPer>(part1, nb);
+    if (first < padded) site32_hops<-1>(op, tbuf, first, acc);
+    if (!sw) {
+      const double2 s2 = warp_sum_short_pairs<kBlockSumPer>(part1, nb);
       const double a = i > 1 ? s2.x - L.st.beta_prev * s2.y : s2.x;
-      if (threadIdx.x == kScalar) seed_step_scalars<float2, false>(bl, i, a, nullptr);
+      if (threadIdx.x == kSiteThreads32) seed_step_scalars<float2, false>(bl, i, a, nullptr);
     }
     __syncthreads();
     if (!L.st.active) break;   // delta_i <= 0
     const float a = (float)L.st.alpha, zeta = (float)L.st.zeta, inv_d = (float)L.st.inv_delta;
     float2 *const wcol = b.Wb != nullptr ? b.Wb + (int64_t)(i - L.st.blk0) * b.ldv : nullptr;
     double aff = 0.0;
-    for (int tile = first_tile; tile >= 0 && tile < tiles; tile += nslots) {
-      if (tile != first_tile) wilson_tile32_grp<-1>(op, tbuf, (int64_t)tile * kWilsonSites, sacc, mu, bar);
+    for (int64_t s = first; s < padded; s += stride) {
+      if (s != first) site32_hops<-1>(op, tbuf, s, acc);
+      const int64_t e0 = (s >> 5) * 384 + (s & 31);
       float pff = 0.f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int o = gt + PT * k, cc = o >> 5, sl = o & 31;
-        const int64_t e = (int64_t)tile * 384 + o;
-        const float2 sum = tile_sum32(sacc, cc, sl);
+      for (int k = 0; k < 12; ++k) {
+        const int64_t e = e0 + 32 * k;
         const float2 tv = tbuf[e], v = vi[e];
-        float2 f = make_float2(fmaf(mk, sum.x, tv.x), fmaf(mk, sum.y, tv.y));
+        float2 f = make_float2(fmaf(mk, acc[k].x, tv.x), fmaf(mk, acc[k].y, tv.y));
         if (i > 1) {
           const float2 m = vm[e];
           f = make_float2(fmaf(-bp, m.x, f.x), fmaf(-bp, m.y, f.y));
@@ -1149,16 +1158,15 @@ __global__ void __launch_bounds__(G * PT + 32, 1) k_seed_run_wilson32g(SeedBufs<
         pff = fmaf(f.y, f.y, fmaf(f.x, f.x, pff));
       }
       aff += (double)pff;
-      if (tile + nslots < tiles) asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(PT) : "memory");
     }
-    if (tw) {
+    if (sw) {
       const double ws = warp_sum(aff);
       if (lane == 0) s_wp[warp][0] = ws;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double s0 = 0.0;
-      for (int w = 0; w < 4 * G; ++w) s0 += s_wp[w][0];
+      for (int w = 0; w < kW; ++w) s0 += s_wp[w][0];
       part2[blockIdx.x] = s0;
     }
     if (!grid_sync(g, epoch)) return;
@@ -2033,11 +2041,8 @@ cudaError_t seed_run_wilson_smem_attr() {
     const cudaError_t e = cudaFuncSetAttribute((const void *)k_seed_run_wilson,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmemBytes);
     if (e != cudaSuccess) return e;
-    const cudaError_t e2 = cudaFuncSetAttribute((const void *)k_seed_run_wilson32,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmemBytes32);
-    if (e2 != cudaSuccess) return e2;
-    return cudaFuncSetAttribute((const void *)k_seed_run_wilson32g<kGroups32>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kGroups32 * kGrpSaccBytes));
+    return cudaFuncSetAttribute((const void *)k_seed_run_wilson32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kResSmemBytes32);
   }();
   return attr;
 }
@@ -2061,10 +2066,10 @@ int persistent_grid(int kind, int sm_count, bool cg, bool fp32) {
     cudaGetLastError();
     return 0;
   }
-  if (wil && fp32) {   // the grouped form of large lattices must fit once per SM too
+  if (wil && fp32) {   // the site form of large lattices must fit once per SM too
     int per_sm_g = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, (const void *)k_seed_run_wilson32g<kGroups32>,
-                                                      kGroups32 * PT + 32, kGroups32 * kGrpSaccBytes) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, (const void *)k_seed_run_wilson32s,
+                                                      kSiteThreads32 + 32, 0) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -2107,9 +2112,9 @@ cudaError_t launch_seed_run_wilson32(const SeedBufs<float2> &b, const WilsonOp32
   void *args[] = {&bb, &o, &tbuf, &g, &tpart, &i_stop};
   const cudaError_t attr = seed_run_wilson_smem_attr();
   if (attr != cudaSuccess) return attr;
-  if (b.n / 384 > grid)   // more tiles than blocks: the grouped form
-    return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson32g<kGroups32>, dim3(grid),
-                                       dim3(kGroups32 * PT + 32), args, kGroups32 * kGrpSaccBytes, s);
+  if (b.n / 384 > grid)   // more tiles than blocks: the site form
+    return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson32s, dim3(grid), dim3(kSiteThreads32 + 32), args,
+                                       0, s);
   return cudaLaunchCooperativeKernel((const void *)k_seed_run_wilson32, dim3(grid), dim3(PTW), args, kResSmemBytes32,
                                      s);
 }

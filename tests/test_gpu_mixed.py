@@ -227,11 +227,11 @@ def test_mixed_wilson_small(seedlib, orc, freq):
 def test_mixed_wilson_more_tiles_than_sms(seedlib, orc):
     """5x6x7x24 lattice (5040 sites, 158 tiles of 32: more than the GB300's 152
     SMs), kappa 0.12, antiperiodic t, 3 RHS, reorthogonalization every 25
-    steps: the persistent FP32 seed run takes its grouped form (four tile
-    groups per block: 158 of the 608 groups own a tile, the others only join
-    the barriers; links and vectors from global memory, one partial sum per
-    block); smaller lattices take the resident form.  The 17x17x15x17 and
-    16^3 x 32 cases below run it with several tiles per group."""
+    steps: the persistent FP32 seed run takes its site form (one thread per
+    site, 448 sites per block: the last blocks of the grid hold no site and
+    only join the barriers; one partial sum per block); smaller lattices take
+    the resident form.  The 17x17x15x17 and 16^3 x 32 cases below run it with
+    two sites per thread."""
     dims, kappa = (5, 6, 7, 24), 0.12
     U = I.random_su3_links(dims, 0.3, seed=11)
     eta = I.point_sources(dims, 3, site=101)
