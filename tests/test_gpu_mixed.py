@@ -231,7 +231,7 @@ def test_mixed_wilson_more_tiles_than_sms(seedlib, orc):
     site, 448 sites per block: the last blocks of the grid hold no site and
     only join the barriers; one partial sum per block); smaller lattices take
     the resident form.  The 17x17x15x17 and 16^3 x 32 cases below run it with
-    two sites per thread."""
+    up to two sites per thread."""
     dims, kappa = (5, 6, 7, 24), 0.12
     U = I.random_su3_links(dims, 0.3, seed=11)
     eta = I.point_sources(dims, 3, site=101)
