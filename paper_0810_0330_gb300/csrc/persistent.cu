@@ -388,7 +388,7 @@ SEED_DEV double2 warp_sum_short_pairs(const double *p, int nb) {
   }
   return warp_sum_pair(sx, sy);
 }
-constexpr int kScalarSumPer = 16;   // 512 partials (128 tiles x 4 warps, the 8^4 lattice) in one round
+constexpr int kScalarSumPer = 16;   // 512 partials (128 tiles x 4 warps, the 8^4 lattice) in one pass
 
 // Resident form of the run, used when every owner block holds at most one tile
 // (lattices with no more 32-site tiles than SMs, e.g. 8^4 with 128 tiles): the
@@ -982,7 +982,7 @@ __global__ void __launch_bounds__(PTW, 1) k_seed_run_wilson32(SeedBufs<float2> b
 // (reproducible grouping).  The first site's stencil of each phase runs
 // while the scalar warp works.
 // ---------------------------------------------------------------------------
-constexpr int kBlockSumPer = 8;     // one partial per block: 256 blocks in one round
+constexpr int kBlockSumPer = 8;     // one partial per block: 256 blocks in one pass
 constexpr int kSiteThreads32 = 448;   // 14 site warps + the scalar warp: 15 warps, at most 4 per sub-partition, 128 registers
 
 template <int MU, int S>
